@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+Nothing here performs a step of the hydro method: these functions only lay
+out initial states (ideal-gas cell averages) and mesh geometry.  Field order:
+rho, s_x, s_y, s_z, E (gas energy), tau (entropy tracer), z_x, z_y, z_z,
+species densities.  tau is set consistent with the internal energy,
+tau = eps^(1/gamma), as the dual-energy formalism (Bryan et al. 1995) defines
+it.  Arrays are float64, C-ordered, x fastest.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NF = 10
+
+
+def conserved_from_primitive(rho, v, p, gamma, z=None, species=None):
+    """Cell averages from density, velocity [3,...], pressure.  Returns [NF,...]."""
+    rho = np.asarray(rho, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    eps = np.asarray(p, dtype=np.float64) / (gamma - 1.0)
+    U = np.zeros((NF,) + rho.shape)
+    U[0] = rho
+    U[1:4] = rho * v
+    U[4] = eps + 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+    U[5] = eps ** (1.0 / gamma)
+    if z is not None:
+        U[6:9] = z
+    U[9] = rho if species is None else species
+    return U
+
+
+def cell_centres(shape, lo, h):
+    """Centres (x, y, z) of a [nz][ny][nx] box with lower corner lo."""
+    nz, ny, nx = shape
+    x = lo[0] + (np.arange(nx) + 0.5) * h
+    y = lo[1] + (np.arange(ny) + 0.5) * h
+    z = lo[2] + (np.arange(nz) + 0.5) * h
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def sedov_box(n: int, gamma: float = 5.0 / 3.0, E_blast: float = 1.0, rho0: float = 1.0, p0: float = 1e-5,
+              L: float = 2.0):
+    """Sedov-Taylor point blast on [-L/2, L/2]^3 with n^3 cells (n even):
+    rho = rho0, p = p0, v = 0, and the blast energy E_blast added uniformly as
+    internal energy to the central 2^3 cells.  Returns (U [NF][n][n][n], h, lo)."""
+    assert n % 2 == 0
+    h = L / n
+    lo = (-L / 2, -L / 2, -L / 2)
+    rho = np.full((n, n, n), rho0)
+    p = np.full((n, n, n), p0)
+    c = slice(n // 2 - 1, n // 2 + 1)
+    p[c, c, c] += (gamma - 1.0) * E_blast / (8.0 * h ** 3)
+    U = conserved_from_primitive(rho, np.zeros((3, n, n, n)), p, gamma)
+    return U, h, lo
+
+
+def sedov_subgrid(gamma: float = 5.0 / 3.0, N: int = 8, G: int = 3):
+    """Single 8^3 sub-grid Sedov blast on [-1,1]^3 (h = 2/N) with periodic
+    ghosts: returns (U [NF][S][S][S], h, origin)."""
+    U, h, lo = sedov_box(N, gamma)
+    Up = np.pad(U, ((0, 0), (G, G), (G, G), (G, G)), mode="wrap")
+    return Up, h, lo
+
+
+def sod_box(n_normal: int, normal: str, gamma: float = 1.4, states=((1.0, 0.0, 1.0), (0.125, 0.0, 0.1)),
+            n_trans: int = 8):
+    """Periodic planar Sod tube on [0,1) along the unit normal 'x', 'xy' or 'xyz'.
+
+    The normal coordinate xi = (n . x) folded onto [0,1); the left state fills
+    xi in [0.25, 0.75) and the right state the rest, so the box holds two
+    Riemann problems (at xi = 0.75 and, mirrored, at 0.25).  Box shapes:
+    'x' -> n x n_trans x n_trans cells of width 1/n; 'xy' -> n x n x n_trans
+    on [0,1)^2 with xi = (x + y) mod 1; 'xyz' -> n^3 with xi = (x+y+z) mod 1.
+    Returns (U [NF][nz][ny][nx], h, lo, xi_of_cell, nvec)."""
+    h = 1.0 / n_normal
+    if normal == "x":
+        shape = (n_trans, n_trans, n_normal)
+        nvec = np.array([1.0, 0.0, 0.0])
+    elif normal == "xy":
+        shape = (n_trans, n_normal, n_normal)
+        nvec = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)
+    elif normal == "xyz":
+        shape = (n_normal, n_normal, n_normal)
+        nvec = np.ones(3) / math.sqrt(3.0)
+    else:
+        raise ValueError(normal)
+    X, Y, Z = cell_centres(shape, (0.0, 0.0, 0.0), h)
+    k = {"x": X, "xy": X + Y, "xyz": X + Y + Z}[normal]
+    xi = np.mod(k, 1.0)  # coordinate along the (unnormalised) normal, period 1
+    left = (xi >= 0.25) & (xi < 0.75)
+    (rl, ul, pl), (rr, ur, pr) = states
+    rho = np.where(left, rl, rr)
+    un = np.where(left, ul, ur)
+    p = np.where(left, pl, pr)
+    v = np.stack([un * nvec[0], un * nvec[1], un * nvec[2]])
+    U = conserved_from_primitive(rho, v, p, gamma)
+    return U, h, (0.0, 0.0, 0.0), xi, nvec
+
+
+def random_subgrids(n_sub: int, seed: int, gamma: float = 5.0 / 3.0, N: int = 8, G: int = 3, smooth: bool = False,
+                    spin: bool = True):
+    """Random ghost-padded sub-grids [n_sub][NF][S][S][S] with positive density
+    and pressure: rho in [0.5, 2], |v| <= 1, p in [0.1, 1] (or smooth sinusoidal
+    fields when smooth=True), random spin z and species fraction."""
+    rng = np.random.default_rng(seed)
+    S = N + 2 * G
+    shp = (n_sub, S, S, S)
+    if smooth:
+        ax = np.arange(S)
+        Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+        ph = rng.uniform(0, 2 * np.pi, (n_sub, 6, 1, 1, 1))
+        k = 2 * np.pi / 23.0
+        rho = 1.0 + 0.3 * np.sin(k * X + ph[:, 0]) * np.cos(k * Y + ph[:, 1])
+        p = 0.6 + 0.2 * np.sin(k * Z + ph[:, 2])
+        v = np.stack([0.3 * np.sin(k * Y + ph[:, 3]), 0.2 * np.cos(k * Z + ph[:, 4]), 0.25 * np.sin(k * X + ph[:, 5])],
+                     axis=1)
+    else:
+        rho = rng.uniform(0.5, 2.0, shp)
+        p = rng.uniform(0.1, 1.0, shp)
+        v = rng.uniform(-1.0, 1.0, (n_sub, 3, S, S, S)) / math.sqrt(3.0)
+    z = rng.uniform(-0.05, 0.05, (n_sub, 3, S, S, S)) if spin else None
+    frac = rng.uniform(0.0, 1.0, shp)
+    out = np.empty((n_sub, NF, S, S, S))
+    for s in range(n_sub):
+        out[s] = conserved_from_primitive(rho[s], v[s], p[s], gamma,
+                                          z=None if z is None else z[s], species=rho[s] * frac[s])
+    return out
+
+
+def uniform_mesh(nb: int, N: int = 8, L: float = 2.0):
+    """Uniform octree level: nb^3 sub-grids of N^3 on [-L/2, L/2]^3.
+    Returns (origins [n_sub][3], h); sub-grid s = (kz*nb + ky)*nb + kx."""
+    h = L / (nb * N)
+    o = np.empty((nb ** 3, 3))
+    s = 0
+    for kz in range(nb):
+        for ky in range(nb):
+            for kx in range(nb):
+                o[s] = (-L / 2 + kx * N * h, -L / 2 + ky * N * h, -L / 2 + kz * N * h)
+                s += 1
+    return o, h
+
+
+def box_to_subgrids(Ug: np.ndarray, N: int = 8):
+    """Interior box [NF][nz][ny][nx] -> [n_sub][NF][N][N][N] (x-fastest sub-grid order)."""
+    nf, nz, ny, nx = Ug.shape
+    nbz, nby, nbx = nz // N, ny // N, nx // N
+    out = np.empty((nbz * nby * nbx, nf, N, N, N))
+    s = 0
+    for kz in range(nbz):
+        for ky in range(nby):
+            for kx in range(nbx):
+                out[s] = Ug[:, kz * N:(kz + 1) * N, ky * N:(ky + 1) * N, kx * N:(kx + 1) * N]
+                s += 1
+    return out
+
+
+def lane_emden(n: float, dxi: float = 1e-4):
+    """Lane-Emden solution theta(xi) of index n (theta'' + 2 theta'/xi + theta^n = 0,
+    theta(0) = 1, theta'(0) = 0), integrated with classical RK4 from a series
+    start until theta = 0.  Returns (xi1, -xi1^2 theta'(xi1), xi grid, theta)."""
+    def rhs(x, y):
+        th, dth = y
+        return np.array([dth, -max(th, 0.0) ** n - 2.0 * dth / x])
+
+    x = dxi
+    y = np.array([1.0 - x * x / 6.0 + n * x ** 4 / 120.0, -x / 3.0 + n * x ** 3 / 30.0])
+    xs, ths = [0.0, x], [1.0, y[0]]
+    while y[0] > 0.0:
+        k1 = rhs(x, y)
+        k2 = rhs(x + dxi / 2, y + dxi / 2 * k1)
+        k3 = rhs(x + dxi / 2, y + dxi / 2 * k2)
+        k4 = rhs(x + dxi, y + dxi * k3)
+        yn = y + dxi / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+        if yn[0] <= 0.0:  # linear interpolation of the zero inside the last step
+            f = y[0] / (y[0] - yn[0])
+            x1 = x + f * dxi
+            dth1 = y[1] + f * (yn[1] - y[1])
+            xs.append(x1)
+            ths.append(0.0)
+            return x1, -x1 * x1 * dth1, np.array(xs), np.array(ths)
+        x, y = x + dxi, yn
+        xs.append(x)
+        ths.append(y[0])
+    raise RuntimeError("unreachable")
