@@ -1,0 +1,334 @@
+"""Benchmark of the hydro hot path on one GB300 (cell-updates/s).
+
+Workload: the Sedov-Taylor blast on a uniform octree level of 512 sub-grids
+of 8^3 cells (64^3 cells on [-1,1]^3), outflow boundaries, 10 FP64 fields,
+gamma = 5/3 -- the paper's pure-hydro benchmark problem (Sec. IV-A) at the
+sub-grid size 8^3.  One benchmark step is one full SSP-RK3 time step: three
+stages of (ghost fill, hydro_step, hydro_update) plus the CFL time step from
+the first stage's amax, all through the C ABI on the device.
+value = cells x time steps / s (the paper's "cells processed per second").
+
+--impl reference times the FP64 CPU oracle on the host cores instead (on a
+bounded sample of the same workload: the central 4x4x4 sub-grids).
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(the step has no cross-GPU exchange in this build); value sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hydro cell-updates/s on 1 GB300: plain FP64 vs batched/mixed at fixed L1 err"
+UNIT = "cell-updates/s (cells x RK3 time steps / s)"
+GAMMA = 5.0 / 3.0
+NB = 8  # 8^3 sub-grids
+N = 8
+CELLS = (NB * N) ** 3
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (an FMA counts as two flops)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rk, lr
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# Algorithmic work of one hydro_step launch per sub-grid, as counted by the
+# oracle's operation-counting scalar (``python -m oracle.count_work``; a CPU
+# test keeps these constants equal to that count): unique PPM line
+# evaluations (13 lines per interior cell, 9 per face-adjacent ghost cell,
+# 10 fields) at the average cost per evaluation on random discontinuous data,
+# 15,552 point fluxes, face sums, divergence and sources.  Bytes: the padded
+# state read once and dU/dt written once.
+ALGO = {"fp64_flops_per_subgrid_stage": 6558794.0, "bytes_per_subgrid_stage": 260520}
+# DRAM bytes per hydro_step launch from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), None until captured for the current kernel.
+TRAFFIC_PER_LAUNCH = None
+
+
+def algorithmic_work():
+    return dict(ALGO, dram_bytes_per_launch_scaled=TRAFFIC_PER_LAUNCH)
+
+
+def make_state(dev):
+    import torch
+    from paper_2107_10987_gb300 import workloads as W
+    Ug, h, lo = W.sedov_box(NB * N, GAMMA)
+    # ghost-padded sub-grids; the first ghost fill of every stage overwrites the ghosts
+    sub = np.zeros((NB ** 3, 10, N + 6, N + 6, N + 6))
+    sub[:, :, 3:-3, 3:-3, 3:-3] = W.box_to_subgrids(Ug, N)
+    o, hh = W.uniform_mesh(NB, N)
+    assert abs(hh - h) < 1e-15
+    U = torch.tensor(sub, device=dev)
+    origin = torch.tensor(o, device=dev)
+    hv = torch.full((NB ** 3,), h, dtype=torch.float64, device=dev)
+    return U, origin, hv, sub
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2107_10987_gb300 import hydro as H
+
+    ws, rk, lr = dist_env()
+    dev = torch.device("cuda", lr)
+    torch.cuda.set_device(dev)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, 0.4)
+    U, origin, hv, host_init = make_state(dev)
+    n = U.shape[0]
+    U0 = torch.empty_like(U)
+    dU = torch.empty((n, 10, N, N, N), dtype=torch.float64, device=dev)
+    am = torch.empty(n, dtype=torch.float64, device=dev)
+    dt = torch.empty(1, dtype=torch.float64, device=dev)
+    B = H.make_batch(U, origin, hv)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    launches_per_step = 10  # 3 x (ghost fill, step, update) + dt
+
+    def rk3_step(step_events=None):
+        U0.copy_(U)
+        for k in range(3):
+            H.hydro_fill_ghosts_uniform(ctx, B, NB, NB, NB, H.HYDRO_BC_OUTFLOW)
+            if step_events is not None:
+                step_events[k][0].record(stream)
+            H.hydro_step(ctx, B, 0.0, dU, am)
+            if step_events is not None:
+                step_events[k][1].record(stream)
+            if k == 0:
+                H.hydro_dt(ctx, am, hv, n, 0.4, dt)
+            H.hydro_update(ctx, B, U0, dU, dt_dev=dt, stage=k)
+
+    for _ in range(args.warmup):
+        rk3_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(3)]
+           for _ in range(args.steps)]
+    with ClockSampler(lr) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[i][0].record(stream)
+            rk3_step(kev[i])
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for st in kev for a, b in st]
+    t_dev = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = t.item()
+    status = H.hydro_status(ctx)
+
+    # end to end: host (pinned) state in, one RK3 step, state back to the host
+    host_U = torch.tensor(host_init).pin_memory()
+    host_out = torch.empty_like(host_U).pin_memory()
+    for _ in range(2):
+        U.copy_(host_U, non_blocking=True)
+        rk3_step()
+        host_out.copy_(U, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        U.copy_(host_U, non_blocking=True)
+        rk3_step()
+        host_out.copy_(U, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = t.item()
+    bytes_step = host_U.numel() * 8
+
+    if rk == 0:
+        work = algorithmic_work()
+        kavg = float(np.mean(kern_ms)) / 1e3
+        flops = work["fp64_flops_per_subgrid_stage"] * n
+        achieved = flops / kavg / 1e12
+        bytes_launch = work["bytes_per_subgrid_stage"] * n
+        pk = peaks()
+        line = {
+            "metric": METRIC, "value": CELLS * args.steps * ws / t_dev, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "Sedov blast, uniform octree level of 512 sub-grids of 8^3 (64^3 on [-1,1]^3), "
+                                   "outflow, 10 FP64 fields, one step = one full RK3 time step (3 stages)",
+                       "sub_grids": n, "cells": CELLS, "precision": "fp64 (plain)", "parallelism": f"replicas x{ws}",
+                       "l2": "flushed (256 MB write) between timed steps, outside the timed events"},
+            "cell_stage_updates_per_s": 3 * CELLS * args.steps * ws / t_dev,
+            "wall_s_timed_region": wall,
+            "kernel_ms": {"hydro_step_fp64 (avg launch)": 1e3 * kavg},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": work.get("dram_bytes_per_launch_scaled"),
+                         "peak_source": "nominal GB300 FP64 from the profiling recipe (1.25 TFLOP/s)",
+                         "hbm_frac": (bytes_launch / kavg / 1e9) / pk["hbm_gbs"] if "hbm_gbs" in pk else None},
+            "e2e": {"value": CELLS * args.steps * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
+                    "d2h_bytes_per_step": bytes_step},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "device_status": status,
+        }
+        if args.cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def oracle_sample():
+    """The central 4x4x4 sub-grids of the workload (32^3 cells, same h)."""
+    from oracle import core, mesh  # noqa: F401
+    from paper_2107_10987_gb300 import workloads as W
+    Ug, h, lo = W.sedov_box(NB * N, GAMMA)
+    c = slice(16, 48)
+    sub = Ug[:, c, c, c].copy()
+    return sub, h, (lo[0] + 16 * h, lo[1] + 16 * h, lo[2] + 16 * h)
+
+
+def cpu_baseline(budget_s: float):
+    """The oracle as it stands, on all host cores, on a bounded sample."""
+    from oracle import core, mesh
+    core.build()
+    Ug, h, lo = oracle_sample()
+    run = mesh.BoxRun(core.OracleParams(gamma=GAMMA), Ug, h, lo, "outflow")
+    run.step(0.4)  # warm-up (thread pool, caches)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s or steps == 0:
+        run.step(0.4)
+        steps += 1
+    dt = time.perf_counter() - t0
+    cells = Ug[0].size
+    return {"value": cells * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{steps} RK3 steps of the central 4x4x4 sub-grids (32^3 cells) of the workload, "
+                      f"{dt:.1f} s, OpenMP over sub-grids on all host cores"}
+
+
+def reference_arm(args):
+    ws, rk, lr = dist_env()
+    if rk != 0:
+        return
+    from oracle import core, mesh
+    core.build()
+    Ug, h, lo = oracle_sample()
+    run = mesh.BoxRun(core.OracleParams(gamma=GAMMA), Ug, h, lo, "outflow")
+    for _ in range(args.warmup):
+        run.step(0.4)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run.step(0.4)
+    dt = time.perf_counter() - t0
+    cells = Ug[0].size
+    v = cells * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Sedov blast, central 4x4x4 sub-grids (32^3 cells, h = 1/32) of the 512-sub-grid "
+                                   "uniform mesh, outflow, one step = one full RK3 time step", "cells": cells},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} RK3 steps of 32^3 cells on all host cores"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ws, rk, _ = dist_env()
+        if rk != 0 or ws > 1:
+            args.cpu_baseline = args.cpu_baseline and rk == 0 and ws == 1
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * hydro.h -- C ABI of the GB300 (sm_103a) hydro step library.
+ *
+ * The library evaluates, for every leaf sub-grid of an adaptive octree, the
+ * per-sub-grid step of the fully three-dimensional reconstruction scheme of
+ * Octo-Tiger's hydro module (arXiv 2107.10987, Sec. III-B): PPM reconstruction
+ * (Colella & Woodward 1984) along the 13 lines through cell centres to the 26
+ * face, edge and vertex points of each cell, the Kurganov-Tadmor (2000)
+ * central flux at the 9 points of every face, the Newton-Cotes (Simpson)
+ * face sum, the flux divergence, rotating-frame and spin-torque sources
+ * (rotating frame: Sec. I), and the maximum signal speed for the CFL time
+ * step; plus the SSP-RK3 stage update with the dual-energy tracer resync of
+ * Bryan et al. (1995) (three hydro iterations per step: Sec. IV-A.2).
+ *
+ * Data layout (all FP64, C order, x fastest):
+ *   U     [n_sub][F][S][S][S]  cell averages with G = 3 ghost layers,
+ *                              S = N + 2G, F = 9 + n_species fields in the order
+ *                              rho, s_x, s_y, s_z, E, tau, z_x, z_y, z_z, species...
+ *   dUdt  [n_sub][F][N][N][N]
+ *   amax  [n_sub]
+ *   origin[n_sub][3] lower corner of each sub-grid's interior; h [n_sub] cell width
+ *   g     [n_sub][3][N][N][N]  optional gravitational acceleration
+ * Device pointers unless stated; every buffer is owned by the caller, the
+ * library never frees or reallocates one.  The library owns the context, its
+ * scratch buffers and the device status word.
+ *
+ * Streams: every call is asynchronous on the given stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream) and never synchronises the
+ * device.  One context per stream; a context is not thread-safe.
+ *
+ * Errors: 0 on success, a negative HYDRO_E* code otherwise.  Argument errors
+ * are detected on the host before any launch.  Faults found on the device
+ * (non-positive density or pressure, NaN, an expired bounded wait) never
+ * trap: they set bits in the context's device status word, read back by
+ * hydro_status() after the caller has synchronised the stream.
+ */
+#ifndef HYDRO_GB300_H
+#define HYDRO_GB300_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define HYDRO_OK 0
+#define HYDRO_EINVAL (-1)   /* bad layout, size, pointer alignment or argument */
+#define HYDRO_ECUDA (-2)    /* a CUDA call failed; hydro_last_cuda_error() has the text */
+#define HYDRO_ENOMEM (-3)   /* scratch allocation failed */
+#define HYDRO_EUNSUP (-4)   /* valid but unsupported configuration */
+
+/* ---- device status bits (hydro_status) --------------------------------- */
+#define HYDRO_ST_NONPHYS 0x1u  /* rho <= 0, eps <= 0 or NaN seen in a step */
+#define HYDRO_ST_TIMEOUT 0x2u  /* a bounded device wait expired; results of that launch are invalid */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define HYDRO_PREC_FP64 0   /* every operation in FP64 (the plain method) */
+#define HYDRO_PREC_MIXED 1  /* reconstruction and fluxes in FP32, accumulation/update in FP64 */
+
+/* ---- boundary conditions of a uniform mesh ------------------------------ */
+#define HYDRO_BC_PERIODIC 0
+#define HYDRO_BC_OUTFLOW 1  /* zero-gradient: a ghost copies the nearest interior cell */
+
+typedef struct hydro_ctx hydro_ctx_t;
+
+/* Sub-grid layout.  N is the number of interior cells per edge (8; the paper's
+ * default sub-grid, Sec. III-B), ghost the ghost depth (must be 3: the 5-cell
+ * PPM stencil plus the face-adjacent ghost row), n_species >= 1. */
+typedef struct {
+  int N;
+  int ghost;
+  int n_species;
+} hydro_layout_t;
+
+/* Run-time options.  de_eta1: dual-energy selection threshold (eps from
+ * E - KE where that exceeds de_eta1*E, else from tau^gamma); de_eta2: tracer
+ * resync threshold (tau <- eps^(1/gamma) where eps > de_eta2*E).  Defaults:
+ * FP64, cfl 0.4, eta1 1e-3, eta2 0.1. */
+typedef struct {
+  int precision;   /* HYDRO_PREC_FP64 or HYDRO_PREC_MIXED */
+  double cfl;
+  double de_eta1;
+  double de_eta2;
+} hydro_mode_t;
+
+/* A batch of leaf sub-grids (device pointers).  g may be NULL. */
+typedef struct {
+  int n_sub;
+  double* U;
+  const double* origin;
+  const double* h;
+  const double* g;
+} hydro_batch_t;
+
+/* Create a context for a field layout, ratio of specific heats gamma > 1 and
+ * frame angular velocity omega (about +z).  Allocates nothing on the device
+ * until the first call that needs scratch.  *out is set on success.
+ * Errors: EINVAL (N not in {8}, ghost != 3, n_species outside [1,7], gamma <= 1,
+ * non-finite omega, out == NULL). */
+int hydro_create(const hydro_layout_t* layout, double gamma, double omega, hydro_ctx_t** out);
+
+/* Replace the run-time options.  Errors: EINVAL (unknown precision, cfl or
+ * thresholds outside (0,1]). */
+int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
+
+/* One stage of the semi-discrete operator on every sub-grid of the batch
+ * (Sec. III-B; the steps are listed at the top of this file):
+ *   dUdt[s] = flux divergence + rotating-frame, gravity and spin sources,
+ *   amax[s] = max over all quadrature points of all faces of the sub-grid's
+ *             N^3 cells (boundary faces included) of |u_n| + c.
+ * B->U must hold filled ghosts.  dt is the stage's time step; the
+ * semi-discrete operator does not depend on it (it is accepted for the
+ * interface's sake and must be finite and >= 0).  dUdt and amax are written
+ * completely.  Alignment: U, dUdt 16-byte aligned.
+ * Errors: EINVAL (NULL ctx/batch/pointers, n_sub < 0, misaligned U, dt < 0),
+ * ENOMEM, ECUDA.  n_sub == 0 is a no-op. */
+int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, void* stream);
+
+/* SSP-RK3 stage update of the interior cells, in place on B->U (ghosts are
+ * not touched):  U <- alpha_k U0 + beta_k (U + dt dUdt) with
+ * (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3) for stage k = 0, 1, 2; then the
+ * tracer resync tau <- eps_E^(1/gamma) where eps_E = E - |s|^2/(2 rho) exceeds
+ * de_eta2 * E.  U0 has U's padded layout (only its interior is read).  The
+ * time step is *dt_dev (a device scalar, e.g. from hydro_dt) when dt_dev is
+ * not NULL, else dt.  Errors: EINVAL (stage outside 0..2, NULL pointers). */
+int hydro_update(hydro_ctx_t* ctx, const hydro_batch_t* B, const double* U0, const double* dUdt, double dt,
+                 const double* dt_dev, int stage, void* stream);
+
+/* CFL time step on the device: *dt_out = cfl * min_s h[s] / amax[s] (cfl <= 0
+ * uses the context's mode).  One launch, no host synchronisation. */
+int hydro_dt(hydro_ctx_t* ctx, const double* amax, const double* h, int n_sub, double cfl, double* dt_out,
+             void* stream);
+
+/* Ghost fill of a uniform mesh of nbx x nby x nbz sub-grids (sub-grid
+ * s = (kz*nby + ky)*nbx + kx, all at one refinement level): every ghost cell
+ * copies the cell of the same global position from the neighbouring
+ * sub-grid's interior; at the domain boundary the position is wrapped
+ * (HYDRO_BC_PERIODIC) or clamped to the nearest interior cell
+ * (HYDRO_BC_OUTFLOW).  Ghost exchange between leaf sub-grids, Sec. IV-A.2.
+ * Requires B->n_sub == nbx*nby*nbz.  Pure copies (bitwise). */
+int hydro_fill_ghosts_uniform(hydro_ctx_t* ctx, const hydro_batch_t* B, int nbx, int nby, int nbz, int bc,
+                              void* stream);
+
+/* Global conservation sums over the interior cells of the batch, FP64:
+ * sums[k] = sum_s sum_cells U[s][k] h_s^3 for k < F, and
+ * sums[F] = sum (x_c s_y - y_c s_x + z_z) h^3 (angular momentum about +z).
+ * sums has F+1 device doubles.  Deterministic (fixed reduction order). */
+int hydro_conserved_sums(hydro_ctx_t* ctx, const hydro_batch_t* B, double* sums, void* stream);
+
+/* Device status bits accumulated since the last call (HYDRO_ST_*), then
+ * cleared.  Synchronises nothing: call after the stream has been synchronised. */
+int hydro_status(hydro_ctx_t* ctx, uint32_t* flags);
+
+/* Human-readable text of an error code (static storage). */
+const char* hydro_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread's calls (static storage per thread). */
+const char* hydro_last_cuda_error(void);
+
+/* Release the context and its scratch (after the caller's work on it has completed). */
+void hydro_destroy(hydro_ctx_t* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYDRO_GB300_H */

@@ -159,6 +159,7 @@ def count_ops(P: OracleParams, U: np.ndarray, origin, h: float) -> dict:
     """Exact operation counts of one sub-grid stage and of one RK update."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     origin = np.ascontiguousarray(origin, dtype=np.float64)
-    out = (C.c_long * 16)()
+    out = (C.c_long * 18)()
     lib().orc_count_ops(C.byref(P.c()), _dp(U), _dp(origin), float(h), out)
-    return {"step": dict(zip(OP_NAMES, out[:8])), "update": dict(zip(OP_NAMES, out[8:]))}
+    return {"step": dict(zip(OP_NAMES, out[:8])), "update": dict(zip(OP_NAMES, out[8:16])),
+            "ppm_ops": out[16], "ppm_calls": out[17]}

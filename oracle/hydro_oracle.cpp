@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -40,8 +41,11 @@ namespace orc {
 // separately (they are sign-bit operations).
 struct Ops {
   long add = 0, mul = 0, div = 0, sqrt = 0, pow = 0, cmp = 0, minmax = 0, sgn = 0;
+  long total() const { return add + mul + div + sqrt + pow + cmp + minmax; }
 };
 static thread_local Ops g_ops;
+// operations spent inside PPM line evaluations, and the number of evaluations
+static thread_local long g_ppm_ops = 0, g_ppm_calls = 0;
 
 struct CD {
   double v;
@@ -240,7 +244,14 @@ int recon_point(const Params& P, const std::vector<T>& Q, int x, int y, int z, c
     T s5[5];
     for (int m = -2; m <= 2; ++m) s5[m + 2] = Q[k * S3 + at(x + m * d[0], y + m * d[1], z + m * d[2])];
     T qp, qm;
-    fl |= ppm_line(s5, qp, qm, want_flag);
+    if constexpr (std::is_same<T, CD>::value) {
+      const long before = g_ops.total();
+      fl |= ppm_line(s5, qp, qm, want_flag);
+      g_ppm_ops += g_ops.total() - before;
+      g_ppm_calls += 1;
+    } else {
+      fl |= ppm_line(s5, qp, qm, want_flag);
+    }
     out[k] = qp;
   }
   return fl;
@@ -518,7 +529,8 @@ void orc_face_values(const orc_params* p, const double* U, int n, const int* cel
 
 // Operation count of one sub-grid stage (step) and of one update, through the
 // counting scalar: out[0..7] = add, mul, div, sqrt, pow, cmp, minmax, sgn for
-// the step; out[8..15] the same for the update.
+// the step; out[8..15] the same for the update; out[16] = operations inside
+// PPM line evaluations of the step, out[17] = number of those evaluations.
 void orc_count_ops(const orc_params* p, const double* U, const double* origin, double h, long* out) {
   const orc::Params P = to_p(p);
   const int S = P.N + 2 * P.G;
@@ -527,8 +539,12 @@ void orc_count_ops(const orc_params* p, const double* U, const double* origin, d
   for (size_t i = 0; i < Uc.size(); ++i) Uc[i] = orc::CD(U[i]);
   orc::CD am;
   orc::g_ops = orc::Ops();
+  orc::g_ppm_ops = 0;
+  orc::g_ppm_calls = 0;
   orc::step_subgrid<orc::CD>(P, Uc.data(), origin, h, nullptr, dU.data(), &am, nullptr);
   const orc::Ops a = orc::g_ops;
+  out[16] = orc::g_ppm_ops;
+  out[17] = orc::g_ppm_calls;
   std::vector<orc::CD> U0 = Uc;
   orc::g_ops = orc::Ops();
   orc::update_subgrid<orc::CD>(P, Uc.data(), U0.data(), dU.data(), 1e-6, 1);

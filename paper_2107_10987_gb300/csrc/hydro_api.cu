@@ -1,0 +1,214 @@
+// hydro_api.cu -- the C ABI (include/hydro.h): context, argument checks,
+// scratch management and dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "hydro.h"
+#include "hydro_common.cuh"
+
+namespace hyd {
+cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st);
+cudaError_t launch_update(double* U, const double* U0, const double* dUdt, double dt, const double* dt_dev,
+                          int stage, double eta2, double gamma, long n_sub, int num_sms, cudaStream_t st);
+cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, double* out, cudaStream_t st);
+cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st);
+cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
+                        double* sums, cudaStream_t st);
+}  // namespace hyd
+
+struct hydro_ctx {
+  int N, G, n_species, F;
+  double gamma, omega;
+  hydro_mode_t mode;
+  int device;
+  int num_sms;
+  unsigned* status;      // device word
+  double* scratch;       // step scratch
+  size_t scratch_bytes;
+  double* part;          // conservation partials
+  size_t part_bytes;
+};
+
+static thread_local char g_cuda_err[256] = "no CUDA error";
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", where, cudaGetErrorString(e));
+  return HYDRO_ECUDA;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int ensure_status(hydro_ctx* c) {
+  if (c->status) return HYDRO_OK;
+  cudaError_t e = cudaMalloc(&c->status, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+  e = cudaMemset(c->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+  return HYDRO_OK;
+}
+
+static int ensure_buf(double** buf, size_t* have, size_t need, const char* what) {
+  if (*have >= need) return HYDRO_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(buf, need);
+  if (e != cudaSuccess) {
+    cuda_fail(e, what);
+    return HYDRO_ENOMEM;
+  }
+  *have = need;
+  return HYDRO_OK;
+}
+
+extern "C" {
+
+int hydro_create(const hydro_layout_t* L, double gamma, double omega, hydro_ctx_t** out) {
+  if (!L || !out) return HYDRO_EINVAL;
+  *out = nullptr;
+  if (L->N != hyd::N || L->ghost != hyd::G || L->n_species < 1) return HYDRO_EINVAL;
+  if (L->n_species != 1) return HYDRO_EUNSUP;
+  if (!(gamma > 1.0) || !std::isfinite(gamma) || !std::isfinite(omega)) return HYDRO_EINVAL;
+  hydro_ctx* c = new (std::nothrow) hydro_ctx();
+  if (!c) return HYDRO_ENOMEM;
+  c->N = L->N;
+  c->G = L->ghost;
+  c->n_species = L->n_species;
+  c->F = 9 + L->n_species;
+  c->gamma = gamma;
+  c->omega = omega;
+  c->mode.precision = HYDRO_PREC_FP64;
+  c->mode.cfl = 0.4;
+  c->mode.de_eta1 = 1e-3;
+  c->mode.de_eta2 = 0.1;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "hydro_create");
+  }
+  *out = c;
+  return HYDRO_OK;
+}
+
+int hydro_set_mode(hydro_ctx_t* c, const hydro_mode_t* m) {
+  if (!c || !m) return HYDRO_EINVAL;
+  if (m->precision != HYDRO_PREC_FP64 && m->precision != HYDRO_PREC_MIXED) return HYDRO_EINVAL;
+  if (!(m->cfl > 0.0 && m->cfl <= 1.0) || !(m->de_eta1 > 0.0 && m->de_eta1 <= 1.0) ||
+      !(m->de_eta2 > 0.0 && m->de_eta2 <= 1.0))
+    return HYDRO_EINVAL;
+  c->mode = *m;
+  return HYDRO_OK;
+}
+
+int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, double* amax, void* stream) {
+  if (!c || !B) return HYDRO_EINVAL;
+  if (B->n_sub < 0 || !std::isfinite(dt) || dt < 0.0) return HYDRO_EINVAL;
+  if (B->n_sub == 0) return HYDRO_OK;
+  if (!B->U || !B->origin || !B->h || !dUdt || !amax) return HYDRO_EINVAL;
+  if (!aligned16(B->U) || !aligned16(dUdt)) return HYDRO_EINVAL;
+  if (c->mode.precision != HYDRO_PREC_FP64) return HYDRO_EUNSUP;
+  int rc = ensure_status(c);
+  if (rc) return rc;
+  const int grid = B->n_sub < c->num_sms ? B->n_sub : c->num_sms;
+  rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
+                  "cudaMalloc(step scratch)");
+  if (rc) return rc;
+  hyd::StepArgs64 A;
+  A.U = B->U;
+  A.origin = B->origin;
+  A.h = B->h;
+  A.g = B->g;
+  A.dUdt = dUdt;
+  A.amax = amax;
+  A.scratch = c->scratch;
+  A.status = c->status;
+  A.n_sub = B->n_sub;
+  A.P.gamma = c->gamma;
+  A.P.gm1 = c->gamma - 1.0;
+  A.P.omega = c->omega;
+  A.P.eta1 = c->mode.de_eta1;
+  cudaError_t e = hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
+  return HYDRO_OK;
+}
+
+int hydro_update(hydro_ctx_t* c, const hydro_batch_t* B, const double* U0, const double* dUdt, double dt,
+                 const double* dt_dev, int stage, void* stream) {
+  if (!c || !B) return HYDRO_EINVAL;
+  if (stage < 0 || stage > 2 || B->n_sub < 0) return HYDRO_EINVAL;
+  if (!dt_dev && (!std::isfinite(dt) || dt < 0.0)) return HYDRO_EINVAL;
+  if (B->n_sub == 0) return HYDRO_OK;
+  if (!B->U || !U0 || !dUdt) return HYDRO_EINVAL;
+  cudaError_t e = hyd::launch_update(B->U, U0, dUdt, dt, dt_dev, stage, c->mode.de_eta2, c->gamma, B->n_sub,
+                                     c->num_sms, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_update");
+  return HYDRO_OK;
+}
+
+int hydro_dt(hydro_ctx_t* c, const double* amax, const double* h, int n_sub, double cfl, double* dt_out,
+             void* stream) {
+  if (!c || !amax || !h || !dt_out || n_sub <= 0) return HYDRO_EINVAL;
+  if (!(cfl > 0.0)) cfl = c->mode.cfl;
+  cudaError_t e = hyd::launch_dt(amax, h, n_sub, cfl, dt_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_dt");
+  return HYDRO_OK;
+}
+
+int hydro_fill_ghosts_uniform(hydro_ctx_t* c, const hydro_batch_t* B, int nbx, int nby, int nbz, int bc,
+                              void* stream) {
+  if (!c || !B || !B->U) return HYDRO_EINVAL;
+  if (nbx <= 0 || nby <= 0 || nbz <= 0 || (long)nbx * nby * nbz != B->n_sub) return HYDRO_EINVAL;
+  if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
+  cudaError_t e = hyd::launch_ghost_uniform(B->U, nbx, nby, nbz, bc, c->num_sms, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_fill_ghosts_uniform");
+  return HYDRO_OK;
+}
+
+int hydro_conserved_sums(hydro_ctx_t* c, const hydro_batch_t* B, double* sums, void* stream) {
+  if (!c || !B || !sums || B->n_sub <= 0 || !B->U || !B->origin || !B->h) return HYDRO_EINVAL;
+  int rc = ensure_buf(&c->part, &c->part_bytes, (size_t)B->n_sub * (hyd::F + 1) * sizeof(double),
+                      "cudaMalloc(sum partials)");
+  if (rc) return rc;
+  cudaError_t e = hyd::launch_sums(B->U, B->origin, B->h, B->n_sub, c->part, sums, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_conserved_sums");
+  return HYDRO_OK;
+}
+
+int hydro_status(hydro_ctx_t* c, uint32_t* flags) {
+  if (!c || !flags) return HYDRO_EINVAL;
+  *flags = 0;
+  if (!c->status) return HYDRO_OK;
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpy(&v, c->status, sizeof v, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_status");
+  e = cudaMemset(c->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_status");
+  *flags = v;
+  return HYDRO_OK;
+}
+
+const char* hydro_strerror(int code) {
+  switch (code) {
+    case HYDRO_OK: return "success";
+    case HYDRO_EINVAL: return "invalid argument (layout, size, pointer, alignment or value)";
+    case HYDRO_ECUDA: return "CUDA error (see hydro_last_cuda_error)";
+    case HYDRO_ENOMEM: return "device scratch allocation failed";
+    case HYDRO_EUNSUP: return "unsupported configuration";
+    default: return "unknown error code";
+  }
+}
+
+const char* hydro_last_cuda_error(void) { return g_cuda_err; }
+
+void hydro_destroy(hydro_ctx_t* c) {
+  if (!c) return;
+  if (c->status) cudaFree(c->status);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->part) cudaFree(c->part);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// hydro_aux.cu -- the kernels around the step: SSP-RK3 stage update with the
+// dual-energy tracer resync, CFL time step, uniform-mesh ghost fill and the
+// global conservation sums.
+#include "hydro_common.cuh"
+
+namespace hyd {
+
+// ---------------------------------------------------------------------------
+// RK3 stage update (three hydro iterations per time step, Sec. IV-A.2),
+// interior cells only:
+//   U <- alpha U0 + beta (U + dt dU/dt), (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3)
+//   then tau <- eps_E^(1/gamma) where eps_E = E - |s|^2/(2 rho) > eta2 E
+//   (tracer resync of the dual-energy formalism, Bryan et al. 1995).
+// Explicitly rounded operations: the same values as the FP64 oracle.
+struct UpdateArgs {
+  double* U;
+  const double* U0;
+  const double* dUdt;
+  const double* dt_dev;
+  double dt;
+  double alpha, beta, eta2, inv_gamma;
+  long n_cells;  // n_sub * N3
+};
+
+__global__ void __launch_bounds__(256) hydro_update_kernel(UpdateArgs A) {
+  const double dt = A.dt_dev ? *A.dt_dev : A.dt;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n_cells; i += (long)gridDim.x * blockDim.x) {
+    const long s = i / N3;
+    const int c = (int)(i % N3);
+    const int x = c % N, y = (c / N) % N, z = c / (N * N);
+    const long uc = (size_t)s * F * S3 + ((z + G) * S + (y + G)) * S + (x + G);
+    const long dc = (size_t)s * F * N3 + c;
+    double u[F];
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+      const double t = radd(A.U[uc + (long)k * S3], rmul(dt, A.dUdt[dc + (long)k * N3]));
+      u[k] = radd(rmul(A.alpha, A.U0[uc + (long)k * S3]), rmul(A.beta, t));
+    }
+    const double rho = u[RHO];
+    const double vx = u[SX] / rho, vy = u[SY] / rho, vz = u[SZ] / rho;
+    const double ek = rmul(rmul(0.5, rho), radd(radd(rmul(vx, vx), rmul(vy, vy)), rmul(vz, vz)));
+    const double eE = rsub(u[EGAS], ek);
+    if (eE > rmul(A.eta2, u[EGAS])) u[TAU] = pow(eE, A.inv_gamma);
+#pragma unroll
+    for (int k = 0; k < F; ++k) A.U[uc + (long)k * S3] = u[k];
+  }
+}
+
+cudaError_t launch_update(double* U, const double* U0, const double* dUdt, double dt, const double* dt_dev,
+                          int stage, double eta2, double gamma, long n_sub, int num_sms, cudaStream_t st) {
+  static const double alpha[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double beta[3] = {1.0, 0.25, 2.0 / 3.0};
+  UpdateArgs A{U, U0, dUdt, dt_dev, dt, alpha[stage], beta[stage], eta2, 1.0 / gamma, n_sub * N3};
+  long blocks = (A.n_cells + 255) / 256;
+  const long cap = (long)num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  hydro_update_kernel<<<(int)blocks, 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CFL time step: dt = cfl * min_s h[s] / amax[s], one block, fixed order.
+__global__ void __launch_bounds__(1024) hydro_dt_kernel(const double* amax, const double* h, int n, double cfl,
+                                                       double* out) {
+  __shared__ double red[32];
+  double m = INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, h[i] / amax[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *out = cfl * m;
+  }
+}
+
+cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, double* out, cudaStream_t st) {
+  hydro_dt_kernel<<<1, 1024, 0, st>>>(amax, h, n, cfl, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Uniform-mesh ghost fill: a ghost cell copies the cell at the same global
+// position; outside the domain the position wraps (periodic) or is clamped
+// to the nearest interior cell (outflow, zero gradient).
+struct GhostArgs {
+  double* U;
+  int nbx, nby, nbz, bc;
+  long n_items;  // n_sub * F * S3
+};
+
+__device__ __forceinline__ int bc_map(int gpos, int n, int bc) {
+  if (bc == 0) return ((gpos % n) + n) % n;
+  return gpos < 0 ? 0 : (gpos >= n ? n - 1 : gpos);
+}
+
+__global__ void __launch_bounds__(256) hydro_ghost_uniform_kernel(GhostArgs A) {
+  const int nx = A.nbx * N, ny = A.nby * N, nz = A.nbz * N;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n_items; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % S3);
+    const long sk = i / S3;  // s * F + k
+    const int k = (int)(sk % F);
+    const long s = sk / F;
+    const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
+    if (lx >= 0 && lx < N && ly >= 0 && ly < N && lz >= 0 && lz < N) continue;
+    const int kx = (int)(s % A.nbx), ky = (int)((s / A.nbx) % A.nby), kz = (int)(s / ((long)A.nbx * A.nby));
+    const int gx = bc_map(kx * N + lx, nx, A.bc), gy = bc_map(ky * N + ly, ny, A.bc), gz = bc_map(kz * N + lz, nz, A.bc);
+    const long os = ((long)(gz / N) * A.nby + (gy / N)) * A.nbx + (gx / N);
+    const int oc = ((gz % N + G) * S + (gy % N + G)) * S + (gx % N + G);
+    A.U[i] = A.U[(os * F + k) * S3 + oc];
+  }
+}
+
+cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st) {
+  GhostArgs A{U, nbx, nby, nbz, bc, (long)nbx * nby * nbz * F * S3};
+  long blocks = (A.n_items + 255) / 256;
+  const long cap = (long)num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  hydro_ghost_uniform_kernel<<<(int)blocks, 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Conservation sums: per sub-grid partials (one block each, fixed tree), then
+// one block over the partials in a fixed order.
+constexpr int NSUM = F + 1;
+
+__global__ void __launch_bounds__(256) hydro_sums_partial_kernel(const double* U, const double* origin,
+                                                                 const double* h, int n_sub, double* part) {
+  __shared__ double red[NSUM][256];
+  const int s = blockIdx.x;
+  if (s >= n_sub) return;
+  const double hs = h[s];
+  const double vol = hs * hs * hs;
+  double acc[NSUM];
+#pragma unroll
+  for (int k = 0; k < NSUM; ++k) acc[k] = 0.0;
+  for (int c = threadIdx.x; c < N3; c += blockDim.x) {
+    const int x = c % N, y = (c / N) % N, z = c / (N * N);
+    const long uc = (size_t)s * F * S3 + ((z + G) * S + (y + G)) * S + (x + G);
+#pragma unroll
+    for (int k = 0; k < F; ++k) acc[k] += U[uc + (long)k * S3];
+    const double xc = origin[3 * s] + (x + 0.5) * hs, yc = origin[3 * s + 1] + (y + 0.5) * hs;
+    acc[F] += (xc * U[uc + SY * S3] - yc * U[uc + SX * S3]) + U[uc + ZZ * S3];
+  }
+#pragma unroll
+  for (int k = 0; k < NSUM; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < NSUM) part[(size_t)s * NSUM + threadIdx.x] = red[threadIdx.x][0] * vol;
+}
+
+__global__ void __launch_bounds__(256) hydro_sums_final_kernel(const double* part, int n_sub, double* sums) {
+  __shared__ double red[NSUM][256];
+  double acc[NSUM];
+#pragma unroll
+  for (int k = 0; k < NSUM; ++k) acc[k] = 0.0;
+  for (int s = threadIdx.x; s < n_sub; s += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) acc[k] += part[(size_t)s * NSUM + k];
+#pragma unroll
+  for (int k = 0; k < NSUM; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < NSUM) sums[threadIdx.x] = red[threadIdx.x][0];
+}
+
+cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
+                        double* sums, cudaStream_t st) {
+  hydro_sums_partial_kernel<<<n_sub, 256, 0, st>>>(U, origin, h, n_sub, part);
+  hydro_sums_final_kernel<<<1, 256, 0, st>>>(part, n_sub, sums);
+  return cudaGetLastError();
+}
+
+}  // namespace hyd

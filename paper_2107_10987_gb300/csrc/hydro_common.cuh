@@ -1,0 +1,103 @@
+// hydro_common.cuh -- layout constants and device helpers shared by the
+// kernels of the GB300 hydro library (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hyd {
+
+// Sub-grid geometry (Sec. III-B: 8^3 cells per leaf sub-grid by default; a
+// 5-cell PPM stencil on the face-adjacent ghost row needs 3 ghost layers).
+constexpr int N = 8;
+constexpr int G = 3;
+constexpr int S = N + 2 * G;         // 14 stored cells per edge
+constexpr int S3 = S * S * S;        // 2744
+constexpr int N3 = N * N * N;        // 512
+constexpr int F = 10;                // rho, s(3), E, tau, z(3), one species
+constexpr int NROW = 3 * N * N;      // 192 rows: 3 axes x 8 x 8 transverse positions
+
+// Field slots of the conserved state and of the reconstructed primitives
+// (rho, v(3), eps, tau, z(3), species share the slots).
+enum { RHO = 0, SX = 1, SY = 2, SZ = 3, EGAS = 4, TAU = 5, ZX = 6, ZY = 7, ZZ = 8, SP0 = 9 };
+
+// Per-axis scratch of one sub-grid: for each axis a and interior cell the 10
+// flux differences Fbar(i+1/2) - Fbar(i-1/2) and the 3 torque differences.
+constexpr int DQ = F + 3;
+constexpr size_t kScratchPerSub = (size_t)3 * DQ * N3;  // doubles
+
+struct StepParams {
+  double gamma, gm1, omega, eta1;
+};
+
+// Arguments of the step kernels (device pointers; layouts as in hydro.h).
+struct StepArgs64 {
+  const double* U;
+  const double* origin;
+  const double* h;
+  const double* g;
+  double* dUdt;
+  double* amax;
+  double* scratch;  // per-CTA scratch, kScratchPerSub doubles per CTA
+  unsigned* status;
+  int n_sub;
+  StepParams P;
+};
+
+// ---- FP64 arithmetic that the compiler may not contract into FMA --------
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+// ---- mbarrier + bulk (TMA) copy, inline PTX -----------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Bulk global->shared copy completing on an mbarrier (size and both
+// addresses multiples of 16 bytes).
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after max_iter polls (each poll itself suspends for
+// a hardware-chosen time) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long max_iter) {
+  for (long i = 0; i < max_iter; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+}  // namespace hyd

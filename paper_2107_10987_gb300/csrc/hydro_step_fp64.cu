@@ -1,0 +1,336 @@
+// hydro_step_fp64.cu -- the per-sub-grid hydro step in FP64 (the plain method).
+//
+// One persistent CTA per SM loops over sub-grids.  For each sub-grid:
+//   1. the ghost-padded state (10 fields x 14^3 doubles, 219,520 B) is staged
+//      into shared memory by bulk TMA copies completing on an mbarrier;
+//   2. primitives (rho, v, eps with the dual-energy selection, tau, z,
+//      species) replace the conserved values in place (Sec. III-B, Bryan 1995);
+//   3. 192 threads, one per (axis a, transverse row), sweep their row along a.
+//      At each cell j they run PPM (Colella & Woodward 1984) on the 9 lines
+//      d = e_a + t1 e_b + t2 e_c; the line's +d end is the left state of face
+//      j+1/2 at point (t1,t2), its -d end the right state of face j-1/2 at
+//      point (-t1,-t2).  The left states are carried to the next cell, so every
+//      line is evaluated once per axis and both of its ends are used.  At each
+//      face the 9 Kurganov-Tadmor point fluxes are summed with the Simpson
+//      weights (1,4,1)x(1,4,1)/36, together with the torques of the momentum
+//      flux about both cell centres;
+//   4. per-axis flux differences go to a per-CTA scratch buffer in global
+//      memory (L2-resident); one thread per interior cell then forms the
+//      divergence in a fixed order, adds the rotating-frame, gravity and spin
+//      sources and writes dU/dt;
+//   5. the maximum signal speed is reduced by warp shuffles, then across warps.
+// The PPM and primitive arithmetic uses explicitly rounded operations (no FMA
+// contraction) so that every limiter branch is decided on exactly the values
+// the FP64 oracle sees; the flux arithmetic may contract.
+#include "hydro_common.cuh"
+
+namespace hyd {
+
+// MC-limited slope of sample j from delta_{j-1} = a and delta_j = b.
+__device__ __forceinline__ double slope64(double a, double b) {
+  if (rmul(a, b) <= 0.0) return 0.0;
+  const double m = fmin(fmin(2.0 * fabs(a), 2.0 * fabs(b)), 0.5 * fabs(radd(a, b)));
+  return b > 0.0 ? m : -m;
+}
+
+// PPM on the five samples s0..s4 of one line: qp = value at the +d end of the
+// centre cell, qm = value at its -d end (limited, monotonised).
+__device__ __forceinline__ void ppm64(double s0, double s1, double s2, double s3, double s4, double& qp,
+                                      double& qm) {
+  const double sixth = 1.0 / 6.0;
+  const double d0 = rsub(s1, s0), d1 = rsub(s2, s1), d2 = rsub(s3, s2), d3 = rsub(s4, s3);
+  const double D0 = slope64(d0, d1), D1 = slope64(d1, d2), D2 = slope64(d2, d3);
+  double p = rsub(rmul(0.5, radd(s2, s3)), rmul(rsub(D2, D1), sixth));
+  double m = rsub(rmul(0.5, radd(s1, s2)), rmul(rsub(D1, D0), sixth));
+  if (rmul(rsub(p, s2), rsub(s2, m)) <= 0.0) {
+    p = s2;
+    m = s2;
+  } else {
+    const double dq = rsub(p, m);
+    const double lhs = rmul(dq, rsub(s2, rmul(0.5, radd(p, m))));
+    const double rhs = rmul(rmul(dq, dq), sixth);
+    if (lhs > rhs) {
+      m = rsub(rmul(3.0, s2), rmul(2.0, p));
+    } else if (lhs < -rhs) {
+      p = rsub(rmul(3.0, s2), rmul(2.0, m));
+    }
+  }
+  qp = p;
+  qm = m;
+}
+
+// All ten primitives along the line through smem cell index c with stride st.
+__device__ __forceinline__ void line10(const double* __restrict__ Q, int c, int st, double qp[F], double qm[F]) {
+#pragma unroll
+  for (int k = 0; k < F; ++k) {
+    const double* q = Q + k * S3 + c;
+    ppm64(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+  }
+}
+
+// Physical side state at a quadrature point: conserved U, flux F along axis a,
+// signal speed |u_n| + c.  u = v - omega z_hat x x_q (rotating frame).
+__device__ __forceinline__ void side64(const double q[F], int a, double xq, double yq, const StepParams& P,
+                                       double U[F], double Fl[F], double& spd) {
+  const double rho = q[RHO], vx = q[1], vy = q[2], vz = q[3], eps = q[4];
+  const double ek = (0.5 * rho) * ((vx * vx + vy * vy) + vz * vz);
+  const double E = eps + ek;
+  const double p = P.gm1 * eps;
+  const double c = sqrt((P.gamma * p) / rho);
+  const double ux = vx + P.omega * yq, uy = vy - P.omega * xq;
+  const double un = (a == 0) ? ux : (a == 1) ? uy : vz;
+  const double va = (a == 0) ? vx : (a == 1) ? vy : vz;
+  U[RHO] = rho;
+  U[SX] = rho * vx;
+  U[SY] = rho * vy;
+  U[SZ] = rho * vz;
+  U[EGAS] = E;
+#pragma unroll
+  for (int k = TAU; k < F; ++k) U[k] = q[k];
+#pragma unroll
+  for (int k = 0; k < F; ++k) Fl[k] = U[k] * un;
+  Fl[SX + a] += p;
+  Fl[EGAS] += p * va;
+  spd = fabs(un) + c;
+}
+
+// Kurganov-Tadmor flux at one point, accumulated with weight w into the face
+// sum and into the torques about the left (rl) and right (rr) cell centres.
+__device__ __forceinline__ void point64(const double qL[F], const double qR[F], int a, double xq, double yq,
+                                        double w, const double rl[3], const double rr[3], const StepParams& P,
+                                        double fsum[F], double tl[3], double tr[3], double& amax) {
+  double UL[F], FL[F], UR[F], FR[F], sL, sR;
+  side64(qL, a, xq, yq, P, UL, FL, sL);
+  side64(qR, a, xq, yq, P, UR, FR, sR);
+  const double aq = fmax(sL, sR);
+  amax = fmax(amax, aq);
+  double Fq[F];
+#pragma unroll
+  for (int k = 0; k < F; ++k) {
+    Fq[k] = 0.5 * (FL[k] + FR[k]) - (0.5 * aq) * (UR[k] - UL[k]);
+    fsum[k] += w * Fq[k];
+  }
+  const double fx = Fq[SX], fy = Fq[SY], fz = Fq[SZ];
+  tl[0] += w * (rl[1] * fz - rl[2] * fy);
+  tl[1] += w * (rl[2] * fx - rl[0] * fz);
+  tl[2] += w * (rl[0] * fy - rl[1] * fx);
+  tr[0] += w * (rr[1] * fz - rr[2] * fy);
+  tr[1] += w * (rr[2] * fx - rr[0] * fz);
+  tr[2] += w * (rr[0] * fy - rr[1] * fx);
+}
+
+constexpr int kThreads64 = NROW;  // 192
+constexpr long kWaitPolls = 1L << 24;
+
+__global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs64 A) {
+  extern __shared__ __align__(128) double Q[];  // [F][S3]
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ double red[kThreads64 / 32];
+  __shared__ int bail;
+  const int tid = threadIdx.x;
+  double* __restrict__ D = A.scratch + (size_t)blockIdx.x * kScratchPerSub;
+
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    bail = 0;
+  }
+  __syncthreads();
+
+  // this thread's row: axis a, transverse axes b < c at positions pb, pc
+  const int a = tid / (N * N);
+  const int r = tid % (N * N);
+  const int pb = r % N, pc = r / N;
+  const int b = (a == 0) ? 1 : 0;
+  const int cx = (a == 2) ? 1 : 2;
+  const int st[3] = {1, S, S * S};
+  const int sa = st[a], sb = st[b], sc = st[cx];
+
+  uint32_t phase = 0;
+  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
+    // ---- 1. stage the sub-grid into shared memory (bulk TMA) ------------
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar, (uint32_t)(F * S3 * sizeof(double)));
+      const double* src = A.U + (size_t)s * F * S3;
+#pragma unroll 1
+      for (int k = 0; k < F; ++k) bulk_g2s(Q + k * S3, src + (size_t)k * S3, S3 * sizeof(double), &bar);
+    }
+    if (!mbar_wait_bounded(&bar, phase, kWaitPolls)) {
+      atomicOr(A.status, 2u);
+      bail = 1;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    if (bail) break;
+
+    // ---- 2. primitives in place ----------------------------------------
+    bool bad = false;
+    for (int c = tid; c < S3; c += kThreads64) {
+      const double rho = Q[RHO * S3 + c];
+      const double vx = Q[SX * S3 + c] / rho, vy = Q[SY * S3 + c] / rho, vz = Q[SZ * S3 + c] / rho;
+      const double E = Q[EGAS * S3 + c];
+      const double ek = rmul(rmul(0.5, rho), radd(radd(rmul(vx, vx), rmul(vy, vy)), rmul(vz, vz)));
+      const double eE = rsub(E, ek);
+      const double eps = (eE > rmul(A.P.eta1, E)) ? eE : pow(Q[TAU * S3 + c], A.P.gamma);
+      Q[SX * S3 + c] = vx;
+      Q[SY * S3 + c] = vy;
+      Q[SZ * S3 + c] = vz;
+      Q[EGAS * S3 + c] = eps;
+      bad |= !(rho > 0.0) || !(eps > 0.0);
+    }
+    if (bad) atomicOr(A.status, 1u);
+    __syncthreads();
+
+    // ---- 3. row sweep ------------------------------------------------------
+    const double h = A.h[s];
+    const double half_h = 0.5 * h;
+    const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
+    double amax = 0.0;
+    double plus[9][F];
+    double fprev[F], trprev[3];
+    // smem index of the row's cell at a-index j
+    int coord0[3];
+    coord0[a] = 0;
+    coord0[b] = pb;
+    coord0[cx] = pc;
+    const int c0 = ((coord0[2] + G) * S + (coord0[1] + G)) * S + (coord0[0] + G);
+#pragma unroll 1
+    for (int j = -1; j <= N; ++j) {
+      const int cj = c0 + j * sa;
+      double fsum[F], tl[3], tr[3];
+#pragma unroll
+      for (int k = 0; k < F; ++k) fsum[k] = 0.0;
+      tl[0] = tl[1] = tl[2] = 0.0;
+      tr[0] = tr[1] = tr[2] = 0.0;
+      // left cell of face j-1/2 is (j-1) along a
+      int ci[3];
+      ci[a] = j - 1;
+      ci[b] = pb;
+      ci[cx] = pc;
+#pragma unroll 1
+      for (int p = 0; p <= 4; ++p) {
+        const int t1 = p / 3 - 1, t2 = p % 3 - 1;  // point p; its mirror 8-p has (-t1,-t2)
+        double qpA[F], qmA[F], qpB[F], qmB[F];
+        line10(Q, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
+        if (p != 4) line10(Q, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        if (j >= 0) {
+#pragma unroll 1
+          for (int side = 0; side < 2; ++side) {
+            if (p == 4 && side == 1) continue;
+            // side 0: point 8-p (offsets -t1,-t2) with right state qmA;
+            // side 1: point p (offsets t1,t2) with right state qmB.
+            const int u1 = side ? t1 : -t1, u2 = side ? t2 : -t2;
+            const int pt = (u1 + 1) * 3 + (u2 + 1);
+            int d[3];
+            d[a] = 1;
+            d[b] = u1;
+            d[cx] = u2;
+            const double xq = o[0] + h * ((ci[0] + 0.5) + 0.5 * d[0]);
+            const double yq = o[1] + h * ((ci[1] + 0.5) + 0.5 * d[1]);
+            const double rl[3] = {half_h * d[0], half_h * d[1], half_h * d[2]};
+            double rr[3] = {rl[0], rl[1], rl[2]};
+            rr[a] = half_h * (d[a] - 2);
+            const double w = (u1 == 0 && u2 == 0) ? (16.0 / 36.0) : (u1 == 0 || u2 == 0) ? (4.0 / 36.0) : (1.0 / 36.0);
+            point64(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, A.P, fsum, tl, tr, amax);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < F; ++k) {
+          plus[p][k] = qpA[k];
+          if (p != 4) plus[8 - p][k] = qpB[k];
+        }
+      }
+      if (j >= 1) {
+        // interior cell i = j-1 along a: differences of its two a-faces
+        const int i = j - 1;
+        int cc[3];
+        cc[a] = i;
+        cc[b] = pb;
+        cc[cx] = pc;
+        const int cell = (cc[2] * N + cc[1]) * N + cc[0];
+        double* Da = D + (size_t)a * DQ * N3 + cell;
+#pragma unroll
+        for (int k = 0; k < F; ++k) Da[k * N3] = fsum[k] - fprev[k];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = tl[m] - trprev[m];
+      }
+      if (j >= 0) {
+#pragma unroll
+        for (int k = 0; k < F; ++k) fprev[k] = fsum[k];
+        trprev[0] = tr[0];
+        trprev[1] = tr[1];
+        trprev[2] = tr[2];
+      }
+    }
+    // block-wide amax; order the generic-proxy shared-memory accesses of this
+    // sub-grid before the next bulk copy overwrites the buffer
+    fence_proxy_async();
+    amax = warp_max(amax);
+    if ((tid & 31) == 0) red[tid >> 5] = amax;
+    __syncthreads();  // also: scratch writes visible, shared Q reads finished
+
+    // ---- 4. divergence + sources, one thread per interior cell -----------
+    const double inv_h = 1.0 / h;
+    const double om = A.P.omega;
+    const double* Us = A.U + (size_t)s * F * S3;
+    double* dU = A.dUdt + (size_t)s * F * N3;
+    for (int c = tid; c < N3; c += kThreads64) {
+      const int x = c % N, y = (c / N) % N, z = c / (N * N);
+      const int uc = ((z + G) * S + (y + G)) * S + (x + G);
+      double du[F];
+#pragma unroll
+      for (int k = 0; k < F; ++k) {
+        const double div = (D[(0 * DQ + k) * N3 + c] + D[(1 * DQ + k) * N3 + c]) + D[(2 * DQ + k) * N3 + c];
+        du[k] = -(div * inv_h);
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const double tq =
+            (D[(0 * DQ + F + m) * N3 + c] + D[(1 * DQ + F + m) * N3 + c]) + D[(2 * DQ + F + m) * N3 + c];
+        du[ZX + m] = du[ZX + m] - tq * inv_h;
+      }
+      const double sx = Us[SX * S3 + uc], sy = Us[SY * S3 + uc], sz = Us[SZ * S3 + uc];
+      du[SX] = du[SX] + om * sy;
+      du[SY] = du[SY] - om * sx;
+      du[ZX] = du[ZX] + om * Us[ZY * S3 + uc];
+      du[ZY] = du[ZY] - om * Us[ZX * S3 + uc];
+      if (A.g) {
+        const double* gs = A.g + (size_t)s * 3 * N3;
+        const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];
+        const double rho = Us[RHO * S3 + uc];
+        du[SX] = du[SX] + rho * gx;
+        du[SY] = du[SY] + rho * gy;
+        du[SZ] = du[SZ] + rho * gz;
+        du[EGAS] = du[EGAS] + ((sx * gx + sy * gy) + sz * gz);
+      }
+#pragma unroll
+      for (int k = 0; k < F; ++k) dU[k * N3 + c] = du[k];
+    }
+    if (tid == 0) {
+      double m = red[0];
+#pragma unroll
+      for (int w = 1; w < kThreads64 / 32; ++w) m = fmax(m, red[w]);
+      A.amax[s] = m;
+    }
+    __syncthreads();  // scratch and red reused by the next sub-grid
+  }
+  __syncthreads();
+  if (tid == 0) mbar_inval(&bar);
+}
+
+size_t step_fp64_smem_bytes() { return (size_t)F * S3 * sizeof(double); }
+
+cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(hydro_step_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_fp64_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  hydro_step_fp64_kernel<<<grid, kThreads64, step_fp64_smem_bytes(), st>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace hyd

@@ -1,0 +1,184 @@
+"""Thin Python binding of the C ABI in include/hydro.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls and takes torch CUDA
+tensors (float64, contiguous) for device buffers; the stream defaults to
+torch's current stream.  No step of the hydro method runs here: all of it runs
+in the CUDA library, and loading fails loudly when that library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import _build
+
+HYDRO_OK, HYDRO_EINVAL, HYDRO_ECUDA, HYDRO_ENOMEM, HYDRO_EUNSUP = 0, -1, -2, -3, -4
+HYDRO_ST_NONPHYS, HYDRO_ST_TIMEOUT = 0x1, 0x2
+HYDRO_PREC_FP64, HYDRO_PREC_MIXED = 0, 1
+HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
+
+EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydro_dt", "hydro_fill_ghosts_uniform",
+           "hydro_conserved_sums", "hydro_status", "hydro_strerror", "hydro_last_cuda_error", "hydro_destroy")
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = _lib()
+        msg = lib.hydro_strerror(code).decode()
+        if code == HYDRO_ECUDA:
+            msg += ": " + lib.hydro_last_cuda_error().decode()
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+class Layout(C.Structure):
+    _fields_ = [("N", C.c_int), ("ghost", C.c_int), ("n_species", C.c_int)]
+
+
+class Mode(C.Structure):
+    _fields_ = [("precision", C.c_int), ("cfl", C.c_double), ("de_eta1", C.c_double), ("de_eta2", C.c_double)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("n_sub", C.c_int), ("U", C.c_void_p), ("origin", C.c_void_p), ("h", C.c_void_p), ("g", C.c_void_p)]
+
+
+_L = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib(load: bool = True):
+    """Load the CUDA library.  It must have been built (``build()``); there is
+    no fallback."""
+    global _L
+    if _L is None and load:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(path)
+        vp, dp, ip = C.c_void_p, C.c_double, C.c_int
+        L.hydro_create.argtypes = [C.POINTER(Layout), dp, dp, C.POINTER(vp)]
+        L.hydro_set_mode.argtypes = [vp, C.POINTER(Mode)]
+        L.hydro_step.argtypes = [vp, C.POINTER(Batch), dp, vp, vp, vp]
+        L.hydro_update.argtypes = [vp, C.POINTER(Batch), vp, vp, dp, vp, ip, vp]
+        L.hydro_dt.argtypes = [vp, vp, vp, ip, dp, vp, vp]
+        L.hydro_fill_ghosts_uniform.argtypes = [vp, C.POINTER(Batch), ip, ip, ip, ip, vp]
+        L.hydro_conserved_sums.argtypes = [vp, C.POINTER(Batch), vp, vp]
+        L.hydro_status.argtypes = [vp, C.POINTER(C.c_uint32)]
+        L.hydro_strerror.argtypes = [ip]
+        L.hydro_strerror.restype = C.c_char_p
+        L.hydro_last_cuda_error.argtypes = []
+        L.hydro_last_cuda_error.restype = C.c_char_p
+        L.hydro_destroy.argtypes = [vp]
+        L.hydro_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy"):
+                getattr(L, name).restype = C.c_int
+        _L = L
+    return _L
+
+
+def _check(rc: int, where: str):
+    if rc != HYDRO_OK:
+        raise HydroError(rc, where)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "expects contiguous float64 CUDA tensors"
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def make_batch(U, origin, h, g=None) -> Batch:
+    n = U.shape[0]
+    return Batch(n, _ptr(U), _ptr(origin), _ptr(h), _ptr(g))
+
+
+class Context:
+    """Owns one hydro_ctx_t (a context per stream)."""
+
+    def __init__(self, gamma: float = 5.0 / 3.0, omega: float = 0.0, N: int = 8, ghost: int = 3, n_species: int = 1):
+        self.ptr = hydro_create(Layout(N, ghost, n_species), gamma, omega)
+        self.gamma, self.omega = gamma, omega
+
+    def close(self):
+        if self.ptr:
+            hydro_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- entry points (same names as the C ABI) ---------------------------------
+def hydro_create(layout: Layout, gamma: float, omega: float) -> int:
+    out = C.c_void_p()
+    _check(_lib().hydro_create(C.byref(layout), gamma, omega, C.byref(out)), "hydro_create")
+    return out.value
+
+
+def hydro_set_mode(ctx, precision=HYDRO_PREC_FP64, cfl=0.4, de_eta1=1e-3, de_eta2=0.1):
+    _check(_lib().hydro_set_mode(_cp(ctx), C.byref(Mode(precision, cfl, de_eta1, de_eta2))), "hydro_set_mode")
+
+
+def _cp(ctx):
+    return ctx.ptr if isinstance(ctx, Context) else ctx
+
+
+def hydro_step(ctx, batch: Batch, dt: float, dUdt, amax, stream=None):
+    _check(_lib().hydro_step(_cp(ctx), C.byref(batch), float(dt), _ptr(dUdt), _ptr(amax), _stream(stream)),
+           "hydro_step")
+
+
+def hydro_update(ctx, batch: Batch, U0, dUdt, dt: float = 0.0, dt_dev=None, stage: int = 0, stream=None):
+    _check(_lib().hydro_update(_cp(ctx), C.byref(batch), _ptr(U0), _ptr(dUdt), float(dt), _ptr(dt_dev), int(stage),
+                               _stream(stream)), "hydro_update")
+
+
+def hydro_dt(ctx, amax, h, n_sub: int, cfl: float, dt_out, stream=None):
+    _check(_lib().hydro_dt(_cp(ctx), _ptr(amax), _ptr(h), int(n_sub), float(cfl), _ptr(dt_out), _stream(stream)),
+           "hydro_dt")
+
+
+def hydro_fill_ghosts_uniform(ctx, batch: Batch, nbx: int, nby: int, nbz: int, bc: int, stream=None):
+    _check(_lib().hydro_fill_ghosts_uniform(_cp(ctx), C.byref(batch), nbx, nby, nbz, bc, _stream(stream)),
+           "hydro_fill_ghosts_uniform")
+
+
+def hydro_conserved_sums(ctx, batch: Batch, sums, stream=None):
+    _check(_lib().hydro_conserved_sums(_cp(ctx), C.byref(batch), _ptr(sums), _stream(stream)), "hydro_conserved_sums")
+
+
+def hydro_status(ctx) -> int:
+    v = C.c_uint32()
+    _check(_lib().hydro_status(_cp(ctx), C.byref(v)), "hydro_status")
+    return v.value
+
+
+def hydro_strerror(code: int) -> str:
+    return _lib().hydro_strerror(code).decode()
+
+
+def hydro_destroy(ctx):
+    _lib().hydro_destroy(_cp(ctx))
+
+
+def hydro_last_cuda_error() -> str:
+    return _lib().hydro_last_cuda_error().decode()
