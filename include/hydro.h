@@ -50,6 +50,7 @@ extern "C" {
 #define HYDRO_ECUDA (-2)    /* a CUDA call failed; hydro_last_cuda_error() has the text */
 #define HYDRO_ENOMEM (-3)   /* scratch allocation failed */
 #define HYDRO_EUNSUP (-4)   /* valid but unsupported configuration */
+#define HYDRO_ERANGE (-5)   /* batch larger than hydro_step_static's fixed scratch */
 
 /* ---- device status bits (hydro_status) --------------------------------- */
 #define HYDRO_ST_NONPHYS 0x1u  /* rho <= 0, eps <= 0 or NaN seen in a step */
@@ -148,6 +149,30 @@ int hydro_fill_ghosts_uniform(hydro_ctx_t* ctx, const hydro_batch_t* B, int nbx,
  * sums[F] = sum (x_c s_y - y_c s_x + z_z) h^3 (angular momentum about +z).
  * sums has F+1 device doubles.  Deterministic (fixed reduction order). */
 int hydro_conserved_sums(hydro_ctx_t* ctx, const hydro_batch_t* B, double* sums, void* stream);
+
+/* Allocation-free variant of hydro_step.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as a host
+ * code that gives all device memory to its own pool allocator, or a time
+ * loop that cannot afford the device-wide synchronisation an allocation may
+ * cause.  It computes exactly what hydro_step computes (FP64 mode only), with
+ * the same kernel, but takes its scratch from a fixed array compiled into
+ * the library: HYDRO_STATIC_MAX_SUB slots of 159,744 bytes (30.7 MB), held by
+ * every GPU that loads the library until the process exits.
+ *   - B->n_sub above HYDRO_STATIC_MAX_SUB returns HYDRO_ERANGE (split the
+ *     batch); n_sub == 0 is a no-op.  Other argument errors as hydro_step.
+ *   - status: optional device word (caller-owned); it is set to zero, then
+ *     receives this call's HYDRO_ST_* bits.  NULL: the bits go to an internal
+ *     word nobody reads.
+ *   - Calls allocate nothing (no cudaMalloc, no library allocation).  The
+ *     first call on a device, with that device current, loads the device
+ *     code and looks up the array's address; make that first call before any
+ *     stream capture.
+ *   - All calls share the array and leave their last contents in it; the
+ *     kernel overwrites whatever it later reads.  Calls whose kernels overlap
+ *     on the GPU (unordered streams) race on the array: order them. */
+#define HYDRO_STATIC_MAX_SUB 192
+int hydro_step_static(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax,
+                      uint32_t* status, void* stream);
 
 /* Device status bits accumulated since the last call (HYDRO_ST_*), then
  * cleared.  Synchronises nothing: call after the stream has been synchronised. */

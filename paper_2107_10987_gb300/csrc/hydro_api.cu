@@ -7,6 +7,7 @@
 
 #include "hydro.h"
 #include "hydro_common.cuh"
+#include "hydro_ctx.h"
 
 namespace hyd {
 cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st);
@@ -18,18 +19,6 @@ cudaError_t launch_sums(const double* U, const double* origin, const double* h, 
                         double* sums, cudaStream_t st);
 }  // namespace hyd
 
-struct hydro_ctx {
-  int N, G, n_species, F;
-  double gamma, omega;
-  hydro_mode_t mode;
-  int device;
-  int num_sms;
-  unsigned* status;      // device word
-  double* scratch;       // step scratch
-  size_t scratch_bytes;
-  double* part;          // conservation partials
-  size_t part_bytes;
-};
 
 static thread_local char g_cuda_err[256] = "no CUDA error";
 
@@ -197,6 +186,7 @@ const char* hydro_strerror(int code) {
     case HYDRO_ECUDA: return "CUDA error (see hydro_last_cuda_error)";
     case HYDRO_ENOMEM: return "device scratch allocation failed";
     case HYDRO_EUNSUP: return "unsupported configuration";
+    case HYDRO_ERANGE: return "batch larger than the fixed scratch of hydro_step_static (HYDRO_STATIC_MAX_SUB)";
     default: return "unknown error code";
   }
 }

@@ -14,13 +14,15 @@ import torch
 
 from . import _build
 
-HYDRO_OK, HYDRO_EINVAL, HYDRO_ECUDA, HYDRO_ENOMEM, HYDRO_EUNSUP = 0, -1, -2, -3, -4
+HYDRO_OK, HYDRO_EINVAL, HYDRO_ECUDA, HYDRO_ENOMEM, HYDRO_EUNSUP, HYDRO_ERANGE = 0, -1, -2, -3, -4, -5
+HYDRO_STATIC_MAX_SUB = 192
 HYDRO_ST_NONPHYS, HYDRO_ST_TIMEOUT = 0x1, 0x2
 HYDRO_PREC_FP64, HYDRO_PREC_MIXED = 0, 1
 HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
 
 EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydro_dt", "hydro_fill_ghosts_uniform",
-           "hydro_conserved_sums", "hydro_status", "hydro_strerror", "hydro_last_cuda_error", "hydro_destroy")
+           "hydro_conserved_sums", "hydro_status", "hydro_strerror", "hydro_last_cuda_error", "hydro_destroy",
+           "hydro_step_static")
 
 
 class HydroError(RuntimeError):
@@ -74,6 +76,7 @@ def _lib(load: bool = True):
         L.hydro_strerror.restype = C.c_char_p
         L.hydro_last_cuda_error.argtypes = []
         L.hydro_last_cuda_error.restype = C.c_char_p
+        L.hydro_step_static.argtypes = [vp, C.POINTER(Batch), dp, vp, vp, vp, vp]
         L.hydro_destroy.argtypes = [vp]
         L.hydro_destroy.restype = None
         for name in EXPORTS:
@@ -182,3 +185,14 @@ def hydro_destroy(ctx):
 
 def hydro_last_cuda_error() -> str:
     return _lib().hydro_last_cuda_error().decode()
+
+
+def hydro_step_static(ctx, batch: Batch, dt: float, dUdt, amax, status=None, stream=None):
+    """Allocation-free hydro_step (fixed scratch; at most HYDRO_STATIC_MAX_SUB sub-grids).
+    status: optional int32/uint32 CUDA tensor of one element receiving this call's bits."""
+    sp = None
+    if status is not None:
+        assert status.is_cuda and status.numel() >= 1 and status.element_size() == 4
+        sp = status.data_ptr()
+    _check(_lib().hydro_step_static(_cp(ctx), C.byref(batch), float(dt), _ptr(dUdt), _ptr(amax), sp,
+                                    _stream(stream)), "hydro_step_static")
