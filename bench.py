@@ -35,6 +35,7 @@ NB = 8  # 8^3 sub-grids
 N = 8
 CELLS = (NB * N) ** 3
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (an FMA counts as two flops)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 80.5: SMs x FP32 lanes x FMA x max clock
 
 
 def peaks():
@@ -109,9 +110,10 @@ class ClockSampler:
 # 15,552 point fluxes, face sums, divergence and sources.  Bytes: the padded
 # state read once and dU/dt written once.
 ALGO = {"fp64_flops_per_subgrid_stage": 6558794.0, "bytes_per_subgrid_stage": 260520}
-# DRAM bytes per hydro_step launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum), None until captured for the current kernel.
-TRAFFIC_PER_LAUNCH = None
+# DRAM bytes per hydro_step launch on this workload from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), per precision form; None
+# until captured for the current kernel.
+TRAFFIC_PER_LAUNCH = {"fp64": None, "mixed": None}
 
 
 def algorithmic_work():
@@ -133,19 +135,13 @@ def make_state(dev):
     return U, origin, hv, sub
 
 
-def gpu_arm(args):
+def run_form(args, H, dev, precision, flush):
+    """Warm-up, then K timed RK3 steps of one precision form; returns timings
+    and the final state."""
     import torch
-    import torch.distributed as dist
-    from paper_2107_10987_gb300 import hydro as H
-
-    ws, rk, lr = dist_env()
-    dev = torch.device("cuda", lr)
-    torch.cuda.set_device(dev)
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream()
     ctx = H.Context(GAMMA, 0.0)
-    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, 0.4)
+    H.hydro_set_mode(ctx, precision, 0.4)
     U, origin, hv, host_init = make_state(dev)
     n = U.shape[0]
     U0 = torch.empty_like(U)
@@ -153,8 +149,6 @@ def gpu_arm(args):
     am = torch.empty(n, dtype=torch.float64, device=dev)
     dt = torch.empty(1, dtype=torch.float64, device=dev)
     B = H.make_batch(U, origin, hv)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
-    launches_per_step = 10  # 3 x (ghost fill, step, update) + dt
 
     def rk3_step(step_events=None):
         U0.copy_(U)
@@ -172,29 +166,18 @@ def gpu_arm(args):
     for _ in range(args.warmup):
         rk3_step()
     torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(3)]
            for _ in range(args.steps)]
-    with ClockSampler(lr) as clk:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps (outside the events)
-            ev[i][0].record(stream)
-            rk3_step(kev[i])
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    kern_ms = [a.elapsed_time(b) for st in kev for a, b in st]
-    t_dev = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = t.item()
-    status = H.hydro_status(ctx)
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        ev[i][0].record(stream)
+        rk3_step(kev[i])
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    out = {"t_dev": sum(a.elapsed_time(b) for a, b in ev) / 1e3,
+           "kern_s": float(np.mean([a.elapsed_time(b) for st in kev for a, b in st])) / 1e3,
+           "status": H.hydro_status(ctx), "rho": U[:, 0, 3:-3, 3:-3, 3:-3].clone(), "n": n}
 
     # end to end: host (pinned) state in, one RK3 step, state back to the host
     host_U = torch.tensor(host_init).pin_memory()
@@ -212,42 +195,94 @@ def gpu_arm(args):
         host_out.copy_(U, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_e2e = e0.elapsed_time(e1) / 1e3
+    out["t_e2e"] = e0.elapsed_time(e1) / 1e3
+    out["bytes_step"] = host_U.numel() * 8
+    ctx.close()
+    return out
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2107_10987_gb300 import hydro as H
+
+    ws, rk, lr = dist_env()
+    dev = torch.device("cuda", lr)
+    torch.cuda.set_device(dev)
     if ws > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = t.item()
-    bytes_step = host_U.numel() * 8
+        dist.init_process_group("nccl", device_id=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    launches_per_step = 10  # 3 x (ghost fill, step, update) + dt
+    forms = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED}
+    order = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    res = {}
+    for name in order:
+        if ws > 1:
+            dist.barrier()
+        if name == order[-1]:
+            with ClockSampler(lr) as clk:
+                t0 = time.perf_counter()
+                res[name] = run_form(args, H, dev, forms[name], flush)
+                res[name]["wall"] = time.perf_counter() - t0
+            res[name]["clocks"] = clk.summary()
+        else:
+            res[name] = run_form(args, H, dev, forms[name], flush)
+        if ws > 1:
+            for key in ("t_dev", "t_e2e"):
+                t = torch.tensor([res[name][key]], dtype=torch.float64, device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                res[name][key] = t.item()
 
     if rk == 0:
         work = algorithmic_work()
-        kavg = float(np.mean(kern_ms)) / 1e3
-        flops = work["fp64_flops_per_subgrid_stage"] * n
-        achieved = flops / kavg / 1e12
-        bytes_launch = work["bytes_per_subgrid_stage"] * n
         pk = peaks()
+        head = order[-1]
+        r = res[head]
+        n = r["n"]
+        flops = work["fp64_flops_per_subgrid_stage"] * n
+        bytes_launch = work["bytes_per_subgrid_stage"] * n
+        peak = FP32_PEAK_TFLOPS if head == "mixed" else FP64_PEAK_TFLOPS
+        achieved = flops / r["kern_s"] / 1e12
         line = {
-            "metric": METRIC, "value": CELLS * args.steps * ws / t_dev, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "metric": METRIC, "value": CELLS * args.steps * ws / r["t_dev"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["t_dev"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed)" if head == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": "Sedov blast, uniform octree level of 512 sub-grids of 8^3 (64^3 on [-1,1]^3), "
                                    "outflow, 10 FP64 fields, one step = one full RK3 time step (3 stages)",
-                       "sub_grids": n, "cells": CELLS, "precision": "fp64 (plain)", "parallelism": f"replicas x{ws}",
+                       "sub_grids": n, "cells": CELLS,
+                       "precision": "mixed: FP32 reconstruction/fluxes, FP64 dual-energy recovery, accumulation "
+                                    "and update" if head == "mixed" else "fp64 (plain)",
+                       "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MB write) between timed steps, outside the timed events"},
-            "cell_stage_updates_per_s": 3 * CELLS * args.steps * ws / t_dev,
-            "wall_s_timed_region": wall,
-            "kernel_ms": {"hydro_step_fp64 (avg launch)": 1e3 * kavg},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": work.get("dram_bytes_per_launch_scaled"),
-                         "peak_source": "nominal GB300 FP64 from the profiling recipe (1.25 TFLOP/s)",
-                         "hbm_frac": (bytes_launch / kavg / 1e9) / pk["hbm_gbs"] if "hbm_gbs" in pk else None},
-            "e2e": {"value": CELLS * args.steps * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
-                    "d2h_bytes_per_step": bytes_step},
+            "cell_stage_updates_per_s": 3 * CELLS * args.steps * ws / r["t_dev"],
+            "wall_s_timed_region": r["wall"],
+            "kernel_ms": {f"hydro_step_{head} (avg launch)": 1e3 * r["kern_s"]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": work.get("dram_bytes_per_launch_scaled", {}).get(head),
+                         "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flops x 2070 MHz (profiling recipe units)"
+                                         if head == "mixed" else "nominal GB300 FP64 from the profiling recipe"),
+                         "flops_counted": "algorithmic ops of the method (oracle count), each op one flop",
+                         "hbm_frac": (bytes_launch / r["kern_s"] / 1e9) / pk["hbm_gbs"] if "hbm_gbs" in pk else None},
+            "e2e": {"value": CELLS * args.steps * ws / r["t_e2e"], "unit": UNIT,
+                    "h2d_bytes_per_step": r["bytes_step"], "d2h_bytes_per_step": r["bytes_step"]},
             "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk.summary(),
-            "device_status": status,
+            "clocks": r["clocks"],
+            "device_status": r["status"],
         }
+        if "fp64" in res and head != "fp64":
+            f = res["fp64"]
+            a64 = flops / f["kern_s"] / 1e12
+            line["plain_fp64"] = {
+                "value": CELLS * args.steps * ws / f["t_dev"], "ms_per_step": 1e3 * f["t_dev"] / args.steps,
+                "kernel_ms": 1e3 * f["kern_s"], "e2e": CELLS * args.steps * ws / f["t_e2e"],
+                "roofline": {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": a64 / FP64_PEAK_TFLOPS,
+                             "traffic": work.get("dram_bytes_per_launch_scaled", {}).get("fp64")}}
+            line["speedup_vs_plain_fp64"] = f["t_dev"] / r["t_dev"]
+            # both forms ran the same steps from the same state: density difference
+            d = (r["rho"] - f["rho"]).abs().max().item() / f["rho"].abs().max().item()
+            line["max_rel_density_diff_vs_fp64"] = d
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -320,6 +355,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
+                    help="both: time the plain FP64 form, then the mixed form (reported as value)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

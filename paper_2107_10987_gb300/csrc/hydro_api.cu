@@ -11,6 +11,7 @@
 
 namespace hyd {
 cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st);
+cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st);
 cudaError_t launch_update(double* U, const double* U0, const double* dUdt, double dt, const double* dt_dev,
                           int stage, double eta2, double gamma, long n_sub, int num_sms, cudaStream_t st);
 cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, double* out, cudaStream_t st);
@@ -98,10 +99,13 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   if (B->n_sub == 0) return HYDRO_OK;
   if (!B->U || !B->origin || !B->h || !dUdt || !amax) return HYDRO_EINVAL;
   if (!aligned16(B->U) || !aligned16(dUdt)) return HYDRO_EINVAL;
-  if (c->mode.precision != HYDRO_PREC_FP64) return HYDRO_EUNSUP;
+  const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
   int rc = ensure_status(c);
   if (rc) return rc;
-  const int grid = B->n_sub < c->num_sms ? B->n_sub : c->num_sms;
+  // persistent CTAs: one per SM for FP64 (219 KB of shared memory each), two
+  // per SM in mixed precision (110 KB each)
+  const int slots = mixed ? 2 * c->num_sms : c->num_sms;
+  const int grid = B->n_sub < slots ? B->n_sub : slots;
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
@@ -119,7 +123,8 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   A.P.gm1 = c->gamma - 1.0;
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
-  cudaError_t e = hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
+  cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, (cudaStream_t)stream)
+                        : hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
   return HYDRO_OK;
 }
