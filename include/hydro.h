@@ -123,15 +123,21 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
  * ENOMEM, ECUDA.  n_sub == 0 is a no-op. */
 int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, void* stream);
 
-/* SSP-RK3 stage update of the interior cells, in place on B->U (ghosts are
- * not touched):  U <- alpha_k U0 + beta_k (U + dt dUdt) with
- * (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3) for stage k = 0, 1, 2; then the
- * tracer resync tau <- eps_E^(1/gamma) where eps_E = E - |s|^2/(2 rho) exceeds
- * de_eta2 * E.  U0 has U's padded layout (only its interior is read).  The
- * time step is *dt_dev (a device scalar, e.g. from hydro_dt) when dt_dev is
- * not NULL, else dt.  Errors: EINVAL (stage outside 0..2, NULL pointers). */
+/* SSP-RK3 stage update of the interior cells (ghosts are not touched):
+ *   U_new <- alpha_k U0 + beta_k (U + dt dUdt), (alpha, beta) = (0,1), (3/4,1/4),
+ *   (1/3,2/3) for stage k = 0, 1, 2; then the tracer resync
+ *   tau <- eps_E^(1/gamma) where eps_E = E - |s|^2/(2 rho) exceeds de_eta2 * E.
+ * U is B->U.  U_out == NULL: in place on B->U.  Otherwise U_new goes to the
+ * interior of U_out (U's padded layout; must not overlap B->U) and B->U is
+ * only read, which lets a caller keep the step's initial state without a
+ * copy (stage 0 with U0 == B->U writing another buffer).  U0 has U's padded
+ * layout (only its interior is read) and may equal B->U.  The time step is
+ * *dt_dev (a device scalar, e.g. from hydro_dt) when dt_dev is not NULL,
+ * else dt.  FP64 mode: the FP64 oracle's rounding exactly (tau to the
+ * library pow's ulps); mixed mode: FMA and an FP32 tracer power.
+ * Errors: EINVAL (stage outside 0..2, NULL pointers, overlapping U_out). */
 int hydro_update(hydro_ctx_t* ctx, const hydro_batch_t* B, const double* U0, const double* dUdt, double dt,
-                 const double* dt_dev, int stage, void* stream);
+                 const double* dt_dev, int stage, double* U_out, void* stream);
 
 /* CFL time step on the device: *dt_out = cfl * min_s h[s] / amax[s] (cfl <= 0
  * uses the context's mode).  One launch, no host synchronisation. */
@@ -177,6 +183,47 @@ int hydro_conserved_sums(hydro_ctx_t* ctx, const hydro_batch_t* B, double* sums,
 #define HYDRO_STATIC_MAX_SUB 192
 int hydro_step_static(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax,
                       uint32_t* status, void* stream);
+
+/* ---- a whole RK3 time step of a uniform mesh, and its CUDA graphs -------
+ * One time step (three hydro iterations, Sec. IV-A.2) of a uniform mesh of
+ * nbx x nby x nbz sub-grids, state X -> Y:
+ *   ghost(X); step(X); dt = cfl min h/amax; Y = X + dt dU      (stage 0)
+ *   ghost(Y); step(Y); Y = 3/4 X + 1/4 (Y + dt dU)              (stage 1)
+ *   ghost(Y); step(Y); Y = 1/3 X + 2/3 (Y + dt dU)              (stage 2)
+ * X and Y are the two state buffers a.U and U_b; the step's initial state is
+ * kept in X without a copy and the following step runs Y -> X.
+ * dUdt, amax, dt: caller-owned work buffers; *dt holds the step's dt after
+ * the step.  All device pointers. */
+typedef struct {
+  hydro_batch_t a;  /* buffer a: state, origin, h, g (shared by both buffers) */
+  double* U_b;      /* buffer b: same layout as a.U, distinct memory */
+  int nbx, nby, nbz, bc;
+  double* dUdt;     /* [n_sub][F][N][N][N] */
+  double* amax;     /* [n_sub] */
+  double* dt;       /* one device double */
+  double cfl;       /* <= 0: the context's mode */
+} hydro_rk3_desc_t;
+
+typedef struct hydro_graph hydro_graph_t;
+
+/* Enqueue one time step on a stream: parity 0 advances a -> b, 1 advances
+ * b -> a.  Ten launches.  Errors: EINVAL (inconsistent descriptor). */
+int hydro_rk3_step_uniform(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
+
+/* Capture the two directions of hydro_rk3_step_uniform once into CUDA graphs
+ * (allocating the context's scratch beforehand, so replays allocate nothing).
+ * The state starts in buffer a.  The descriptor's buffers must stay valid
+ * and unchanged in address while the graph exists. */
+int hydro_rk3_graph_create(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, hydro_graph_t** out);
+
+/* Replay one time step on a stream (alternating a -> b and b -> a). */
+int hydro_rk3_graph_launch(hydro_graph_t* g, void* stream);
+
+/* Which buffer holds the current state: 0 = a, 1 = b. */
+int hydro_rk3_graph_state(const hydro_graph_t* g);
+
+/* Release the graphs (after their replays have completed). */
+void hydro_rk3_graph_destroy(hydro_graph_t* g);
 
 /* Device status bits accumulated since the last call (HYDRO_ST_*), then
  * cleared.  Synchronises nothing: call after the stream has been synchronised. */

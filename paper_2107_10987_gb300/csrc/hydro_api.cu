@@ -12,8 +12,11 @@
 namespace hyd {
 cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st);
 cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st);
-cudaError_t launch_update(double* U, const double* U0, const double* dUdt, double dt, const double* dt_dev,
-                          int stage, double eta2, double gamma, long n_sub, int num_sms, cudaStream_t st);
+cudaError_t prepare_step_fp64();
+cudaError_t prepare_step_mixed();
+cudaError_t launch_update(const double* U, double* Uout, const double* U0, const double* dUdt, double dt,
+                          const double* dt_dev, int stage, double eta2, double gamma, int n_sub, bool mixed,
+                          int num_sms, cudaStream_t st);
 cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, double* out, cudaStream_t st);
 cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st);
 cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
@@ -50,6 +53,26 @@ static int ensure_buf(double** buf, size_t* have, size_t need, const char* what)
     return HYDRO_ENOMEM;
   }
   *have = need;
+  return HYDRO_OK;
+}
+
+static int step_slots(const hydro_ctx* c, bool mixed) {
+  // persistent CTAs: one per SM for FP64 (219 KB of shared memory each), two
+  // per SM in mixed precision (110 KB each)
+  return mixed ? 2 * c->num_sms : c->num_sms;
+}
+
+int hydro_ctx_prepare(hydro_ctx* c, int n_sub) {
+  int rc = ensure_status(c);
+  if (rc) return rc;
+  const int slots = step_slots(c, true) > step_slots(c, false) ? step_slots(c, true) : step_slots(c, false);
+  const int grid = n_sub < slots ? n_sub : slots;
+  rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
+                  "cudaMalloc(step scratch)");
+  if (rc) return rc;
+  cudaError_t e = hyd::prepare_step_fp64();
+  if (e == cudaSuccess) e = hyd::prepare_step_mixed();
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_ctx_prepare");
   return HYDRO_OK;
 }
 
@@ -102,9 +125,7 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
   int rc = ensure_status(c);
   if (rc) return rc;
-  // persistent CTAs: one per SM for FP64 (219 KB of shared memory each), two
-  // per SM in mixed precision (110 KB each)
-  const int slots = mixed ? 2 * c->num_sms : c->num_sms;
+  const int slots = step_slots(c, mixed);
   const int grid = B->n_sub < slots ? B->n_sub : slots;
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
@@ -130,14 +151,21 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
 }
 
 int hydro_update(hydro_ctx_t* c, const hydro_batch_t* B, const double* U0, const double* dUdt, double dt,
-                 const double* dt_dev, int stage, void* stream) {
+                 const double* dt_dev, int stage, double* U_out, void* stream) {
   if (!c || !B) return HYDRO_EINVAL;
   if (stage < 0 || stage > 2 || B->n_sub < 0) return HYDRO_EINVAL;
   if (!dt_dev && (!std::isfinite(dt) || dt < 0.0)) return HYDRO_EINVAL;
   if (B->n_sub == 0) return HYDRO_OK;
   if (!B->U || !U0 || !dUdt) return HYDRO_EINVAL;
-  cudaError_t e = hyd::launch_update(B->U, U0, dUdt, dt, dt_dev, stage, c->mode.de_eta2, c->gamma, B->n_sub,
-                                     c->num_sms, (cudaStream_t)stream);
+  double* out = U_out ? U_out : B->U;
+  if (out != B->U) {
+    // out of place: the two state buffers may not overlap
+    const size_t bytes = (size_t)B->n_sub * hyd::F * hyd::S3 * sizeof(double);
+    const char *a = (const char*)B->U, *b = (const char*)out;
+    if (a < b + bytes && b < a + bytes) return HYDRO_EINVAL;
+  }
+  cudaError_t e = hyd::launch_update(B->U, out, U0, dUdt, dt, dt_dev, stage, c->mode.de_eta2, c->gamma, B->n_sub,
+                                     c->mode.precision == HYDRO_PREC_MIXED, c->num_sms, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_update");
   return HYDRO_OK;
 }

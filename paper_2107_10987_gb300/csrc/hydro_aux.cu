@@ -11,50 +11,74 @@ namespace hyd {
 //   U <- alpha U0 + beta (U + dt dU/dt), (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3)
 //   then tau <- eps_E^(1/gamma) where eps_E = E - |s|^2/(2 rho) > eta2 E
 //   (tracer resync of the dual-energy formalism, Bryan et al. 1995).
-// Explicitly rounded operations: the same values as the FP64 oracle.
+// FP64 form: explicitly rounded operations, the same values as the FP64
+// oracle.  Mixed form: the update and eps_E stay FP64 (FMA allowed, 1/rho
+// from an FP32 reciprocal refined by a Newton step), the tracer power is
+// taken in FP32 like the rest of the tracer's arithmetic in that form.
+// Out of place when Uout != U (the interior of Uout is written, U untouched).
 struct UpdateArgs {
-  double* U;
+  const double* U;
+  double* Uout;
   const double* U0;
   const double* dUdt;
   const double* dt_dev;
   double dt;
   double alpha, beta, eta2, inv_gamma;
-  long n_cells;  // n_sub * N3
+  int n_sub;
 };
 
+template <bool kMixed>
 __global__ void __launch_bounds__(256) hydro_update_kernel(UpdateArgs A) {
   const double dt = A.dt_dev ? *A.dt_dev : A.dt;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n_cells; i += (long)gridDim.x * blockDim.x) {
-    const long s = i / N3;
-    const int c = (int)(i % N3);
-    const int x = c % N, y = (c / N) % N, z = c / (N * N);
-    const long uc = (size_t)s * F * S3 + ((z + G) * S + (y + G)) * S + (x + G);
-    const long dc = (size_t)s * F * N3 + c;
-    double u[F];
+  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
+    const size_t ub = (size_t)s * F * S3, db = (size_t)s * F * N3;
+    for (int c = threadIdx.x; c < N3; c += blockDim.x) {
+      const int x = c & (N - 1), y = (c >> 3) & (N - 1), z = c >> 6;
+      const size_t uc = ub + ((z + G) * S + (y + G)) * S + (x + G);
+      const size_t dc = db + c;
+      double u[F];
 #pragma unroll
-    for (int k = 0; k < F; ++k) {
-      const double t = radd(A.U[uc + (long)k * S3], rmul(dt, A.dUdt[dc + (long)k * N3]));
-      u[k] = radd(rmul(A.alpha, A.U0[uc + (long)k * S3]), rmul(A.beta, t));
+      for (int k = 0; k < F; ++k) {
+        const double U = A.U[uc + (size_t)k * S3], U0 = A.U0[uc + (size_t)k * S3];
+        const double R = A.dUdt[dc + (size_t)k * N3];
+        if (kMixed) {
+          u[k] = fma(A.alpha, U0, A.beta * fma(dt, R, U));
+        } else {
+          const double t = radd(U, rmul(dt, R));
+          u[k] = radd(rmul(A.alpha, U0), rmul(A.beta, t));
+        }
+      }
+      const double rho = u[RHO];
+      if (kMixed) {
+        const double r0 = (double)__frcp_rn((float)rho);
+        const double ri = r0 * fma(-rho, r0, 2.0);
+        const double s2 = fma(u[SZ], u[SZ], fma(u[SY], u[SY], u[SX] * u[SX]));
+        const double eE = u[EGAS] - 0.5 * s2 * ri;
+        if (eE > A.eta2 * u[EGAS]) u[TAU] = (double)__powf((float)eE, (float)A.inv_gamma);
+      } else {
+        const double vx = u[SX] / rho, vy = u[SY] / rho, vz = u[SZ] / rho;
+        const double ek = rmul(rmul(0.5, rho), radd(radd(rmul(vx, vx), rmul(vy, vy)), rmul(vz, vz)));
+        const double eE = rsub(u[EGAS], ek);
+        if (eE > rmul(A.eta2, u[EGAS])) u[TAU] = pow(eE, A.inv_gamma);
+      }
+#pragma unroll
+      for (int k = 0; k < F; ++k) A.Uout[uc + (size_t)k * S3] = u[k];
     }
-    const double rho = u[RHO];
-    const double vx = u[SX] / rho, vy = u[SY] / rho, vz = u[SZ] / rho;
-    const double ek = rmul(rmul(0.5, rho), radd(radd(rmul(vx, vx), rmul(vy, vy)), rmul(vz, vz)));
-    const double eE = rsub(u[EGAS], ek);
-    if (eE > rmul(A.eta2, u[EGAS])) u[TAU] = pow(eE, A.inv_gamma);
-#pragma unroll
-    for (int k = 0; k < F; ++k) A.U[uc + (long)k * S3] = u[k];
   }
 }
 
-cudaError_t launch_update(double* U, const double* U0, const double* dUdt, double dt, const double* dt_dev,
-                          int stage, double eta2, double gamma, long n_sub, int num_sms, cudaStream_t st) {
+cudaError_t launch_update(const double* U, double* Uout, const double* U0, const double* dUdt, double dt,
+                          const double* dt_dev, int stage, double eta2, double gamma, int n_sub, bool mixed,
+                          int num_sms, cudaStream_t st) {
   static const double alpha[3] = {0.0, 0.75, 1.0 / 3.0};
   static const double beta[3] = {1.0, 0.25, 2.0 / 3.0};
-  UpdateArgs A{U, U0, dUdt, dt_dev, dt, alpha[stage], beta[stage], eta2, 1.0 / gamma, n_sub * N3};
-  long blocks = (A.n_cells + 255) / 256;
-  const long cap = (long)num_sms * 8;
-  if (blocks > cap) blocks = cap;
-  hydro_update_kernel<<<(int)blocks, 256, 0, st>>>(A);
+  UpdateArgs A{U, Uout, U0, dUdt, dt_dev, dt, alpha[stage], beta[stage], eta2, 1.0 / gamma, n_sub};
+  const int cap = num_sms * 8;
+  const int blocks = n_sub < cap ? n_sub : cap;
+  if (mixed)
+    hydro_update_kernel<true><<<blocks, 256, 0, st>>>(A);
+  else
+    hydro_update_kernel<false><<<blocks, 256, 0, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -85,41 +109,42 @@ cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, do
 // ---------------------------------------------------------------------------
 // Uniform-mesh ghost fill: a ghost cell copies the cell at the same global
 // position; outside the domain the position wraps (periodic) or is clamped
-// to the nearest interior cell (outflow, zero gradient).
+// to the nearest interior cell (outflow, zero gradient).  One block per
+// sub-grid, one thread per ghost cell (all ten fields).
 struct GhostArgs {
   double* U;
-  int nbx, nby, nbz, bc;
-  long n_items;  // n_sub * F * S3
+  int nbx, nby, nbz, bc, n_sub;
 };
 
 __device__ __forceinline__ int bc_map(int gpos, int n, int bc) {
-  if (bc == 0) return ((gpos % n) + n) % n;
+  if (bc == 0) return gpos < 0 ? gpos + n : (gpos >= n ? gpos - n : gpos);  // |offset| <= G < n
   return gpos < 0 ? 0 : (gpos >= n ? n - 1 : gpos);
 }
 
 __global__ void __launch_bounds__(256) hydro_ghost_uniform_kernel(GhostArgs A) {
   const int nx = A.nbx * N, ny = A.nby * N, nz = A.nbz * N;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n_items; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % S3);
-    const long sk = i / S3;  // s * F + k
-    const int k = (int)(sk % F);
-    const long s = sk / F;
-    const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
-    if (lx >= 0 && lx < N && ly >= 0 && ly < N && lz >= 0 && lz < N) continue;
-    const int kx = (int)(s % A.nbx), ky = (int)((s / A.nbx) % A.nby), kz = (int)(s / ((long)A.nbx * A.nby));
-    const int gx = bc_map(kx * N + lx, nx, A.bc), gy = bc_map(ky * N + ly, ny, A.bc), gz = bc_map(kz * N + lz, nz, A.bc);
-    const long os = ((long)(gz / N) * A.nby + (gy / N)) * A.nbx + (gx / N);
-    const int oc = ((gz % N + G) * S + (gy % N + G)) * S + (gx % N + G);
-    A.U[i] = A.U[(os * F + k) * S3 + oc];
+  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
+    const int kx = s % A.nbx, ky = (s / A.nbx) % A.nby, kz = s / (A.nbx * A.nby);
+    double* dst = A.U + (size_t)s * F * S3;
+    for (int c = threadIdx.x; c < S3; c += blockDim.x) {
+      const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
+      if ((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N) continue;
+      const int gx = bc_map(kx * N + lx, nx, A.bc), gy = bc_map(ky * N + ly, ny, A.bc);
+      const int gz = bc_map(kz * N + lz, nz, A.bc);
+      const int os = ((gz >> 3) * A.nby + (gy >> 3)) * A.nbx + (gx >> 3);
+      const int oc = (((gz & 7) + G) * S + ((gy & 7) + G)) * S + ((gx & 7) + G);
+      const double* src = A.U + (size_t)os * F * S3 + oc;
+#pragma unroll
+      for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c] = src[(size_t)k * S3];
+    }
   }
 }
 
 cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st) {
-  GhostArgs A{U, nbx, nby, nbz, bc, (long)nbx * nby * nbz * F * S3};
-  long blocks = (A.n_items + 255) / 256;
-  const long cap = (long)num_sms * 16;
-  if (blocks > cap) blocks = cap;
-  hydro_ghost_uniform_kernel<<<(int)blocks, 256, 0, st>>>(A);
+  const int n_sub = nbx * nby * nbz;
+  GhostArgs A{U, nbx, nby, nbz, bc, n_sub};
+  const int cap = num_sms * 8;
+  hydro_ghost_uniform_kernel<<<n_sub < cap ? n_sub : cap, 256, 0, st>>>(A);
   return cudaGetLastError();
 }
 

@@ -16,3 +16,8 @@ struct hydro_ctx {
   double* part;          // conservation partials
   size_t part_bytes;
 };
+
+// Allocate the context's status word and the step scratch for a batch of
+// n_sub sub-grids, and opt the step kernels in to their shared memory, so
+// that later launches allocate nothing (needed before a stream capture).
+int hydro_ctx_prepare(hydro_ctx* c, int n_sub);

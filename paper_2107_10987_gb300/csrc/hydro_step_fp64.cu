@@ -321,7 +321,9 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
 
 size_t step_fp64_smem_bytes() { return (size_t)F * S3 * sizeof(double); }
 
-cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {
+// Opt in to the kernel's dynamic shared memory once per process (no
+// allocation; call before any stream capture).
+cudaError_t prepare_step_fp64() {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(hydro_step_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -329,6 +331,12 @@ cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {
+  cudaError_t e = prepare_step_fp64();
+  if (e != cudaSuccess) return e;
   hydro_step_fp64_kernel<<<grid, kThreads64, step_fp64_smem_bytes(), st>>>(A);
   return cudaGetLastError();
 }

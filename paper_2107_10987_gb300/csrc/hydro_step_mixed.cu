@@ -277,7 +277,9 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
 
 size_t step_mixed_smem_bytes() { return (size_t)F * S3 * sizeof(float); }
 
-cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st) {
+// Opt in to the kernel's dynamic shared memory once per process (no
+// allocation; call before any stream capture).
+cudaError_t prepare_step_mixed() {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(hydro_step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -285,6 +287,12 @@ cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st) {
+  cudaError_t e = prepare_step_mixed();
+  if (e != cudaSuccess) return e;
   hydro_step_mixed_kernel<<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   return cudaGetLastError();
 }

@@ -22,7 +22,8 @@ HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
 
 EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydro_dt", "hydro_fill_ghosts_uniform",
            "hydro_conserved_sums", "hydro_status", "hydro_strerror", "hydro_last_cuda_error", "hydro_destroy",
-           "hydro_step_static")
+           "hydro_step_static", "hydro_rk3_step_uniform", "hydro_rk3_graph_create", "hydro_rk3_graph_launch",
+           "hydro_rk3_graph_state", "hydro_rk3_graph_destroy")
 
 
 class HydroError(RuntimeError):
@@ -47,6 +48,11 @@ class Batch(C.Structure):
     _fields_ = [("n_sub", C.c_int), ("U", C.c_void_p), ("origin", C.c_void_p), ("h", C.c_void_p), ("g", C.c_void_p)]
 
 
+class RK3Desc(C.Structure):
+    _fields_ = [("a", Batch), ("U_b", C.c_void_p), ("nbx", C.c_int), ("nby", C.c_int), ("nbz", C.c_int),
+                ("bc", C.c_int), ("dUdt", C.c_void_p), ("amax", C.c_void_p), ("dt", C.c_void_p), ("cfl", C.c_double)]
+
+
 _L = None
 
 
@@ -67,7 +73,7 @@ def _lib(load: bool = True):
         L.hydro_create.argtypes = [C.POINTER(Layout), dp, dp, C.POINTER(vp)]
         L.hydro_set_mode.argtypes = [vp, C.POINTER(Mode)]
         L.hydro_step.argtypes = [vp, C.POINTER(Batch), dp, vp, vp, vp]
-        L.hydro_update.argtypes = [vp, C.POINTER(Batch), vp, vp, dp, vp, ip, vp]
+        L.hydro_update.argtypes = [vp, C.POINTER(Batch), vp, vp, dp, vp, ip, vp, vp]
         L.hydro_dt.argtypes = [vp, vp, vp, ip, dp, vp, vp]
         L.hydro_fill_ghosts_uniform.argtypes = [vp, C.POINTER(Batch), ip, ip, ip, ip, vp]
         L.hydro_conserved_sums.argtypes = [vp, C.POINTER(Batch), vp, vp]
@@ -79,8 +85,13 @@ def _lib(load: bool = True):
         L.hydro_step_static.argtypes = [vp, C.POINTER(Batch), dp, vp, vp, vp, vp]
         L.hydro_destroy.argtypes = [vp]
         L.hydro_destroy.restype = None
+        L.hydro_rk3_step_uniform.argtypes = [vp, C.POINTER(RK3Desc), ip, vp]
+        L.hydro_rk3_graph_create.argtypes = [vp, C.POINTER(RK3Desc), C.POINTER(vp)]
+        L.hydro_rk3_graph_launch.argtypes = [vp, vp]
+        L.hydro_rk3_graph_state.argtypes = [vp]
+        L.hydro_rk3_graph_destroy.argtypes = [vp]
         for name in EXPORTS:
-            if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy"):
+            if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy", "hydro_rk3_graph_destroy"):
                 getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -150,9 +161,10 @@ def hydro_step(ctx, batch: Batch, dt: float, dUdt, amax, stream=None):
            "hydro_step")
 
 
-def hydro_update(ctx, batch: Batch, U0, dUdt, dt: float = 0.0, dt_dev=None, stage: int = 0, stream=None):
+def hydro_update(ctx, batch: Batch, U0, dUdt, dt: float = 0.0, dt_dev=None, stage: int = 0, U_out=None,
+                 stream=None):
     _check(_lib().hydro_update(_cp(ctx), C.byref(batch), _ptr(U0), _ptr(dUdt), float(dt), _ptr(dt_dev), int(stage),
-                               _stream(stream)), "hydro_update")
+                               _ptr(U_out), _stream(stream)), "hydro_update")
 
 
 def hydro_dt(ctx, amax, h, n_sub: int, cfl: float, dt_out, stream=None):
@@ -196,3 +208,32 @@ def hydro_step_static(ctx, batch: Batch, dt: float, dUdt, amax, status=None, str
         sp = status.data_ptr()
     _check(_lib().hydro_step_static(_cp(ctx), C.byref(batch), float(dt), _ptr(dUdt), _ptr(amax), sp,
                                     _stream(stream)), "hydro_step_static")
+
+
+def make_rk3_desc(Ua, Ub, origin, h, nb, bc, dUdt, amax, dt, cfl=0.4, g=None) -> RK3Desc:
+    """Descriptor of one RK3 time step of a uniform mesh of nb = (nbx, nby, nbz) sub-grids."""
+    return RK3Desc(make_batch(Ua, origin, h, g), _ptr(Ub), nb[0], nb[1], nb[2], bc, _ptr(dUdt), _ptr(amax), _ptr(dt),
+                   float(cfl))
+
+
+def hydro_rk3_step_uniform(ctx, desc: RK3Desc, parity: int, stream=None):
+    _check(_lib().hydro_rk3_step_uniform(_cp(ctx), C.byref(desc), int(parity), _stream(stream)),
+           "hydro_rk3_step_uniform")
+
+
+def hydro_rk3_graph_create(ctx, desc: RK3Desc) -> int:
+    out = C.c_void_p()
+    _check(_lib().hydro_rk3_graph_create(_cp(ctx), C.byref(desc), C.byref(out)), "hydro_rk3_graph_create")
+    return out.value
+
+
+def hydro_rk3_graph_launch(graph: int, stream=None):
+    _check(_lib().hydro_rk3_graph_launch(graph, _stream(stream)), "hydro_rk3_graph_launch")
+
+
+def hydro_rk3_graph_state(graph: int) -> int:
+    return _lib().hydro_rk3_graph_state(graph)
+
+
+def hydro_rk3_graph_destroy(graph: int):
+    _lib().hydro_rk3_graph_destroy(graph)
