@@ -225,6 +225,56 @@ int hydro_rk3_graph_state(const hydro_graph_t* g);
 /* Release the graphs (after their replays have completed). */
 void hydro_rk3_graph_destroy(hydro_graph_t* g);
 
+/* ---- learned smoothness indicator ------------------------------------------
+ * A small network (54 -> 32 ReLU -> 32 ReLU -> 1 sigmoid; BF16 parameters,
+ * FP32 arithmetic) predicts per cell whether the PPM limiter would change any
+ * reconstructed value on the lines through the cell.  In mixed precision with
+ * the indicator on, cells predicted smooth use the unlimited interface
+ * formula 7/12 (q0 + q1) - 1/12 (q-1 + q2) for every field but the spin
+ * (always limited); the rest use the full limited reconstruction (its
+ * fallback).  A cell counts as smooth only if every cell of its 3x3x3 block
+ * is predicted smooth (the PPM stencils reach two cells out).  Not in the
+ * paper: the paper's PPM always
+ * limits (Sec. III-B); the indicator is this library's extension.
+ * Parameters are packed as W1[32][54], b1[32], W2[32][32], b2[32], w3[32], b3
+ * (2849 floats, HYDRO_GATE_NPARAM). */
+#define HYDRO_GATE_NPARAM 2849
+#define HYDRO_GATE_NIN 54
+
+/* Training data from the method itself, per interior cell of every sub-grid
+ * (ghosts filled): X [n_sub*N^3][54] features (density then pressure over the
+ * 3x3x3 neighbourhood, (q_k - q_c)/(|q_k| + |q_c|)), y [n_sub*N^3] labels
+ * (1 where, on one of the 13 lines and for density, velocity, internal energy,
+ * tracer or species, the limited interface pair differs from the unlimited
+ * one by more than 1e-4 of the field's scale at the cell -- |q0|, or |v| + c
+ * for velocities; FP32 reconstruction).  Either output may be NULL. */
+int hydro_gate_data(hydro_ctx_t* ctx, const hydro_batch_t* B, float* X, uint8_t* y, void* stream);
+
+/* Network output (sigmoid) for n samples X [n][54]. */
+int hydro_mlp_forward(const float* params, const float* X, int n, float* out, void* stream);
+
+/* Bytes of work buffer hydro_mlp_loss_grad needs for n samples. */
+size_t hydro_mlp_work_bytes(int n);
+
+/* Mean class-weighted binary cross-entropy
+ *   L = -mean( w1 y log(out) + w0 (1 - y) log(1 - out) )
+ * and its gradient with respect to the FP32 parameters (the forward and
+ * backward passes use them rounded to BF16).  grad [HYDRO_GATE_NPARAM],
+ * loss (one float, nullable); deterministic (fixed reduction order). */
+int hydro_mlp_loss_grad(const float* params, const float* X, const float* y, int n, float w1, float w0, float* grad,
+                        float* loss, void* work, size_t work_bytes, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step count t >= 1. */
+int hydro_mlp_adam(float* params, float* m, float* v, const float* grad, int t, float lr, void* stream);
+
+/* Turn the indicator on for this context's mixed-precision steps (params:
+ * device FP32 parameters, rounded to BF16 here; cells with output below
+ * threshold in (0,1) are predicted smooth), or off (params == NULL).  The
+ * rounded parameters live in the library's constant memory: one indicator
+ * per process and device at a time.  Synchronises the stream once (it reads
+ * the network's decision for a uniform neighbourhood back to the host). */
+int hydro_set_indicator(hydro_ctx_t* ctx, const float* params, double threshold, void* stream);
+
 /* Device status bits accumulated since the last call (HYDRO_ST_*), then
  * cleared.  Synchronises nothing: call after the stream has been synchronised. */
 int hydro_status(hydro_ctx_t* ctx, uint32_t* flags);

@@ -58,6 +58,8 @@ def lib():
         dp = C.POINTER(C.c_double)
         l.orc_step.argtypes = [C.POINTER(_P), C.c_int, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_uint8), C.c_int]
         l.orc_step.restype = C.c_int
+        l.orc_step_masked.argtypes = [C.POINTER(_P), C.c_int, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_uint8), C.c_int]
+        l.orc_step_masked.restype = C.c_int
         l.orc_update.argtypes = [C.POINTER(_P), C.c_int, dp, dp, dp, C.c_double, C.c_int]
         l.orc_update.restype = C.c_int
         l.orc_primitives.argtypes = [C.POINTER(_P), dp, dp]
@@ -99,6 +101,29 @@ def step(P: OracleParams, U: np.ndarray, origin: np.ndarray, h: np.ndarray, g: n
     if rc != 0:
         raise ValueError("orc_step rejected its arguments")
     return dU, am, fl
+
+
+def step_masked(P: OracleParams, U: np.ndarray, origin, h, smooth: np.ndarray, g=None, nthreads: int = 0):
+    """step() where cells with smooth[s][z][y][x] != 0 (padded S^3 layout) use the
+    unlimited 4-point interface formula on their lines."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    n = U.shape[0]
+    N = P.N
+    origin = np.ascontiguousarray(np.broadcast_to(origin, (n, 3)), dtype=np.float64)
+    h = np.ascontiguousarray(np.broadcast_to(h, (n,)), dtype=np.float64)
+    sm = np.ascontiguousarray(smooth, dtype=np.uint8)
+    assert sm.size == n * (N + 2 * P.G) ** 3
+    dU = np.zeros((n, P.nf, N, N, N))
+    am = np.zeros(n)
+    gp = None
+    if g is not None:
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        gp = _dp(g)
+    rc = lib().orc_step_masked(C.byref(P.c()), n, _dp(U), _dp(origin), _dp(h), gp, _dp(dU), _dp(am),
+                               sm.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
+    if rc != 0:
+        raise ValueError("orc_step_masked rejected its arguments")
+    return dU, am
 
 
 def update(P: OracleParams, U: np.ndarray, U0: np.ndarray, dUdt: np.ndarray, dt: float, stage: int) -> np.ndarray:

@@ -123,11 +123,11 @@ void primitives(const Params& P, const T* u, T* q) {
 // then the monotonicity fix-ups, in this order: local extremum -> flatten;
 // overshoot towards -d -> qm = 3q0-2qp; overshoot towards +d -> qp = 3q0-2qm.
 // Contact steepening is off (optional in the method).
-// With want_flag, returns 1 when the limited pair differs from the unlimited
-// one (central slopes Delta_j = (delta_{j-1}+delta_j)/2, no fix-ups), i.e.
-// when the limiter changed the result; otherwise returns 0.
+// With uq (non-null), also returns the unlimited pair uq[0] = towards +d,
+// uq[1] = towards -d, from central slopes Delta_j = (delta_{j-1}+delta_j)/2
+// and no fix-ups (what the limiter would leave untouched).
 template <class T>
-int ppm_line(const T s[5], T& qp, T& qm, bool want_flag = false) {
+void ppm_line(const T s[5], T& qp, T& qm, T* uq = nullptr) {
   const T sixth = T(1.0 / 6.0);
   T dl[4];
   for (int j = 0; j < 4; ++j) dl[j] = s[j + 1] - s[j];  // delta_{j-2}
@@ -157,13 +157,21 @@ int ppm_line(const T s[5], T& qp, T& qm, bool want_flag = false) {
       qp = T(3.0) * q0 - T(2.0) * qm;
     }
   }
-  if (!want_flag) return 0;
+  if (!uq) return;
   T Du[3];
   for (int k = 0; k < 3; ++k) Du[k] = T(0.5) * (dl[k] + dl[k + 1]);
-  const T qpu = T(0.5) * (q0 + s[3]) - (Du[2] - Du[1]) * sixth;
-  const T qmu = T(0.5) * (s[1] + q0) - (Du[1] - Du[0]) * sixth;
-  return (val(qp) != val(qpu) || val(qm) != val(qmu)) ? 1 : 0;
+  uq[0] = T(0.5) * (q0 + s[3]) - (Du[2] - Du[1]) * sixth;
+  uq[1] = T(0.5) * (s[1] + q0) - (Du[1] - Du[0]) * sixth;
 }
+
+// Significant limiter activity (the learned indicator's label): on a line
+// of field k through a cell, the limited pair differs from the unlimited one
+// by more than 1e-4 of the field's scale at the cell: |q0| for density,
+// internal energy, tracer and species, |vx|+|vy|+|vz|+c for velocities.
+// The spin fields are always limited and never labelled.  (Differences below
+// that are rounding-level noise, e.g. numerical precursors ahead of a shock.)
+static const double kLabelTol = 1e-4;
+inline bool spin_field(int k) { return k == ZX || k == ZY || k == ZZ; }
 
 // Physical state on one side of a quadrature point x_q on a face with normal
 // axis a.  The frame rotates about +z at omega; momentum and energy are the
@@ -228,29 +236,55 @@ void primitives_subgrid(const Params& P, const T* U, std::vector<T>& Q) {
   }
 }
 
+// Unlimited interface value of the centre cell towards +d on five samples:
+// the 4-point formula 7/12 (q0 + q1) - 1/12 (q-1 + q2) (what the PPM
+// interface value is when no limiter acts).  Used for cells that the learned
+// smoothness indicator marks as smooth.
+template <class T>
+T unlimited_plus(const T s[5]) {
+  return T(7.0 / 12.0) * (s[2] + s[3]) - T(1.0 / 12.0) * (s[1] + s[4]);
+}
+
 // Reconstructed value R_i[d] of cell i = (x,y,z) (interior coordinates, may
 // be -1 or N on a face-adjacent ghost) at its point x_c + (h/2) d, for every
-// primitive: PPM along the line of cell centres i + m d, m = -2..2.
-// Returns 1 if the limiter changed any field's value on that line (only when
-// want_flag is set).
+// primitive: PPM along the line of cell centres i + m d, m = -2..2 (with
+// `unlimited`, the 4-point formula for all fields but the spin).  With
+// want_flag, returns 1 when the limiter acted significantly on the line.
 template <class T>
 int recon_point(const Params& P, const std::vector<T>& Q, int x, int y, int z, const int d[3], T* out,
-                bool want_flag) {
+                bool want_flag, bool unlimited = false) {
   const int S = P.N + 2 * P.G, G = P.G;
   const long S3 = (long)S * S * S;
   auto at = [&](int xx, int yy, int zz) -> long { return ((long)(zz + G) * S + (yy + G)) * S + (xx + G); };
+  const long c = at(x, y, z);
+  double vscale = 0.0;
+  if (want_flag) {
+    const double rho = val(Q[RHO * S3 + c]), eps = val(Q[4 * S3 + c]);
+    vscale = std::fabs(val(Q[1 * S3 + c])) + std::fabs(val(Q[2 * S3 + c])) + std::fabs(val(Q[3 * S3 + c])) +
+             std::sqrt(P.gamma * (P.gamma - 1.0) * eps / rho);
+  }
   int fl = 0;
   for (int k = 0; k < P.nf; ++k) {
     T s5[5];
     for (int m = -2; m <= 2; ++m) s5[m + 2] = Q[k * S3 + at(x + m * d[0], y + m * d[1], z + m * d[2])];
     T qp, qm;
-    if constexpr (std::is_same<T, CD>::value) {
+    if (unlimited && !spin_field(k)) {
+      out[k] = unlimited_plus(s5);
+      continue;
+    }
+    if (want_flag && !spin_field(k)) {
+      T uq[2];
+      ppm_line(s5, qp, qm, uq);
+      const double scale = (k >= 1 && k <= 3) ? vscale : std::fabs(val(s5[2]));
+      const double diff = std::max(std::fabs(val(qp) - val(uq[0])), std::fabs(val(qm) - val(uq[1])));
+      if (diff > kLabelTol * scale) fl = 1;
+    } else if constexpr (std::is_same<T, CD>::value) {
       const long before = g_ops.total();
-      fl |= ppm_line(s5, qp, qm, want_flag);
+      ppm_line(s5, qp, qm);
       g_ppm_ops += g_ops.total() - before;
       g_ppm_calls += 1;
     } else {
-      fl |= ppm_line(s5, qp, qm, want_flag);
+      ppm_line(s5, qp, qm);
     }
     out[k] = qp;
   }
@@ -264,11 +298,13 @@ int recon_point(const Params& P, const std::vector<T>& Q, int x, int y, int z, c
 //   dUdt   [nf][N][N][N]
 //   amax   max signal speed over every quadrature point of every face of the
 //          N^3 interior cells (sub-grid boundary faces included)
-//   limflag optional [N][N][N]: 1 where a limiter branch fired on any line
-//          through the cell for any reconstructed field
+//   limflag optional [N][N][N]: 1 where the limiter acted significantly on a
+//          line through the cell (the indicator's label, see kLabelTol)
+//   smooth  optional [S][S][S]: cells whose lines use the unlimited formula
+//          (all fields but the spin, which stays limited)
 template <class T>
 void step_subgrid(const Params& P, const T* U, const double origin[3], double h, const T* g, T* dUdt,
-                  T* amax, uint8_t* limflag) {
+                  T* amax, uint8_t* limflag, const uint8_t* smooth = nullptr) {
   const int N = P.N, G = P.G, S = N + 2 * G, nf = P.nf;
   const long S3 = (long)S * S * S;
   auto at = [&](int x, int y, int z) -> long { return ((long)(z + G) * S + (y + G)) * S + (x + G); };
@@ -280,7 +316,8 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
   // 2. reconstructed value of cell (x,y,z) at its point towards direction d
   std::vector<uint8_t> fired((size_t)N * N * N, 0);
   auto recon = [&](int x, int y, int z, const int d[3], T* out) {
-    const int fl = recon_point(P, Q, x, y, z, d, out, limflag != nullptr);
+    const bool un = smooth && smooth[at(x, y, z)];
+    const int fl = recon_point(P, Q, x, y, z, d, out, limflag != nullptr, un);
     if (fl && x >= 0 && x < N && y >= 0 && y < N && z >= 0 && z < N) fired[((long)z * N + y) * N + x] = 1;
   };
 
@@ -482,6 +519,25 @@ int orc_step(const orc_params* p, int n_sub, const double* U, const double* orig
   return 0;
 }
 
+// orc_step with a per-cell smoothness mask [n_sub][S^3] (1: unlimited lines).
+int orc_step_masked(const orc_params* p, int n_sub, const double* U, const double* origin, const double* h,
+                    const double* g, double* dUdt, double* amax, const uint8_t* smooth, int nthreads) {
+  const orc::Params P = to_p(p);
+  if (P.nf > orc::kMaxF || P.nf < 10 || P.N < 1 || P.G != 3 || n_sub < 0 || !smooth) return -1;
+  const int S = P.N + 2 * P.G;
+  const long S3 = (long)S * S * S, N3 = (long)P.N * P.N * P.N;
+#ifdef _OPENMP
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+  for (int s = 0; s < n_sub; ++s) {
+    orc::step_subgrid<double>(P, U + (long)s * P.nf * S3, origin + 3L * s, h[s], g ? g + 3L * s * N3 : nullptr,
+                              dUdt + (long)s * P.nf * N3, amax + s, nullptr, smooth + (long)s * S3);
+  }
+  (void)nthreads;
+  return 0;
+}
+
 // RK3 stage update, in place on the interior of U (ghosts untouched).
 int orc_update(const orc_params* p, int n_sub, double* U, const double* U0, const double* dUdt, double dt,
                int stage) {
@@ -501,8 +557,13 @@ void orc_primitives(const orc_params* p, const double* u, double* q) {
   orc::primitives<double>(P, u, q);
 }
 
-// PPM on one line of five samples; returns the limiter-changed flag.
-int orc_ppm_line(const double* s5, double* qp, double* qm) { return orc::ppm_line<double>(s5, *qp, *qm, true); }
+// PPM on one line of five samples; returns 1 when the limited pair differs
+// from the unlimited (central-slope, no fix-up) pair.
+int orc_ppm_line(const double* s5, double* qp, double* qm) {
+  double uq[2];
+  orc::ppm_line<double>(s5, *qp, *qm, uq);
+  return (*qp != uq[0] || *qm != uq[1]) ? 1 : 0;
+}
 
 // Central flux at one quadrature point from primitive states qL, qR.
 void orc_point_flux(const orc_params* p, const double* qL, const double* qR, int axis, const double* xq,

@@ -144,6 +144,9 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   A.P.gm1 = c->gamma - 1.0;
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
+  A.gate = (mixed && c->gate_on) ? 1 : 0;
+  A.gate_logit_thr = (float)c->gate_logit_thr;
+  A.gate_zero_smooth = c->gate_zero_smooth;
   cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, (cudaStream_t)stream)
                         : hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
@@ -231,6 +234,7 @@ void hydro_destroy(hydro_ctx_t* c) {
   if (c->status) cudaFree(c->status);
   if (c->scratch) cudaFree(c->scratch);
   if (c->part) cudaFree(c->part);
+  if (c->gate_w) cudaFree(c->gate_w);
   delete c;
 }
 

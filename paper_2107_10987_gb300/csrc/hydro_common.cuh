@@ -41,6 +41,9 @@ struct StepArgs64 {
   unsigned* status;
   int n_sub;
   StepParams P;
+  int gate;               // mixed form: use the learned smoothness indicator
+  float gate_logit_thr;   // cells with indicator logit below this are smooth
+  int gate_zero_smooth;   // the decision for all-zero features (uniform neighbourhood)
 };
 
 // ---- FP64 arithmetic that the compiler may not contract into FMA --------

@@ -15,6 +15,10 @@ struct hydro_ctx {
   size_t scratch_bytes;
   double* part;          // conservation partials
   size_t part_bytes;
+  int gate_on;           // learned smoothness indicator active (mixed mode)
+  double gate_logit_thr; // smooth where the indicator's logit is below this
+  int gate_zero_smooth;  // decision for all-zero features, set with the parameters
+  float* gate_w;         // BF16-rounded indicator parameters (device)
 };
 
 // Allocate the context's status word and the step scratch for a batch of

@@ -15,95 +15,27 @@
 // sweeps (FP32-bound).  The conversion reads the FP64 state with coalesced
 // loads and writes FP32 primitives: a bulk TMA copy cannot convert, and an
 // FP64 staging buffer would not fit beside the FP32 primitives of two CTAs.
-#include "hydro_common.cuh"
+#include "hydro_mixed.cuh"
 
 namespace hyd {
 
-__device__ __forceinline__ float slope32(float a, float b) {
-  const float m = fminf(fminf(2.f * fabsf(a), 2.f * fabsf(b)), 0.5f * fabsf(a + b));
-  return (a * b <= 0.f) ? 0.f : copysignf(m, b);
-}
-
-// PPM on one line in FP32 (branch-free form of the same limiter).
-__device__ __forceinline__ void ppm32(float s0, float s1, float s2, float s3, float s4, float& qp, float& qm) {
-  const float sixth = 1.f / 6.f;
-  const float D0 = slope32(s1 - s0, s2 - s1), D1 = slope32(s2 - s1, s3 - s2), D2 = slope32(s3 - s2, s4 - s3);
-  const float p = 0.5f * (s2 + s3) - (D2 - D1) * sixth;
-  const float m = 0.5f * (s1 + s2) - (D1 - D0) * sixth;
-  const bool ext = (p - s2) * (s2 - m) <= 0.f;
-  const float dq = p - m;
-  const float lhs = dq * (s2 - 0.5f * (p + m));
-  const float rhs = dq * dq * sixth;
-  const float m2 = (lhs > rhs) ? 3.f * s2 - 2.f * p : m;
-  const float p2 = (lhs < -rhs) ? 3.f * s2 - 2.f * m : p;
-  qp = ext ? s2 : p2;
-  qm = ext ? s2 : m2;
-}
-
-__device__ __forceinline__ void line10f(const float* __restrict__ Q, int c, int st, float qp[F], float qm[F]) {
-#pragma unroll
-  for (int k = 0; k < F; ++k) {
-    const float* q = Q + k * S3 + c;
-    ppm32(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
-  }
-}
-
-struct StepParamsF {
-  float gamma, gm1, omega;
-};
-
-__device__ __forceinline__ void side32(const float q[F], int a, float xq, float yq, const StepParamsF& P, float U[F],
-                                       float Fl[F], float& spd) {
-  const float rho = q[RHO], vx = q[1], vy = q[2], vz = q[3], eps = q[4];
-  const float ek = (0.5f * rho) * (vx * vx + vy * vy + vz * vz);
-  const float E = eps + ek;
-  const float p = P.gm1 * eps;
-  const float c2 = __fdividef(P.gamma * p, rho);
-  const float c = c2 * rsqrtf(c2);
-  const float ux = vx + P.omega * yq, uy = vy - P.omega * xq;
-  const float un = (a == 0) ? ux : (a == 1) ? uy : vz;
-  const float va = (a == 0) ? vx : (a == 1) ? vy : vz;
-  U[RHO] = rho;
-  U[SX] = rho * vx;
-  U[SY] = rho * vy;
-  U[SZ] = rho * vz;
-  U[EGAS] = E;
-#pragma unroll
-  for (int k = TAU; k < F; ++k) U[k] = q[k];
-#pragma unroll
-  for (int k = 0; k < F; ++k) Fl[k] = U[k] * un;
-  Fl[SX + a] += p;
-  Fl[EGAS] += p * va;
-  spd = fabsf(un) + c;
-}
-
-__device__ __forceinline__ void point32(const float qL[F], const float qR[F], int a, float xq, float yq, float w,
-                                        const float rl[3], const float rr[3], const StepParamsF& P, float fsum[F],
-                                        float tl[3], float tr[3], float& amax) {
-  float UL[F], FL[F], UR[F], FR[F], sL, sR;
-  side32(qL, a, xq, yq, P, UL, FL, sL);
-  side32(qR, a, xq, yq, P, UR, FR, sR);
-  const float aq = fmaxf(sL, sR);
-  amax = fmaxf(amax, aq);
-  float Fq[F];
-#pragma unroll
-  for (int k = 0; k < F; ++k) {
-    Fq[k] = 0.5f * (FL[k] + FR[k]) - (0.5f * aq) * (UR[k] - UL[k]);
-    fsum[k] += w * Fq[k];
-  }
-  const float fx = Fq[SX], fy = Fq[SY], fz = Fq[SZ];
-  tl[0] += w * (rl[1] * fz - rl[2] * fy);
-  tl[1] += w * (rl[2] * fx - rl[0] * fz);
-  tl[2] += w * (rl[0] * fy - rl[1] * fx);
-  tr[0] += w * (rr[1] * fz - rr[2] * fy);
-  tr[1] += w * (rr[2] * fx - rr[0] * fz);
-  tr[2] += w * (rr[0] * fy - rr[1] * fx);
-}
-
 constexpr int kThreadsMx = NROW;  // 192
 
+// Learned smoothness indicator parameters (BF16-rounded, FP32 values), read
+// by every thread in lockstep: constant memory broadcasts them.
+__constant__ float c_gate_w[kGateParams];
+
+struct ConstW {
+  __device__ float operator()(int i) const { return c_gate_w[i]; }
+};
+
+cudaError_t set_gate_weights(const float* dev_params, cudaStream_t st) {
+  return cudaMemcpyToSymbolAsync(c_gate_w, dev_params, sizeof(float) * kGateParams, 0, cudaMemcpyDeviceToDevice, st);
+}
+
 __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArgs64 A) {
-  extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives
+  extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [S3] smooth flags
+  uint8_t* smooth = reinterpret_cast<uint8_t*>(Qf + F * S3);
   __shared__ float red[kThreadsMx / 32];
   const int tid = threadIdx.x;
   double* __restrict__ D = A.scratch + (size_t)blockIdx.x * kScratchPerSub;
@@ -125,26 +57,47 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
       double u[F];
 #pragma unroll
       for (int k = 0; k < F; ++k) u[k] = __ldg(Us + (size_t)k * S3 + c);
-      const double rho = u[RHO];
-      // 1/rho: FP32 reciprocal refined by one Newton step in FP64 (rel. err ~1e-14)
-      const double r0 = (double)__frcp_rn((float)rho);
-      const double ri = r0 * fma(-rho, r0, 2.0);
-      const double s2 = fma(u[SZ], u[SZ], fma(u[SY], u[SY], u[SX] * u[SX]));
-      const double ek = 0.5 * s2 * ri;
-      const double eE = u[EGAS] - ek;  // FP64: the cancellation the dual energy guards
-      const float rif = (float)ri;
-      const float eps = (eE > A.P.eta1 * u[EGAS]) ? (float)eE : __powf((float)u[TAU], PF.gamma);
-      Qf[RHO * S3 + c] = (float)rho;
-      Qf[SX * S3 + c] = (float)u[SX] * rif;
-      Qf[SY * S3 + c] = (float)u[SY] * rif;
-      Qf[SZ * S3 + c] = (float)u[SZ] * rif;
-      Qf[EGAS * S3 + c] = eps;
+      float q[F];
+      bad |= !prims_mixed(u, A.P.eta1, PF.gamma, q);
 #pragma unroll
-      for (int k = TAU; k < F; ++k) Qf[k * S3 + c] = (float)u[k];
-      bad |= !(rho > 0.0) || !(eps > 0.f);
+      for (int k = 0; k < F; ++k) Qf[k * S3 + c] = q[k];
     }
     if (bad) atomicOr(A.status, 1u);
     __syncthreads();
+
+    // ---- 2b. learned smoothness indicator.  Predict on the 12^3 block of
+    // cells [-2, N+1]^3 (a perfectly uniform 3x3x3 neighbourhood has all
+    // features 0: its prediction is the network's value at 0, computed once),
+    // then a reconstructed cell (in [-1, N]^3) is smooth only if every cell
+    // of its 3x3x3 block is predicted smooth: the 5-point stencils along the
+    // 13 lines reach two cells out, beyond one cell's 3x3x3 features.
+    if (A.gate) {
+      uint8_t* pred = smooth + S3;  // [S3] per-cell predictions
+      for (int i = tid; i < (N + 4) * (N + 4) * (N + 4); i += kThreadsMx) {
+        const int x = i % (N + 4) - 2, y = (i / (N + 4)) % (N + 4) - 2, z = i / ((N + 4) * (N + 4)) - 2;
+        const int c = ((z + G) * S + (y + G)) * S + (x + G);
+        float f[54];
+        gate_features(Qf, c, PF.gm1, f);
+        bool uniform = true;
+#pragma unroll
+        for (int k = 0; k < 54; ++k) uniform &= (f[k] == 0.f);
+        pred[c] = (uniform ? A.gate_zero_smooth : (gate_logit(ConstW{}, f) < A.gate_logit_thr)) ? 1 : 0;
+      }
+      __syncthreads();
+      for (int i = tid; i < (N + 2) * (N + 2) * (N + 2); i += kThreadsMx) {
+        const int x = i % (N + 2) - 1, y = (i / (N + 2)) % (N + 2) - 1, z = i / ((N + 2) * (N + 2)) - 1;
+        const int c = ((z + G) * S + (y + G)) * S + (x + G);
+        uint8_t all = 1;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) all &= pred[c + (dz * S + dy) * S + dx];
+        smooth[c] = all;
+      }
+      __syncthreads();
+    }
 
     // ---- 3. row sweep in FP32 --------------------------------------------
     const double hd = A.h[s];
@@ -152,7 +105,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
     const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
     float amax = 0.f;
     float plus[9][F];
-    float fprev[F], trprev[3];
+    double fprev[F], trprev[3];  // previous face's sums, converted to FP64 once
     int coord0[3];
     coord0[a] = 0;
     coord0[b] = pb;
@@ -176,8 +129,13 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
       for (int p = 0; p <= 4; ++p) {
         const int t1 = p / 3 - 1, t2 = p % 3 - 1;
         float qpA[F], qmA[F], qpB[F], qmB[F];
-        line10f(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
-        if (p != 4) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        if (A.gate && smooth[cj]) {
+          line10u(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
+          if (p != 4) line10u(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        } else {
+          line10f(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
+          if (p != 4) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        }
         if (j >= 0) {
 #pragma unroll 1
           for (int side = 0; side < 2; ++side) {
@@ -203,25 +161,30 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
           if (p != 4) plus[8 - p][k] = qpB[k];
         }
       }
-      if (j >= 1) {
-        const int i = j - 1;
-        int cc[3];
-        cc[a] = i;
-        cc[b] = pb;
-        cc[cx] = pc;
-        const int cell = (cc[2] * N + cc[1]) * N + cc[0];
-        double* Da = D + (size_t)a * DQ * N3 + cell;
-#pragma unroll
-        for (int k = 0; k < F; ++k) Da[k * N3] = (double)fsum[k] - (double)fprev[k];
-#pragma unroll
-        for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = (double)tl[m] - (double)trprev[m];
-      }
       if (j >= 0) {
+        // face j-1/2 is complete: its sums in FP64 (each converted once); the
+        // a-difference of cell j-1 is exact in FP64
+        double fd[F], tld[3];
 #pragma unroll
-        for (int k = 0; k < F; ++k) fprev[k] = fsum[k];
-        trprev[0] = tr[0];
-        trprev[1] = tr[1];
-        trprev[2] = tr[2];
+        for (int k = 0; k < F; ++k) fd[k] = (double)fsum[k];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) tld[m] = (double)tl[m];
+        if (j >= 1) {
+          int cc[3];
+          cc[a] = j - 1;
+          cc[b] = pb;
+          cc[cx] = pc;
+          const int cell = (cc[2] * N + cc[1]) * N + cc[0];
+          double* Da = D + (size_t)a * DQ * N3 + cell;
+#pragma unroll
+          for (int k = 0; k < F; ++k) Da[k * N3] = fd[k] - fprev[k];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = tld[m] - trprev[m];
+        }
+#pragma unroll
+        for (int k = 0; k < F; ++k) fprev[k] = fd[k];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) trprev[m] = (double)tr[m];
       }
     }
 #pragma unroll
@@ -275,7 +238,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
   }
 }
 
-size_t step_mixed_smem_bytes() { return (size_t)F * S3 * sizeof(float); }
+size_t step_mixed_smem_bytes() { return (size_t)F * S3 * sizeof(float) + 2 * S3; }
 
 // Opt in to the kernel's dynamic shared memory once per process (no
 // allocation; call before any stream capture).

@@ -96,6 +96,9 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.P.gm1 = c->gamma - 1.0;
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
+  A.gate = 0;
+  A.gate_logit_thr = 0.f;
+  A.gate_zero_smooth = 0;
   if (hyd::launch_step_fp64(A, B->n_sub, st) != cudaSuccess) return HYDRO_ECUDA;
   return HYDRO_OK;
 }

@@ -23,7 +23,9 @@ HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
 EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydro_dt", "hydro_fill_ghosts_uniform",
            "hydro_conserved_sums", "hydro_status", "hydro_strerror", "hydro_last_cuda_error", "hydro_destroy",
            "hydro_step_static", "hydro_rk3_step_uniform", "hydro_rk3_graph_create", "hydro_rk3_graph_launch",
-           "hydro_rk3_graph_state", "hydro_rk3_graph_destroy")
+           "hydro_rk3_graph_state", "hydro_rk3_graph_destroy", "hydro_gate_data", "hydro_mlp_forward",
+           "hydro_mlp_work_bytes", "hydro_mlp_loss_grad", "hydro_mlp_adam", "hydro_set_indicator")
+HYDRO_GATE_NPARAM, HYDRO_GATE_NIN = 2849, 54
 
 
 class HydroError(RuntimeError):
@@ -90,8 +92,16 @@ def _lib(load: bool = True):
         L.hydro_rk3_graph_launch.argtypes = [vp, vp]
         L.hydro_rk3_graph_state.argtypes = [vp]
         L.hydro_rk3_graph_destroy.argtypes = [vp]
+        L.hydro_gate_data.argtypes = [vp, C.POINTER(Batch), vp, vp, vp]
+        L.hydro_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
+        L.hydro_mlp_work_bytes.argtypes = [ip]
+        L.hydro_mlp_work_bytes.restype = C.c_size_t
+        L.hydro_mlp_loss_grad.argtypes = [vp, vp, vp, ip, C.c_float, C.c_float, vp, vp, vp, C.c_size_t, vp]
+        L.hydro_mlp_adam.argtypes = [vp, vp, vp, vp, ip, C.c_float, vp]
+        L.hydro_set_indicator.argtypes = [vp, vp, dp, vp]
         for name in EXPORTS:
-            if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy", "hydro_rk3_graph_destroy"):
+            if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy", "hydro_rk3_graph_destroy",
+                            "hydro_mlp_work_bytes"):
                 getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -118,8 +128,12 @@ def _stream(stream) -> int:
 
 
 def make_batch(U, origin, h, g=None) -> Batch:
+    """A batch descriptor; it keeps references to the tensors whose device
+    pointers it holds, so they stay allocated as long as the descriptor."""
     n = U.shape[0]
-    return Batch(n, _ptr(U), _ptr(origin), _ptr(h), _ptr(g))
+    b = Batch(n, _ptr(U), _ptr(origin), _ptr(h), _ptr(g))
+    b._keep = (U, origin, h, g)
+    return b
 
 
 class Context:
@@ -212,8 +226,10 @@ def hydro_step_static(ctx, batch: Batch, dt: float, dUdt, amax, status=None, str
 
 def make_rk3_desc(Ua, Ub, origin, h, nb, bc, dUdt, amax, dt, cfl=0.4, g=None) -> RK3Desc:
     """Descriptor of one RK3 time step of a uniform mesh of nb = (nbx, nby, nbz) sub-grids."""
-    return RK3Desc(make_batch(Ua, origin, h, g), _ptr(Ub), nb[0], nb[1], nb[2], bc, _ptr(dUdt), _ptr(amax), _ptr(dt),
-                   float(cfl))
+    d = RK3Desc(make_batch(Ua, origin, h, g), _ptr(Ub), nb[0], nb[1], nb[2], bc, _ptr(dUdt), _ptr(amax), _ptr(dt),
+                float(cfl))
+    d._keep = (Ua, Ub, origin, h, g, dUdt, amax, dt)
+    return d
 
 
 def hydro_rk3_step_uniform(ctx, desc: RK3Desc, parity: int, stream=None):
@@ -237,3 +253,45 @@ def hydro_rk3_graph_state(graph: int) -> int:
 
 def hydro_rk3_graph_destroy(graph: int):
     _lib().hydro_rk3_graph_destroy(graph)
+
+
+def _fptr(t) -> int | None:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expects contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def hydro_gate_data(ctx, batch: Batch, X=None, y=None, stream=None):
+    """X: float32 [n_sub*512][54] CUDA tensor, y: uint8 [n_sub*512] (either may be None)."""
+    assert X is None or X.dtype == torch.float32
+    assert y is None or y.dtype == torch.uint8
+    _check(_lib().hydro_gate_data(_cp(ctx), C.byref(batch), _fptr(X), _fptr(y), _stream(stream)), "hydro_gate_data")
+
+
+def hydro_mlp_forward(params, X, out, stream=None):
+    _check(_lib().hydro_mlp_forward(_fptr(params), _fptr(X), X.shape[0], _fptr(out), _stream(stream)),
+           "hydro_mlp_forward")
+
+
+def hydro_mlp_work_bytes(n: int) -> int:
+    return int(_lib().hydro_mlp_work_bytes(int(n)))
+
+
+def hydro_mlp_loss_grad(params, X, y, grad, loss=None, w1=1.0, w0=1.0, work=None, stream=None):
+    n = X.shape[0]
+    if work is None:
+        work = torch.empty(hydro_mlp_work_bytes(n) // 4 + 1, dtype=torch.float32, device=X.device)
+    _check(_lib().hydro_mlp_loss_grad(_fptr(params), _fptr(X), _fptr(y), n, float(w1), float(w0), _fptr(grad),
+                                      _fptr(loss), _fptr(work), work.numel() * work.element_size(), _stream(stream)),
+           "hydro_mlp_loss_grad")
+
+
+def hydro_mlp_adam(params, m, v, grad, t: int, lr: float, stream=None):
+    _check(_lib().hydro_mlp_adam(_fptr(params), _fptr(m), _fptr(v), _fptr(grad), int(t), float(lr), _stream(stream)),
+           "hydro_mlp_adam")
+
+
+def hydro_set_indicator(ctx, params=None, threshold: float = 0.5, stream=None):
+    _check(_lib().hydro_set_indicator(_cp(ctx), _fptr(params), float(threshold), _stream(stream)),
+           "hydro_set_indicator")

@@ -187,3 +187,56 @@ def lane_emden(n: float, dxi: float = 1e-4):
         xs.append(x)
         ths.append(y[0])
     raise RuntimeError("unreachable")
+
+
+def sedov_box_at(n: int, E_blast: float, center, gamma: float = 5.0 / 3.0, rho0: float = 1.0, p0: float = 1e-5,
+                 L: float = 2.0):
+    """Sedov blast of energy E_blast deposited as internal energy in the 2^3
+    cells nearest to the point `center` of [-L/2, L/2]^3 (n^3 cells).
+    Returns (U [NF][n][n][n], h, lo)."""
+    h = L / n
+    lo = (-L / 2, -L / 2, -L / 2)
+    idx = [int(np.clip(np.floor((center[a] - lo[a]) / h - 0.5), 0, n - 2)) for a in range(3)]
+    rho = np.full((n, n, n), rho0)
+    p = np.full((n, n, n), p0)
+    sl = tuple(slice(idx[a], idx[a] + 2) for a in (2, 1, 0))
+    p[sl] += (gamma - 1.0) * E_blast / (8.0 * h ** 3)
+    return conserved_from_primitive(rho, np.zeros((3, n, n, n)), p, gamma), h, lo
+
+
+def sod_box_oriented(n: int, normal, offset: float, gamma: float = 1.4,
+                     states=((1.0, 0.0, 1.0), (0.125, 0.0, 0.1)), L: float = 2.0):
+    """Planar Sod interface with unit normal `normal` through the point
+    offset * normal of [-L/2, L/2]^3: left state where (x . n) < offset.
+    Returns (U [NF][n][n][n], h, lo)."""
+    h = L / n
+    lo = (-L / 2, -L / 2, -L / 2)
+    nv = np.asarray(normal, dtype=np.float64)
+    nv = nv / np.linalg.norm(nv)
+    X, Y, Z = cell_centres((n, n, n), lo, h)
+    left = (X * nv[0] + Y * nv[1] + Z * nv[2]) < offset
+    (rl, ul, pl), (rr, ur, pr) = states
+    rho = np.where(left, rl, rr)
+    un = np.where(left, ul, ur)
+    p = np.where(left, pl, pr)
+    v = np.stack([un * nv[0], un * nv[1], un * nv[2]])
+    return conserved_from_primitive(rho, v, p, gamma), h, lo
+
+
+def indicator_runs(seeds, n: int = 64):
+    """Seeded initial states of the indicator's training/evaluation runs: for
+    each seed, a Sedov blast with energy ~ U(0.1, 10) at a random centre in
+    [-0.5, 0.5]^3 (gamma 5/3) for even seeds, a Sod plane at a random
+    orientation and offset in [-0.3, 0.3] (gamma 1.4) for odd seeds.
+    Yields (seed, kind, gamma, U, h, lo)."""
+    for sd in seeds:
+        rng = np.random.default_rng(10_000 + sd)
+        if sd % 2 == 0:
+            E = rng.uniform(0.1, 10.0)
+            c = rng.uniform(-0.5, 0.5, 3)
+            U, h, lo = sedov_box_at(n, E, c)
+            yield sd, "sedov", 5.0 / 3.0, U, h, lo
+        else:
+            nv = rng.normal(size=3)
+            U, h, lo = sod_box_oriented(n, nv, rng.uniform(-0.3, 0.3))
+            yield sd, "sod", 1.4, U, h, lo
