@@ -135,7 +135,24 @@ def make_state(dev):
     return U, origin, hv, sub
 
 
-def run_form(args, H, dev, precision, flush):
+def train_indicator(dev):
+    """Train the learned smoothness indicator from seeded runs (Sedov blasts at
+    random energy and centre, Sod planes at random orientation; none of them
+    the benchmark's own problem) on the GPU's own kernels; threshold for
+    99.95% recall of limiter-active cells.  Outside the timed region."""
+    from paper_2107_10987_gb300 import gate as GT
+    t0 = time.perf_counter()
+    X, y, ch = GT.collect(range(0, 8), n=32, snapshots=(6, 16, 30), device=dev)
+    params, hist = GT.train(X, y, iters=600, batch=16384, lr=3e-3)
+    thr = GT.choose_threshold(params, X, y, ch, recall=0.9995)
+    Xh, yh, chh = GT.collect(range(1000, 1004), n=32, snapshots=(6, 16, 30), device=dev)
+    ev = GT.evaluate(params, thr, Xh, yh, chh)
+    ev["train_s"] = time.perf_counter() - t0
+    ev["final_loss"] = hist[-1][1]
+    return params, thr, ev
+
+
+def run_form(args, H, dev, precision, flush, indicator=None):
     """Warm-up, then K timed RK3 steps of one precision form; returns timings
     and the final state.  The launch sequence of a step is the one the C
     ABI's graph captures (hydro_rk3_step_uniform): the first stage writes
@@ -144,6 +161,8 @@ def run_form(args, H, dev, precision, flush):
     stream = torch.cuda.current_stream()
     ctx = H.Context(GAMMA, 0.0)
     H.hydro_set_mode(ctx, precision, 0.4)
+    if indicator is not None:
+        H.hydro_set_indicator(ctx, indicator[0], indicator[1])
     Ua, origin, hv, host_init = make_state(dev)
     Ub = torch.zeros_like(Ua)
     bufs = [Ua, Ub]
@@ -235,20 +254,25 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     launches_per_step = 10  # 3 x (ghost fill, step, update) + dt; no copies
-    forms = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED}
-    order = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    forms = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED, "gated": H.HYDRO_PREC_MIXED}
+    order = {"all": ["fp64", "gated", "mixed"], "both": ["fp64", "mixed"]}.get(args.precision, [args.precision])
+    indicator = ind_eval = None
+    if "gated" in order:
+        params, thr, ind_eval = train_indicator(dev)
+        indicator = (params, thr)
     res = {}
     for name in order:
         if ws > 1:
             dist.barrier()
+        ind = indicator if name == "gated" else None
         if name == order[-1]:
             with ClockSampler(lr) as clk:
                 t0 = time.perf_counter()
-                res[name] = run_form(args, H, dev, forms[name], flush)
+                res[name] = run_form(args, H, dev, forms[name], flush, ind)
                 res[name]["wall"] = time.perf_counter() - t0
             res[name]["clocks"] = clk.summary()
         else:
-            res[name] = run_form(args, H, dev, forms[name], flush)
+            res[name] = run_form(args, H, dev, forms[name], flush, ind)
         if ws > 1:
             for key in ("t_dev", "t_e2e"):
                 t = torch.tensor([res[name][key]], dtype=torch.float64, device=dev)
@@ -263,18 +287,18 @@ def gpu_arm(args):
         n = r["n"]
         flops = work["fp64_flops_per_subgrid_stage"] * n
         bytes_launch = work["bytes_per_subgrid_stage"] * n
-        peak = FP32_PEAK_TFLOPS if head == "mixed" else FP64_PEAK_TFLOPS
+        peak = FP64_PEAK_TFLOPS if head == "fp64" else FP32_PEAK_TFLOPS
         achieved = flops / r["kern_s"] / 1e12
         line = {
             "metric": METRIC, "value": CELLS * args.steps * ws / r["t_dev"], "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["t_dev"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64 (mixed)" if head == "mixed" else "f64", "data": "synthetic",
+            "dtype": "f64" if head == "fp64" else "f32+f64 (mixed)", "data": "synthetic",
             "config": {"workload": "Sedov blast, uniform octree level of 512 sub-grids of 8^3 (64^3 on [-1,1]^3), "
                                    "outflow, 10 FP64 fields, one step = one full RK3 time step (3 stages)",
                        "sub_grids": n, "cells": CELLS,
                        "precision": "mixed: FP32 reconstruction/fluxes, FP64 dual-energy recovery, accumulation "
-                                    "and update" if head == "mixed" else "fp64 (plain)",
+                                    "and update" if head != "fp64" else "fp64 (plain)",
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MB write) between timed steps, outside the timed events"},
             "cell_stage_updates_per_s": 3 * CELLS * args.steps * ws / r["t_dev"],
@@ -286,7 +310,7 @@ def gpu_arm(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": work.get("dram_bytes_per_launch_scaled", {}).get(head),
                          "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flops x 2070 MHz (profiling recipe units)"
-                                         if head == "mixed" else "nominal GB300 FP64 from the profiling recipe"),
+                                         if head != "fp64" else "nominal GB300 FP64 from the profiling recipe"),
                          "flops_counted": "algorithmic ops of the method (oracle count), each op one flop",
                          "hbm_frac": (bytes_launch / r["kern_s"] / 1e9) / pk["hbm_gbs"] if "hbm_gbs" in pk else None},
             "e2e": {"value": CELLS * args.steps * ws / r["t_e2e"], "unit": UNIT,
@@ -308,6 +332,15 @@ def gpu_arm(args):
             # both forms ran the same steps from the same state: density difference
             d = (r["rho"] - f["rho"]).abs().max().item() / f["rho"].abs().max().item()
             line["max_rel_density_diff_vs_fp64"] = d
+        if "gated" in res:
+            gr = res["gated"]
+            line["mixed_with_indicator"] = {
+                "value": CELLS * args.steps * ws / gr["t_dev"], "ms_per_step": 1e3 * gr["t_dev"] / args.steps,
+                "kernel_ms": 1e3 * gr["kern_s"],
+                "speedup_vs_mixed": r["t_dev"] / gr["t_dev"] if head == "mixed" else None,
+                "max_rel_density_diff_vs_fp64": ((gr["rho"] - res["fp64"]["rho"]).abs().max().item() /
+                                                 res["fp64"]["rho"].abs().max().item()) if "fp64" in res else None,
+                "indicator_held_out": ind_eval}
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -380,8 +413,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
-                    help="both: time the plain FP64 form, then the mixed form (reported as value)")
+    ap.add_argument("--precision", default="all", choices=["all", "both", "mixed", "fp64", "gated"],
+                    help="all: time the plain FP64 form, the mixed form with the learned indicator, then the "
+                         "mixed form (reported as value); both: FP64 then mixed")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
