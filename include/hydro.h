@@ -55,6 +55,7 @@ extern "C" {
 /* ---- device status bits (hydro_status) --------------------------------- */
 #define HYDRO_ST_NONPHYS 0x1u  /* rho <= 0, eps <= 0 or NaN seen in a step */
 #define HYDRO_ST_TIMEOUT 0x2u  /* a bounded device wait expired; results of that launch are invalid */
+#define HYDRO_ST_MESH 0x4u     /* an adaptive mesh violated 2:1 balance where a ghost or flux needed it */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define HYDRO_PREC_FP64 0   /* every operation in FP64 (the plain method) */
@@ -119,9 +120,15 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
  * context's mode: HYDRO_PREC_FP64 matches the FP64 oracle to 1e-12 (per-field
  * normalised error); HYDRO_PREC_MIXED to the FP32 error budget stated in the
  * tests (about 1e-6).
+ * face_flux (nullable): the sub-grid boundary faces' sums for coarse-fine
+ * flux correction, [n_sub][6][F+3][N][N]: face slot 2a (lower) / 2a+1
+ * (upper) of axis a; per face cell [c][b] (b < c the transverse axes) the F
+ * face-averaged fluxes and the 3 components of the momentum-flux torque
+ * about the adjacent interior cell.
  * Errors: EINVAL (NULL ctx/batch/pointers, n_sub < 0, misaligned U, dt < 0),
  * ENOMEM, ECUDA.  n_sub == 0 is a no-op. */
-int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, void* stream);
+int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, double* face_flux,
+               void* stream);
 
 /* SSP-RK3 stage update of the interior cells (ghosts are not touched):
  *   U_new <- alpha_k U0 + beta_k (U + dt dUdt), (alpha, beta) = (0,1), (3/4,1/4),
@@ -154,6 +161,7 @@ int hydro_dt(hydro_ctx_t* ctx, const double* amax, const double* h, int n_sub, d
 int hydro_fill_ghosts_uniform(hydro_ctx_t* ctx, const hydro_batch_t* B, int nbx, int nby, int nbz, int bc,
                               void* stream);
 
+
 /* Global conservation sums over the interior cells of the batch, FP64:
  * sums[k] = sum_s sum_cells U[s][k] h_s^3 for k < F, and
  * sums[F] = sum (x_c s_y - y_c s_x + z_z) h^3 (angular momentum about +z).
@@ -184,7 +192,43 @@ int hydro_conserved_sums(hydro_ctx_t* ctx, const hydro_batch_t* B, double* sums,
 int hydro_step_static(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax,
                       uint32_t* status, void* stream);
 
-/* ---- a whole RK3 time step of a uniform mesh, and its CUDA graphs -------
+/* ---- adaptive octree meshes -------------------------------------------------
+ * Leaves are 8^3 sub-grids of an octree on [-1,1]^3 (Sec. III-B), 2:1 balanced
+ * across faces, edges and vertices; leaf s has level leaf_level[s] and integer
+ * position leaf_ijk[3s..3s+2] in [0, 2^l)^3 (origin -1 + ijk * 2/2^l, cell
+ * width 2/(8 2^l)).  table concatenates, for l = lmin..lmax, the (2^l)^3 entries
+ * ((k 2^l) + j) 2^l + i: the leaf index at that position, -1 where it is
+ * refined, -2 where it lies inside a coarser leaf.  All device pointers. */
+typedef struct {
+  int lmin, lmax;
+  const int* table;
+  const int* leaf_level;
+  const int* leaf_ijk;
+  int bc;               /* HYDRO_BC_OUTFLOW or HYDRO_BC_PERIODIC */
+} hydro_amr_t;
+
+/* Ghost fill of the leaves of an adaptive mesh (the ghost exchange of Sec.
+ * IV-A.2 across refinement levels), two launches: (1) a ghost cell held by a
+ * same-level leaf is copied; one over a refined position is the mean of its 8
+ * finer cells (in (dz, dy, dx) order a0..a7, summed ((a0+a1)+(a2+a3)) +
+ * ((a4+a5)+(a6+a7)), times 1/8); (2) one inside a
+ * coarser leaf is prolonged from the coarse cell: U_C + sum_a s_a o_a with
+ * o_a = -1/4 or +1/4 and s_a = minmod(U[C+e_a] - U_C, U_C - U[C-e_a])
+ * (conservative).  Outside the domain the position is clamped (outflow) or
+ * wrapped (periodic) first.  A 2:1 violation sets HYDRO_ST_MESH. */
+int hydro_fill_ghosts_amr(hydro_ctx_t* ctx, const hydro_batch_t* B, const hydro_amr_t* mesh, void* stream);
+
+/* Coarse-fine flux correction of dUdt in place: for a coarse boundary cell
+ * whose face borders finer leaves, its face flux is replaced by the mean of
+ * the 4 fine sub-face fluxes and its spin torque by the mean of the fine
+ * torques moved to the coarse cell centre (T(x_C) = T(x_f) + (x_f - x_C) x
+ * F_s).  face_flux: hydro_step's boundary-face output for the same batch.
+ * With it the adaptive mesh conserves mass, momentum, energy and angular
+ * momentum to round-off. */
+int hydro_flux_correct_amr(hydro_ctx_t* ctx, const hydro_batch_t* B, const hydro_amr_t* mesh,
+                           const double* face_flux, double* dUdt, void* stream);
+
+/* ---- a whole RK3 time step of a mesh, and its CUDA graphs -----------------
  * One time step (three hydro iterations, Sec. IV-A.2) of a uniform mesh of
  * nbx x nby x nbz sub-grids, state X -> Y:
  *   ghost(X); step(X); dt = cfl min h/amax; Y = X + dt dU      (stage 0)
@@ -202,15 +246,21 @@ typedef struct {
   double* amax;     /* [n_sub] */
   double* dt;       /* one device double */
   double cfl;       /* <= 0: the context's mode */
+  /* Adaptive mesh (NULL: the uniform nbx x nby x nbz mesh above).  With a mesh
+   * each stage runs hydro_fill_ghosts_amr, hydro_step with face_flux and
+   * hydro_flux_correct_amr instead of the uniform ghost fill (nbx, nby, nbz
+   * and bc are then ignored). */
+  const hydro_amr_t* amr;
+  double* face_flux;  /* [n_sub][6][F+3][N][N], used with amr */
 } hydro_rk3_desc_t;
 
 typedef struct hydro_graph hydro_graph_t;
 
 /* Enqueue one time step on a stream: parity 0 advances a -> b, 1 advances
  * b -> a.  Ten launches.  Errors: EINVAL (inconsistent descriptor). */
-int hydro_rk3_step_uniform(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
+int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
 
-/* Capture the two directions of hydro_rk3_step_uniform once into CUDA graphs
+/* Capture the two directions of hydro_rk3_step once into CUDA graphs
  * (allocating the context's scratch beforehand, so replays allocate nothing).
  * The state starts in buffer a.  The descriptor's buffers must stay valid
  * and unchanged in address while the graph exists. */

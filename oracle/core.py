@@ -56,7 +56,7 @@ def lib():
     if _lib is None:
         l = C.CDLL(build())
         dp = C.POINTER(C.c_double)
-        l.orc_step.argtypes = [C.POINTER(_P), C.c_int, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_uint8), C.c_int]
+        l.orc_step.argtypes = [C.POINTER(_P), C.c_int, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_uint8), dp, C.c_int]
         l.orc_step.restype = C.c_int
         l.orc_step_masked.argtypes = [C.POINTER(_P), C.c_int, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_uint8), C.c_int]
         l.orc_step_masked.restype = C.c_int
@@ -79,11 +79,12 @@ def _dp(a: np.ndarray):
 
 
 def step(P: OracleParams, U: np.ndarray, origin: np.ndarray, h: np.ndarray, g: np.ndarray | None = None,
-         want_flags: bool = False, nthreads: int = 0):
+         want_flags: bool = False, nthreads: int = 0, faces: bool = False):
     """One stage of the semi-discrete operator on a batch of sub-grids.
 
     U [n_sub][nf][S][S][S] (ghosts filled) -> (dUdt [n_sub][nf][N][N][N], amax [n_sub],
-    limflag [n_sub][N][N][N] or None)."""
+    limflag [n_sub][N][N][N] or None); with faces=True a fourth result, the
+    boundary-face sums [n_sub][6][nf+3][N][N]."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     n = U.shape[0]
     N = P.N
@@ -96,10 +97,14 @@ def step(P: OracleParams, U: np.ndarray, origin: np.ndarray, h: np.ndarray, g: n
     if g is not None:
         g = np.ascontiguousarray(g, dtype=np.float64)
         gp = _dp(g)
+    ff = np.zeros((n, 6, P.nf + 3, N, N)) if faces else None
     rc = lib().orc_step(C.byref(P.c()), n, _dp(U), _dp(origin), _dp(h), gp, _dp(dU), _dp(am),
-                        fl.ctypes.data_as(C.POINTER(C.c_uint8)) if fl is not None else None, nthreads)
+                        fl.ctypes.data_as(C.POINTER(C.c_uint8)) if fl is not None else None,
+                        _dp(ff) if ff is not None else None, nthreads)
     if rc != 0:
         raise ValueError("orc_step rejected its arguments")
+    if faces:
+        return dU, am, fl, ff
     return dU, am, fl
 
 

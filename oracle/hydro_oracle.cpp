@@ -302,9 +302,13 @@ int recon_point(const Params& P, const std::vector<T>& Q, int x, int y, int z, c
 //          line through the cell (the indicator's label, see kLabelTol)
 //   smooth  optional [S][S][S]: cells whose lines use the unlimited formula
 //          (all fields but the spin, which stays limited)
+//   face_flux optional [6][nf+3][N][N]: the sub-grid's boundary faces (slot
+//          2a lower, 2a+1 upper face of axis a), per face cell [c][b] (b < c
+//          the transverse axes) the face sums and the torque about the
+//          adjacent interior cell
 template <class T>
 void step_subgrid(const Params& P, const T* U, const double origin[3], double h, const T* g, T* dUdt,
-                  T* amax, uint8_t* limflag, const uint8_t* smooth = nullptr) {
+                  T* amax, uint8_t* limflag, const uint8_t* smooth = nullptr, T* face_flux = nullptr) {
   const int N = P.N, G = P.G, S = N + 2 * G, nf = P.nf;
   const long S3 = (long)S * S * S;
   auto at = [&](int x, int y, int z) -> long { return ((long)(z + G) * S + (y + G)) * S + (x + G); };
@@ -387,6 +391,28 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
           for (int k = 0; k < nf; ++k) Fbar[f * nf + k] = fsum[k];
           for (int m = 0; m < 3; ++m) { TqL[f * 3 + m] = tl[m]; TqR[f * 3 + m] = tr[m]; }
         }
+  }
+
+  if (face_flux) {
+    const int q = nf + 3;
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a == 0) ? 1 : 0, cax = (a == 2) ? 1 : 2;
+      for (int side = 0; side < 2; ++side) {
+        const int f = 2 * a + side;
+        for (int pc = 0; pc < N; ++pc)
+          for (int pb = 0; pb < N; ++pb) {
+            int ci[3];
+            ci[a] = side ? N - 1 : -1;
+            ci[b] = pb;
+            ci[cax] = pc;
+            const long fi = fidx(a, ci[0], ci[1], ci[2]);
+            T* out = face_flux + (long)f * q * N * N + (long)pc * N + pb;
+            for (int k = 0; k < nf; ++k) out[(long)k * N * N] = Fbar[fi * nf + k];
+            for (int m = 0; m < 3; ++m)
+              out[(long)(nf + m) * N * N] = side ? TqL[fi * 3 + m] : TqR[fi * 3 + m];
+          }
+      }
+    }
   }
 
   // 4-5. divergence and sources on the interior cells:
@@ -502,7 +528,7 @@ static orc::Params to_p(const orc_params* p) {
 //   dUdt [n_sub][nf][N^3], amax [n_sub], limflag nullable [n_sub][N^3]
 // nthreads <= 0 uses the OpenMP default.
 int orc_step(const orc_params* p, int n_sub, const double* U, const double* origin, const double* h,
-             const double* g, double* dUdt, double* amax, uint8_t* limflag, int nthreads) {
+             const double* g, double* dUdt, double* amax, uint8_t* limflag, double* face_flux, int nthreads) {
   const orc::Params P = to_p(p);
   if (P.nf > orc::kMaxF || P.nf < 10 || P.N < 1 || P.G != 3 || n_sub < 0) return -1;
   const int S = P.N + 2 * P.G;
@@ -513,7 +539,8 @@ int orc_step(const orc_params* p, int n_sub, const double* U, const double* orig
 #endif
   for (int s = 0; s < n_sub; ++s) {
     orc::step_subgrid<double>(P, U + (long)s * P.nf * S3, origin + 3L * s, h[s], g ? g + 3L * s * N3 : nullptr,
-                              dUdt + (long)s * P.nf * N3, amax + s, limflag ? limflag + (long)s * N3 : nullptr);
+                              dUdt + (long)s * P.nf * N3, amax + s, limflag ? limflag + (long)s * N3 : nullptr,
+                              nullptr, face_flux ? face_flux + (long)s * 6 * (P.nf + 3) * P.N * P.N : nullptr);
   }
   (void)nthreads;
   return 0;

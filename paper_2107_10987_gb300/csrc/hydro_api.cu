@@ -116,7 +116,8 @@ int hydro_set_mode(hydro_ctx_t* c, const hydro_mode_t* m) {
   return HYDRO_OK;
 }
 
-int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, double* amax, void* stream) {
+int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, double* amax, double* face_flux,
+               void* stream) {
   if (!c || !B) return HYDRO_EINVAL;
   if (B->n_sub < 0 || !std::isfinite(dt) || dt < 0.0) return HYDRO_EINVAL;
   if (B->n_sub == 0) return HYDRO_OK;
@@ -137,6 +138,7 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   A.g = B->g;
   A.dUdt = dUdt;
   A.amax = amax;
+  A.face_flux = face_flux;
   A.scratch = c->scratch;
   A.status = c->status;
   A.n_sub = B->n_sub;

@@ -25,6 +25,14 @@ enum { RHO = 0, SX = 1, SY = 2, SZ = 3, EGAS = 4, TAU = 5, ZX = 6, ZY = 7, ZZ = 
 constexpr int DQ = F + 3;
 constexpr size_t kScratchPerSub = (size_t)3 * DQ * N3;  // doubles
 
+// Boundary-face export of one sub-grid face (axis a, side): the 10 face-
+// averaged fluxes and the 3 torque components about the adjacent interior
+// cell, on the N x N face cells indexed [c][b] (b < c the transverse axes).
+// Face slot f = 2a for the lower face, 2a + 1 for the upper face.
+__device__ __forceinline__ size_t face_index(int s, int f, int q, int pc, int pb) {
+  return ((((size_t)s * 6 + f) * DQ + q) * N + pc) * N + pb;
+}
+
 struct StepParams {
   double gamma, gm1, omega, eta1;
 };
@@ -37,6 +45,7 @@ struct StepArgs64 {
   const double* g;
   double* dUdt;
   double* amax;
+  double* face_flux;  // optional [n_sub][6][DQ][N][N] boundary-face sums (null: none)
   double* scratch;  // per-CTA scratch, kScratchPerSub doubles per CTA
   unsigned* status;
   int n_sub;

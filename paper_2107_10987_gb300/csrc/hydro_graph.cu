@@ -1,4 +1,5 @@
-// hydro_graph.cu -- a whole RK3 time step of a uniform mesh as a sequence of
+// hydro_graph.cu -- a whole RK3 time step of a mesh (uniform, or adaptive with
+// its two-pass ghost fill and coarse-fine flux correction) as a sequence of
 // launches on one stream, and the same sequence captured once into CUDA
 // graphs that are replayed step after step.
 //
@@ -32,8 +33,14 @@ static int rk3_enqueue(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, 
   int rc;
   for (int k = 0; k < 3; ++k) {
     const hydro_batch_t* B = (k == 0) ? &X : &Y;
-    if ((rc = hydro_fill_ghosts_uniform(ctx, B, d->nbx, d->nby, d->nbz, d->bc, st))) return rc;
-    if ((rc = hydro_step(ctx, B, 0.0, d->dUdt, d->amax, st))) return rc;
+    if (d->amr) {
+      if ((rc = hydro_fill_ghosts_amr(ctx, B, d->amr, st))) return rc;
+      if ((rc = hydro_step(ctx, B, 0.0, d->dUdt, d->amax, d->face_flux, st))) return rc;
+      if ((rc = hydro_flux_correct_amr(ctx, B, d->amr, d->face_flux, d->dUdt, st))) return rc;
+    } else {
+      if ((rc = hydro_fill_ghosts_uniform(ctx, B, d->nbx, d->nby, d->nbz, d->bc, st))) return rc;
+      if ((rc = hydro_step(ctx, B, 0.0, d->dUdt, d->amax, nullptr, st))) return rc;
+    }
     if (k == 0 && (rc = hydro_dt(ctx, d->amax, d->a.h, d->a.n_sub, d->cfl, d->dt, st))) return rc;
     if ((rc = hydro_update(ctx, B, X.U, d->dUdt, 0.0, d->dt, k, k == 0 ? Y.U : nullptr, st))) return rc;
   }
@@ -41,13 +48,16 @@ static int rk3_enqueue(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, 
 }
 
 static bool desc_ok(const hydro_rk3_desc_t* d) {
-  return d && d->a.U && d->U_b && d->a.origin && d->a.h && d->dUdt && d->amax && d->dt && d->a.n_sub > 0 &&
-         (long)d->nbx * d->nby * d->nbz == d->a.n_sub && d->a.U != d->U_b;
+  if (!(d && d->a.U && d->U_b && d->a.origin && d->a.h && d->dUdt && d->amax && d->dt && d->a.n_sub > 0 &&
+        d->a.U != d->U_b))
+    return false;
+  if (d->amr) return d->face_flux != nullptr;
+  return (long)d->nbx * d->nby * d->nbz == d->a.n_sub;
 }
 
 extern "C" {
 
-int hydro_rk3_step_uniform(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream) {
+int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream) {
   if (!ctx || !desc_ok(d) || (parity != 0 && parity != 1)) return HYDRO_EINVAL;
   return rk3_enqueue(ctx, d, parity, (cudaStream_t)stream);
 }

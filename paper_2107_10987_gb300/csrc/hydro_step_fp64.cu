@@ -262,6 +262,14 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
         trprev[1] = tr[1];
         trprev[2] = tr[2];
       }
+      if (A.face_flux && (j == 0 || j == N)) {
+        // sub-grid boundary face: sums and the torque about the interior cell
+        const int f = 2 * a + (j == N ? 1 : 0);
+#pragma unroll
+        for (int k = 0; k < F; ++k) A.face_flux[face_index(s, f, k, pc, pb)] = fsum[k];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = (j == N) ? tl[m] : tr[m];
+      }
     }
     // block-wide amax; order the generic-proxy shared-memory accesses of this
     // sub-grid before the next bulk copy overwrites the buffer

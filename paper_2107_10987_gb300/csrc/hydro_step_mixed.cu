@@ -185,6 +185,14 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
         for (int k = 0; k < F; ++k) fprev[k] = fd[k];
 #pragma unroll
         for (int m = 0; m < 3; ++m) trprev[m] = (double)tr[m];
+        if (A.face_flux && (j == 0 || j == N)) {
+          // sub-grid boundary face: sums and the torque about the interior cell
+          const int f = 2 * a + (j == N ? 1 : 0);
+#pragma unroll
+          for (int k = 0; k < F; ++k) A.face_flux[face_index(s, f, k, pc, pb)] = fd[k];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = (j == N) ? tld[m] : trprev[m];
+        }
       }
     }
 #pragma unroll

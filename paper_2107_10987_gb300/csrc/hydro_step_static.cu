@@ -89,6 +89,7 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.g = B->g;
   A.dUdt = dUdt;
   A.amax = amax;
+  A.face_flux = nullptr;
   A.scratch = a.scratch;  // one slot per CTA, one CTA per sub-grid
   A.status = word;
   A.n_sub = B->n_sub;

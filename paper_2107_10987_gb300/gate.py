@@ -1,7 +1,7 @@
 """Training driver of the learned smoothness indicator (host-side loop only).
 
 Every arithmetic step runs in the library's kernels through the C ABI:
-the runs that generate the data (hydro_rk3_step_uniform, mixed precision),
+the runs that generate the data (hydro_rk3_step, mixed precision),
 the features and labels (hydro_gate_data), the loss and gradient
 (hydro_mlp_loss_grad) and the optimiser (hydro_mlp_adam).  This module only
 orders the calls, draws minibatch indices and picks the decision threshold.
@@ -44,7 +44,7 @@ def collect(seeds, n: int = 64, snapshots=(8, 24, 48), device="cuda"):
         step = 0
         for target in snapshots:
             while step < target:
-                H.hydro_rk3_step_uniform(ctx, desc, step % 2)
+                H.hydro_rk3_step(ctx, desc, step % 2)
                 step += 1
             cur = bufs[step % 2]
             B = H.make_batch(cur, o, hv)

@@ -22,9 +22,11 @@ HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
 
 EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydro_dt", "hydro_fill_ghosts_uniform",
            "hydro_conserved_sums", "hydro_status", "hydro_strerror", "hydro_last_cuda_error", "hydro_destroy",
-           "hydro_step_static", "hydro_rk3_step_uniform", "hydro_rk3_graph_create", "hydro_rk3_graph_launch",
+           "hydro_step_static", "hydro_rk3_step", "hydro_rk3_graph_create", "hydro_rk3_graph_launch",
            "hydro_rk3_graph_state", "hydro_rk3_graph_destroy", "hydro_gate_data", "hydro_mlp_forward",
-           "hydro_mlp_work_bytes", "hydro_mlp_loss_grad", "hydro_mlp_adam", "hydro_set_indicator")
+           "hydro_mlp_work_bytes", "hydro_mlp_loss_grad", "hydro_mlp_adam", "hydro_set_indicator",
+           "hydro_fill_ghosts_amr", "hydro_flux_correct_amr")
+HYDRO_ST_MESH = 0x4
 HYDRO_GATE_NPARAM, HYDRO_GATE_NIN = 2849, 54
 
 
@@ -52,7 +54,8 @@ class Batch(C.Structure):
 
 class RK3Desc(C.Structure):
     _fields_ = [("a", Batch), ("U_b", C.c_void_p), ("nbx", C.c_int), ("nby", C.c_int), ("nbz", C.c_int),
-                ("bc", C.c_int), ("dUdt", C.c_void_p), ("amax", C.c_void_p), ("dt", C.c_void_p), ("cfl", C.c_double)]
+                ("bc", C.c_int), ("dUdt", C.c_void_p), ("amax", C.c_void_p), ("dt", C.c_void_p), ("cfl", C.c_double),
+                ("amr", C.c_void_p), ("face_flux", C.c_void_p)]
 
 
 _L = None
@@ -74,7 +77,7 @@ def _lib(load: bool = True):
         vp, dp, ip = C.c_void_p, C.c_double, C.c_int
         L.hydro_create.argtypes = [C.POINTER(Layout), dp, dp, C.POINTER(vp)]
         L.hydro_set_mode.argtypes = [vp, C.POINTER(Mode)]
-        L.hydro_step.argtypes = [vp, C.POINTER(Batch), dp, vp, vp, vp]
+        L.hydro_step.argtypes = [vp, C.POINTER(Batch), dp, vp, vp, vp, vp]
         L.hydro_update.argtypes = [vp, C.POINTER(Batch), vp, vp, dp, vp, ip, vp, vp]
         L.hydro_dt.argtypes = [vp, vp, vp, ip, dp, vp, vp]
         L.hydro_fill_ghosts_uniform.argtypes = [vp, C.POINTER(Batch), ip, ip, ip, ip, vp]
@@ -87,7 +90,7 @@ def _lib(load: bool = True):
         L.hydro_step_static.argtypes = [vp, C.POINTER(Batch), dp, vp, vp, vp, vp]
         L.hydro_destroy.argtypes = [vp]
         L.hydro_destroy.restype = None
-        L.hydro_rk3_step_uniform.argtypes = [vp, C.POINTER(RK3Desc), ip, vp]
+        L.hydro_rk3_step.argtypes = [vp, C.POINTER(RK3Desc), ip, vp]
         L.hydro_rk3_graph_create.argtypes = [vp, C.POINTER(RK3Desc), C.POINTER(vp)]
         L.hydro_rk3_graph_launch.argtypes = [vp, vp]
         L.hydro_rk3_graph_state.argtypes = [vp]
@@ -99,6 +102,8 @@ def _lib(load: bool = True):
         L.hydro_mlp_loss_grad.argtypes = [vp, vp, vp, ip, C.c_float, C.c_float, vp, vp, vp, C.c_size_t, vp]
         L.hydro_mlp_adam.argtypes = [vp, vp, vp, vp, ip, C.c_float, vp]
         L.hydro_set_indicator.argtypes = [vp, vp, dp, vp]
+        L.hydro_fill_ghosts_amr.argtypes = [vp, C.POINTER(Batch), vp, vp]
+        L.hydro_flux_correct_amr.argtypes = [vp, C.POINTER(Batch), vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy", "hydro_rk3_graph_destroy",
                             "hydro_mlp_work_bytes"):
@@ -170,9 +175,9 @@ def _cp(ctx):
     return ctx.ptr if isinstance(ctx, Context) else ctx
 
 
-def hydro_step(ctx, batch: Batch, dt: float, dUdt, amax, stream=None):
-    _check(_lib().hydro_step(_cp(ctx), C.byref(batch), float(dt), _ptr(dUdt), _ptr(amax), _stream(stream)),
-           "hydro_step")
+def hydro_step(ctx, batch: Batch, dt: float, dUdt, amax, face_flux=None, stream=None):
+    _check(_lib().hydro_step(_cp(ctx), C.byref(batch), float(dt), _ptr(dUdt), _ptr(amax), _ptr(face_flux),
+                             _stream(stream)), "hydro_step")
 
 
 def hydro_update(ctx, batch: Batch, U0, dUdt, dt: float = 0.0, dt_dev=None, stage: int = 0, U_out=None,
@@ -224,17 +229,20 @@ def hydro_step_static(ctx, batch: Batch, dt: float, dUdt, amax, status=None, str
                                     _stream(stream)), "hydro_step_static")
 
 
-def make_rk3_desc(Ua, Ub, origin, h, nb, bc, dUdt, amax, dt, cfl=0.4, g=None) -> RK3Desc:
-    """Descriptor of one RK3 time step of a uniform mesh of nb = (nbx, nby, nbz) sub-grids."""
+def make_rk3_desc(Ua, Ub, origin, h, nb, bc, dUdt, amax, dt, cfl=0.4, g=None, mesh=None, face_flux=None) -> RK3Desc:
+    """Descriptor of one RK3 time step: of a uniform mesh of nb = (nbx, nby, nbz)
+    sub-grids, or (mesh: an amr.AMRMesh, face_flux its work buffer) of an
+    adaptive mesh."""
+    nb = nb or (0, 0, 0)
     d = RK3Desc(make_batch(Ua, origin, h, g), _ptr(Ub), nb[0], nb[1], nb[2], bc, _ptr(dUdt), _ptr(amax), _ptr(dt),
-                float(cfl))
-    d._keep = (Ua, Ub, origin, h, g, dUdt, amax, dt)
+                float(cfl), C.addressof(mesh.desc) if mesh is not None else None, _ptr(face_flux))
+    d._keep = (Ua, Ub, origin, h, g, dUdt, amax, dt, mesh, face_flux)
     return d
 
 
-def hydro_rk3_step_uniform(ctx, desc: RK3Desc, parity: int, stream=None):
-    _check(_lib().hydro_rk3_step_uniform(_cp(ctx), C.byref(desc), int(parity), _stream(stream)),
-           "hydro_rk3_step_uniform")
+def hydro_rk3_step(ctx, desc: RK3Desc, parity: int, stream=None):
+    _check(_lib().hydro_rk3_step(_cp(ctx), C.byref(desc), int(parity), _stream(stream)),
+           "hydro_rk3_step")
 
 
 def hydro_rk3_graph_create(ctx, desc: RK3Desc) -> int:
@@ -295,3 +303,14 @@ def hydro_mlp_adam(params, m, v, grad, t: int, lr: float, stream=None):
 def hydro_set_indicator(ctx, params=None, threshold: float = 0.5, stream=None):
     _check(_lib().hydro_set_indicator(_cp(ctx), _fptr(params), float(threshold), _stream(stream)),
            "hydro_set_indicator")
+
+
+def hydro_fill_ghosts_amr(ctx, batch: Batch, mesh, stream=None):
+    """mesh: an amr.AMRMesh (its .desc is the hydro_amr_t)."""
+    _check(_lib().hydro_fill_ghosts_amr(_cp(ctx), C.byref(batch), C.addressof(mesh.desc), _stream(stream)),
+           "hydro_fill_ghosts_amr")
+
+
+def hydro_flux_correct_amr(ctx, batch: Batch, mesh, face_flux, dUdt, stream=None):
+    _check(_lib().hydro_flux_correct_amr(_cp(ctx), C.byref(batch), C.addressof(mesh.desc), _ptr(face_flux),
+                                         _ptr(dUdt), _stream(stream)), "hydro_flux_correct_amr")

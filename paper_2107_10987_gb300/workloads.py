@@ -240,3 +240,139 @@ def indicator_runs(seeds, n: int = 64):
             nv = rng.normal(size=3)
             U, h, lo = sod_box_oriented(n, nv, rng.uniform(-0.3, 0.3))
             yield sd, "sod", 1.4, U, h, lo
+
+
+# ---------------------------------------------------------------------------
+# Adaptive octree meshes on [-1, 1]^3.  A leaf at level l has integer
+# coordinates (i, j, k) in [0, 2^l)^3, width 2 / 2^l and cell width
+# h = 2 / (N 2^l); its origin is -1 + (i, j, k) * width.
+
+def _shell_density(r, R=0.3, gamma=5.0 / 3.0):
+    """Stand-in density of a blast shell of radius R used only to decide
+    refinement: 1 outside, (g+1)/(g-1) (r/R)^(3/(g-1)) inside (the power-law
+    behaviour of the self-similar profile behind a strong shock)."""
+    jump = (gamma + 1.0) / (gamma - 1.0)
+    return np.where(r < R, jump * np.maximum(r / R, 1e-12) ** (3.0 / (gamma - 1.0)) + 1e-12, 1.0)
+
+
+def _needs_refinement(level, ijk, theta, R):
+    """Refine where the stand-in shell density varies across the node by more
+    than theta: (max - min) / (max + min) over the node's 5^3 sample points
+    (corners included), a bounded measure of |grad rho| / rho times the width."""
+    w = 2.0 / 2 ** level
+    lo = -1.0 + np.asarray(ijk, dtype=np.float64) * w
+    t = np.linspace(0.0, 1.0, 5)
+    P = lo + w * np.stack(np.meshgrid(t, t, t, indexing="ij"), -1).reshape(-1, 3)
+    rho = _shell_density(np.linalg.norm(P, axis=1), R)
+    return bool((rho.max() - rho.min()) / (rho.max() + rho.min()) > theta)
+
+
+def _balance(leaves):
+    """Refine until every pair of leaves sharing a face, edge or vertex
+    differs by at most one level (2:1 balance)."""
+    leaves = set(leaves)
+
+    def covering(l, i, j, k):
+        # the leaf containing the level-l node (l, i, j, k), or None if that
+        # node is refined further
+        for lv in range(l, -1, -1):
+            sh = l - lv
+            key = (lv, i >> sh, j >> sh, k >> sh)
+            if key in leaves:
+                return key
+        return None
+
+    queue = sorted(leaves, key=lambda t: t[0])
+    while queue:
+        leaf = queue.pop()
+        if leaf not in leaves:
+            continue
+        l, i, j, k = leaf
+        n = 2 ** l
+        for di in (-1, 0, 1):
+            for dj in (-1, 0, 1):
+                for dk in (-1, 0, 1):
+                    a, b, c = i + di, j + dj, k + dk
+                    if not (0 <= a < n and 0 <= b < n and 0 <= c < n) or (di, dj, dk) == (0, 0, 0):
+                        continue
+                    cov = covering(l, a, b, c)
+                    if cov is not None and cov[0] < l - 1:
+                        leaves.remove(cov)
+                        lc, ic, jc, kc = cov
+                        for d in range(8):
+                            child = (lc + 1, 2 * ic + (d & 1), 2 * jc + ((d >> 1) & 1), 2 * kc + (d >> 2))
+                            leaves.add(child)
+                            queue.append(child)
+                        queue.append(leaf)
+    return sorted(leaves)
+
+
+def octree_shell_mesh(theta: float, lmin: int = 3, lmax: int = 6, R: float = 0.3):
+    """Leaves (level, i, j, k) of the octree refined around a blast shell of
+    radius R, 2:1 balanced."""
+    leaves = []
+    stack = [(lmin, i, j, k) for i in range(2 ** lmin) for j in range(2 ** lmin) for k in range(2 ** lmin)]
+    while stack:
+        l, i, j, k = stack.pop()
+        if l < lmax and _needs_refinement(l, (i, j, k), theta, R):
+            for d in range(8):
+                stack.append((l + 1, 2 * i + (d & 1), 2 * j + ((d >> 1) & 1), 2 * k + (d >> 2)))
+        else:
+            leaves.append((l, i, j, k))
+    return _balance(leaves)
+
+
+def amr_shell_mesh(n_target: int = 4096, seed: int = 1234, lmin: int = 3, lmax: int = 6, R: float = 0.3):
+    """The batched-AMR configuration: an octree of about n_target leaves at
+    levels lmin..lmax, refined around a blast shell of radius R (threshold
+    bisected to hit the target), 2:1 balanced, leaf order shuffled by seed.
+    Returns (level [n] int32, ijk [n][3] int32, theta)."""
+    lo_t, hi_t = 1e-3, 0.999
+    best = None
+    for _ in range(30):
+        th = 0.5 * (lo_t + hi_t)
+        leaves = octree_shell_mesh(th, lmin, lmax, R)
+        if best is None or abs(len(leaves) - n_target) < abs(len(best[0]) - n_target):
+            best = (leaves, th)
+        if abs(len(leaves) - n_target) <= 0.02 * n_target:
+            break
+        if len(leaves) > n_target:
+            lo_t = th
+        else:
+            hi_t = th
+    leaves, th = best
+    order = np.random.default_rng(seed).permutation(len(leaves))
+    arr = np.array(leaves, dtype=np.int32)[order]
+    return arr[:, 0].copy(), arr[:, 1:].copy(), th
+
+
+def amr_geometry(level, ijk, N: int = 8):
+    """Origins [n][3] and cell widths [n] of the leaves."""
+    w = 2.0 / (2.0 ** np.asarray(level, dtype=np.float64))
+    return -1.0 + np.asarray(ijk, dtype=np.float64) * w[:, None], w / N
+
+
+def amr_shell_state(level, ijk, gamma: float = 5.0 / 3.0, R: float = 0.3, N: int = 8, G: int = 3):
+    """A blast-shell state on AMR leaves (cell-centre values, ghosts zero):
+    outside r = R gas at rest (rho 1, p 1e-5); inside the shell the stand-in
+    density profile, radial velocity 0.75 r/R and pressure 0.3 + 0.45 (r/R)^2.
+    Returns [n][NF][S][S][S]."""
+    o, h = amr_geometry(level, ijk, N)
+    n = len(level)
+    S = N + 2 * G
+    out = np.zeros((n, NF, S, S, S))
+    idx = np.arange(N) + 0.5
+    for s in range(n):
+        X = o[s, 0] + idx[None, None, :] * h[s]
+        Y = o[s, 1] + idx[None, :, None] * h[s]
+        Z = o[s, 2] + idx[:, None, None] * h[s]
+        X, Y, Z = np.broadcast_arrays(X, Y, Z)
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        inside = r < R
+        rho = np.where(inside, np.maximum(_shell_density(r, R, gamma), 1e-3), 1.0)
+        vr = np.where(inside, 0.75 * r / R, 0.0)
+        rr = np.maximum(r, 1e-12)
+        v = np.stack([vr * X / rr, vr * Y / rr, vr * Z / rr])
+        p = np.where(inside, 0.3 + 0.45 * (r / R) ** 2, 1e-5)
+        out[s, :, G:G + N, G:G + N, G:G + N] = conserved_from_primitive(rho, v, p, gamma)
+    return out

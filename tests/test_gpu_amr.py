@@ -1,0 +1,156 @@
+"""Adaptive meshes on the GPU against the oracle: the two-pass ghost fill
+(bitwise), the boundary-face export and coarse-fine flux correction, whole
+RK3 steps (FP64, <= 1e-12), conservation to round-off, and the batched
+4,096-leaf configuration (one launch over all levels equals per-level
+launches, graph replay equals direct launches)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2107_10987_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GAMMA = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2107_10987_gb300 import _build, hydro
+    _build.build()
+    return hydro
+
+
+def small():
+    from test_oracle_amr import _blob_state, small_mesh
+    lev, ijk = small_mesh()
+    U, o, h = _blob_state(lev, ijk)
+    return lev, ijk, U, o, h
+
+
+def test_amr_ghost_fill_bitwise(H, oracle_mod):
+    from oracle import amr
+    from paper_2107_10987_gb300.amr import AMRMesh
+    lev, ijk, U, o, h = small()
+    rng = np.random.default_rng(2)
+    U[:, :, 3:-3, 3:-3, 3:-3] *= rng.uniform(0.9, 1.1, U[:, :, 3:-3, 3:-3, 3:-3].shape)  # non-smooth data
+    want = amr.fill_ghosts(amr.Octree(lev, ijk), U)
+    ctx = H.Context(GAMMA, 0.0)
+    mesh = AMRMesh(lev, ijk)
+    Ut = torch.tensor(U, device="cuda")
+    B = H.make_batch(Ut, torch.tensor(o, device="cuda"), torch.tensor(h, device="cuda"))
+    H.hydro_fill_ghosts_amr(ctx, B, mesh)
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    assert np.array_equal(Ut.cpu().numpy(), want)
+
+
+def test_amr_faces_and_flux_correction(H, oracle_mod):
+    from oracle import amr, core
+    from oracle.compare import max_rel_error
+    from paper_2107_10987_gb300.amr import AMRMesh
+    lev, ijk, U, o, h = small()
+    tree = amr.Octree(lev, ijk)
+    Uf = amr.fill_ghosts(tree, U)
+    dUo, amo, _, fo = core.step(core.OracleParams(gamma=GAMMA), Uf, o, h, faces=True)
+    dUc = amr.flux_correct(tree, dUo, fo, h)
+    ctx = H.Context(GAMMA, 0.0)
+    mesh = AMRMesh(lev, ijk)
+    n = len(lev)
+    Ut = torch.tensor(Uf, device="cuda")
+    B = H.make_batch(Ut, torch.tensor(o, device="cuda"), torch.tensor(h, device="cuda"))
+    dU = torch.empty((n, 10, 8, 8, 8), dtype=torch.float64, device="cuda")
+    am = torch.empty(n, dtype=torch.float64, device="cuda")
+    ff = torch.empty((n, 6, 13, 8, 8), dtype=torch.float64, device="cuda")
+    H.hydro_step(ctx, B, 0.0, dU, am, ff)
+    torch.cuda.synchronize()
+    fs = np.abs(fo).max(axis=(0, 1, 3, 4))
+    fs[fs == 0] = 1.0
+    assert np.max(np.abs(ff.cpu().numpy() - fo) / fs[None, None, :, None, None]) <= 1e-13
+    # correction applied to the oracle's own rates and faces: bitwise
+    dUt = torch.tensor(dUo, device="cuda")
+    fot = torch.tensor(fo, device="cuda")
+    H.hydro_flux_correct_amr(ctx, B, mesh, fot, dUt)
+    torch.cuda.synchronize()
+    assert np.array_equal(dUt.cpu().numpy(), dUc)
+    # and on the GPU's own step results
+    H.hydro_flux_correct_amr(ctx, B, mesh, ff, dU)
+    torch.cuda.synchronize()
+    assert max_rel_error(dU.cpu().numpy(), dUc, h.max()) <= 1e-12
+
+
+def test_amr_rk3_steps_match_oracle_and_conserve(H, oracle_mod):
+    from oracle import amr, core
+    from oracle.compare import max_rel_error
+    from paper_2107_10987_gb300.amr import AMRRun
+    lev, ijk, U, o, h = small()
+    tree = amr.Octree(lev, ijk)
+    P = core.OracleParams(gamma=GAMMA)
+    Uo = U.copy()
+    for _ in range(2):
+        Uo, dto = amr.rk3_step(P, tree, Uo, o, h)
+    ctx = H.Context(GAMMA, 0.0)
+    run = AMRRun(ctx, U, lev, ijk)
+    sums0 = torch.empty(11, dtype=torch.float64, device="cuda")
+    B0 = H.make_batch(run.U, run.origin, run.h)
+    H.hydro_conserved_sums(ctx, B0, sums0)
+    for _ in range(2):
+        run.step()
+    torch.cuda.synchronize()
+    got = run.U.cpu().numpy()[:, :, 3:-3, 3:-3, 3:-3]
+    assert run.dt.item() == pytest.approx(dto, rel=1e-14)
+    assert max_rel_error(got, Uo[:, :, 3:-3, 3:-3, 3:-3], h.max()) <= 1e-12
+    sums1 = torch.empty(11, dtype=torch.float64, device="cuda")
+    H.hydro_conserved_sums(ctx, H.make_batch(run.U, run.origin, run.h), sums1)
+    torch.cuda.synchronize()
+    a, b = sums0.cpu().numpy(), sums1.cpu().numpy()
+    # tau is excluded: the dual-energy resync after each stage resets it
+    for k in (0, 1, 2, 3, 4, 9):
+        assert abs(b[k] - a[k]) <= 1e-13 * max(abs(a[k]), 1.0), (k, a[k], b[k])
+    assert H.hydro_status(ctx) == 0
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batched_4096_leaf_mesh(H, mixed):
+    """The batched configuration: ~4,096 leaves at levels 3-6 in shuffled order.
+    One launch over all levels equals per-level launches (level-sorted copy),
+    graph replays equal direct launches, mass is conserved."""
+    from paper_2107_10987_gb300.amr import AMRMesh, AMRRun
+    lev, ijk, th = W.amr_shell_mesh()
+    U = W.amr_shell_state(lev, ijk, GAMMA)
+    ctx = H.Context(GAMMA, 0.0)
+    if mixed:
+        H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
+    runs = [AMRRun(ctx, U, lev, ijk) for _ in range(2)]
+    for k in range(4):
+        runs[0].step(use_graph=False)
+        runs[1].step(use_graph=True)
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    assert torch.equal(runs[0].U, runs[1].U)
+    runs[1].close()
+    # per-level launches of the step on a level-sorted copy
+    order = np.argsort(lev, kind="stable")
+    run = runs[0]
+    Ug = run.U
+    B = H.make_batch(Ug, run.origin, run.h)
+    H.hydro_fill_ghosts_amr(ctx, B, run.mesh)
+    dU_all = torch.empty_like(run.dU)
+    am_all = torch.empty_like(run.am)
+    H.hydro_step(ctx, B, 0.0, dU_all, am_all)
+    Us = Ug[torch.tensor(order, device="cuda")].contiguous()
+    os_ = run.origin[torch.tensor(order, device="cuda")].contiguous()
+    hs = run.h[torch.tensor(order, device="cuda")].contiguous()
+    dU_lv = torch.empty_like(dU_all)
+    am_lv = torch.empty_like(am_all)
+    start = 0
+    for l in np.unique(lev):
+        cnt = int((lev == l).sum())
+        Bl = H.make_batch(Us[start:start + cnt], os_[start:start + cnt], hs[start:start + cnt])
+        H.hydro_step(ctx, Bl, 0.0, dU_lv[start:start + cnt], am_lv[start:start + cnt])
+        start += cnt
+    torch.cuda.synchronize()
+    inv = torch.tensor(np.argsort(order), device="cuda")
+    assert torch.equal(dU_lv[inv], dU_all) and torch.equal(am_lv[inv], am_all)

@@ -323,7 +323,7 @@ def test_rk3_graph_replay_equals_direct_launches(H, mixed):
     Ua2, Ub2, dU2, am2, dt2 = buffers()
     d2 = H.make_rk3_desc(Ua2, Ub2, o, hh, nb, H.HYDRO_BC_OUTFLOW, dU2, am2, dt2)
     for k in range(4):
-        H.hydro_rk3_step_uniform(ctx, d2, k % 2)
+        H.hydro_rk3_step(ctx, d2, k % 2)
     torch.cuda.synchronize()
     assert np.array_equal(Ua2[:, :, 3:-3, 3:-3, 3:-3].cpu().numpy(), graph_state)
     # in place with a copy of the initial state
