@@ -155,7 +155,7 @@ def train_indicator(dev):
 def run_form(args, H, dev, precision, flush, indicator=None):
     """Warm-up, then K timed RK3 steps of one precision form; returns timings
     and the final state.  The launch sequence of a step is the one the C
-    ABI's graph captures (hydro_rk3_step_uniform): the first stage writes
+    ABI's graph captures (hydro_rk3_step): the first stage writes
     the second state buffer, so no copy of the step's initial state is made."""
     import torch
     stream = torch.cuda.current_stream()
@@ -238,6 +238,74 @@ def run_form(args, H, dev, precision, flush, indicator=None):
     torch.cuda.synchronize()
     out["t_e2e"] = e0.elapsed_time(e1) / 1e3
     out["bytes_step"] = host_U.numel() * 8
+    ctx.close()
+    return out
+
+
+def amr_measure(args, H, dev, flush, precision, steps):
+    """The batched adaptive configuration: ~4,096 leaves at levels 3-6 around a
+    blast shell, leaf order shuffled.  Times one RK3 step (direct launches and
+    graph replay) and the step kernel alone as one persistent launch over all
+    levels (default grid, then the autotuned grid) against one launch per
+    level on a level-sorted copy."""
+    import torch
+    from paper_2107_10987_gb300 import workloads as W
+    from paper_2107_10987_gb300.amr import AMRRun
+    lev, ijk, theta = W.amr_shell_mesh()
+    U = W.amr_shell_state(lev, ijk, GAMMA)
+    cells = len(lev) * 512
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, precision, 0.4)
+    stream = torch.cuda.current_stream()
+    out = {"leaves": len(lev), "cells": cells, "levels": {int(l): int((lev == l).sum()) for l in np.unique(lev)}}
+
+    def timed(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for i in range(n):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    run = AMRRun(ctx, U, lev, ijk)
+    for _ in range(2):
+        run.step()
+    out["rk3_step_ms_direct"] = timed(run.step, steps)
+    grun = AMRRun(ctx, U, lev, ijk)
+    grun.step(use_graph=True)
+    grun.step(use_graph=True)
+    out["rk3_step_ms_graph"] = timed(lambda: grun.step(use_graph=True), steps)
+    grun.close()
+    out["value_graph"] = cells / (out["rk3_step_ms_graph"] / 1e3)
+    # the step kernel alone on the current state
+    B = H.make_batch(run.U, run.origin, run.h)
+    H.hydro_fill_ghosts_amr(ctx, B, run.mesh)
+    dU, am = torch.empty_like(run.dU), torch.empty_like(run.am)
+    H.hydro_step(ctx, B, 0.0, dU, am)
+    out["step_ms_one_launch"] = timed(lambda: H.hydro_step(ctx, B, 0.0, dU, am), steps)
+    order = torch.tensor(np.argsort(lev, kind="stable"), device=dev)
+    Us, os_, hs = run.U[order].contiguous(), run.origin[order].contiguous(), run.h[order].contiguous()
+    lv = np.sort(lev)
+    batches = []
+    start = 0
+    for l in np.unique(lv):
+        cnt = int((lv == l).sum())
+        batches.append((H.make_batch(Us[start:start + cnt], os_[start:start + cnt], hs[start:start + cnt]),
+                        dU[start:start + cnt], am[start:start + cnt]))
+        start += cnt
+
+    def per_level():
+        for Bl, d, a in batches:
+            H.hydro_step(ctx, Bl, 0.0, d, a)
+
+    per_level()
+    out["step_ms_per_level_launches"] = timed(per_level, steps)
+    out["autotuned_slots"] = H.hydro_autotune_step(ctx, B, dU, am)
+    out["step_ms_one_launch_autotuned"] = timed(lambda: H.hydro_step(ctx, B, 0.0, dU, am), steps)
+    out["status"] = H.hydro_status(ctx)
+    run.close()
     ctx.close()
     return out
 
@@ -341,6 +409,11 @@ def gpu_arm(args):
                 "max_rel_density_diff_vs_fp64": ((gr["rho"] - res["fp64"]["rho"]).abs().max().item() /
                                                  res["fp64"]["rho"].abs().max().item()) if "fp64" in res else None,
                 "indicator_held_out": ind_eval}
+        if args.amr:
+            line["amr_batched"] = {"workload": "adaptive octree, ~4,096 leaves of 8^3 at levels 3-6 refined around a "
+                                               "blast shell of radius 0.3, leaf order shuffled (seed 1234), outflow",
+                                   "mixed": amr_measure(args, H, dev, flush, H.HYDRO_PREC_MIXED, args.steps),
+                                   "fp64": amr_measure(args, H, dev, flush, H.HYDRO_PREC_FP64, max(2, args.steps // 5))}
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -413,6 +486,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-amr", dest="amr", action="store_false", help="skip the batched adaptive-mesh measurement")
     ap.add_argument("--precision", default="all", choices=["all", "both", "mixed", "fp64", "gated"],
                     help="all: time the plain FP64 form, the mixed form with the learned indicator, then the "
                          "mixed form (reported as value); both: FP64 then mixed")

@@ -130,6 +130,15 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
 int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, double* face_flux,
                void* stream);
 
+/* Autotuner of the step's launch shape for this batch size and the context's
+ * precision: times hydro_step (one warm-up, three timed launches each) with
+ * persistent grids of 1, 1.5 and 2 CTAs per SM where they fit, and the
+ * smallest grid that keeps the number of rounds over the batch, and keeps
+ * the fastest for later steps of this context (*slots_out, nullable).
+ * Overwrites dUdt and amax; synchronises the stream.  Not in the paper. */
+int hydro_autotune_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double* dUdt, double* amax, int* slots_out,
+                        void* stream);
+
 /* SSP-RK3 stage update of the interior cells (ghosts are not touched):
  *   U_new <- alpha_k U0 + beta_k (U + dt dUdt), (alpha, beta) = (0,1), (3/4,1/4),
  *   (1/3,2/3) for stage k = 0, 1, 2; then the tracer resync

@@ -54,7 +54,7 @@ __device__ __forceinline__ int bc_amr(int g, int n, int bc) {
   return g < 0 ? 0 : (g >= n ? n - 1 : g);
 }
 
-template <int kPass>
+// Pass 1: same-level copies and restrictions.
 __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int l = A.leaf_level[s];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
       if ((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N) continue;
       const int gx = bc_amr(bx + lx, ncell, A.bc), gy = bc_amr(by + ly, ncell, A.bc), gz = bc_amr(bz + lz, ncell, A.bc);
       const int t = lookup(A, l, gx, gy, gz);
-      if (kPass == 1) {
+      {
         if (t >= 0) {
           const double* src = A.U + (size_t)t * F * S3 + (((gz & 7) + G) * S + ((gy & 7) + G)) * S + ((gx & 7) + G);
 #pragma unroll
@@ -90,29 +90,113 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
             dst[o + c] = rmul(acc, 0.125);
           }
         }
-      } else if (t == -2) {
-        const int cx = gx >> 1, cy = gy >> 1, cz = gz >> 1;
-        const int tc = lookup(A, l - 1, cx, cy, cz);
-        if (tc < 0) {
-          atomicOr(A.status, 4u);
-          continue;
-        }
-        const double* C = A.U + (size_t)tc * F * S3 + (((cz & 7) + G) * S + ((cy & 7) + G)) * S + ((cx & 7) + G);
-        const double off[3] = {(gx & 1) ? 0.25 : -0.25, (gy & 1) ? 0.25 : -0.25, (gz & 1) ? 0.25 : -0.25};
-        const int st[3] = {1, S, S * S};
+      }
+    }
+  }
+}
+
+// Prolongation of one fine ghost cell from coarse cell C (padded pointer to
+// field 0): U_C + s_x o_x + s_y o_y + s_z o_z, all ten fields.
+__device__ __forceinline__ void prolong_cell(const double* C, const double off[3], double* dst) {
+  const int st[3] = {1, S, S * S};
 #pragma unroll
-        for (int k = 0; k < F; ++k) {
-          const double* q = C + (size_t)k * S3;
-          double v = q[0];
+  for (int k = 0; k < F; ++k) {
+    const double* q = C + (size_t)k * S3;
+    double v = q[0];
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
-            const double mm = (rmul(dp, dm) <= 0.0) ? 0.0 : (fabs(dp) < fabs(dm) ? dp : dm);
-            v = radd(v, rmul(mm, off[d]));
-          }
-          dst[(size_t)k * S3 + c] = v;
+    for (int d = 0; d < 3; ++d) {
+      const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
+      const double mm = (rmul(dp, dm) <= 0.0) ? 0.0 : (fabs(dp) < fabs(dm) ? dp : dm);
+      v = radd(v, rmul(mm, off[d]));
+    }
+    dst[(size_t)k * S3] = v;
+  }
+}
+
+// Pass 2: ghost cells inside coarser leaves.  One thread per coarse cell of
+// the 8^3 coarse block covering the leaf's padded region computes the ten
+// fields' minmod slopes once and writes every child that is one of the
+// leaf's ghost cells (the same values as prolonging child by child).  Ghost
+// cells outside the domain (outflow: clamped positions) are prolonged one by
+// one afterwards.
+__global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A) {
+  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
+    const int l = A.leaf_level[s];
+    if (l <= A.lmin) continue;  // no coarser leaves
+    const int b[3] = {A.leaf_ijk[3 * s] * N, A.leaf_ijk[3 * s + 1] * N, A.leaf_ijk[3 * s + 2] * N};
+    const int ncell = N << l, nc = ncell >> 1;
+    double* dstb = A.U + (size_t)s * F * S3;
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+      int C[3], Cw[3];
+      const int ii[3] = {i & 7, (i >> 3) & 7, i >> 6};
+      bool out = false;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        C[d] = (b[d] >> 1) - 2 + ii[d];
+        Cw[d] = C[d];
+        if (C[d] < 0 || C[d] >= nc) {
+          if (A.bc == 0) Cw[d] = C[d] < 0 ? C[d] + nc : C[d] - nc;
+          else out = true;
         }
       }
+      if (out) continue;
+      // children of C that are ghost cells of this leaf (padded range, not interior)
+      int mask = 0;
+#pragma unroll
+      for (int dch = 0; dch < 8; ++dch) {
+        const int f[3] = {2 * C[0] + (dch & 1) - b[0], 2 * C[1] + ((dch >> 1) & 1) - b[1], 2 * C[2] + (dch >> 2) - b[2]};
+        const bool in = f[0] >= -G && f[0] < N + G && f[1] >= -G && f[1] < N + G && f[2] >= -G && f[2] < N + G;
+        const bool interior = (unsigned)f[0] < (unsigned)N && (unsigned)f[1] < (unsigned)N && (unsigned)f[2] < (unsigned)N;
+        if (in && !interior) mask |= 1 << dch;
+      }
+      if (!mask) continue;
+      const int tc = lookup(A, l - 1, Cw[0], Cw[1], Cw[2]);
+      if (tc == -2) atomicOr(A.status, 4u);  // two levels coarser: not 2:1 balanced
+      if (tc < 0) continue;                  // refined at level l-1: pass 1 filled these
+      const double* Cp =
+          A.U + (size_t)tc * F * S3 + (((Cw[2] & 7) + G) * S + ((Cw[1] & 7) + G)) * S + ((Cw[0] & 7) + G);
+      double slope[F][3];
+      const int st[3] = {1, S, S * S};
+#pragma unroll
+      for (int k = 0; k < F; ++k) {
+        const double* q = Cp + (size_t)k * S3;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
+          slope[k][d] = (rmul(dp, dm) <= 0.0) ? 0.0 : (fabs(dp) < fabs(dm) ? dp : dm);
+        }
+      }
+      for (int dch = 0; dch < 8; ++dch) {
+        if (!(mask & (1 << dch))) continue;
+        const int f[3] = {2 * C[0] + (dch & 1) - b[0], 2 * C[1] + ((dch >> 1) & 1) - b[1], 2 * C[2] + (dch >> 2) - b[2]};
+        const double off[3] = {(dch & 1) ? 0.25 : -0.25, ((dch >> 1) & 1) ? 0.25 : -0.25, (dch >> 2) ? 0.25 : -0.25};
+        double* dst = dstb + ((f[2] + G) * S + (f[1] + G)) * S + (f[0] + G);
+#pragma unroll
+        for (int k = 0; k < F; ++k) {
+          double v = Cp[(size_t)k * S3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) v = radd(v, rmul(slope[k][d], off[d]));
+          dst[(size_t)k * S3] = v;
+        }
+      }
+    }
+    if (A.bc == 0) continue;
+    // outflow: ghost cells outside the domain, clamped, one by one
+    for (int c = threadIdx.x; c < S3; c += blockDim.x) {
+      const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
+      const int gx = b[0] + lx, gy = b[1] + ly, gz = b[2] + lz;
+      if (gx >= 0 && gx < ncell && gy >= 0 && gy < ncell && gz >= 0 && gz < ncell) continue;
+      const int cx = bc_amr(gx, ncell, 1), cy = bc_amr(gy, ncell, 1), cz = bc_amr(gz, ncell, 1);
+      if (lookup(A, l, cx, cy, cz) != -2) continue;
+      const int px = cx >> 1, py = cy >> 1, pz = cz >> 1;
+      const int tc = lookup(A, l - 1, px, py, pz);
+      if (tc < 0) {
+        atomicOr(A.status, 4u);
+        continue;
+      }
+      const double* Cp = A.U + (size_t)tc * F * S3 + (((pz & 7) + G) * S + ((py & 7) + G)) * S + ((px & 7) + G);
+      const double off[3] = {(cx & 1) ? 0.25 : -0.25, (cy & 1) ? 0.25 : -0.25, (cz & 1) ? 0.25 : -0.25};
+      prolong_cell(Cp, off, dstb + c);
     }
   }
 }
@@ -240,8 +324,8 @@ int hydro_fill_ghosts_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_am
   const int cap = c->num_sms * 8;
   const int grid = B->n_sub < cap ? B->n_sub : cap;
   cudaStream_t st = (cudaStream_t)stream;
-  hyd::hydro_ghost_amr_kernel<1><<<grid, 256, 0, st>>>(A);
-  hyd::hydro_ghost_amr_kernel<2><<<grid, 256, 0, st>>>(A);
+  hyd::hydro_ghost_amr_kernel<<<grid, 256, 0, st>>>(A);
+  hyd::hydro_ghost_amr_prolong_kernel<<<grid, 256, 0, st>>>(A);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 

@@ -58,14 +58,15 @@ static int ensure_buf(double** buf, size_t* have, size_t need, const char* what)
 
 static int step_slots(const hydro_ctx* c, bool mixed) {
   // persistent CTAs: one per SM for FP64 (219 KB of shared memory each), two
-  // per SM in mixed precision (110 KB each)
+  // per SM in mixed precision (110 KB each), unless the autotuner chose fewer
+  if (c->slots_tuned[mixed ? 1 : 0] > 0) return c->slots_tuned[mixed ? 1 : 0];
   return mixed ? 2 * c->num_sms : c->num_sms;
 }
 
 int hydro_ctx_prepare(hydro_ctx* c, int n_sub) {
   int rc = ensure_status(c);
   if (rc) return rc;
-  const int slots = step_slots(c, true) > step_slots(c, false) ? step_slots(c, true) : step_slots(c, false);
+  const int slots = 2 * c->num_sms;  // the most any launch uses
   const int grid = n_sub < slots ? n_sub : slots;
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
@@ -153,6 +154,50 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
                         : hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
   return HYDRO_OK;
+}
+
+int hydro_autotune_step(hydro_ctx_t* c, const hydro_batch_t* B, double* dUdt, double* amax, int* slots_out,
+                        void* stream) {
+  if (!c || !B || B->n_sub <= 0 || !dUdt || !amax) return HYDRO_EINVAL;
+  const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
+  const int idx = mixed ? 1 : 0;
+  int rc = hydro_ctx_prepare(c, B->n_sub);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HYDRO_ECUDA;
+  // candidates: whole rounds of the batch over 1, 1.5 and 2 CTAs per SM
+  // (mixed), or 1 CTA per SM and the smallest grid with the same number of
+  // rounds (FP64); three timed launches each after one warm-up
+  int cand[4], nc = 0;
+  const int maxs = mixed ? 2 * c->num_sms : c->num_sms;
+  const int per[3] = {c->num_sms, (3 * c->num_sms) / 2, 2 * c->num_sms};
+  for (int i = 0; i < 3; ++i)
+    if (per[i] <= maxs) cand[nc++] = per[i];
+  const int rounds = (B->n_sub + maxs - 1) / maxs;
+  cand[nc++] = (B->n_sub + rounds - 1) / rounds;  // balanced: same rounds, fewer idle CTAs in the last one
+  float best = 1e30f;
+  int best_s = maxs;
+  for (int i = 0; i < nc && rc == HYDRO_OK; ++i) {
+    c->slots_tuned[idx] = cand[i];
+    rc = hydro_step(c, B, 0.0, dUdt, amax, nullptr, stream);
+    if (rc) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && rc == HYDRO_OK; ++r) rc = hydro_step(c, B, 0.0, dUdt, amax, nullptr, stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = HYDRO_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == HYDRO_OK && ms < best) {
+      best = ms;
+      best_s = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->slots_tuned[idx] = rc == HYDRO_OK ? best_s : 0;
+  if (slots_out) *slots_out = c->slots_tuned[idx];
+  return rc;
 }
 
 int hydro_update(hydro_ctx_t* c, const hydro_batch_t* B, const double* U0, const double* dUdt, double dt,

@@ -10,6 +10,7 @@ struct hydro_ctx {
   hydro_mode_t mode;
   int device;
   int num_sms;
+  int slots_tuned[2];    // persistent CTAs chosen by hydro_autotune_step (0: default), [fp64, mixed]
   unsigned* status;      // device word
   double* scratch;       // step scratch
   size_t scratch_bytes;

@@ -25,7 +25,7 @@ EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydr
            "hydro_step_static", "hydro_rk3_step", "hydro_rk3_graph_create", "hydro_rk3_graph_launch",
            "hydro_rk3_graph_state", "hydro_rk3_graph_destroy", "hydro_gate_data", "hydro_mlp_forward",
            "hydro_mlp_work_bytes", "hydro_mlp_loss_grad", "hydro_mlp_adam", "hydro_set_indicator",
-           "hydro_fill_ghosts_amr", "hydro_flux_correct_amr")
+           "hydro_fill_ghosts_amr", "hydro_flux_correct_amr", "hydro_autotune_step")
 HYDRO_ST_MESH = 0x4
 HYDRO_GATE_NPARAM, HYDRO_GATE_NIN = 2849, 54
 
@@ -103,6 +103,7 @@ def _lib(load: bool = True):
         L.hydro_mlp_adam.argtypes = [vp, vp, vp, vp, ip, C.c_float, vp]
         L.hydro_set_indicator.argtypes = [vp, vp, dp, vp]
         L.hydro_fill_ghosts_amr.argtypes = [vp, C.POINTER(Batch), vp, vp]
+        L.hydro_autotune_step.argtypes = [vp, C.POINTER(Batch), vp, vp, C.POINTER(C.c_int), vp]
         L.hydro_flux_correct_amr.argtypes = [vp, C.POINTER(Batch), vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy", "hydro_rk3_graph_destroy",
@@ -314,3 +315,11 @@ def hydro_fill_ghosts_amr(ctx, batch: Batch, mesh, stream=None):
 def hydro_flux_correct_amr(ctx, batch: Batch, mesh, face_flux, dUdt, stream=None):
     _check(_lib().hydro_flux_correct_amr(_cp(ctx), C.byref(batch), C.addressof(mesh.desc), _ptr(face_flux),
                                          _ptr(dUdt), _stream(stream)), "hydro_flux_correct_amr")
+
+
+def hydro_autotune_step(ctx, batch: Batch, dUdt, amax, stream=None) -> int:
+    """Pick and keep the fastest persistent grid for this batch; returns it."""
+    out = C.c_int()
+    _check(_lib().hydro_autotune_step(_cp(ctx), C.byref(batch), _ptr(dUdt), _ptr(amax), C.byref(out),
+                                      _stream(stream)), "hydro_autotune_step")
+    return out.value
