@@ -109,7 +109,7 @@ class ClockSampler:
 # 10 fields) at the average cost per evaluation on random discontinuous data,
 # 15,552 point fluxes, face sums, divergence and sources.  Bytes: the padded
 # state read once and dU/dt written once.
-ALGO = {"fp64_flops_per_subgrid_stage": 6558794.0, "bytes_per_subgrid_stage": 260520}
+ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 260520}
 # DRAM bytes per hydro_step launch on this workload from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), per precision form; None
 # until captured for the current kernel.
@@ -310,6 +310,80 @@ def amr_measure(args, H, dev, flush, precision, steps):
     return out
 
 
+def polytrope_measure(args, H, dev, flush):
+    """The rotating n = 1.5 polytrope (Lane-Emden profile, radius 0.5, rigid
+    rotation at 0.2 of the Keplerian rate, rotating frame Omega = 0.2, its
+    static gravitational field as an input array, ambient density 1e-10,
+    outflow).  Throughput of RK3 steps of both forms (graph replay) on
+    32,768 sub-grids (256^3); then both forms run --polytrope-steps steps on
+    --polytrope-nb^3 sub-grids from the same initial state, and each reports
+    the L1 density error against that state, the drift of the total angular
+    momentum about z and of the mass."""
+    import torch
+    from paper_2107_10987_gb300 import workloads as W
+    from paper_2107_10987_gb300.uniform import UniformRun
+    stream = torch.cuda.current_stream()
+    omega = 0.2
+    forms = (("mixed", H.HYDRO_PREC_MIXED), ("fp64", H.HYDRO_PREC_FP64))
+    out = {"workload": "rotating n=1.5 polytrope, 32,768 sub-grids of 8^3 (256^3 on [-1,1]^3), static gravity "
+                       "field input, rotating frame omega=0.2, ambient rho 1e-10, outflow", "omega": omega}
+
+    def timed(run, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for i in range(n):
+            flush.zero_()
+            ev[i][0].record(stream)
+            run.step(use_graph=True)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev])) / 1e3
+
+    nb = 32
+    Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
+    cells = Ui.shape[0] * 512
+    for name, prec in forms:
+        ctx = H.Context(GAMMA, omega)
+        H.hydro_set_mode(ctx, prec, 0.4)
+        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g)
+        steps = args.steps if name == "mixed" else max(2, args.steps // 10)
+        for _ in range(2):
+            run.step(use_graph=True)
+        t = timed(run, steps)
+        out[name] = {"value": cells / t, "ms_per_step": 1e3 * t, "steps_timed": steps,
+                     "status": H.hydro_status(ctx)}
+        run.close()
+        del run
+        ctx.close()
+        torch.cuda.empty_cache()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+
+    nb = args.polytrope_nb
+    Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
+    rho_ic = Ui[:, 0]
+    acc = {"sub_grids": nb ** 3, "cells": nb ** 3 * 512, "steps": args.polytrope_steps}
+    for name, prec in forms:
+        ctx = H.Context(GAMMA, omega)
+        H.hydro_set_mode(ctx, prec, 0.4)
+        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g)
+        c0 = run.sums()
+        t = 0.0
+        for _ in range(args.polytrope_steps):
+            run.step(use_graph=True)
+            t += run.last_dt()
+        c1 = run.sums()
+        rho = run.interior()[:, 0].cpu().numpy()
+        acc[name] = {"t": t, "l1_density": W.density_l1(rho, rho_ic, h),
+                     "angular_momentum_drift": float((c1[10] - c0[10]) / c0[10]),
+                     "mass_drift": float((c1[0] - c0[0]) / c0[0]), "status": H.hydro_status(ctx)}
+        run.close()
+        del run
+        ctx.close()
+        torch.cuda.empty_cache()
+    acc["l1_mixed_over_fp64"] = acc["mixed"]["l1_density"] / acc["fp64"]["l1_density"]
+    out["accuracy"] = acc
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -414,6 +488,8 @@ def gpu_arm(args):
                                                "blast shell of radius 0.3, leaf order shuffled (seed 1234), outflow",
                                    "mixed": amr_measure(args, H, dev, flush, H.HYDRO_PREC_MIXED, args.steps),
                                    "fp64": amr_measure(args, H, dev, flush, H.HYDRO_PREC_FP64, max(2, args.steps // 5))}
+        if args.polytrope:
+            line["rotating_polytrope"] = polytrope_measure(args, H, dev, flush)
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -487,6 +563,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-amr", dest="amr", action="store_false", help="skip the batched adaptive-mesh measurement")
+    ap.add_argument("--no-polytrope", dest="polytrope", action="store_false",
+                    help="skip the rotating-polytrope measurement")
+    ap.add_argument("--polytrope-nb", type=int, default=16,
+                    help="sub-grids per axis of the polytrope accuracy runs (32: the full 256^3 mesh)")
+    ap.add_argument("--polytrope-steps", type=int, default=100)
     ap.add_argument("--precision", default="all", choices=["all", "both", "mixed", "fp64", "gated"],
                     help="all: time the plain FP64 form, the mixed form with the learned indicator, then the "
                          "mixed form (reported as value); both: FP64 then mixed")

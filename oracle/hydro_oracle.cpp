@@ -422,6 +422,15 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
   //          conserved by the fluxes alone.
   //   frame: ds/dt += -omega z_hat x s = (omega s_y, -omega s_x, 0); the same
   //          rotation of components applies to the spin vector z (reading).
+  //          The face torques above take the momentum flux s u_n with the grid
+  //          velocity w = -omega z_hat x x = (omega y, -omega x, 0) inside u;
+  //          the part s w_n is not a symmetric stress, and its torque belongs
+  //          to the change of frame, not to an exchange between orbital and
+  //          spin angular momentum.  dz/dt += w(x_c) x s removes it (for a
+  //          uniform stream exactly), so that sum (x_c x s + z)_z h^3, which
+  //          the frame source on s alone changes by
+  //          -omega sum (x_c s_x + y_c s_y) h^3, is conserved for omega != 0
+  //          as it is in the continuum (reading).
   //   gravity (optional): ds/dt += rho g, dE/dt += s.g.
   const T inv_h = T(1.0 / h);
   const T om = T(P.omega);
@@ -458,6 +467,13 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
         du[SY] = du[SY] - om * s[0];
         du[ZX] = du[ZX] + om * zz[1];
         du[ZY] = du[ZY] - om * zz[0];
+        {
+          const T xc = T(origin[0]) + T(h) * T(x + 0.5), yc = T(origin[1]) + T(h) * T(y + 0.5);
+          const T wx = om * yc, wy = -(om * xc);  // w_z = 0
+          du[ZX] = du[ZX] + wy * s[2];
+          du[ZY] = du[ZY] - wx * s[2];
+          du[ZZ] = du[ZZ] + (wx * s[1] - wy * s[0]);
+        }
         if (g) {
           const T gv[3] = {g[0 * N3 + c], g[1 * N3 + c], g[2 * N3 + c]};
           for (int m = 0; m < 3; ++m) du[SX + m] = du[SX + m] + rho * gv[m];

@@ -224,6 +224,17 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
       du[SY] = du[SY] - om * sx;
       du[ZX] = du[ZX] + om * Us[ZY * S3 + uc];
       du[ZY] = du[ZY] - om * Us[ZX * S3 + uc];
+      {
+        // spin source w(x_c) x s, w = -omega z_hat x x_c: removes the torque
+        // that the frame part s w_n of the momentum flux leaves in the face
+        // torques, so that sum (x_c x s + z)_z is conserved for omega != 0
+        const double xc = __dadd_rn(o[0], __dmul_rn(hd, x + 0.5));
+        const double yc = __dadd_rn(o[1], __dmul_rn(hd, y + 0.5));
+        const double wx = om * yc, wy = -(om * xc);
+        du[ZX] = du[ZX] + wy * sz;
+        du[ZY] = du[ZY] - wx * sz;
+        du[ZZ] = du[ZZ] + (wx * sy - wy * sx);
+      }
       if (A.g) {
         const double* gs = A.g + (size_t)s * 3 * N3;
         const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];

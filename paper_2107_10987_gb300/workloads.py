@@ -159,17 +159,19 @@ def box_to_subgrids(Ug: np.ndarray, N: int = 8):
     return out
 
 
-def lane_emden(n: float, dxi: float = 1e-4):
-    """Lane-Emden solution theta(xi) of index n (theta'' + 2 theta'/xi + theta^n = 0,
+def lane_emden_table(n: float, dxi: float = 1e-4):
+    """Lane-Emden solution of index n (theta'' + 2 theta'/xi + theta^n = 0,
     theta(0) = 1, theta'(0) = 0), integrated with classical RK4 from a series
-    start until theta = 0.  Returns (xi1, -xi1^2 theta'(xi1), xi grid, theta)."""
+    start until theta = 0.  Returns (xi, theta, m) on the grid up to the first
+    zero xi1, with the mass function m(xi) = -xi^2 theta'(xi) (the integral of
+    x^2 theta^n from 0 to xi)."""
     def rhs(x, y):
         th, dth = y
         return np.array([dth, -max(th, 0.0) ** n - 2.0 * dth / x])
 
     x = dxi
     y = np.array([1.0 - x * x / 6.0 + n * x ** 4 / 120.0, -x / 3.0 + n * x ** 3 / 30.0])
-    xs, ths = [0.0, x], [1.0, y[0]]
+    xs, ths, ms = [0.0, x], [1.0, y[0]], [0.0, -x * x * y[1]]
     while y[0] > 0.0:
         k1 = rhs(x, y)
         k2 = rhs(x + dxi / 2, y + dxi / 2 * k1)
@@ -182,11 +184,82 @@ def lane_emden(n: float, dxi: float = 1e-4):
             dth1 = y[1] + f * (yn[1] - y[1])
             xs.append(x1)
             ths.append(0.0)
-            return x1, -x1 * x1 * dth1, np.array(xs), np.array(ths)
+            ms.append(-x1 * x1 * dth1)
+            return np.array(xs), np.array(ths), np.array(ms)
         x, y = x + dxi, yn
         xs.append(x)
         ths.append(y[0])
+        ms.append(-x * x * y[1])
     raise RuntimeError("unreachable")
+
+
+def lane_emden(n: float, dxi: float = 1e-4):
+    """Returns (xi1, -xi1^2 theta'(xi1), xi grid, theta) of lane_emden_table."""
+    xs, ths, ms = lane_emden_table(n, dxi)
+    return xs[-1], ms[-1], xs, ths
+
+
+def polytrope_model(n: float = 1.5, R: float = 0.5, rho_c: float = 1.0, G: float = 1.0, dxi: float = 1e-4):
+    """A polytrope p = K rho^(1+1/n) of radius R and central density rho_c in
+    hydrostatic equilibrium: rho = rho_c theta(r/alpha)^n with alpha = R/xi1,
+    K from alpha^2 = (n+1) K rho_c^(1/n-1) / (4 pi G), enclosed mass
+    M(r) = 4 pi alpha^3 rho_c m(r/alpha), total M, and the Keplerian rate at
+    the surface Omega_K = sqrt(G M / R^3)."""
+    xs, ths, ms = lane_emden_table(n, dxi)
+    alpha = R / xs[-1]
+    K = 4.0 * math.pi * G * alpha * alpha * rho_c ** (1.0 - 1.0 / n) / (n + 1.0)
+    M = 4.0 * math.pi * alpha ** 3 * rho_c * ms[-1]
+    return {"n": n, "R": R, "rho_c": rho_c, "G": G, "alpha": alpha, "K": K, "M": M,
+            "omega_K": math.sqrt(G * M / R ** 3), "xi": xs, "theta": ths, "m": ms}
+
+
+def polytrope_point(model, X, Y, Z, spin: float = 0.2, rho_amb: float = 1e-10):
+    """Density, inertial velocity [3,...], pressure and the static gravitational
+    acceleration [3,...] of the model at points (X, Y, Z).  Inside r < R the
+    star rotates rigidly about +z at spin * Omega_K; the ambient medium is at
+    rest with density rho_amb on the same polytropic K.  g = -G M(r) x / r^3
+    (zero at the centre)."""
+    mo = model
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    xi = r / mo["alpha"]
+    th = np.interp(xi, mo["xi"], mo["theta"], right=0.0)
+    rho = np.maximum(mo["rho_c"] * th ** mo["n"], rho_amb)
+    p = mo["K"] * rho ** (1.0 + 1.0 / mo["n"])
+    w = spin * mo["omega_K"]
+    inside = r < mo["R"]
+    v = np.stack([np.where(inside, -w * Y, 0.0), np.where(inside, w * X, 0.0), np.zeros_like(X)])
+    Mr = 4.0 * math.pi * mo["alpha"] ** 3 * mo["rho_c"] * np.interp(xi, mo["xi"], mo["m"], right=mo["m"][-1])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f = np.where(r > 0.0, -mo["G"] * Mr / (r * r * r), 0.0)
+    g = np.stack([f * X, f * Y, f * Z])
+    return rho, v, p, g
+
+
+def rotating_polytrope(nb: int, gamma: float = 5.0 / 3.0, spin: float = 0.2, rho_amb: float = 1e-10,
+                       n: float = 1.5, R: float = 0.5, N: int = 8, L: float = 2.0):
+    """Rotating n = 1.5 polytrope on a uniform octree level of nb^3 sub-grids
+    of N^3 cells covering [-L/2, L/2]^3 (nb = 32: 32,768 sub-grids, 256^3
+    cells).  Cell averages are the point values at cell centres.  Returns
+    (U [n_sub][NF][N][N][N] interiors, g [n_sub][3][N][N][N], origins
+    [n_sub][3], h, model); sub-grid order as uniform_mesh."""
+    model = polytrope_model(n, R)
+    o, h = uniform_mesh(nb, N, L)
+    c = (np.arange(N) + 0.5) * h
+    ns = o.shape[0]
+    X = np.broadcast_to(o[:, 0, None, None, None] + c[None, None, None, :], (ns, N, N, N))
+    Y = np.broadcast_to(o[:, 1, None, None, None] + c[None, None, :, None], (ns, N, N, N))
+    Z = np.broadcast_to(o[:, 2, None, None, None] + c[None, :, None, None], (ns, N, N, N))
+    rho, v, p, g = polytrope_point(model, X, Y, Z, spin, rho_amb)
+    U = np.ascontiguousarray(np.moveaxis(conserved_from_primitive(rho, v, p, gamma), 0, 1))
+    g = np.ascontiguousarray(np.moveaxis(g, 0, 1))
+    return U, g, o, h, model
+
+
+def density_l1(rho, rho_ic, h, R: float = 0.5) -> float:
+    """Density error sum |rho_IC - rho| h^3 / V over the whole domain, with V the
+    initial volume 4 pi R^3 / 3 of the star (the rotating-star error measure
+    of Sec. VI, read with an absolute value)."""
+    return float(np.sum(np.abs(np.asarray(rho_ic) - np.asarray(rho))) * h ** 3 / (4.0 * math.pi * R ** 3 / 3.0))
 
 
 def sedov_box_at(n: int, E_blast: float, center, gamma: float = 5.0 / 3.0, rho0: float = 1.0, p0: float = 1e-5,

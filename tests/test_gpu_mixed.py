@@ -60,14 +60,14 @@ def gpu_step(H, ctx, U, origin, h, g=None):
 
 
 def check_budget(orc, P, U, origin, h, g, dU, am):
-    from oracle.compare import field_scales
-    ref, amo, _ = orc.step(P, U, origin, h, g)
+    from oracle.compare import field_scales, mixed_budget
+    ref, amo, _, faces = orc.step(P, U, origin, h, g, faces=True)
     pert, _, _ = orc.step(P, U.astype(np.float32).astype(np.float64), origin, h, g)
+    budget, sens = mixed_budget(ref, pert, faces, np.max(h))
     sc = field_scales(ref, np.max(h))[None, :, None, None, None]
     err = (np.abs(dU - ref) / sc).max(axis=(0, 2, 3, 4))
-    sens = (np.abs(pert - ref) / sc).max(axis=(0, 2, 3, 4))
     assert np.all(np.isfinite(dU))
-    assert np.all(err <= 8 * sens + 4e-7), (err, sens)
+    assert np.all(err <= budget), (err, budget)
     assert np.allclose(am, amo, rtol=1e-6, atol=0)
     return err, sens
 
