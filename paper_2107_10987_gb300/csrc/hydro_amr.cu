@@ -66,11 +66,16 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
       if ((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N) continue;
       const int gx = bc_amr(bx + lx, ncell, A.bc), gy = bc_amr(by + ly, ncell, A.bc), gz = bc_amr(bz + lz, ncell, A.bc);
       const int t = lookup(A, l, gx, gy, gz);
+      // pass 1 reads interior cells only and writes ghost cells only: all
+      // loads of a cell go out (read-only path) before its stores
       {
         if (t >= 0) {
           const double* src = A.U + (size_t)t * F * S3 + (((gz & 7) + G) * S + ((gy & 7) + G)) * S + ((gx & 7) + G);
+          double v[F];
 #pragma unroll
-          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c] = src[(size_t)k * S3];
+          for (int k = 0; k < F; ++k) v[k] = __ldg(src + (size_t)k * S3);
+#pragma unroll
+          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c] = v[k];
         } else if (t == -1) {
           const double* kid[8];
           bool ok = true;
@@ -82,13 +87,16 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
                      ((fx & 7) + G);
           }
           if (!ok) atomicOr(A.status, 4u);
+          double v[F];
 #pragma unroll
           for (int k = 0; k < F; ++k) {
             const size_t o = (size_t)k * S3;
-            const double acc = radd(radd(radd(kid[0][o], kid[1][o]), radd(kid[2][o], kid[3][o])),
-                                    radd(radd(kid[4][o], kid[5][o]), radd(kid[6][o], kid[7][o])));
-            dst[o + c] = rmul(acc, 0.125);
+            const double acc = radd(radd(radd(__ldg(kid[0] + o), __ldg(kid[1] + o)), radd(__ldg(kid[2] + o), __ldg(kid[3] + o))),
+                                    radd(radd(__ldg(kid[4] + o), __ldg(kid[5] + o)), radd(__ldg(kid[6] + o), __ldg(kid[7] + o))));
+            v[k] = rmul(acc, 0.125);
           }
+#pragma unroll
+          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c] = v[k];
         }
       }
     }
@@ -155,11 +163,12 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
       if (tc < 0) continue;                  // refined at level l-1: pass 1 filled these
       const double* Cp =
           A.U + (size_t)tc * F * S3 + (((Cw[2] & 7) + G) * S + ((Cw[1] & 7) + G)) * S + ((Cw[0] & 7) + G);
-      double slope[F][3];
+      double slope[F][3], centre[F];
       const int st[3] = {1, S, S * S};
 #pragma unroll
       for (int k = 0; k < F; ++k) {
         const double* q = Cp + (size_t)k * S3;
+        centre[k] = q[0];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
         double* dst = dstb + ((f[2] + G) * S + (f[1] + G)) * S + (f[0] + G);
 #pragma unroll
         for (int k = 0; k < F; ++k) {
-          double v = Cp[(size_t)k * S3];
+          double v = centre[k];
 #pragma unroll
           for (int d = 0; d < 3; ++d) v = radd(v, rmul(slope[k][d], off[d]));
           dst[(size_t)k * S3] = v;

@@ -121,21 +121,40 @@ __device__ __forceinline__ int bc_map(int gpos, int n, int bc) {
   return gpos < 0 ? 0 : (gpos >= n ? n - 1 : gpos);
 }
 
+// The kernel reads only interior cells and writes only ghost cells, so the
+// two sets never overlap: all loads of a batch of cells are issued before
+// their stores (through the read-only path), instead of one dependent
+// load-store pair per field.
+constexpr int kGhostBatch = 2;
+
 __global__ void __launch_bounds__(256) hydro_ghost_uniform_kernel(GhostArgs A) {
   const int nx = A.nbx * N, ny = A.nby * N, nz = A.nbz * N;
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int kx = s % A.nbx, ky = (s / A.nbx) % A.nby, kz = s / (A.nbx * A.nby);
     double* dst = A.U + (size_t)s * F * S3;
-    for (int c = threadIdx.x; c < S3; c += blockDim.x) {
-      const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
-      if ((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N) continue;
-      const int gx = bc_map(kx * N + lx, nx, A.bc), gy = bc_map(ky * N + ly, ny, A.bc);
-      const int gz = bc_map(kz * N + lz, nz, A.bc);
-      const int os = ((gz >> 3) * A.nby + (gy >> 3)) * A.nbx + (gx >> 3);
-      const int oc = (((gz & 7) + G) * S + ((gy & 7) + G)) * S + ((gx & 7) + G);
-      const double* src = A.U + (size_t)os * F * S3 + oc;
+    for (int c0 = threadIdx.x; c0 < S3; c0 += kGhostBatch * blockDim.x) {
+      double v[kGhostBatch][F];
+      bool ghost[kGhostBatch];
 #pragma unroll
-      for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c] = src[(size_t)k * S3];
+      for (int j = 0; j < kGhostBatch; ++j) {
+        const int c = c0 + j * blockDim.x;
+        const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
+        ghost[j] = c < S3 && !((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N);
+        if (ghost[j]) {
+          const int gx = bc_map(kx * N + lx, nx, A.bc), gy = bc_map(ky * N + ly, ny, A.bc);
+          const int gz = bc_map(kz * N + lz, nz, A.bc);
+          const int os = ((gz >> 3) * A.nby + (gy >> 3)) * A.nbx + (gx >> 3);
+          const int oc = (((gz & 7) + G) * S + ((gy & 7) + G)) * S + ((gx & 7) + G);
+          const double* src = A.U + (size_t)os * F * S3 + oc;
+#pragma unroll
+          for (int k = 0; k < F; ++k) v[j][k] = __ldg(src + (size_t)k * S3);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kGhostBatch; ++j)
+        if (ghost[j])
+#pragma unroll
+          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c0 + j * blockDim.x] = v[j][k];
     }
   }
 }
