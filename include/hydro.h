@@ -167,6 +167,21 @@ int hydro_dt(hydro_ctx_t* ctx, const double* amax, const double* h, int n_sub, d
  * (HYDRO_BC_PERIODIC) or clamped to the nearest interior cell
  * (HYDRO_BC_OUTFLOW).  Ghost exchange between leaf sub-grids, Sec. IV-A.2.
  * Requires B->n_sub == nbx*nby*nbz.  Pure copies (bitwise). */
+/* Interior cells between a compact array and the batch's padded state.  The
+ * compact layout holds only the N^3 interior cells of every sub-grid,
+ * interior[n_sub][F][N][N][N] FP64 (x fastest; 40,960 bytes per sub-grid
+ * instead of the 219,520 of the padded state): the form in which a caller
+ * keeps or exchanges the evolved variables of the leaf sub-grids (Sec.
+ * III-B), the ghost cells being derived from them by the ghost fill.
+ *   hydro_scatter_interior: B->U's interior cells <- interior (ghost cells
+ *     untouched);
+ *   hydro_gather_interior:  interior <- B->U's interior cells.
+ * interior: device, caller-owned, 16-byte aligned, not overlapping B->U.
+ * n_sub == 0 is a no-op; NULL or misaligned pointers give HYDRO_EINVAL.
+ * Pure copies (bitwise), asynchronous on the stream. */
+int hydro_scatter_interior(hydro_ctx_t* ctx, const hydro_batch_t* B, const double* interior, void* stream);
+int hydro_gather_interior(hydro_ctx_t* ctx, const hydro_batch_t* B, double* interior, void* stream);
+
 int hydro_fill_ghosts_uniform(hydro_ctx_t* ctx, const hydro_batch_t* B, int nbx, int nby, int nbz, int bc,
                               void* stream);
 

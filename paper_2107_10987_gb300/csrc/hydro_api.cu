@@ -19,6 +19,7 @@ cudaError_t launch_update(const double* U, double* Uout, const double* U0, const
                           int num_sms, cudaStream_t st);
 cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, double* out, cudaStream_t st);
 cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st);
+cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, cudaStream_t st);
 cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
                         double* sums, cudaStream_t st);
 }  // namespace hyd
@@ -237,6 +238,23 @@ int hydro_fill_ghosts_uniform(hydro_ctx_t* c, const hydro_batch_t* B, int nbx, i
   cudaError_t e = hyd::launch_ghost_uniform(B->U, nbx, nby, nbz, bc, c->num_sms, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_fill_ghosts_uniform");
   return HYDRO_OK;
+}
+
+static int interior_copy(hydro_ctx_t* c, const hydro_batch_t* B, const double* I, bool scatter, void* stream) {
+  if (!c || !B || B->n_sub < 0) return HYDRO_EINVAL;
+  if (B->n_sub == 0) return HYDRO_OK;
+  if (!B->U || !I || !aligned16(I)) return HYDRO_EINVAL;
+  cudaError_t e = hyd::launch_interior(B->U, const_cast<double*>(I), B->n_sub, scatter, c->num_sms, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, scatter ? "hydro_scatter_interior" : "hydro_gather_interior");
+  return HYDRO_OK;
+}
+
+int hydro_scatter_interior(hydro_ctx_t* c, const hydro_batch_t* B, const double* interior, void* stream) {
+  return interior_copy(c, B, interior, true, stream);
+}
+
+int hydro_gather_interior(hydro_ctx_t* c, const hydro_batch_t* B, double* interior, void* stream) {
+  return interior_copy(c, B, interior, false, stream);
 }
 
 int hydro_conserved_sums(hydro_ctx_t* c, const hydro_batch_t* B, double* sums, void* stream) {

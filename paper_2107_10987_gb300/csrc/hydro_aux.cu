@@ -159,6 +159,41 @@ __global__ void __launch_bounds__(256) hydro_ghost_uniform_kernel(GhostArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Interior copies between the compact layout [n_sub][F][N][N][N] and the
+// ghost-padded state: one thread per two neighbouring cells along x (one
+// 16-byte access on the compact side).
+template <bool kScatter>
+__global__ void __launch_bounds__(256) hydro_interior_kernel(double* U, double* I, long long pairs) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < pairs;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long e = 2 * i;  // compact element index, x even
+    const int c = (int)(e % N3);
+    const long long sk = e / N3;  // s * F + field
+    const int x = c & (N - 1), y = (c >> 3) & (N - 1), z = c >> 6;
+    double* u = U + sk * S3 + ((z + G) * S + (y + G)) * S + (x + G);
+    double2* q = reinterpret_cast<double2*>(I + e);
+    if (kScatter) {
+      const double2 v = *q;
+      u[0] = v.x;
+      u[1] = v.y;
+    } else {
+      *q = make_double2(u[0], u[1]);
+    }
+  }
+}
+
+cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, cudaStream_t st) {
+  const long long pairs = (long long)n_sub * F * N3 / 2;
+  const long long want = (pairs + 255) / 256;
+  const int blocks = (int)(want < (long long)num_sms * 16 ? want : (long long)num_sms * 16);
+  if (scatter)
+    hydro_interior_kernel<true><<<blocks, 256, 0, st>>>(U, I, pairs);
+  else
+    hydro_interior_kernel<false><<<blocks, 256, 0, st>>>(U, I, pairs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st) {
   const int n_sub = nbx * nby * nbz;
   GhostArgs A{U, nbx, nby, nbz, bc, n_sub};

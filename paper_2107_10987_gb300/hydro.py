@@ -83,6 +83,8 @@ def _lib(load: bool = True):
         L.hydro_fill_ghosts_uniform.argtypes = [vp, C.POINTER(Batch), ip, ip, ip, ip, vp]
         L.hydro_conserved_sums.argtypes = [vp, C.POINTER(Batch), vp, vp]
         L.hydro_status.argtypes = [vp, C.POINTER(C.c_uint32)]
+        L.hydro_scatter_interior.argtypes = [vp, C.POINTER(Batch), vp, vp]
+        L.hydro_gather_interior.argtypes = [vp, C.POINTER(Batch), vp, vp]
         L.hydro_strerror.argtypes = [ip]
         L.hydro_strerror.restype = C.c_char_p
         L.hydro_last_cuda_error.argtypes = []
@@ -195,6 +197,18 @@ def hydro_dt(ctx, amax, h, n_sub: int, cfl: float, dt_out, stream=None):
 def hydro_fill_ghosts_uniform(ctx, batch: Batch, nbx: int, nby: int, nbz: int, bc: int, stream=None):
     _check(_lib().hydro_fill_ghosts_uniform(_cp(ctx), C.byref(batch), nbx, nby, nbz, bc, _stream(stream)),
            "hydro_fill_ghosts_uniform")
+
+
+def hydro_scatter_interior(ctx, batch: Batch, interior, stream=None):
+    """interior: [n_sub][F][N][N][N] float64 CUDA tensor -> the batch's interior cells."""
+    _check(_lib().hydro_scatter_interior(_cp(ctx), C.byref(batch), _ptr(interior), _stream(stream)),
+           "hydro_scatter_interior")
+
+
+def hydro_gather_interior(ctx, batch: Batch, interior, stream=None):
+    """The batch's interior cells -> interior [n_sub][F][N][N][N] float64 CUDA tensor."""
+    _check(_lib().hydro_gather_interior(_cp(ctx), C.byref(batch), _ptr(interior), _stream(stream)),
+           "hydro_gather_interior")
 
 
 def hydro_conserved_sums(ctx, batch: Batch, sums, stream=None):

@@ -27,14 +27,14 @@ class UniformRun:
         n = U.shape[0]
         assert n == self.nb[0] * self.nb[1] * self.nb[2]
         a = torch.zeros((n, 10, 14, 14, 14), dtype=torch.float64, device=device)
-        if U.shape[-1] == 8:
-            a[:, :, 3:11, 3:11, 3:11] = U.to(device)
-        else:
-            a.copy_(U)
         self.bufs = (a, torch.zeros_like(a))
         self.origin = torch.as_tensor(np.asarray(origin, dtype=np.float64)).to(device).contiguous()
         self.h = torch.as_tensor(np.broadcast_to(np.asarray(h, dtype=np.float64), (n,)).copy()).to(device)
         self.g = torch.as_tensor(g).to(device).contiguous() if g is not None else None
+        if U.shape[-1] == 8:
+            H.hydro_scatter_interior(ctx, H.make_batch(a, self.origin, self.h), U.to(device).contiguous())
+        else:
+            a.copy_(U)
         self.dU = torch.empty((n, 10, 8, 8, 8), dtype=torch.float64, device=device)
         self.am = torch.empty(n, dtype=torch.float64, device=device)
         self.dt = torch.empty(1, dtype=torch.float64, device=device)
@@ -72,7 +72,10 @@ class UniformRun:
         return self.sums_buf.cpu().numpy()
 
     def interior(self) -> torch.Tensor:
-        return self.U[:, :, 3:11, 3:11, 3:11]
+        """The current interiors, [n][F][N][N][N] (a new tensor)."""
+        out = torch.empty((self.n, 10, 8, 8, 8), dtype=torch.float64, device=self.U.device)
+        H.hydro_gather_interior(self.ctx, self.batches[self.parity], out)
+        return out
 
     def close(self):
         if self.graph is not None:

@@ -330,3 +330,31 @@ def test_rk3_graph_replay_equals_direct_launches(H, mixed):
     ctx = fresh()
     got, t, _ = run_rk3_gpu(H, ctx, Ug, h, lo, "outflow", nb, steps=4)
     assert np.array_equal(got, mesh.join(graph_state, 2, 2, 2))
+
+
+def test_interior_scatter_gather(H):
+    """Compact interiors <-> padded state: bitwise copies of the interior
+    cells, ghost cells untouched, and argument checks."""
+    dev = "cuda"
+    rng = np.random.default_rng(17)
+    n = 37
+    U = torch.tensor(rng.normal(size=(n, 10, 14, 14, 14)), device=dev)
+    before = U.clone()
+    I = torch.tensor(rng.normal(size=(n, 10, 8, 8, 8)), device=dev)
+    o = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    hh = torch.full((n,), 0.1, dtype=torch.float64, device=dev)
+    ctx = H.Context(GAMMA, 0.0)
+    B = H.make_batch(U, o, hh)
+    H.hydro_scatter_interior(ctx, B, I)
+    torch.cuda.synchronize()
+    assert torch.equal(U[:, :, 3:11, 3:11, 3:11], I)
+    ghost = torch.ones_like(U, dtype=torch.bool)
+    ghost[:, :, 3:11, 3:11, 3:11] = False
+    assert torch.equal(U[ghost], before[ghost])
+    out = torch.full_like(I, float("nan"))
+    H.hydro_gather_interior(ctx, B, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, I)
+    flat = torch.empty(I.numel() + 1, dtype=torch.float64, device=dev)
+    with pytest.raises(RuntimeError):
+        H.hydro_gather_interior(ctx, B, flat[1:])  # 8-byte offset: not 16-byte aligned
