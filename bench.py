@@ -53,6 +53,24 @@ def dist_env():
     return ws, rk, lr
 
 
+def max_over_ranks(values: dict, device=None) -> dict:
+    """Each timing's largest value over the ranks of the job (the slowest
+    rank sets the job's time); unchanged for a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return dict(values)
+    keys = sorted(values)
+    t = torch.tensor([float(values[k]) for k in keys], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return dict(zip(keys, t.tolist()))
+
+
+def job_rate(units_per_rank: float, world_size: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return units_per_rank * world_size / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -426,11 +444,7 @@ def gpu_arm(args):
             res[name]["clocks"] = clk.summary()
         else:
             res[name] = run_form(args, H, dev, forms[name], flush, ind)
-        if ws > 1:
-            for key in ("t_dev", "t_e2e"):
-                t = torch.tensor([res[name][key]], dtype=torch.float64, device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                res[name][key] = t.item()
+        res[name].update(max_over_ranks({k: res[name][k] for k in ("t_dev", "t_e2e", "t_graph")}, dev))
 
     if rk == 0:
         work = algorithmic_work()
@@ -443,7 +457,7 @@ def gpu_arm(args):
         peak = FP64_PEAK_TFLOPS if head == "fp64" else FP32_PEAK_TFLOPS
         achieved = flops / r["kern_s"] / 1e12
         line = {
-            "metric": METRIC, "value": CELLS * args.steps * ws / r["t_dev"], "unit": UNIT, "n_gpus": ws,
+            "metric": METRIC, "value": job_rate(CELLS * args.steps, ws, r["t_dev"]), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["t_dev"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if head == "fp64" else "f32+f64 (mixed)", "data": "synthetic",
@@ -454,8 +468,8 @@ def gpu_arm(args):
                                     "and update" if head != "fp64" else "fp64 (plain)",
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MB write) between timed steps, outside the timed events"},
-            "cell_stage_updates_per_s": 3 * CELLS * args.steps * ws / r["t_dev"],
-            "graph_replay": {"value": CELLS * args.steps * ws / r["t_graph"],
+            "cell_stage_updates_per_s": 3 * job_rate(CELLS * args.steps, ws, r["t_dev"]),
+            "graph_replay": {"value": job_rate(CELLS * args.steps, ws, r["t_graph"]),
                              "ms_per_step": 1e3 * r["t_graph"] / args.steps,
                              "note": "the same RK3 step captured once into a CUDA graph (hydro_rk3_graph_*)"},
             "wall_s_timed_region": r["wall"],
@@ -466,7 +480,7 @@ def gpu_arm(args):
                                          if head != "fp64" else "nominal GB300 FP64 from the profiling recipe"),
                          "flops_counted": "algorithmic ops of the method (oracle count), each op one flop",
                          "hbm_frac": (bytes_launch / r["kern_s"] / 1e9) / pk["hbm_gbs"] if "hbm_gbs" in pk else None},
-            "e2e": {"value": CELLS * args.steps * ws / r["t_e2e"], "unit": UNIT,
+            "e2e": {"value": job_rate(CELLS * args.steps, ws, r["t_e2e"]), "unit": UNIT,
                     "h2d_bytes_per_step": r["bytes_step"], "d2h_bytes_per_step": r["bytes_step"]},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": r["clocks"],
@@ -476,8 +490,8 @@ def gpu_arm(args):
             f = res["fp64"]
             a64 = flops / f["kern_s"] / 1e12
             line["plain_fp64"] = {
-                "value": CELLS * args.steps * ws / f["t_dev"], "ms_per_step": 1e3 * f["t_dev"] / args.steps,
-                "kernel_ms": 1e3 * f["kern_s"], "e2e": CELLS * args.steps * ws / f["t_e2e"],
+                "value": job_rate(CELLS * args.steps, ws, f["t_dev"]), "ms_per_step": 1e3 * f["t_dev"] / args.steps,
+                "kernel_ms": 1e3 * f["kern_s"], "e2e": job_rate(CELLS * args.steps, ws, f["t_e2e"]),
                 "roofline": {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": a64 / FP64_PEAK_TFLOPS,
                              "traffic": work.get("dram_bytes_per_launch_scaled", {}).get("fp64")}}
@@ -488,7 +502,7 @@ def gpu_arm(args):
         if "gated" in res:
             gr = res["gated"]
             line["mixed_with_indicator"] = {
-                "value": CELLS * args.steps * ws / gr["t_dev"], "ms_per_step": 1e3 * gr["t_dev"] / args.steps,
+                "value": job_rate(CELLS * args.steps, ws, gr["t_dev"]), "ms_per_step": 1e3 * gr["t_dev"] / args.steps,
                 "kernel_ms": 1e3 * gr["kern_s"],
                 "speedup_vs_mixed": r["t_dev"] / gr["t_dev"] if head == "mixed" else None,
                 "max_rel_density_diff_vs_fp64": ((gr["rho"] - res["fp64"]["rho"]).abs().max().item() /

@@ -28,3 +28,56 @@ def test_reference_arm_json_line(oracle_mod):
     assert line["impl"] == "reference" and line["value"] > 0
     for k in ("metric", "unit", "cpu_baseline", "e2e", "config", "higher_is_better"):
         assert k in line
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        # per-rank timings of a replicated step: the slowest rank sets the job's time
+        got = bench.max_over_ranks({"t_dev": 1.0 + 0.5 * rank, "t_e2e": 3.0 - rank, "t_graph": 2.0})
+        dist.barrier()
+        q.put((rank, got, bench.job_rate(262144 * 20, world, got["t_dev"])))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    """The N>1 path (independent replicas, one per rank): every rank sees the
+    largest time of each timing, and the whole-job value counts the units
+    of all ranks over that time."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, got, rate in out:
+        assert got == {"t_dev": 1.5, "t_e2e": 3.0, "t_graph": 2.0}
+        assert rate == pytest.approx(262144 * 20 * 2 / 1.5)
+
+
+def test_single_process_timings_unchanged():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks({"t_dev": 0.25}) == {"t_dev": 0.25}
+    assert bench.job_rate(100.0, 1, 0.5) == 200.0
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
