@@ -271,7 +271,7 @@ def run_form(args, H, dev, precision, flush, indicator=None):
     return out
 
 
-def amr_measure(args, H, dev, flush, precision, steps):
+def amr_measure(args, H, dev, flush, precision, steps, indicator=None):
     """The batched adaptive configuration: ~4,096 leaves at levels 3-6 around a
     blast shell, leaf order shuffled.  Times one RK3 step (direct launches and
     graph replay) and the step kernel alone as one persistent launch over all
@@ -285,6 +285,8 @@ def amr_measure(args, H, dev, flush, precision, steps):
     cells = len(lev) * 512
     ctx = H.Context(GAMMA, 0.0)
     H.hydro_set_mode(ctx, precision, 0.4)
+    if indicator is not None:
+        H.hydro_set_indicator(ctx, indicator[0], indicator[1])
     stream = torch.cuda.current_stream()
     out = {"leaves": len(lev), "cells": cells, "levels": {int(l): int((lev == l).sum()) for l in np.unique(lev)}}
 
@@ -339,7 +341,7 @@ def amr_measure(args, H, dev, flush, precision, steps):
     return out
 
 
-def polytrope_measure(args, H, dev, flush):
+def polytrope_measure(args, H, dev, flush, indicator=None):
     """The rotating n = 1.5 polytrope (Lane-Emden profile, radius 0.5, rigid
     rotation at 0.2 of the Keplerian rate, rotating frame Omega = 0.2, its
     static gravitational field as an input array, ambient density 1e-10,
@@ -347,13 +349,24 @@ def polytrope_measure(args, H, dev, flush):
     32,768 sub-grids (256^3); then both forms run --polytrope-steps steps on
     --polytrope-nb^3 sub-grids from the same initial state, and each reports
     the L1 density error against that state, the drift of the total angular
-    momentum about z and of the mass."""
+    momentum about z and of the mass.  With an indicator, the mixed form with
+    the learned smoothness indicator ("gated") runs beside them."""
     import torch
     from paper_2107_10987_gb300 import workloads as W
     from paper_2107_10987_gb300.uniform import UniformRun
     stream = torch.cuda.current_stream()
     omega = 0.2
     forms = (("mixed", H.HYDRO_PREC_MIXED), ("fp64", H.HYDRO_PREC_FP64))
+    if indicator is not None:
+        forms = forms + (("gated", H.HYDRO_PREC_MIXED), ("fp64_gated", H.HYDRO_PREC_FP64))
+
+    def context(name, prec):
+        c = H.Context(GAMMA, omega)
+        H.hydro_set_mode(c, prec, 0.4)
+        if name in ("gated", "fp64_gated"):
+            H.hydro_set_indicator(c, indicator[0], indicator[1])
+        return c
+
     out = {"workload": "rotating n=1.5 polytrope, 32,768 sub-grids of 8^3 (256^3 on [-1,1]^3), static gravity "
                        "field input, rotating frame omega=0.2, ambient rho 1e-10, outflow", "omega": omega}
 
@@ -371,10 +384,9 @@ def polytrope_measure(args, H, dev, flush):
     Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
     cells = Ui.shape[0] * 512
     for name, prec in forms:
-        ctx = H.Context(GAMMA, omega)
-        H.hydro_set_mode(ctx, prec, 0.4)
+        ctx = context(name, prec)
         run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g)
-        steps = args.steps if name == "mixed" else max(2, args.steps // 10)
+        steps = max(2, args.steps // 10) if name.startswith("fp64") else args.steps
         for _ in range(2):
             run.step(use_graph=True)
         t = timed(run, steps)
@@ -385,14 +397,16 @@ def polytrope_measure(args, H, dev, flush):
         ctx.close()
         torch.cuda.empty_cache()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    if indicator is not None:
+        out["speedup_gated_vs_mixed"] = out["mixed"]["ms_per_step"] / out["gated"]["ms_per_step"]
+        out["speedup_fp64_gated_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp64_gated"]["ms_per_step"]
 
     nb = args.polytrope_nb
     Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
     rho_ic = Ui[:, 0]
     acc = {"sub_grids": nb ** 3, "cells": nb ** 3 * 512, "steps": args.polytrope_steps}
     for name, prec in forms:
-        ctx = H.Context(GAMMA, omega)
-        H.hydro_set_mode(ctx, prec, 0.4)
+        ctx = context(name, prec)
         run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g)
         c0 = run.sums()
         t = 0.0
@@ -409,6 +423,9 @@ def polytrope_measure(args, H, dev, flush):
         ctx.close()
         torch.cuda.empty_cache()
     acc["l1_mixed_over_fp64"] = acc["mixed"]["l1_density"] / acc["fp64"]["l1_density"]
+    if indicator is not None:
+        acc["l1_gated_over_fp64"] = acc["gated"]["l1_density"] / acc["fp64"]["l1_density"]
+        acc["l1_fp64_gated_over_fp64"] = acc["fp64_gated"]["l1_density"] / acc["fp64"]["l1_density"]
     out["accuracy"] = acc
     return out
 
@@ -425,17 +442,19 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     launches_per_step = 10  # 3 x (ghost fill, step, update) + dt; no copies
-    forms = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED, "gated": H.HYDRO_PREC_MIXED}
-    order = {"all": ["fp64", "gated", "mixed"], "both": ["fp64", "mixed"]}.get(args.precision, [args.precision])
+    forms = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED, "gated": H.HYDRO_PREC_MIXED,
+             "fp64_gated": H.HYDRO_PREC_FP64}
+    order = {"all": ["fp64", "fp64_gated", "gated", "mixed"],
+             "both": ["fp64", "mixed"]}.get(args.precision, [args.precision])
     indicator = ind_eval = None
-    if "gated" in order:
+    if "gated" in order or "fp64_gated" in order:
         params, thr, ind_eval = train_indicator(dev)
         indicator = (params, thr)
     res = {}
     for name in order:
         if ws > 1:
             dist.barrier()
-        ind = indicator if name == "gated" else None
+        ind = indicator if name in ("gated", "fp64_gated") else None
         if name == order[-1]:
             with ClockSampler(lr) as clk:
                 t0 = time.perf_counter()
@@ -499,6 +518,12 @@ def gpu_arm(args):
             # both forms ran the same steps from the same state: density difference
             d = (r["rho"] - f["rho"]).abs().max().item() / f["rho"].abs().max().item()
             line["max_rel_density_diff_vs_fp64"] = d
+        if "fp64_gated" in res and "fp64" in res:
+            fg, f = res["fp64_gated"], res["fp64"]
+            line["plain_fp64_with_indicator"] = {
+                "value": job_rate(CELLS * args.steps, ws, fg["t_dev"]), "ms_per_step": 1e3 * fg["t_dev"] / args.steps,
+                "kernel_ms": 1e3 * fg["kern_s"], "speedup_vs_plain_fp64": f["t_dev"] / fg["t_dev"],
+                "max_rel_density_diff_vs_fp64": (fg["rho"] - f["rho"]).abs().max().item() / f["rho"].abs().max().item()}
         if "gated" in res:
             gr = res["gated"]
             line["mixed_with_indicator"] = {
@@ -513,8 +538,13 @@ def gpu_arm(args):
                                                "blast shell of radius 0.3, leaf order shuffled (seed 1234), outflow",
                                    "mixed": amr_measure(args, H, dev, flush, H.HYDRO_PREC_MIXED, args.steps),
                                    "fp64": amr_measure(args, H, dev, flush, H.HYDRO_PREC_FP64, max(2, args.steps // 5))}
+            if indicator is not None:
+                line["amr_batched"]["gated"] = amr_measure(args, H, dev, flush, H.HYDRO_PREC_MIXED, args.steps,
+                                                           indicator)
+                line["amr_batched"]["fp64_gated"] = amr_measure(args, H, dev, flush, H.HYDRO_PREC_FP64,
+                                                                max(2, args.steps // 5), indicator)
         if args.polytrope:
-            line["rotating_polytrope"] = polytrope_measure(args, H, dev, flush)
+            line["rotating_polytrope"] = polytrope_measure(args, H, dev, flush, indicator)
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -593,9 +623,9 @@ def main():
     ap.add_argument("--polytrope-nb", type=int, default=16,
                     help="sub-grids per axis of the polytrope accuracy runs (32: the full 256^3 mesh)")
     ap.add_argument("--polytrope-steps", type=int, default=100)
-    ap.add_argument("--precision", default="all", choices=["all", "both", "mixed", "fp64", "gated"],
-                    help="all: time the plain FP64 form, the mixed form with the learned indicator, then the "
-                         "mixed form (reported as value); both: FP64 then mixed")
+    ap.add_argument("--precision", default="all", choices=["all", "both", "mixed", "fp64", "gated", "fp64_gated"],
+                    help="all: time the plain FP64 form, the FP64 and mixed forms with the learned indicator, "
+                         "then the mixed form (reported as value); both: FP64 then mixed")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -17,7 +17,10 @@ Definitions written out plainly:
     (|q0|; |v| + c for velocities); the spin fields are always limited;
   * network: h1 = relu(W1 x + b1) (32), h2 = relu(W2 h1 + b2) (32),
     out = sigmoid(w3 . h2 + b3); parameters packed in the order
-    W1[32][54], b1[32], W2[32][32], b2[32], w3[32], b3;
+    W1[32][54], b1[32], W2[32][32], b2[32], w3[32], b3.  Training uses it
+    with BF16-rounded parameters and exact activations (forward); the
+    deployed form also rounds x and h1 to BF16 (forward_infer: BF16
+    operands of the tensor cores, FP32 accumulation);
   * loss: class-weighted binary cross-entropy, mean over the batch,
         L = -mean( w1 y log(out) + w0 (1-y) log(1-out) ).
 """
@@ -85,6 +88,19 @@ def forward(theta: np.ndarray, X: np.ndarray):
     z3 = h2 @ p["w3"] + p["b3"][0]
     out = 1.0 / (1.0 + np.exp(-z3))
     return out, (X, z1, h1, z2, h2, z3)
+
+
+def forward_infer(theta: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """The deployed indicator (BF16 operands, FP32 accumulation, as in the
+    step kernel's tensor-core evaluation): the features and the first hidden
+    layer are rounded to BF16 (ties to even), everything else is exact here.
+    theta: parameters already rounded to BF16.  Returns the sigmoid output."""
+    p = unpack(theta)
+    xb = bf16_round(X)
+    h1 = bf16_round(np.maximum(xb @ p["W1"].T + p["b1"], 0.0))
+    h2 = np.maximum(h1 @ p["W2"].T + p["b2"], 0.0)
+    z3 = h2 @ p["w3"] + p["b3"][0]
+    return 1.0 / (1.0 + np.exp(-z3))
 
 
 def loss_and_grad(theta: np.ndarray, X: np.ndarray, y: np.ndarray, w1: float = 1.0, w0: float = 1.0):

@@ -148,7 +148,8 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   A.P.gm1 = c->gamma - 1.0;
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
-  A.gate = (mixed && c->gate_on) ? 1 : 0;
+  A.gate = c->gate_on ? 1 : 0;
+  A.gate_w = c->gate_w;
   A.gate_logit_thr = (float)c->gate_logit_thr;
   A.gate_zero_smooth = c->gate_zero_smooth;
   cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, (cudaStream_t)stream)

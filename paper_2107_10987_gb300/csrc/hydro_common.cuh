@@ -51,6 +51,7 @@ struct StepArgs64 {
   int n_sub;
   StepParams P;
   int gate;               // mixed form: use the learned smoothness indicator
+  const float* gate_w;    // its BF16-rounded parameters (device, kGateParams floats)
   float gate_logit_thr;   // cells with indicator logit below this are smooth
   int gate_zero_smooth;   // the decision for all-zero features (uniform neighbourhood)
 };

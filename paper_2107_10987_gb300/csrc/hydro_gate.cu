@@ -98,14 +98,13 @@ __global__ void __launch_bounds__(256, 2) hydro_gate_data_kernel(GateDataArgs A)
 // ---- MLP training ----------------------------------------------------------
 constexpr int kTile = 128;
 
-__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-
 struct SmemW {
   const float* w;
   __device__ float operator()(int i) const { return w[i]; }
 };
 
-// Forward only: out[i] = sigmoid(logit(x_i)).
+// Forward only, in the deployed form (BF16 inputs and first hidden layer,
+// FP32 accumulation; gate_logit_infer): out[i] = sigmoid(logit(x_i)).
 __global__ void __launch_bounds__(kTile) hydro_mlp_forward_kernel(const float* params, const float* X, int n,
                                                                   float* out) {
   __shared__ float w[kGateParams];
@@ -115,7 +114,7 @@ __global__ void __launch_bounds__(kTile) hydro_mlp_forward_kernel(const float* p
     float x[54];
 #pragma unroll
     for (int k = 0; k < 54; ++k) x[k] = X[(size_t)t * 54 + k];
-    const float z = gate_logit(SmemW{w}, x);
+    const float z = gate_logit_infer(SmemW{w}, x);
     out[t] = 1.f / (1.f + __expf(-z));
   }
 }
@@ -243,7 +242,7 @@ __global__ void hydro_gate_zero_kernel(const float* w, float* out) {
   float x[54];
 #pragma unroll
   for (int k = 0; k < 54; ++k) x[k] = 0.f;
-  out[0] = gate_logit(SmemW{w}, x);
+  out[0] = gate_logit_infer(SmemW{w}, x);
 }
 
 __global__ void hydro_bf16_round_kernel(const float* in, float* out, int n) {
@@ -254,8 +253,6 @@ __global__ void hydro_bf16_round_kernel(const float* in, float* out, int n) {
 size_t mlp_grad_smem() {
   return sizeof(float) * (kGateParams + 3 + kTile * kGateIn + 4 * kTile * kGateH + 2 * kTile);
 }
-
-cudaError_t set_gate_weights(const float* dev_params, cudaStream_t st);  // hydro_step_mixed.cu
 
 }  // namespace hyd
 
@@ -334,7 +331,7 @@ int hydro_set_indicator(hydro_ctx_t* c, const float* params, double threshold, v
   }
   cudaStream_t st = (cudaStream_t)stream;
   hyd::hydro_bf16_round_kernel<<<(hyd::kGateParams + 255) / 256, 256, 0, st>>>(params, c->gate_w, hyd::kGateParams);
-  if (cudaGetLastError() != cudaSuccess || hyd::set_gate_weights(c->gate_w, st) != cudaSuccess) rc = HYDRO_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) rc = HYDRO_ECUDA;
   if (rc == HYDRO_OK) {
     // the network's decision at all-zero features (a uniform neighbourhood),
     // evaluated once with the same rounded parameters and arithmetic

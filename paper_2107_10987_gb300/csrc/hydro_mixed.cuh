@@ -1,6 +1,8 @@
 // hydro_mixed.cuh -- FP32 device functions of the mixed-precision path,
 // shared by the step kernel and the smoothness-indicator kernels.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "hydro_common.cuh"
 
 namespace hyd {
@@ -150,6 +152,10 @@ __device__ __forceinline__ void gate_features(const float* __restrict__ Q, int c
 // packed W1[32][54], b1[32], W2[32][32], b2[32], w3[32], b3.
 constexpr int kGateIn = 54, kGateH = 32;
 constexpr int kGateParams = kGateH * kGateIn + kGateH + kGateH * kGateH + kGateH + kGateH + 1;  // 2849
+constexpr int kGateB1 = kGateH * kGateIn, kGateW2 = kGateB1 + kGateH, kGateB2 = kGateW2 + kGateH * kGateH,
+              kGateW3 = kGateB2 + kGateH, kGateB3 = kGateW3 + kGateH;
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 template <class W>
 __device__ __forceinline__ float gate_logit(const W& w, const float x[54]) {
@@ -171,6 +177,249 @@ __device__ __forceinline__ float gate_logit(const W& w, const float x[54]) {
     out = fmaf(w(o2 + kGateH * kGateH + kGateH + j), fmaxf(z, 0.f), out);
   }
   return out;
+}
+
+// The deployed (inference) form of the network: the inputs and the first
+// hidden layer rounded to BF16, products and sums in FP32 -- the arithmetic
+// of the tensor-core evaluation in the step kernel (BF16 operands, FP32
+// accumulation), here written sequentially.  Parameters already rounded.
+template <class W>
+__device__ __forceinline__ float gate_logit_infer(const W& w, const float x[54]) {
+  float h1[kGateH];
+#pragma unroll
+  for (int j = 0; j < kGateH; ++j) {
+    float z = w(kGateB1 + j);
+#pragma unroll
+    for (int i = 0; i < kGateIn; ++i) z = fmaf(w(j * kGateIn + i), bf16r(x[i]), z);
+    h1[j] = bf16r(fmaxf(z, 0.f));
+  }
+  float out = w(kGateB3);
+#pragma unroll 4
+  for (int j = 0; j < kGateH; ++j) {
+    float z = w(kGateB2 + j);
+#pragma unroll
+    for (int i = 0; i < kGateH; ++i) z = fmaf(w(kGateW2 + j * kGateH + i), h1[i], z);
+    out = fmaf(w(kGateW3 + j), fmaxf(z, 0.f), out);
+  }
+  return out;
+}
+
+// ---- the indicator on the tensor cores (mma.sync m16n8k16, BF16 in, FP32 out)
+// A warp evaluates the network for a tile of 16 cells: A = features [16 x 64]
+// (54 used), B = W1^T [64 x 32], then A = the first hidden layer [16 x 32],
+// B = W2^T [32 x 32].  Fragments (lane = 4 g + t): A holds rows g and g + 8,
+// columns 2t, 2t+1, 2t+8, 2t+9 of a 16-column step; B holds rows 2t, 2t+1,
+// 2t+8, 2t+9 of column g; the FP32 accumulator holds rows g, g + 8 and
+// columns 2t, 2t+1 of an 8-column tile -- so the first layer's accumulators,
+// rounded to BF16, are the second layer's A fragments in place.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Weight fragments of one lane (BF16 pairs), loaded once per sub-grid.
+struct GateFrags {
+  uint32_t w1[4][4][2];  // [k-step][n-tile][reg]
+  uint32_t w2[2][4][2];
+  float b1[4][2], b2[4][2], w3[4][2], b3;
+};
+
+__device__ __forceinline__ void gate_load_frags(const float* __restrict__ w, int lane, GateFrags& f) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int n = 8 * nt + g;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int k0 = 16 * ks + 2 * t;
+      auto W1 = [&](int k) { return k < kGateIn ? __ldg(w + n * kGateIn + k) : 0.f; };
+      f.w1[ks][nt][0] = pack_bf16x2(W1(k0), W1(k0 + 1));
+      f.w1[ks][nt][1] = pack_bf16x2(W1(k0 + 8), W1(k0 + 9));
+    }
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int k0 = 16 * ks + 2 * t;
+      f.w2[ks][nt][0] = pack_bf16x2(__ldg(w + kGateW2 + n * kGateH + k0), __ldg(w + kGateW2 + n * kGateH + k0 + 1));
+      f.w2[ks][nt][1] =
+          pack_bf16x2(__ldg(w + kGateW2 + n * kGateH + k0 + 8), __ldg(w + kGateW2 + n * kGateH + k0 + 9));
+    }
+    const int c0 = 8 * nt + 2 * t;
+    f.b1[nt][0] = __ldg(w + kGateB1 + c0);
+    f.b1[nt][1] = __ldg(w + kGateB1 + c0 + 1);
+    f.b2[nt][0] = __ldg(w + kGateB2 + c0);
+    f.b2[nt][1] = __ldg(w + kGateB2 + c0 + 1);
+    f.w3[nt][0] = __ldg(w + kGateW3 + c0);
+    f.w3[nt][1] = __ldg(w + kGateW3 + c0 + 1);
+  }
+  f.b3 = __ldg(w + kGateB3);
+}
+
+// Shared-memory offset of the j-th feature's neighbour: density (j < 27) or
+// internal energy (27 <= j < 54) of neighbour k_j (z, y, x order) relative
+// to the cell's density slot; the padding columns 54..63 point at the cell.
+struct GateOffsets {
+  int off[64];
+};
+__host__ __device__ constexpr GateOffsets make_gate_offsets() {
+  GateOffsets t{};
+  for (int j = 0; j < 64; ++j) {
+    const int jj = j < 27 ? j : j - 27;
+    const int nb = ((jj / 9 - 1) * S + ((jj / 3) % 3 - 1)) * S + (jj % 3 - 1);
+    t.off[j] = j < 27 ? nb : (j < kGateIn ? (EGAS - RHO) * S3 + nb : 0);
+  }
+  return t;
+}
+__constant__ const GateOffsets c_gate_off = make_gate_offsets();
+
+// One indicator feature (index j of 54) of the cell at padded index c:
+// (q(c + k_j) - q(c)) / (|q(c + k_j)| + |q(c)|), q = density (j < 27) or
+// pressure (gm1 * eps), k_j the j-th neighbour in (z, y, x) order.
+template <class T>
+__device__ __forceinline__ float gate_feature(const T* __restrict__ Q, int c, float rc, float pc, float gm1, int j) {
+  const float v = (float)Q[RHO * S3 + c + c_gate_off.off[j]];
+  const float qk = j < 27 ? v : gm1 * v;
+  const float qc = j < 27 ? rc : pc;
+  return __fdividef(qk - qc, fabsf(qk) + fabsf(qc));
+}
+
+// Logits of the two cells (rows g and g + 8 of the tile) held by this lane's
+// group; cells c0, c1 are padded indices of the primitives Q (FP32, or FP64
+// read in FP32: the features are defined in FP32).  zero0/zero1: whether
+// every feature of the cell is zero (a uniform neighbourhood).
+template <class T>
+__device__ __forceinline__ void gate_tile_mma(const T* __restrict__ Q, float gm1, int c0, int c1,
+                                              const GateFrags& f, int lane, float& logit0, float& logit1,
+                                              bool& zero0, bool& zero1) {
+  const int t = lane & 3;
+  const float r0 = (float)Q[RHO * S3 + c0], p0 = gm1 * (float)Q[EGAS * S3 + c0];
+  const float r1 = (float)Q[RHO * S3 + c1], p1 = gm1 * (float)Q[EGAS * S3 + c1];
+  uint32_t a[4][4];
+  bool nz0 = false, nz1 = false;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    float v0[4], v1[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 16 * ks + 2 * t + (e & 1) + ((e >> 1) << 3);  // columns 2t, 2t+1, 2t+8, 2t+9
+      v0[e] = j < kGateIn ? gate_feature(Q, c0, r0, p0, gm1, j) : 0.f;
+      v1[e] = j < kGateIn ? gate_feature(Q, c1, r1, p1, gm1, j) : 0.f;
+      nz0 |= v0[e] != 0.f;
+      nz1 |= v1[e] != 0.f;
+    }
+    a[ks][0] = pack_bf16x2(v0[0], v0[1]);
+    a[ks][1] = pack_bf16x2(v1[0], v1[1]);
+    a[ks][2] = pack_bf16x2(v0[2], v0[3]);
+    a[ks][3] = pack_bf16x2(v1[2], v1[3]);
+  }
+  nz0 |= __shfl_xor_sync(0xffffffffu, nz0, 1);
+  nz0 |= __shfl_xor_sync(0xffffffffu, nz0, 2);
+  nz1 |= __shfl_xor_sync(0xffffffffu, nz1, 1);
+  nz1 |= __shfl_xor_sync(0xffffffffu, nz1, 2);
+  zero0 = !nz0;
+  zero1 = !nz1;
+  logit0 = logit1 = 0.f;
+  if (!__any_sync(0xffffffffu, nz0 || nz1)) return;  // a uniform tile: the caller uses the zero-feature decision
+  float acc[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    acc[nt][0] = acc[nt][2] = f.b1[nt][0];
+    acc[nt][1] = acc[nt][3] = f.b1[nt][1];
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) mma_bf16_16816(acc[nt], a[ks], f.w1[ks][nt][0], f.w1[ks][nt][1]);
+  }
+  uint32_t h[2][4];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    h[ks][0] = pack_bf16x2(fmaxf(acc[2 * ks][0], 0.f), fmaxf(acc[2 * ks][1], 0.f));
+    h[ks][1] = pack_bf16x2(fmaxf(acc[2 * ks][2], 0.f), fmaxf(acc[2 * ks][3], 0.f));
+    h[ks][2] = pack_bf16x2(fmaxf(acc[2 * ks + 1][0], 0.f), fmaxf(acc[2 * ks + 1][1], 0.f));
+    h[ks][3] = pack_bf16x2(fmaxf(acc[2 * ks + 1][2], 0.f), fmaxf(acc[2 * ks + 1][3], 0.f));
+  }
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    float d[4] = {f.b2[nt][0], f.b2[nt][1], f.b2[nt][0], f.b2[nt][1]};
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) mma_bf16_16816(d, h[ks], f.w2[ks][nt][0], f.w2[ks][nt][1]);
+    s0 = fmaf(f.w3[nt][0], fmaxf(d[0], 0.f), s0);
+    s0 = fmaf(f.w3[nt][1], fmaxf(d[1], 0.f), s0);
+    s1 = fmaf(f.w3[nt][0], fmaxf(d[2], 0.f), s1);
+    s1 = fmaf(f.w3[nt][1], fmaxf(d[3], 0.f), s1);
+  }
+  // the group's four lanes hold eight columns each: fixed-order sum
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+  logit0 = s0 + f.b3;
+  logit1 = s1 + f.b3;
+}
+
+// The indicator's decision for every reconstructed cell of a sub-grid whose
+// primitives Q (FP32 or FP64) are in shared memory: predict on the 12^3 block
+// of cells [-2, N+1]^3, 16 cells per warp-wide tensor-core tile (a cell whose
+// 3x3x3 neighbourhood is uniform has all features 0 and takes the network's
+// decision at 0, computed once with the parameters; a tile of such cells
+// skips the MMAs; a sub-grid whose padded density and internal energy are
+// uniform skips the network altogether), then a reconstructed cell (in
+// [-1, N]^3) is smooth only if every cell of its 3x3x3 block is predicted
+// smooth: the 5-point stencils along the 13 lines reach two cells out,
+// beyond one cell's 3x3x3 features.  smooth and pred: [S3] bytes each.
+// Called by all threads of the block; ends with a block barrier.
+template <class T, int kThreads>
+__device__ __forceinline__ void gate_phase(const T* __restrict__ Q, float gm1, const float* __restrict__ gate_w,
+                                           float logit_thr, int zero_smooth, uint8_t* smooth, uint8_t* pred) {
+  const int tid = threadIdx.x;
+  const T r0 = Q[RHO * S3], e0 = Q[EGAS * S3];
+  bool same = true;
+  for (int c = tid; c < S3; c += kThreads) same &= (Q[RHO * S3 + c] == r0) & (Q[EGAS * S3 + c] == e0);
+  if (__syncthreads_and(same)) {
+    for (int c = tid; c < S3; c += kThreads) smooth[c] = (uint8_t)zero_smooth;
+    __syncthreads();
+    return;
+  }
+  const int lane = tid & 31;
+  GateFrags gf;
+  gate_load_frags(gate_w, lane, gf);
+  constexpr int kBlock = (N + 4) * (N + 4) * (N + 4);  // 1728 = 108 tiles of 16
+  for (int tile = tid >> 5; tile < kBlock / 16; tile += kThreads / 32) {
+    int cc[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i = 16 * tile + (lane >> 2) + 8 * r;
+      const int x = i % (N + 4) - 2, y = (i / (N + 4)) % (N + 4) - 2, z = i / ((N + 4) * (N + 4)) - 2;
+      cc[r] = ((z + G) * S + (y + G)) * S + (x + G);
+    }
+    float l0, l1;
+    bool z0, z1;
+    gate_tile_mma(Q, gm1, cc[0], cc[1], gf, lane, l0, l1, z0, z1);
+    if ((lane & 3) == 0) {
+      pred[cc[0]] = (z0 ? zero_smooth : (l0 < logit_thr)) ? 1 : 0;
+      pred[cc[1]] = (z1 ? zero_smooth : (l1 < logit_thr)) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < (N + 2) * (N + 2) * (N + 2); i += kThreads) {
+    const int x = i % (N + 2) - 1, y = (i / (N + 2)) % (N + 2) - 1, z = i / ((N + 2) * (N + 2)) - 1;
+    const int c = ((z + G) * S + (y + G)) * S + (x + G);
+    uint8_t all = 1;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) all &= pred[c + (dz * S + dy) * S + dx];
+    smooth[c] = all;
+  }
+  __syncthreads();
 }
 
 }  // namespace hyd

@@ -23,6 +23,7 @@
 // contraction) so that every limiter branch is decided on exactly the values
 // the FP64 oracle sees; the flux arithmetic may contract.
 #include "hydro_common.cuh"
+#include "hydro_mixed.cuh"
 
 namespace hyd {
 
@@ -65,6 +66,23 @@ __device__ __forceinline__ void line10(const double* __restrict__ Q, int c, int 
   for (int k = 0; k < F; ++k) {
     const double* q = Q + k * S3 + c;
     ppm64(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+  }
+}
+
+// Lines of a cell the learned indicator marks smooth: the unlimited 4-point
+// interface values q+ = 7/12 (q0 + q1) - 1/12 (q-1 + q2) towards +d (and the
+// mirror towards -d) for every field but the spin, which stays limited.
+__device__ __forceinline__ void line10u(const double* __restrict__ Q, int c, int st, double qp[F], double qm[F]) {
+  const double c7 = 7.0 / 12.0, c1 = 1.0 / 12.0;
+#pragma unroll
+  for (int k = 0; k < F; ++k) {
+    const double* q = Q + k * S3 + c;
+    if (k == ZX || k == ZY || k == ZZ) {
+      ppm64(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+    } else {
+      qp[k] = rsub(rmul(c7, radd(q[0], q[st])), rmul(c1, radd(q[-st], q[2 * st])));
+      qm[k] = rsub(rmul(c7, radd(q[0], q[-st])), rmul(c1, radd(q[st], q[-2 * st])));
+    }
   }
 }
 
@@ -122,8 +140,13 @@ __device__ __forceinline__ void point64(const double qL[F], const double qR[F], 
 constexpr int kThreads64 = NROW;  // 192
 constexpr long kWaitPolls = 1L << 24;
 
+// kGate: the learned smoothness indicator is on (A.gate): its decisions per
+// reconstructed cell follow the primitives in shared memory ([S3] bytes of
+// flags and [S3] of predictions after the state).
+template <bool kGate>
 __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs64 A) {
-  extern __shared__ __align__(128) double Q[];  // [F][S3]
+  extern __shared__ __align__(128) double Q[];  // [F][S3], then the indicator's flags
+  uint8_t* smooth = reinterpret_cast<uint8_t*>(Q + F * S3);
   __shared__ __align__(8) uint64_t bar;
   __shared__ double red[kThreads64 / 32];
   __shared__ int bail;
@@ -182,6 +205,11 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
     if (bad) atomicOr(A.status, 1u);
     __syncthreads();
 
+    // ---- 2b. learned smoothness indicator (gate_phase; features in FP32) ----
+    if (kGate)
+      gate_phase<double, kThreads64>(Q, (float)A.P.gm1, A.gate_w, A.gate_logit_thr, A.gate_zero_smooth, smooth,
+                                     smooth + S3);
+
     // ---- 3. row sweep ------------------------------------------------------
     const double h = A.h[s];
     const double half_h = 0.5 * h;
@@ -212,8 +240,13 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
       for (int p = 0; p <= 4; ++p) {
         const int t1 = p / 3 - 1, t2 = p % 3 - 1;  // point p; its mirror 8-p has (-t1,-t2)
         double qpA[F], qmA[F], qpB[F], qmB[F];
-        line10(Q, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
-        if (p != 4) line10(Q, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        if (kGate && smooth[cj]) {
+          line10u(Q, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
+          if (p != 4) line10u(Q, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        } else {
+          line10(Q, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
+          if (p != 4) line10(Q, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        }
         if (j >= 0) {
 #pragma unroll 1
           for (int side = 0; side < 2; ++side) {
@@ -338,15 +371,18 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
   if (tid == 0) mbar_inval(&bar);
 }
 
-size_t step_fp64_smem_bytes() { return (size_t)F * S3 * sizeof(double); }
+size_t step_fp64_smem_bytes(bool gate = false) { return (size_t)F * S3 * sizeof(double) + (gate ? 2 * S3 : 0); }
 
 // Opt in to the kernel's dynamic shared memory once per process (no
 // allocation; call before any stream capture).
 cudaError_t prepare_step_fp64() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(hydro_step_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_fp64_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_fp64_smem_bytes(false));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hydro_step_fp64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)step_fp64_smem_bytes(true));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -356,7 +392,10 @@ cudaError_t prepare_step_fp64() {
 cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {
   cudaError_t e = prepare_step_fp64();
   if (e != cudaSuccess) return e;
-  hydro_step_fp64_kernel<<<grid, kThreads64, step_fp64_smem_bytes(), st>>>(A);
+  if (A.gate)
+    hydro_step_fp64_kernel<true><<<grid, kThreads64, step_fp64_smem_bytes(true), st>>>(A);
+  else
+    hydro_step_fp64_kernel<false><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);
   return cudaGetLastError();
 }
 

@@ -21,18 +21,9 @@ namespace hyd {
 
 constexpr int kThreadsMx = NROW;  // 192
 
-// Learned smoothness indicator parameters (BF16-rounded, FP32 values), read
-// by every thread in lockstep: constant memory broadcasts them.
-__constant__ float c_gate_w[kGateParams];
-
-struct ConstW {
-  __device__ float operator()(int i) const { return c_gate_w[i]; }
-};
-
-cudaError_t set_gate_weights(const float* dev_params, cudaStream_t st) {
-  return cudaMemcpyToSymbolAsync(c_gate_w, dev_params, sizeof(float) * kGateParams, 0, cudaMemcpyDeviceToDevice, st);
-}
-
+// kGate: the learned smoothness indicator is on (A.gate); the kernel without
+// it carries none of the indicator's registers.
+template <bool kGate>
 __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArgs64 A) {
   extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [S3] smooth flags
   uint8_t* smooth = reinterpret_cast<uint8_t*>(Qf + F * S3);
@@ -65,39 +56,9 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
     if (bad) atomicOr(A.status, 1u);
     __syncthreads();
 
-    // ---- 2b. learned smoothness indicator.  Predict on the 12^3 block of
-    // cells [-2, N+1]^3 (a perfectly uniform 3x3x3 neighbourhood has all
-    // features 0: its prediction is the network's value at 0, computed once),
-    // then a reconstructed cell (in [-1, N]^3) is smooth only if every cell
-    // of its 3x3x3 block is predicted smooth: the 5-point stencils along the
-    // 13 lines reach two cells out, beyond one cell's 3x3x3 features.
-    if (A.gate) {
-      uint8_t* pred = smooth + S3;  // [S3] per-cell predictions
-      for (int i = tid; i < (N + 4) * (N + 4) * (N + 4); i += kThreadsMx) {
-        const int x = i % (N + 4) - 2, y = (i / (N + 4)) % (N + 4) - 2, z = i / ((N + 4) * (N + 4)) - 2;
-        const int c = ((z + G) * S + (y + G)) * S + (x + G);
-        float f[54];
-        gate_features(Qf, c, PF.gm1, f);
-        bool uniform = true;
-#pragma unroll
-        for (int k = 0; k < 54; ++k) uniform &= (f[k] == 0.f);
-        pred[c] = (uniform ? A.gate_zero_smooth : (gate_logit(ConstW{}, f) < A.gate_logit_thr)) ? 1 : 0;
-      }
-      __syncthreads();
-      for (int i = tid; i < (N + 2) * (N + 2) * (N + 2); i += kThreadsMx) {
-        const int x = i % (N + 2) - 1, y = (i / (N + 2)) % (N + 2) - 1, z = i / ((N + 2) * (N + 2)) - 1;
-        const int c = ((z + G) * S + (y + G)) * S + (x + G);
-        uint8_t all = 1;
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) all &= pred[c + (dz * S + dy) * S + dx];
-        smooth[c] = all;
-      }
-      __syncthreads();
-    }
+    // ---- 2b. learned smoothness indicator (gate_phase) ---------------------
+    if (kGate)
+      gate_phase<float, kThreadsMx>(Qf, PF.gm1, A.gate_w, A.gate_logit_thr, A.gate_zero_smooth, smooth, smooth + S3);
 
     // ---- 3. row sweep in FP32 --------------------------------------------
     const double hd = A.h[s];
@@ -129,7 +90,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
       for (int p = 0; p <= 4; ++p) {
         const int t1 = p / 3 - 1, t2 = p % 3 - 1;
         float qpA[F], qmA[F], qpB[F], qmB[F];
-        if (A.gate && smooth[cj]) {
+        if (kGate && smooth[cj]) {
           line10u(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
           if (p != 4) line10u(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
         } else {
@@ -264,8 +225,11 @@ size_t step_mixed_smem_bytes() { return (size_t)F * S3 * sizeof(float) + 2 * S3;
 cudaError_t prepare_step_mixed() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(hydro_step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)step_mixed_smem_bytes());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)step_mixed_smem_bytes());
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -275,7 +239,10 @@ cudaError_t prepare_step_mixed() {
 cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st) {
   cudaError_t e = prepare_step_mixed();
   if (e != cudaSuccess) return e;
-  hydro_step_mixed_kernel<<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+  if (A.gate)
+    hydro_step_mixed_kernel<true><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+  else
+    hydro_step_mixed_kernel<false><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   return cudaGetLastError();
 }
 

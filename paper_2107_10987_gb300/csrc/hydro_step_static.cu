@@ -98,6 +98,7 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
   A.gate = 0;
+  A.gate_w = nullptr;
   A.gate_logit_thr = 0.f;
   A.gate_zero_smooth = 0;
   if (hyd::launch_step_fp64(A, B->n_sub, st) != cudaSuccess) return HYDRO_ECUDA;

@@ -113,7 +113,7 @@ def test_amr_rk3_steps_match_oracle_and_conserve(H, oracle_mod):
 
 
 @pytest.mark.parametrize("mixed", [False, True])
-def test_batched_4096_leaf_mesh(H, mixed):
+def test_batched_4096_leaf_mesh(H, mixed, oracle_mod):
     """The batched configuration: ~4,096 leaves at levels 3-6 in shuffled order.
     One launch over all levels equals per-level launches (level-sorted copy),
     graph replays equal direct launches, mass is conserved."""
@@ -154,3 +154,23 @@ def test_batched_4096_leaf_mesh(H, mixed):
     torch.cuda.synchronize()
     inv = torch.tensor(np.argsort(order), device="cuda")
     assert torch.equal(dU_lv[inv], dU_all) and torch.equal(am_lv[inv], am_all)
+    # the whole-mesh launch against the oracle on 48 seeded leaves of every level
+    from oracle import core
+    from oracle.compare import field_scales, max_rel_error, mixed_budget
+    rng = np.random.default_rng(77)
+    idx = np.unique(np.concatenate([rng.choice(np.flatnonzero(lev == l), 12, replace=False) for l in np.unique(lev)]))
+    ti = torch.tensor(idx, device="cuda")
+    Us = Ug[ti].cpu().numpy()
+    o_s, h_s = run.origin[ti].cpu().numpy(), run.h[ti].cpu().numpy()
+    P = core.OracleParams(gamma=GAMMA)
+    ref, amo, _, faces = core.step(P, Us, o_s, h_s, faces=True)
+    got = dU_all[ti].cpu().numpy()
+    if not mixed:
+        assert max_rel_error(got, ref, h_s.max()) <= 1e-12
+        assert np.allclose(am_all[ti].cpu().numpy(), amo, rtol=1e-14, atol=0)
+    else:
+        pert, _, _ = core.step(P, Us.astype(np.float32).astype(np.float64), o_s, h_s)
+        budget, _ = mixed_budget(ref, pert, faces, h_s, Us, amo)
+        sc = field_scales(ref, h_s.max())[None, :, None, None, None]
+        err = (np.abs(got - ref) / sc).max(axis=(0, 2, 3, 4))
+        assert np.all(err <= budget), (err, budget)

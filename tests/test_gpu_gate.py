@@ -5,8 +5,9 @@
 * gradients: the GPU loss and gradient against a hand-written FP64
   backpropagation on the same BF16-rounded parameters (tolerance: FP32
   accumulation over the batch, 1e-4 of the largest gradient entry);
-* gated step: with seeded parameters, the fused indicator's decisions and the
-  gated step against the oracle's masked step (its own FP64 decisions);
+* gated step: with seeded parameters, the fused indicator (tensor cores,
+  BF16 operands, FP32 accumulation) and the gated step against the oracle's
+  masked step (its own decisions with the same BF16 rounding);
 * gain: a short training on seeded runs, evaluated on held-out seeds, and the
   gated mixed step against the ungated one at equal L1 error.
 """
@@ -83,7 +84,8 @@ def test_mlp_gradient_matches_cpu_backprop(H, oracle_mod):
     torch.cuda.synchronize()
     th = gate.bf16_round(theta)
     Lo, go = gate.loss_and_grad(th, X.astype(np.float64), y.astype(np.float64), 4.0, 0.5)
-    oo, _ = gate.forward(th, X.astype(np.float64))
+    # the standalone forward is the deployed form: BF16 inputs and first hidden layer
+    oo = gate.forward_infer(th, X.astype(np.float64))
     assert loss.item() == pytest.approx(Lo, rel=1e-5)
     assert np.max(np.abs(grad.cpu().numpy() - go)) <= 1e-4 * np.max(np.abs(go))
     assert np.max(np.abs(out.cpu().numpy() - oo)) < 1e-5
@@ -98,12 +100,14 @@ def test_mlp_gradient_matches_cpu_backprop(H, oracle_mod):
     assert np.all(np.sign(moved[nz]) == -np.sign(gg[nz]))
 
 
-def test_gated_step_matches_masked_oracle(H, oracle_mod):
+@pytest.mark.parametrize("fp64", [False, True])
+def test_gated_step_matches_masked_oracle(H, oracle_mod, fp64):
     """Seeded parameters; a threshold placed in a gap of the oracle's outputs
-    so that FP32 and FP64 decisions cannot differ; the gated mixed step then
-    matches the oracle's masked step within the mixed-precision budget."""
+    so that the kernel's and the oracle's decisions cannot differ; the gated
+    step then matches the oracle's masked step: the FP64 form to 1e-12, the
+    mixed form within the mixed-precision budget."""
     from oracle import core, gate
-    from oracle.compare import field_scales
+    from oracle.compare import field_scales, max_rel_error
     # smooth data only: seeded random parameters also gate cells at jumps,
     # where the unlimited formula may leave density or energy negative
     U = W.random_subgrids(10, 8, GAMMA, smooth=True)
@@ -114,7 +118,7 @@ def test_gated_step_matches_masked_oracle(H, oracle_mod):
     # predictions on the 12^3 block [-2, N+1]^3, then the dilated decision on
     # the 10^3 reconstructed cells: smooth iff the whole 3x3x3 block is
     Xo = gate.features(U, GAMMA, lo=-2, hi=10)
-    out, _ = gate.forward(th, Xo)
+    out = gate.forward_infer(th, Xo)  # the step kernel evaluates it on the tensor cores
     srt = np.sort(out)
     gaps = np.diff(srt)
     lo_i, hi_i = len(srt) // 10, 9 * len(srt) // 10
@@ -134,7 +138,7 @@ def test_gated_step_matches_masked_oracle(H, oracle_mod):
     ref, amo = core.step_masked(P, U, origin, 0.05, mask)
     pert, _ = core.step_masked(P, U.astype(np.float32).astype(np.float64), origin, 0.05, mask)
     ctx = H.Context(GAMMA, 0.0)
-    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64 if fp64 else H.HYDRO_PREC_MIXED)
     H.hydro_set_indicator(ctx, torch.tensor(theta, device="cuda"), float(thr))
     Ut, B = _batch(H, U)
     dU = torch.full((n, 10, 8, 8, 8), np.nan, dtype=torch.float64, device="cuda")
@@ -142,11 +146,15 @@ def test_gated_step_matches_masked_oracle(H, oracle_mod):
     H.hydro_step(ctx, B, 0.0, dU, am)
     torch.cuda.synchronize()
     got = dU.cpu().numpy()
+    assert 0.02 < mask.sum() / (n * 1000) < 0.98
+    if fp64:
+        assert max_rel_error(got, ref, 0.05) <= 1e-12
+        assert np.allclose(am.cpu().numpy(), amo, rtol=1e-14, atol=0)
+        return
     sc = field_scales(ref, 0.05)[None, :, None, None, None]
     err = (np.abs(got - ref) / sc).max(axis=(0, 2, 3, 4))
     sens = (np.abs(pert - ref) / sc).max(axis=(0, 2, 3, 4))
     assert np.all(err <= 8 * sens + 4e-7), (err, sens)
-    assert 0.02 < mask.sum() / (n * 1000) < 0.98
     # the indicator off again: the plain mixed step
     H.hydro_set_indicator(ctx, None)
     H.hydro_step(ctx, B, 0.0, dU, am)

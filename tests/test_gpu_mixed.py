@@ -63,7 +63,7 @@ def check_budget(orc, P, U, origin, h, g, dU, am):
     from oracle.compare import field_scales, mixed_budget
     ref, amo, _, faces = orc.step(P, U, origin, h, g, faces=True)
     pert, _, _ = orc.step(P, U.astype(np.float32).astype(np.float64), origin, h, g)
-    budget, sens = mixed_budget(ref, pert, faces, np.max(h))
+    budget, sens = mixed_budget(ref, pert, faces, h, U, amo)
     sc = field_scales(ref, np.max(h))[None, :, None, None, None]
     err = (np.abs(dU - ref) / sc).max(axis=(0, 2, 3, 4))
     assert np.all(np.isfinite(dU))

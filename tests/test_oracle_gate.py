@@ -62,3 +62,32 @@ def test_labels_flag_extrema_not_uniform_or_linear(oracle_mod):
     U[0, 6, 6, 6] *= 1.5  # a density spike: limiter active around it
     lab = gate.labels(U[None], 5 / 3).reshape(8, 8, 8)
     assert lab[3, 3, 3] == 1 and lab[0, 7, 0] == 0
+
+
+def test_inference_rounds_inputs_and_first_hidden_layer(oracle_mod):
+    """forward_infer rounds x and h1 to BF16 and nothing else: with W1 the
+    identity on the first two features, one hidden unit passing through to
+    the output, the output is exactly sigmoid of the twice-rounded input."""
+    from oracle import gate
+    p = {name: np.zeros(shape) for name, shape in gate.SIZES}
+    p["W1"][0, 0] = 1.0
+    p["W1"][1, 1] = 0.5
+    p["W2"][0, 0] = 1.0
+    p["W2"][0, 1] = 0.25
+    p["w3"][0] = 1.0
+    theta = np.concatenate([p[name].ravel() for name, _ in gate.SIZES])
+    x = np.zeros((3, gate.NIN))
+    x[0, 0] = 1.0 + 2.0 ** -9          # halfway between two BF16 values: ties to even -> 1
+    x[1, 0] = 1.0 + 3 * 2.0 ** -9      # above halfway -> 1 + 2^-7
+    x[2, 0], x[2, 1] = 0.3, 0.7
+    out = gate.forward_infer(theta, x)
+
+    def b(v):
+        return float(gate.bf16_round(np.array([v]))[0])
+
+    want = [b(x[i, 0]) + 0.25 * b(0.5 * b(x[i, 1])) for i in range(3)]
+    assert b(x[0, 0]) == 1.0 and b(x[1, 0]) == 1.0 + 2.0 ** -7
+    assert np.array_equal(np.log(out / (1 - out)).round(12), np.array(want).round(12))
+    # exact activations differ where the rounding matters
+    ref, _ = gate.forward(theta, x)
+    assert not np.allclose(out, ref, rtol=0, atol=1e-9)
