@@ -324,7 +324,9 @@ void hydro_rk3_graph_destroy(hydro_graph_t* g);
  * for velocities; FP32 reconstruction).  Either output may be NULL. */
 int hydro_gate_data(hydro_ctx_t* ctx, const hydro_batch_t* B, float* X, uint8_t* y, void* stream);
 
-/* Network output (sigmoid) for n samples X [n][54]. */
+/* Network output (sigmoid) for n samples X [n][54], in the deployed form
+ * that hydro_step evaluates: parameters, features and the first hidden
+ * layer rounded to BF16, FP32 accumulation. */
 int hydro_mlp_forward(const float* params, const float* X, int n, float* out, void* stream);
 
 /* Bytes of work buffer hydro_mlp_loss_grad needs for n samples. */
@@ -341,12 +343,17 @@ int hydro_mlp_loss_grad(const float* params, const float* X, const float* y, int
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step count t >= 1. */
 int hydro_mlp_adam(float* params, float* m, float* v, const float* grad, int t, float lr, void* stream);
 
-/* Turn the indicator on for this context's mixed-precision steps (params:
- * device FP32 parameters, rounded to BF16 here; cells with output below
- * threshold in (0,1) are predicted smooth), or off (params == NULL).  The
- * rounded parameters live in the library's constant memory: one indicator
- * per process and device at a time.  Synchronises the stream once (it reads
- * the network's decision for a uniform neighbourhood back to the host). */
+/* Turn the learned smoothness indicator on for this context's steps, in
+ * either precision (params: device FP32 parameters, rounded to BF16 into a
+ * copy the context owns; cells with output below threshold in (0,1) are
+ * predicted smooth), or off (params == NULL).  hydro_step then evaluates
+ * the network on the tensor cores (BF16 features and first hidden layer,
+ * FP32 accumulation) for the 12^3 block around every sub-grid, and a
+ * reconstructed cell whose 3x3x3 block is predicted smooth uses the
+ * unlimited interface formula on its lines (spin fields stay limited).
+ * Synchronises the stream once (it reads the network's decision for a
+ * uniform neighbourhood back to the host).  Changing the parameters while a
+ * captured graph of this context may run is the caller's race. */
 int hydro_set_indicator(hydro_ctx_t* ctx, const float* params, double threshold, void* stream);
 
 /* Device status bits accumulated since the last call (HYDRO_ST_*), then
