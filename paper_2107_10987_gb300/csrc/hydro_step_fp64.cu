@@ -27,11 +27,52 @@
 
 namespace hyd {
 
-// MC-limited slope of sample j from delta_{j-1} = a and delta_j = b.
+// Smaller of two non-negative doubles: their bit patterns order like their
+// values, so an integer minimum gives fmin's result on the integer pipes
+// (GB300 issues FP64 at 1/64 of the FP32 rate).
+__device__ __forceinline__ double min_nonneg(double x, double y) {
+  const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+  return __longlong_as_double(a < b ? a : b);
+}
+
+__device__ __forceinline__ double max_nonneg(double x, double y) {
+  const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+  return __longlong_as_double(a > b ? a : b);
+}
+
+// An integer that orders like the double (for non-NaN values; -0 sorts just
+// below +0).  x > y with y >= +0, and x < -y with y >= +0 (-y <= -0), give the
+// IEEE results through these keys: the two cases where the key order and
+// IEEE disagree, -0 against +0, then both answer false as IEEE does.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+// 2x for a finite double x >= 0, exactly: a normal x gains one in the
+// exponent field, a subnormal x (exponent field 0) doubles its pattern, which
+// carries into the exponent field where 2x is normal.
+__device__ __forceinline__ double twice_nonneg(double x) {
+  const long long b = __double_as_longlong(x);
+  return __longlong_as_double(b < (1LL << 52) ? b + b : b + (1LL << 52));
+}
+
+// x <= 0 for a non-NaN double: +0 has the bit pattern 0 and every value with
+// the sign bit set (-0 and the negatives) is negative as a signed integer.
+__device__ __forceinline__ bool nonpositive(double x) { return __double_as_longlong(x) <= 0LL; }
+
+// MC-limited slope of sample j from delta_{j-1} = a and delta_j = b:
+// 0 if a b <= 0, else sgn(b) min(2|a|, 2|b|, |a + b|/2).  The product test is
+// the FP64 product, compared on its bit pattern; min(2|a|, 2|b|) =
+// 2 min(|a|, |b|) exactly, the minima of non-negative values are taken and
+// the doubling done on the bit patterns, and with a b > 0 the sign of the
+// result is the sign bit of b: the same bits as the FP64 multiplications,
+// fmin and comparisons, with 3 instead of 9 FP64 instructions.
 __device__ __forceinline__ double slope64(double a, double b) {
-  if (rmul(a, b) <= 0.0) return 0.0;
-  const double m = fmin(fmin(2.0 * fabs(a), 2.0 * fabs(b)), 0.5 * fabs(radd(a, b)));
-  return b > 0.0 ? m : -m;
+  if (nonpositive(rmul(a, b))) return 0.0;
+  const double m = min_nonneg(twice_nonneg(min_nonneg(fabs(a), fabs(b))), rmul(0.5, fabs(radd(a, b))));
+  const long long sign = __double_as_longlong(b) & (long long)0x8000000000000000ull;
+  return __longlong_as_double(__double_as_longlong(m) | sign);
 }
 
 // PPM on the five samples s0..s4 of one line: qp = value at the +d end of the
@@ -43,16 +84,17 @@ __device__ __forceinline__ void ppm64(double s0, double s1, double s2, double s3
   const double D0 = slope64(d0, d1), D1 = slope64(d1, d2), D2 = slope64(d2, d3);
   double p = rsub(rmul(0.5, radd(s2, s3)), rmul(rsub(D2, D1), sixth));
   double m = rsub(rmul(0.5, radd(s1, s2)), rmul(rsub(D1, D0), sixth));
-  if (rmul(rsub(p, s2), rsub(s2, m)) <= 0.0) {
+  if (nonpositive(rmul(rsub(p, s2), rsub(s2, m)))) {
     p = s2;
     m = s2;
   } else {
     const double dq = rsub(p, m);
     const double lhs = rmul(dq, rsub(s2, rmul(0.5, radd(p, m))));
-    const double rhs = rmul(rmul(dq, dq), sixth);
-    if (lhs > rhs) {
+    const double rhs = rmul(rmul(dq, dq), sixth);  // >= +0
+    const long long kl = order_key(lhs);
+    if (kl > order_key(rhs)) {
       m = rsub(rmul(3.0, s2), rmul(2.0, p));
-    } else if (lhs < -rhs) {
+    } else if (kl < order_key(-rhs)) {
       p = rsub(rmul(3.0, s2), rmul(2.0, m));
     }
   }
@@ -120,8 +162,8 @@ __device__ __forceinline__ void point64(const double qL[F], const double qR[F], 
   double UL[F], FL[F], UR[F], FR[F], sL, sR;
   side64(qL, a, xq, yq, P, UL, FL, sL);
   side64(qR, a, xq, yq, P, UR, FR, sR);
-  const double aq = fmax(sL, sR);
-  amax = fmax(amax, aq);
+  const double aq = max_nonneg(sL, sR);  // signal speeds are >= 0
+  amax = max_nonneg(amax, aq);
   double Fq[F];
 #pragma unroll
   for (int k = 0; k < F; ++k) {
