@@ -136,7 +136,11 @@ __device__ __forceinline__ void side64(const double q[F], int a, double xq, doub
   const double ek = (0.5 * rho) * ((vx * vx + vy * vy) + vz * vz);
   const double E = eps + ek;
   const double p = P.gm1 * eps;
-  const double c = sqrt((P.gamma * p) / rho);
+  // c = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal
+  // square root instead of a division and a square root (a few ulps from the
+  // correctly rounded value); c = 0 where p <= 0 (a non-physical state)
+  const double gp = P.gamma * p;
+  const double c = (__double_as_longlong(gp) <= 0LL) ? 0.0 : gp * rsqrt(gp * rho);
   const double ux = vx + P.omega * yq, uy = vy - P.omega * xq;
   const double un = (a == 0) ? ux : (a == 1) ? uy : vz;
   const double va = (a == 0) ? vx : (a == 1) ? vy : vz;
