@@ -81,3 +81,21 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_clock_sampler_summary_and_missing_tool():
+    """The clocks record: median SM clock, max clock, active throttle reasons;
+    without nvidia-smi (this CPU host) the sampler records no samples."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.out = ("2070, 2070, 900.1, Not Active, Not Active, Not Active, Active\n"
+             "1980, 2070, 1300, Not Active, Not Active, Not Active, Not Active\n"
+             "2050, 2070, 1200, Not Active, Not Active, Not Active, Not Active\n")
+    sm = c.summary()
+    assert sm == {"sm_mhz": 2050.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    import shutil
+    if shutil.which("nvidia-smi") is None:
+        with bench.ClockSampler(0) as c2:
+            pass
+        assert c2.summary()["samples"] == 0
