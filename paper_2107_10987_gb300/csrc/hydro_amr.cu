@@ -103,6 +103,17 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
   }
 }
 
+// minmod(dp, dm) = 0 if dp dm <= 0, else the one of smaller magnitude: the
+// FP64 product's sign and the magnitudes compared on their bit patterns
+// (exact equivalents of the FP64 comparisons; GB300 issues FP64 at 1/64 of
+// the FP32 rate).
+__device__ __forceinline__ double minmod64(double dp, double dm) {
+  if (__double_as_longlong(rmul(dp, dm)) <= 0LL) return 0.0;
+  const long long a = __double_as_longlong(dp) & 0x7fffffffffffffffLL;
+  const long long b = __double_as_longlong(dm) & 0x7fffffffffffffffLL;
+  return a < b ? dp : dm;
+}
+
 // Prolongation of one fine ghost cell from coarse cell C (padded pointer to
 // field 0): U_C + s_x o_x + s_y o_y + s_z o_z, all ten fields.
 __device__ __forceinline__ void prolong_cell(const double* C, const double off[3], double* dst) {
@@ -114,8 +125,7 @@ __device__ __forceinline__ void prolong_cell(const double* C, const double off[3
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
-      const double mm = (rmul(dp, dm) <= 0.0) ? 0.0 : (fabs(dp) < fabs(dm) ? dp : dm);
-      v = radd(v, rmul(mm, off[d]));
+      v = radd(v, rmul(minmod64(dp, dm), off[d]));
     }
     dst[(size_t)k * S3] = v;
   }
@@ -163,29 +173,41 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
       if (tc < 0) continue;                  // refined at level l-1: pass 1 filled these
       const double* Cp =
           A.U + (size_t)tc * F * S3 + (((Cw[2] & 7) + G) * S + ((Cw[1] & 7) + G)) * S + ((Cw[0] & 7) + G);
-      double slope[F][3], centre[F];
+      // per field: the quarter slopes t_d = s_d / 4 once (the child offsets are
+      // +-1/4, and -(s/4) = s * (-1/4) exactly), then the children's values
+      // ((c +- t_x) +- t_y) +- t_z as a tree of partial sums -- the same
+      // additions, in the same order, as prolonging child by child
       const int st[3] = {1, S, S * S};
-#pragma unroll
+      const int need_x = ((mask & 0x55) ? 1 : 0) | ((mask & 0xaa) ? 2 : 0);  // children with x offset -, +
+      double* dst0 = dstb + ((2 * C[2] - b[2] + G) * S + (2 * C[1] - b[1] + G)) * S + (2 * C[0] - b[0] + G);
+#pragma unroll 1
       for (int k = 0; k < F; ++k) {
         const double* q = Cp + (size_t)k * S3;
-        centre[k] = q[0];
+        const double c = q[0];
+        double t[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
-          slope[k][d] = (rmul(dp, dm) <= 0.0) ? 0.0 : (fabs(dp) < fabs(dm) ? dp : dm);
+          const double dp = rsub(q[st[d]], c), dm = rsub(c, q[-st[d]]);
+          t[d] = rmul(minmod64(dp, dm), 0.25);
         }
-      }
-      for (int dch = 0; dch < 8; ++dch) {
-        if (!(mask & (1 << dch))) continue;
-        const int f[3] = {2 * C[0] + (dch & 1) - b[0], 2 * C[1] + ((dch >> 1) & 1) - b[1], 2 * C[2] + (dch >> 2) - b[2]};
-        const double off[3] = {(dch & 1) ? 0.25 : -0.25, ((dch >> 1) & 1) ? 0.25 : -0.25, (dch >> 2) ? 0.25 : -0.25};
-        double* dst = dstb + ((f[2] + G) * S + (f[1] + G)) * S + (f[0] + G);
+        double vx[2];
+        if (need_x & 1) vx[0] = radd(c, -t[0]);
+        if (need_x & 2) vx[1] = radd(c, t[0]);
 #pragma unroll
-        for (int k = 0; k < F; ++k) {
-          double v = centre[k];
+        for (int iy = 0; iy < 2; ++iy) {
+          if (!(mask & (0x33 << (2 * iy)))) continue;  // children 2iy, 2iy+1, 2iy+4, 2iy+5
 #pragma unroll
-          for (int d = 0; d < 3; ++d) v = radd(v, rmul(slope[k][d], off[d]));
-          dst[(size_t)k * S3] = v;
+          for (int ix = 0; ix < 2; ++ix) {
+            const int m2 = (1 << (ix + 2 * iy)) | (1 << (ix + 2 * iy + 4));  // the two children below/above in z
+            if (!(mask & m2)) continue;
+            const double vxy = radd(vx[ix], iy ? t[1] : -t[1]);
+#pragma unroll
+            for (int iz = 0; iz < 2; ++iz) {
+              const int dch = ix + 2 * iy + 4 * iz;
+              if (!(mask & (1 << dch))) continue;
+              dst0[(size_t)k * S3 + (iz * S + iy) * S + ix] = radd(vxy, iz ? t[2] : -t[2]);
+            }
+          }
         }
       }
     }
