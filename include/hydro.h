@@ -176,9 +176,13 @@ int hydro_dt(hydro_ctx_t* ctx, const double* amax, const double* h, int n_sub, d
  *   hydro_scatter_interior: B->U's interior cells <- interior (ghost cells
  *     untouched);
  *   hydro_gather_interior:  interior <- B->U's interior cells.
- * interior: device, caller-owned, 16-byte aligned, not overlapping B->U.
- * n_sub == 0 is a no-op; NULL or misaligned pointers give HYDRO_EINVAL.
- * Pure copies (bitwise), asynchronous on the stream. */
+ * interior: caller-owned, 16-byte aligned, not overlapping B->U; device
+ * memory, or page-locked host memory (cudaHostAlloc / cudaHostRegister),
+ * which the kernel then reads or writes directly over the host link (no
+ * staging copy; the caller must not touch it until the stream reaches the
+ * call).  n_sub == 0 is a no-op; NULL, misaligned or pageable host pointers
+ * give HYDRO_EINVAL before any launch.  Pure copies (bitwise), asynchronous
+ * on the stream. */
 int hydro_scatter_interior(hydro_ctx_t* ctx, const hydro_batch_t* B, const double* interior, void* stream);
 int hydro_gather_interior(hydro_ctx_t* ctx, const hydro_batch_t* B, double* interior, void* stream);
 

@@ -241,11 +241,35 @@ int hydro_fill_ghosts_uniform(hydro_ctx_t* c, const hydro_batch_t* B, int nbx, i
   return HYDRO_OK;
 }
 
+// The address at which a kernel reaches buffer p: device or managed memory as
+// is; page-locked host memory through its device mapping (with unified
+// addressing every cudaHostAlloc'd or registered buffer has one, and the
+// kernel's loads and stores then cross the host link directly); null for
+// pageable host memory, which no kernel may touch.
+static double* device_view(const double* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of the query
+    return nullptr;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+      return const_cast<double*>(p);
+    case cudaMemoryTypeHost:
+      return static_cast<double*>(at.devicePointer);
+    default:
+      return nullptr;
+  }
+}
+
 static int interior_copy(hydro_ctx_t* c, const hydro_batch_t* B, const double* I, bool scatter, void* stream) {
   if (!c || !B || B->n_sub < 0) return HYDRO_EINVAL;
   if (B->n_sub == 0) return HYDRO_OK;
-  if (!B->U || !I || !aligned16(I)) return HYDRO_EINVAL;
-  cudaError_t e = hyd::launch_interior(B->U, const_cast<double*>(I), B->n_sub, scatter, c->num_sms, (cudaStream_t)stream);
+  if (!B->U || !I) return HYDRO_EINVAL;
+  double* Id = device_view(I);
+  if (!Id || !aligned16(Id)) return HYDRO_EINVAL;
+  cudaError_t e = hyd::launch_interior(B->U, Id, B->n_sub, scatter, c->num_sms, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, scatter ? "hydro_scatter_interior" : "hydro_gather_interior");
   return HYDRO_OK;
 }

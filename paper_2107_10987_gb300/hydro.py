@@ -199,16 +199,27 @@ def hydro_fill_ghosts_uniform(ctx, batch: Batch, nbx: int, nby: int, nbz: int, b
            "hydro_fill_ghosts_uniform")
 
 
+def _ptr_device_or_pinned(t) -> int:
+    """A contiguous float64 tensor on the GPU or in page-locked host memory."""
+    if isinstance(t, int):
+        return t
+    assert t.dtype == torch.float64 and t.is_contiguous(), "expects a contiguous float64 tensor"
+    assert t.is_cuda or t.is_pinned(), "expects a CUDA tensor or a pinned host tensor"
+    return t.data_ptr()
+
+
 def hydro_scatter_interior(ctx, batch: Batch, interior, stream=None):
-    """interior: [n_sub][F][N][N][N] float64 CUDA tensor -> the batch's interior cells."""
-    _check(_lib().hydro_scatter_interior(_cp(ctx), C.byref(batch), _ptr(interior), _stream(stream)),
-           "hydro_scatter_interior")
+    """interior: [n_sub][F][N][N][N] float64 tensor (CUDA, or pinned host memory
+    read directly by the kernel) -> the batch's interior cells."""
+    _check(_lib().hydro_scatter_interior(_cp(ctx), C.byref(batch), _ptr_device_or_pinned(interior),
+                                         _stream(stream)), "hydro_scatter_interior")
 
 
 def hydro_gather_interior(ctx, batch: Batch, interior, stream=None):
-    """The batch's interior cells -> interior [n_sub][F][N][N][N] float64 CUDA tensor."""
-    _check(_lib().hydro_gather_interior(_cp(ctx), C.byref(batch), _ptr(interior), _stream(stream)),
-           "hydro_gather_interior")
+    """The batch's interior cells -> interior [n_sub][F][N][N][N] float64 tensor
+    (CUDA, or pinned host memory written directly by the kernel)."""
+    _check(_lib().hydro_gather_interior(_cp(ctx), C.byref(batch), _ptr_device_or_pinned(interior),
+                                        _stream(stream)), "hydro_gather_interior")
 
 
 def hydro_conserved_sums(ctx, batch: Batch, sums, stream=None):

@@ -358,3 +358,14 @@ def test_interior_scatter_gather(H):
     flat = torch.empty(I.numel() + 1, dtype=torch.float64, device=dev)
     with pytest.raises(RuntimeError):
         H.hydro_gather_interior(ctx, B, flat[1:])  # 8-byte offset: not 16-byte aligned
+    # page-locked host memory: the kernels read and write it over the host link
+    hI = torch.tensor(rng.normal(size=(n, 10, 8, 8, 8))).pin_memory()
+    H.hydro_scatter_interior(ctx, B, hI)
+    hout = torch.full(hI.shape, float("nan"), dtype=torch.float64).pin_memory()
+    H.hydro_gather_interior(ctx, B, hout)
+    torch.cuda.synchronize()
+    assert torch.equal(hout, hI) and torch.equal(U[:, :, 3:11, 3:11, 3:11].cpu(), hI)
+    # pageable host memory is refused before any launch
+    page = np.zeros(I.numel())
+    with pytest.raises(RuntimeError):
+        H.hydro_gather_interior(ctx, B, page.ctypes.data)
