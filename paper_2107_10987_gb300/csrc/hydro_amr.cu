@@ -54,51 +54,109 @@ __device__ __forceinline__ int bc_amr(int g, int n, int bc) {
   return g < 0 ? 0 : (g >= n ? n - 1 : g);
 }
 
-// Pass 1: same-level copies and restrictions.
+// Position of a ghost cell's sub-grid relative to a base position, after the
+// boundary map: in lo..lo+span-1 (periodic wrap-around mapped back).
+__device__ __forceinline__ int rel_pos(int p, int base, int n, int bc, int lo, int span) {
+  int r = p - base;
+  if (bc == 0) {
+    if (r > lo + span - 1) r -= n;
+    else if (r < lo) r += n;
+  }
+  return r;
+}
+
+// Pass 1: same-level copies and restrictions.  A leaf's ghost cells (G < N)
+// lie in the 26 positions around it at its level, and the finer cells of a
+// restricted ghost cell in the 4^3 positions 2p-1 .. 2p+2 one level down: the
+// table entries of both sets are read once per leaf into shared memory.
+// Pass 1 reads interior cells only and writes ghost cells only, so each
+// thread takes two ghost cells at a time and issues all their loads (read-
+// only path) before their stores.
+constexpr int kAmrBatch = 2;
+
 __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
+  __shared__ int nb[27];   // level l:   relative position (-1..1)^3
+  __shared__ int nbf[64];  // level l+1: relative position (-1..2)^3 from 2p
+  const int tid = threadIdx.x;
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int l = A.leaf_level[s];
-    const int bx = A.leaf_ijk[3 * s] * N, by = A.leaf_ijk[3 * s + 1] * N, bz = A.leaf_ijk[3 * s + 2] * N;
-    const int ncell = N << l;
+    const int pi[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
+    const int n = 1 << l, ncell = N << l;
+    __syncthreads();  // the previous leaf's tables are no longer read
+    if (tid < 27) {
+      const int q[3] = {pi[0] + tid % 3 - 1, pi[1] + (tid / 3) % 3 - 1, pi[2] + tid / 9 - 1};
+      int w[3];
+      bool inside = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        w[d] = (A.bc == 0) ? (q[d] + n) % n : q[d];
+        inside &= (w[d] >= 0 && w[d] < n);
+      }
+      nb[tid] = inside ? A.table[level_offset(l, A.lmin) + ((long)w[2] * n + w[1]) * n + w[0]] : -3;
+    } else if (tid >= 64 && tid < 128) {
+      const int i = tid - 64, nf = 2 * n;
+      const int q[3] = {2 * pi[0] + i % 4 - 1, 2 * pi[1] + (i / 4) % 4 - 1, 2 * pi[2] + i / 16 - 1};
+      int w[3];
+      bool inside = l < A.lmax;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        w[d] = (A.bc == 0) ? (q[d] + nf) % nf : q[d];
+        inside &= (w[d] >= 0 && w[d] < nf);
+      }
+      nbf[i] = inside ? A.table[level_offset(l + 1, A.lmin) + ((long)w[2] * nf + w[1]) * nf + w[0]] : -3;
+    }
+    __syncthreads();
     double* dst = A.U + (size_t)s * F * S3;
-    for (int c = threadIdx.x; c < S3; c += blockDim.x) {
-      const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
-      if ((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N) continue;
-      const int gx = bc_amr(bx + lx, ncell, A.bc), gy = bc_amr(by + ly, ncell, A.bc), gz = bc_amr(bz + lz, ncell, A.bc);
-      const int t = lookup(A, l, gx, gy, gz);
-      // pass 1 reads interior cells only and writes ghost cells only: all
-      // loads of a cell go out (read-only path) before its stores
-      {
+    for (int c0 = tid; c0 < S3; c0 += kAmrBatch * blockDim.x) {
+      double v[kAmrBatch][F];
+      bool put[kAmrBatch];
+#pragma unroll
+      for (int j = 0; j < kAmrBatch; ++j) {
+        const int c = c0 + j * blockDim.x;
+        const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
+        put[j] = c < S3 && !((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N);
+        if (!put[j]) continue;
+        const int g[3] = {bc_amr(pi[0] * N + lx, ncell, A.bc), bc_amr(pi[1] * N + ly, ncell, A.bc),
+                          bc_amr(pi[2] * N + lz, ncell, A.bc)};
+        const int r[3] = {rel_pos(g[0] >> 3, pi[0], n, A.bc, -1, 3), rel_pos(g[1] >> 3, pi[1], n, A.bc, -1, 3),
+                          rel_pos(g[2] >> 3, pi[2], n, A.bc, -1, 3)};
+        const int t = nb[((r[2] + 1) * 3 + (r[1] + 1)) * 3 + (r[0] + 1)];
         if (t >= 0) {
-          const double* src = A.U + (size_t)t * F * S3 + (((gz & 7) + G) * S + ((gy & 7) + G)) * S + ((gx & 7) + G);
-          double v[F];
+          const double* src =
+              A.U + (size_t)t * F * S3 + (((g[2] & 7) + G) * S + ((g[1] & 7) + G)) * S + ((g[0] & 7) + G);
 #pragma unroll
-          for (int k = 0; k < F; ++k) v[k] = __ldg(src + (size_t)k * S3);
-#pragma unroll
-          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c] = v[k];
+          for (int k = 0; k < F; ++k) v[j][k] = __ldg(src + (size_t)k * S3);
         } else if (t == -1) {
           const double* kid[8];
           bool ok = true;
+#pragma unroll
           for (int d = 0; d < 8; ++d) {
-            const int fx = 2 * gx + (d & 1), fy = 2 * gy + ((d >> 1) & 1), fz = 2 * gz + (d >> 2);
-            const int tf = lookup(A, l + 1, fx, fy, fz);
+            const int f[3] = {2 * g[0] + (d & 1), 2 * g[1] + ((d >> 1) & 1), 2 * g[2] + (d >> 2)};
+            const int rf[3] = {rel_pos(f[0] >> 3, 2 * pi[0], 2 * n, A.bc, -1, 4),
+                               rel_pos(f[1] >> 3, 2 * pi[1], 2 * n, A.bc, -1, 4),
+                               rel_pos(f[2] >> 3, 2 * pi[2], 2 * n, A.bc, -1, 4)};
+            const int tf = nbf[((rf[2] + 1) * 4 + (rf[1] + 1)) * 4 + (rf[0] + 1)];
             ok &= tf >= 0;
-            kid[d] = A.U + (size_t)(tf < 0 ? s : tf) * F * S3 + (((fz & 7) + G) * S + ((fy & 7) + G)) * S +
-                     ((fx & 7) + G);
+            kid[d] = A.U + (size_t)(tf < 0 ? s : tf) * F * S3 + (((f[2] & 7) + G) * S + ((f[1] & 7) + G)) * S +
+                     ((f[0] & 7) + G);
           }
           if (!ok) atomicOr(A.status, 4u);
-          double v[F];
 #pragma unroll
           for (int k = 0; k < F; ++k) {
             const size_t o = (size_t)k * S3;
             const double acc = radd(radd(radd(__ldg(kid[0] + o), __ldg(kid[1] + o)), radd(__ldg(kid[2] + o), __ldg(kid[3] + o))),
                                     radd(radd(__ldg(kid[4] + o), __ldg(kid[5] + o)), radd(__ldg(kid[6] + o), __ldg(kid[7] + o))));
-            v[k] = rmul(acc, 0.125);
+            v[j][k] = rmul(acc, 0.125);
           }
-#pragma unroll
-          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c] = v[k];
+        } else {
+          put[j] = false;  // inside a coarser leaf: pass 2
         }
       }
+#pragma unroll
+      for (int j = 0; j < kAmrBatch; ++j)
+        if (put[j])
+#pragma unroll
+          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c0 + j * blockDim.x] = v[j][k];
     }
   }
 }

@@ -47,6 +47,36 @@ def test_amr_ghost_fill_bitwise(H, oracle_mod):
     assert np.array_equal(Ut.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("bc", ["periodic", "outflow"])
+def test_single_level_octree_equals_uniform_ghost_fill(H, bc):
+    """All leaves on one level, in shuffled order: the adaptive ghost fill
+    must reproduce the uniform-level fill bit for bit, including the
+    wrap-around of periodic boundaries (which the oracle's octree fill does
+    not model)."""
+    from paper_2107_10987_gb300.amr import AMRMesh
+    nb = 4
+    rng = np.random.default_rng(31)
+    Uu = np.zeros((nb ** 3, 10, 14, 14, 14))
+    Uu[:, :, 3:-3, 3:-3, 3:-3] = rng.normal(size=(nb ** 3, 10, 8, 8, 8))
+    code = {"periodic": H.HYDRO_BC_PERIODIC, "outflow": H.HYDRO_BC_OUTFLOW}[bc]
+    ctx = H.Context(GAMMA, 0.0)
+    # uniform fill (sub-grid s = (kz*nb + ky)*nb + kx)
+    Ut = torch.tensor(Uu, device="cuda")
+    z = torch.zeros((nb ** 3, 3), dtype=torch.float64, device="cuda")
+    hh = torch.full((nb ** 3,), 0.1, dtype=torch.float64, device="cuda")
+    H.hydro_fill_ghosts_uniform(ctx, H.make_batch(Ut, z, hh), nb, nb, nb, code)
+    # the same sub-grids as level-2 leaves in shuffled order
+    perm = rng.permutation(nb ** 3)
+    kk = np.arange(nb ** 3)
+    ijk = np.stack([kk % nb, (kk // nb) % nb, kk // (nb * nb)], 1)[perm]
+    mesh = AMRMesh(np.full(nb ** 3, 2), ijk, bc=code)
+    Ua = torch.tensor(Uu[perm], device="cuda")
+    H.hydro_fill_ghosts_amr(ctx, H.make_batch(Ua, z, hh), mesh)
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    assert torch.equal(Ua, Ut[torch.tensor(perm, device="cuda")])
+
+
 def test_amr_faces_and_flux_correction(H, oracle_mod):
     from oracle import amr, core
     from oracle.compare import max_rel_error
