@@ -56,6 +56,16 @@ struct StepArgs64 {
   int gate_zero_smooth;   // the decision for all-zero features (uniform neighbourhood)
 };
 
+// Component i (0 = x, 1 = y, 2 = z) of a vector given by its components va,
+// vb, vc along a row sweep's axes a, b, c (a permutation of 0, 1, 2): a
+// select, so that no small array is indexed by the runtime axis (which
+// would place it in local memory).
+template <class T>
+__device__ __forceinline__ T axis_comp(int i, int a, int b, T va, T vb, T vc) {
+  return i == a ? va : (i == b ? vb : vc);
+}
+__device__ __forceinline__ int axis_stride(int i) { return i == 0 ? 1 : (i == 1 ? S : S * S); }
+
 // ---- FP64 arithmetic that the compiler may not contract into FMA --------
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }

@@ -212,8 +212,7 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
   const int pb = r % N, pc = r / N;
   const int b = (a == 0) ? 1 : 0;
   const int cx = (a == 2) ? 1 : 2;
-  const int st[3] = {1, S, S * S};
-  const int sa = st[a], sb = st[b], sc = st[cx];
+  const int sa = axis_stride(a), sb = axis_stride(b), sc = axis_stride(cx);
 
   uint32_t phase = 0;
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
@@ -264,11 +263,8 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
     double plus[9][F];
     double fprev[F], trprev[3];
     // smem index of the row's cell at a-index j
-    int coord0[3];
-    coord0[a] = 0;
-    coord0[b] = pb;
-    coord0[cx] = pc;
-    const int c0 = ((coord0[2] + G) * S + (coord0[1] + G)) * S + (coord0[0] + G);
+    const int c0 = ((axis_comp(2, a, b, 0, pb, pc) + G) * S + (axis_comp(1, a, b, 0, pb, pc) + G)) * S +
+                   (axis_comp(0, a, b, 0, pb, pc) + G);
 #pragma unroll 1
     for (int j = -1; j <= N; ++j) {
       const int cj = c0 + j * sa;
@@ -278,10 +274,7 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
       tl[0] = tl[1] = tl[2] = 0.0;
       tr[0] = tr[1] = tr[2] = 0.0;
       // left cell of face j-1/2 is (j-1) along a
-      int ci[3];
-      ci[a] = j - 1;
-      ci[b] = pb;
-      ci[cx] = pc;
+      const int ci0 = axis_comp(0, a, b, j - 1, pb, pc), ci1 = axis_comp(1, a, b, j - 1, pb, pc);
 #pragma unroll 1
       for (int p = 0; p <= 4; ++p) {
         const int t1 = p / 3 - 1, t2 = p % 3 - 1;  // point p; its mirror 8-p has (-t1,-t2)
@@ -301,15 +294,13 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
             // side 1: point p (offsets t1,t2) with right state qmB.
             const int u1 = side ? t1 : -t1, u2 = side ? t2 : -t2;
             const int pt = (u1 + 1) * 3 + (u2 + 1);
-            int d[3];
-            d[a] = 1;
-            d[b] = u1;
-            d[cx] = u2;
-            const double xq = o[0] + h * ((ci[0] + 0.5) + 0.5 * d[0]);
-            const double yq = o[1] + h * ((ci[1] + 0.5) + 0.5 * d[1]);
-            const double rl[3] = {half_h * d[0], half_h * d[1], half_h * d[2]};
-            double rr[3] = {rl[0], rl[1], rl[2]};
-            rr[a] = half_h * (d[a] - 2);
+            const int d0 = axis_comp(0, a, b, 1, u1, u2), d1 = axis_comp(1, a, b, 1, u1, u2),
+                      d2 = axis_comp(2, a, b, 1, u1, u2);
+            const double xq = o[0] + h * ((ci0 + 0.5) + 0.5 * d0);
+            const double yq = o[1] + h * ((ci1 + 0.5) + 0.5 * d1);
+            const double rl[3] = {half_h * d0, half_h * d1, half_h * d2};
+            // about the right cell the a-offset is d_a - 2 = -1
+            const double rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
             const double w = (u1 == 0 && u2 == 0) ? (16.0 / 36.0) : (u1 == 0 || u2 == 0) ? (4.0 / 36.0) : (1.0 / 36.0);
             point64(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, A.P, fsum, tl, tr, amax);
           }
@@ -323,11 +314,8 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
       if (j >= 1) {
         // interior cell i = j-1 along a: differences of its two a-faces
         const int i = j - 1;
-        int cc[3];
-        cc[a] = i;
-        cc[b] = pb;
-        cc[cx] = pc;
-        const int cell = (cc[2] * N + cc[1]) * N + cc[0];
+        const int cell = (axis_comp(2, a, b, i, pb, pc) * N + axis_comp(1, a, b, i, pb, pc)) * N +
+                         axis_comp(0, a, b, i, pb, pc);
         double* Da = D + (size_t)a * DQ * N3 + cell;
 #pragma unroll
         for (int k = 0; k < F; ++k) Da[k * N3] = fsum[k] - fprev[k];

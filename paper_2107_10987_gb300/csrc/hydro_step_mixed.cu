@@ -37,8 +37,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
   const int pb = r % N, pc = r / N;
   const int b = (a == 0) ? 1 : 0;
   const int cx = (a == 2) ? 1 : 2;
-  const int st[3] = {1, S, S * S};
-  const int sa = st[a], sb = st[b], sc = st[cx];
+  const int sa = axis_stride(a), sb = axis_stride(b), sc = axis_stride(cx);
 
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     // ---- 1-2. load the FP64 state, recover primitives, store FP32 -------
@@ -67,11 +66,8 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
     float amax = 0.f;
     float plus[9][F];
     double fprev[F], trprev[3];  // previous face's sums, converted to FP64 once
-    int coord0[3];
-    coord0[a] = 0;
-    coord0[b] = pb;
-    coord0[cx] = pc;
-    const int c0 = ((coord0[2] + G) * S + (coord0[1] + G)) * S + (coord0[0] + G);
+    const int c0 = ((axis_comp(2, a, b, 0, pb, pc) + G) * S + (axis_comp(1, a, b, 0, pb, pc) + G)) * S +
+                   (axis_comp(0, a, b, 0, pb, pc) + G);
 #pragma unroll 1
     for (int j = -1; j <= N; ++j) {
       const int cj = c0 + j * sa;
@@ -80,12 +76,9 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
       for (int k = 0; k < F; ++k) fsum[k] = 0.f;
       tl[0] = tl[1] = tl[2] = 0.f;
       tr[0] = tr[1] = tr[2] = 0.f;
-      int ci[3];
-      ci[a] = j - 1;
-      ci[b] = pb;
-      ci[cx] = pc;
-      // cell-centre coordinates of the left cell (FP64 -> FP32 once)
-      const float xc = (float)(o[0] + hd * (ci[0] + 0.5)), yc = (float)(o[1] + hd * (ci[1] + 0.5));
+      // cell-centre coordinates of the left cell j - 1 (FP64 -> FP32 once)
+      const float xc = (float)(o[0] + hd * (axis_comp(0, a, b, j - 1, pb, pc) + 0.5)),
+                  yc = (float)(o[1] + hd * (axis_comp(1, a, b, j - 1, pb, pc) + 0.5));
 #pragma unroll 1
       for (int p = 0; p <= 4; ++p) {
         const int t1 = p / 3 - 1, t2 = p % 3 - 1;
@@ -103,15 +96,12 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
             if (p == 4 && side == 1) continue;
             const int u1 = side ? t1 : -t1, u2 = side ? t2 : -t2;
             const int pt = (u1 + 1) * 3 + (u2 + 1);
-            int d[3];
-            d[a] = 1;
-            d[b] = u1;
-            d[cx] = u2;
-            const float xq = xc + half_h * d[0];
-            const float yq = yc + half_h * d[1];
-            const float rl[3] = {half_h * d[0], half_h * d[1], half_h * d[2]};
-            float rr[3] = {rl[0], rl[1], rl[2]};
-            rr[a] = -half_h;
+            const int d0 = axis_comp(0, a, b, 1, u1, u2), d1 = axis_comp(1, a, b, 1, u1, u2),
+                      d2 = axis_comp(2, a, b, 1, u1, u2);
+            const float xq = xc + half_h * d0;
+            const float yq = yc + half_h * d1;
+            const float rl[3] = {half_h * d0, half_h * d1, half_h * d2};
+            const float rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
             const float w = (u1 == 0 && u2 == 0) ? (16.f / 36.f) : (u1 == 0 || u2 == 0) ? (4.f / 36.f) : (1.f / 36.f);
             point32(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, PF, fsum, tl, tr, amax);
           }
@@ -131,11 +121,8 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
 #pragma unroll
         for (int m = 0; m < 3; ++m) tld[m] = (double)tl[m];
         if (j >= 1) {
-          int cc[3];
-          cc[a] = j - 1;
-          cc[b] = pb;
-          cc[cx] = pc;
-          const int cell = (cc[2] * N + cc[1]) * N + cc[0];
+          const int cell = (axis_comp(2, a, b, j - 1, pb, pc) * N + axis_comp(1, a, b, j - 1, pb, pc)) * N +
+                           axis_comp(0, a, b, j - 1, pb, pc);
           double* Da = D + (size_t)a * DQ * N3 + cell;
 #pragma unroll
           for (int k = 0; k < F; ++k) Da[k * N3] = fd[k] - fprev[k];
