@@ -147,7 +147,7 @@ ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 26
 # DRAM bytes per hydro_step launch on this workload from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), per precision form; None
 # until captured for the current kernel.
-TRAFFIC_PER_LAUNCH = {"fp64": 224351744.0, "mixed": 266578432.0}
+TRAFFIC_PER_LAUNCH = {"fp64": 205798400.0, "mixed": 248572160.0}
 
 
 def algorithmic_work():
