@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
     const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
     float amax = 0.f;
     float plus[9][F];
-    double fprev[F], trprev[3];  // previous face's sums, converted to FP64 once
+    // the previous face's FP32 sums (their FP64 values are these converted: exact)
+    float fprev[F], trprev[3];
     const int c0 = ((axis_comp(2, a, b, 0, pb, pc) + G) * S + (axis_comp(1, a, b, 0, pb, pc) + G)) * S +
                    (axis_comp(0, a, b, 0, pb, pc) + G);
 #pragma unroll 1
@@ -125,21 +126,21 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArg
                            axis_comp(0, a, b, j - 1, pb, pc);
           double* Da = D + (size_t)a * DQ * N3 + cell;
 #pragma unroll
-          for (int k = 0; k < F; ++k) Da[k * N3] = fd[k] - fprev[k];
+          for (int k = 0; k < F; ++k) Da[k * N3] = fd[k] - (double)fprev[k];
 #pragma unroll
-          for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = tld[m] - trprev[m];
+          for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = tld[m] - (double)trprev[m];
         }
 #pragma unroll
-        for (int k = 0; k < F; ++k) fprev[k] = fd[k];
+        for (int k = 0; k < F; ++k) fprev[k] = fsum[k];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) trprev[m] = (double)tr[m];
+        for (int m = 0; m < 3; ++m) trprev[m] = tr[m];
         if (A.face_flux && (j == 0 || j == N)) {
           // sub-grid boundary face: sums and the torque about the interior cell
           const int f = 2 * a + (j == N ? 1 : 0);
 #pragma unroll
           for (int k = 0; k < F; ++k) A.face_flux[face_index(s, f, k, pc, pb)] = fd[k];
 #pragma unroll
-          for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = (j == N) ? tld[m] : trprev[m];
+          for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = (j == N) ? tld[m] : (double)trprev[m];
         }
       }
     }
