@@ -280,12 +280,24 @@ typedef struct {
    * and bc are then ignored). */
   const hydro_amr_t* amr;
   double* face_flux;  /* [n_sub][6][F+3][N][N], used with amr */
+  /* Nonzero: the whole time step as one persistent launch (uniform mesh and
+   * HYDRO_PREC_MIXED only; otherwise the step returns EUNSUP).  Ghost cells
+   * are read from the neighbouring sub-grids' interiors instead of being
+   * filled, stages 1 and 2 apply their update inside the launch, and a
+   * sub-grid's third stage starts as soon as its 27 neighbours have finished
+   * their second (bounded waits; HYDRO_ST_TIMEOUT if one expires).  The
+   * interiors of the new state and *dt equal the separate launches' bit for
+   * bit; the ghost layers of the destination buffer are not written, and
+   * dUdt then holds the first stage's rates. */
+  int fused;
 } hydro_rk3_desc_t;
 
 typedef struct hydro_graph hydro_graph_t;
 
 /* Enqueue one time step on a stream: parity 0 advances a -> b, 1 advances
- * b -> a.  Ten launches.  Errors: EINVAL (inconsistent descriptor). */
+ * b -> a.  Ten launches (two with fused: a clear of the context's sync words
+ * and the step).  Errors: EINVAL (inconsistent descriptor), EUNSUP (fused
+ * with an adaptive mesh or in FP64), ENOMEM. */
 int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
 
 /* Capture the two directions of hydro_rk3_step once into CUDA graphs

@@ -20,6 +20,11 @@ cudaError_t launch_update(const double* U, double* Uout, const double* U0, const
 cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, double* out, cudaStream_t st);
 cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st);
 cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, cudaStream_t st);
+cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
+                             int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
+                             cudaStream_t st);
+cudaError_t prepare_rk3_fused(int num_sms, int* max_grid);
+size_t rk3_fused_sync_words(int n_sub);
 cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
                         double* sums, cudaStream_t st);
 }  // namespace hyd
@@ -62,6 +67,65 @@ static int step_slots(const hydro_ctx* c, bool mixed) {
   // per SM in mixed precision (110 KB each), unless the autotuner chose fewer
   if (c->slots_tuned[mixed ? 1 : 0] > 0) return c->slots_tuned[mixed ? 1 : 0];
   return mixed ? 2 * c->num_sms : c->num_sms;
+}
+
+static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, double* dUdt, double* amax,
+                                 double* face_flux) {
+  hyd::StepArgs64 A;
+  A.U = B->U;
+  A.origin = B->origin;
+  A.h = B->h;
+  A.g = B->g;
+  A.dUdt = dUdt;
+  A.amax = amax;
+  A.face_flux = face_flux;
+  A.scratch = c->scratch;
+  A.status = c->status;
+  A.n_sub = B->n_sub;
+  A.P.gamma = c->gamma;
+  A.P.gm1 = c->gamma - 1.0;
+  A.P.omega = c->omega;
+  A.P.eta1 = c->mode.de_eta1;
+  A.gate = c->gate_on ? 1 : 0;
+  A.gate_w = c->gate_w;
+  A.gate_logit_thr = (float)c->gate_logit_thr;
+  A.gate_zero_smooth = c->gate_zero_smooth;
+  return A;
+}
+
+int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
+  int rc = hydro_ctx_prepare(c, n_sub);
+  if (rc) return rc;
+  rc = ensure_buf(&c->u2, &c->u2_bytes, (size_t)n_sub * hyd::F * hyd::N3 * sizeof(double),
+                  "cudaMalloc(fused second-stage state)");
+  if (rc) return rc;
+  const size_t words = hyd::rk3_fused_sync_words(n_sub);
+  rc = ensure_buf(&c->sync, &c->sync_bytes, (words * sizeof(unsigned) + 7) / 8 * 8, "cudaMalloc(fused sync words)");
+  if (rc) return rc;
+  int max_grid = 0;
+  cudaError_t e = hyd::prepare_rk3_fused(c->num_sms, &max_grid);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_ctx_prepare_fused");
+  return HYDRO_OK;
+}
+
+int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st) {
+  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED) return HYDRO_EUNSUP;
+  if (d->bc != HYDRO_BC_PERIODIC && d->bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
+  if (!aligned16(d->a.U) || !aligned16(d->U_b) || !aligned16(d->dUdt)) return HYDRO_EINVAL;
+  int rc = hydro_ctx_prepare_fused(c, d->a.n_sub);
+  if (rc) return rc;
+  hydro_batch_t X = d->a;
+  double* Y = d->U_b;
+  if (parity) {
+    X.U = d->U_b;
+    Y = d->a.U;
+  }
+  const hyd::StepArgs64 S = step_args(c, &X, d->dUdt, d->amax, nullptr);
+  const double cfl = d->cfl > 0.0 ? d->cfl : c->mode.cfl;
+  cudaError_t e = hyd::launch_rk3_fused(S, Y, c->u2, d->dt, reinterpret_cast<unsigned*>(c->sync), d->nbx, d->nby,
+                                        d->nbz, d->bc, cfl, c->mode.de_eta2, c->gamma, c->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_rk3_step (fused)");
+  return HYDRO_OK;
 }
 
 int hydro_ctx_prepare(hydro_ctx* c, int n_sub) {
@@ -133,25 +197,7 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
-  hyd::StepArgs64 A;
-  A.U = B->U;
-  A.origin = B->origin;
-  A.h = B->h;
-  A.g = B->g;
-  A.dUdt = dUdt;
-  A.amax = amax;
-  A.face_flux = face_flux;
-  A.scratch = c->scratch;
-  A.status = c->status;
-  A.n_sub = B->n_sub;
-  A.P.gamma = c->gamma;
-  A.P.gm1 = c->gamma - 1.0;
-  A.P.omega = c->omega;
-  A.P.eta1 = c->mode.de_eta1;
-  A.gate = c->gate_on ? 1 : 0;
-  A.gate_w = c->gate_w;
-  A.gate_logit_thr = (float)c->gate_logit_thr;
-  A.gate_zero_smooth = c->gate_zero_smooth;
+  const hyd::StepArgs64 A = step_args(c, B, dUdt, amax, face_flux);
   cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, (cudaStream_t)stream)
                         : hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
@@ -325,6 +371,8 @@ void hydro_destroy(hydro_ctx_t* c) {
   if (c->scratch) cudaFree(c->scratch);
   if (c->part) cudaFree(c->part);
   if (c->gate_w) cudaFree(c->gate_w);
+  if (c->u2) cudaFree(c->u2);
+  if (c->sync) cudaFree(c->sync);
   delete c;
 }
 

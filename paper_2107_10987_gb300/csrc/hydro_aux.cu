@@ -6,16 +6,10 @@
 namespace hyd {
 
 // ---------------------------------------------------------------------------
-// RK3 stage update (three hydro iterations per time step, Sec. IV-A.2),
-// interior cells only:
-//   U <- alpha U0 + beta (U + dt dU/dt), (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3)
-//   then tau <- eps_E^(1/gamma) where eps_E = E - |s|^2/(2 rho) > eta2 E
-//   (tracer resync of the dual-energy formalism, Bryan et al. 1995).
-// FP64 form: explicitly rounded operations, the same values as the FP64
-// oracle.  Mixed form: the update and eps_E stay FP64 (FMA allowed, 1/rho
-// from an FP32 reciprocal refined by a Newton step), the tracer power is
-// taken in FP32 like the rest of the tracer's arithmetic in that form.
-// Out of place when Uout != U (the interior of Uout is written, U untouched).
+// RK3 stage update (three hydro iterations per time step, Sec. IV-A.2) of
+// the interior cells: the stage combination and tracer resync of rk3_cell,
+// FP64 or mixed form.  Out of place when Uout != U (the interior of Uout is
+// written, U untouched).
 struct UpdateArgs {
   const double* U;
   double* Uout;
@@ -36,31 +30,14 @@ __global__ void __launch_bounds__(256) hydro_update_kernel(UpdateArgs A) {
       const int x = c & (N - 1), y = (c >> 3) & (N - 1), z = c >> 6;
       const size_t uc = ub + ((z + G) * S + (y + G)) * S + (x + G);
       const size_t dc = db + c;
-      double u[F];
+      double U[F], U0[F], R[F], u[F];
 #pragma unroll
       for (int k = 0; k < F; ++k) {
-        const double U = A.U[uc + (size_t)k * S3], U0 = A.U0[uc + (size_t)k * S3];
-        const double R = A.dUdt[dc + (size_t)k * N3];
-        if (kMixed) {
-          u[k] = fma(A.alpha, U0, A.beta * fma(dt, R, U));
-        } else {
-          const double t = radd(U, rmul(dt, R));
-          u[k] = radd(rmul(A.alpha, U0), rmul(A.beta, t));
-        }
+        U[k] = A.U[uc + (size_t)k * S3];
+        U0[k] = A.U0[uc + (size_t)k * S3];
+        R[k] = A.dUdt[dc + (size_t)k * N3];
       }
-      const double rho = u[RHO];
-      if (kMixed) {
-        const double r0 = (double)__frcp_rn((float)rho);
-        const double ri = r0 * fma(-rho, r0, 2.0);
-        const double s2 = fma(u[SZ], u[SZ], fma(u[SY], u[SY], u[SX] * u[SX]));
-        const double eE = u[EGAS] - 0.5 * s2 * ri;
-        if (eE > A.eta2 * u[EGAS]) u[TAU] = (double)__powf((float)eE, (float)A.inv_gamma);
-      } else {
-        const double vx = u[SX] / rho, vy = u[SY] / rho, vz = u[SZ] / rho;
-        const double ek = rmul(rmul(0.5, rho), radd(radd(rmul(vx, vx), rmul(vy, vy)), rmul(vz, vz)));
-        const double eE = rsub(u[EGAS], ek);
-        if (eE > rmul(A.eta2, u[EGAS])) u[TAU] = pow(eE, A.inv_gamma);
-      }
+      rk3_cell<kMixed>(U, U0, R, dt, A.alpha, A.beta, A.eta2, A.inv_gamma, u);
 #pragma unroll
       for (int k = 0; k < F; ++k) A.Uout[uc + (size_t)k * S3] = u[k];
     }
@@ -116,10 +93,6 @@ struct GhostArgs {
   int nbx, nby, nbz, bc, n_sub;
 };
 
-__device__ __forceinline__ int bc_map(int gpos, int n, int bc) {
-  if (bc == 0) return gpos < 0 ? gpos + n : (gpos >= n ? gpos - n : gpos);  // |offset| <= G < n
-  return gpos < 0 ? 0 : (gpos >= n ? n - 1 : gpos);
-}
 
 // The kernel reads only interior cells and writes only ghost cells, so the
 // two sets never overlap: all loads of a batch of cells are issued before

@@ -71,6 +71,50 @@ __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 
+// ---- SSP-RK3 stage combination of one cell (Sec. IV-A.2) ----------------
+//   u <- alpha U0 + beta (U + dt dU/dt), (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3)
+//   then tau <- eps_E^(1/gamma) where eps_E = E - |s|^2/(2 rho) > eta2 E
+//   (tracer resync of the dual-energy formalism, Bryan et al. 1995).
+// One definition for every kernel that applies a stage, so that the separate
+// update kernel and the fused RK3 step give the same bits.
+// FP64 form: explicitly rounded operations (the oracle's values).  Mixed
+// form: FMA allowed, 1/rho from an FP32 reciprocal refined by a Newton step,
+// the tracer power in FP32 like the rest of the tracer's arithmetic there.
+template <bool kMixed>
+__device__ __forceinline__ void rk3_cell(const double U[F], const double U0[F], const double R[F], double dt,
+                                         double alpha, double beta, double eta2, double inv_gamma, double u[F]) {
+#pragma unroll
+  for (int k = 0; k < F; ++k) {
+    if (kMixed) {
+      u[k] = fma(alpha, U0[k], beta * fma(dt, R[k], U[k]));
+    } else {
+      const double t = radd(U[k], rmul(dt, R[k]));
+      u[k] = radd(rmul(alpha, U0[k]), rmul(beta, t));
+    }
+  }
+  const double rho = u[RHO];
+  if (kMixed) {
+    const double r0 = (double)__frcp_rn((float)rho);
+    const double ri = r0 * fma(-rho, r0, 2.0);
+    const double s2 = fma(u[SZ], u[SZ], fma(u[SY], u[SY], u[SX] * u[SX]));
+    const double eE = u[EGAS] - 0.5 * s2 * ri;
+    if (eE > eta2 * u[EGAS]) u[TAU] = (double)__powf((float)eE, (float)inv_gamma);
+  } else {
+    const double vx = u[SX] / rho, vy = u[SY] / rho, vz = u[SZ] / rho;
+    const double ek = rmul(rmul(0.5, rho), radd(radd(rmul(vx, vx), rmul(vy, vy)), rmul(vz, vz)));
+    const double eE = rsub(u[EGAS], ek);
+    if (eE > rmul(eta2, u[EGAS])) u[TAU] = pow(eE, inv_gamma);
+  }
+}
+
+// Uniform-mesh boundary map of one global cell coordinate (n cells along the
+// axis, |overshoot| <= G < n): periodic wraps, outflow clamps to the nearest
+// interior cell (zero gradient).
+__device__ __forceinline__ int bc_map(int gpos, int n, int bc) {
+  if (bc == 0) return gpos < 0 ? gpos + n : (gpos >= n ? gpos - n : gpos);
+  return gpos < 0 ? 0 : (gpos >= n ? n - 1 : gpos);
+}
+
 // ---- mbarrier + bulk (TMA) copy, inline PTX -----------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

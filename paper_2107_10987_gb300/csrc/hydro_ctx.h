@@ -2,6 +2,8 @@
 #pragma once
 #include <cstddef>
 
+#include <cuda_runtime.h>
+
 #include "hydro.h"
 
 struct hydro_ctx {
@@ -20,9 +22,19 @@ struct hydro_ctx {
   double gate_logit_thr; // smooth where the indicator's logit is below this
   int gate_zero_smooth;  // decision for all-zero features, set with the parameters
   float* gate_w;         // BF16-rounded indicator parameters (device)
+  double* u2;            // fused RK3 step: second-stage state [n_sub][F][N^3]
+  size_t u2_bytes;
+  double* sync;          // fused RK3 step: barrier, work counter and per-sub-grid flags (unsigned words)
+  size_t sync_bytes;
 };
 
 // Allocate the context's status word and the step scratch for a batch of
 // n_sub sub-grids, and opt the step kernels in to their shared memory, so
 // that later launches allocate nothing (needed before a stream capture).
 int hydro_ctx_prepare(hydro_ctx* c, int n_sub);
+
+// Enqueue the fused RK3 time step (hydro_rk3_desc_t.fused) of a uniform mesh,
+// allocating its buffers on first use (hydro_ctx_prepare_fused before a
+// capture).
+int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub);
+int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st);

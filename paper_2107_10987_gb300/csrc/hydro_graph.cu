@@ -3,7 +3,9 @@
 // launches on one stream, and the same sequence captured once into CUDA
 // graphs that are replayed step after step.
 //
-// One time step (three hydro iterations, Sec. IV-A.2), state X -> Y:
+// One time step (three hydro iterations, Sec. IV-A.2), state X -> Y (the
+// fused form, one persistent launch for a uniform mesh in mixed precision,
+// is in hydro_rk3_fused.cu):
 //   ghost(X); step(X) -> dU, amax; dt = cfl min h/amax; Y = X + dt dU
 //   ghost(Y); step(Y);            Y = 3/4 X + 1/4 (Y + dt dU)
 //   ghost(Y); step(Y);            Y = 1/3 X + 2/3 (Y + dt dU)
@@ -27,6 +29,7 @@ struct hydro_graph {
 };
 
 static int rk3_enqueue(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, cudaStream_t st) {
+  if (d->fused) return hydro_rk3_fused_enqueue(ctx, d, parity, st);
   hydro_batch_t X = d->a, Y = d->a;
   if (parity) X.U = d->U_b;
   else Y.U = d->U_b;
@@ -75,7 +78,7 @@ int hydro_rk3_graph_create(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, hydro_gr
     return HYDRO_ECUDA;
   }
   // everything the launches need is allocated before the capture
-  int rc = hydro_ctx_prepare(ctx, d->a.n_sub);
+  int rc = d->fused ? hydro_ctx_prepare_fused(ctx, d->a.n_sub) : hydro_ctx_prepare(ctx, d->a.n_sub);
   for (int p = 0; p < 2 && rc == HYDRO_OK; ++p) {
     if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       rc = HYDRO_ECUDA;

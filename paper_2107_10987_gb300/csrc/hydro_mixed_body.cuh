@@ -1,0 +1,236 @@
+// hydro_mixed_body.cuh -- one sub-grid of the mixed-precision hydro step.
+// The body is shared by the step kernel (hydro_step_mixed.cu) and the fused
+// uniform-mesh RK3 step (hydro_rk3_fused.cu).  They differ only in where the
+// sub-grid's state comes from and where its results go (the Io policy below).
+//
+// Same sweep as the FP64 step (see hydro_step_fp64.cu): PPM on the 13 lines
+// through each cell, Kurganov-Tadmor fluxes at the 9 points of every face,
+// Simpson face sums, divergence, sources, amax.  Precision split:
+//   FP64: the dual-energy internal-energy recovery eps_E = E - |s|^2/(2 rho)
+//         and its selection (cancellation between E and the kinetic energy),
+//         the per-axis flux differences F(i+1/2) - F(i-1/2) (exact in FP64
+//         from FP32 face sums), the divergence accumulation, the sources and
+//         the output dU/dt;
+//   FP32: primitives in shared memory, PPM, the point fluxes, signal speeds
+//         and the face quadrature.
+// The primitives are half the size of the FP64 stage, so two CTAs share an
+// SM: while one converts its next sub-grid (HBM/L2-bound loads), the other
+// sweeps (FP32-bound).  The conversion reads the FP64 state with coalesced
+// loads and writes FP32 primitives: a bulk TMA copy cannot convert, and an
+// FP64 staging buffer would not fit beside the FP32 primitives of two CTAs.
+#pragma once
+#include "hydro_mixed.cuh"
+
+namespace hyd {
+
+constexpr int kThreadsMx = NROW;  // 192
+
+// Dynamic shared memory of one CTA: FP32 primitives [F][S3], then two
+// [S3] byte arrays of smooth flags (learned indicator).
+constexpr size_t kMixedSmemBytes = (size_t)F * S3 * sizeof(float) + 2 * S3;
+
+// This thread's row: axis a, transverse axes b < cx at positions pb, pc.
+// Warp w of the axis takes pb in [4w, 4w+4) x pc in [0, 8).  With the cell
+// strides (1, 14, 196) every FP32 stencil load of a warp then spans 32
+// (y rows) or 16 (x and z rows) distinct banks: 1- or 2-way conflicts,
+// against 2- to 4-way with pb running fastest over the warp.
+struct RowMap {
+  int a, b, cx, pb, pc, sa, sb, sc;
+};
+__device__ __forceinline__ RowMap row_map(int tid) {
+  static_assert(N == 8 && S == 14, "row-to-warp map assumes 8^3 interiors with 3-cell ghosts");
+  RowMap R;
+  R.a = tid / (N * N);
+  const int r = tid % (N * N);
+  R.pb = ((r >> 5) << 2) | (r & 3);
+  R.pc = (r & 31) >> 2;
+  R.b = (R.a == 0) ? 1 : 0;
+  R.cx = (R.a == 2) ? 1 : 2;
+  R.sa = axis_stride(R.a);
+  R.sb = axis_stride(R.b);
+  R.sc = axis_stride(R.cx);
+  return R;
+}
+
+// One sub-grid s.  Io supplies the state and takes the results:
+//   typename Io::Sub io.begin(s)                    per-sub-grid context
+//   io.load(sub, c, u)        conserved state u[F] of padded cell c
+//   io.own(sub, c, uc, u)     conserved state of interior cell c (padded index uc)
+//   io.store(sub, c, uc, du, u)  dU/dt of interior cell c; u is its state from own()
+//   io.amax(sub, m)           the sub-grid's maximum signal speed (thread 0)
+// Qf: the CTA's dynamic shared memory; red: [kThreadsMx / 32] floats of
+// shared memory; D: the CTA's scratch (kScratchPerSub doubles).  Ends with
+// a barrier, so the next sub-grid may reuse all of them.
+template <bool kGate, class Io>
+__device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io, int s, const RowMap& R, float* Qf,
+                                              float* red, double* __restrict__ D) {
+  uint8_t* smooth = reinterpret_cast<uint8_t*>(Qf + F * S3);
+  const int tid = threadIdx.x;
+  const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega};
+  const int a = R.a, b = R.b, pb = R.pb, pc = R.pc, sa = R.sa, sb = R.sb, sc = R.sc;
+  const typename Io::Sub sub = io.begin(s);
+
+  // ---- 1-2. load the FP64 state, recover primitives, store FP32 ---------
+  bool bad = false;
+  for (int c = tid; c < S3; c += kThreadsMx) {
+    double u[F];
+    io.load(sub, c, u);
+    float q[F];
+    bad |= !prims_mixed(u, A.P.eta1, PF.gamma, q);
+#pragma unroll
+    for (int k = 0; k < F; ++k) Qf[k * S3 + c] = q[k];
+  }
+  if (bad) atomicOr(A.status, 1u);
+  __syncthreads();
+
+  // ---- 2b. learned smoothness indicator (gate_phase) ---------------------
+  if (kGate)
+    gate_phase<float, kThreadsMx>(Qf, PF.gm1, A.gate_w, A.gate_logit_thr, A.gate_zero_smooth, smooth, smooth + S3);
+
+  // ---- 3. row sweep in FP32 --------------------------------------------
+  const double hd = A.h[s];
+  const float h = (float)hd, half_h = 0.5f * h;
+  const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
+  float amax = 0.f;
+  float plus[9][F];
+  // the previous face's FP32 sums (their FP64 values are these converted: exact)
+  float fprev[F], trprev[3];
+  const int c0 = ((axis_comp(2, a, b, 0, pb, pc) + G) * S + (axis_comp(1, a, b, 0, pb, pc) + G)) * S +
+                 (axis_comp(0, a, b, 0, pb, pc) + G);
+#pragma unroll 1
+  for (int j = -1; j <= N; ++j) {
+    const int cj = c0 + j * sa;
+    float fsum[F], tl[3], tr[3];
+#pragma unroll
+    for (int k = 0; k < F; ++k) fsum[k] = 0.f;
+    tl[0] = tl[1] = tl[2] = 0.f;
+    tr[0] = tr[1] = tr[2] = 0.f;
+    // cell-centre coordinates of the left cell j - 1 (FP64 -> FP32 once)
+    const float xc = (float)(o[0] + hd * (axis_comp(0, a, b, j - 1, pb, pc) + 0.5)),
+                yc = (float)(o[1] + hd * (axis_comp(1, a, b, j - 1, pb, pc) + 0.5));
+#pragma unroll 1
+    for (int p = 0; p <= 4; ++p) {
+      const int t1 = p / 3 - 1, t2 = p % 3 - 1;
+      float qpA[F], qmA[F], qpB[F], qmB[F];
+      if (kGate && smooth[cj]) {
+        line10u(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
+        if (p != 4) line10u(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+      } else {
+        line10f(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
+        if (p != 4) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+      }
+      if (j >= 0) {
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+          if (p == 4 && side == 1) continue;
+          const int u1 = side ? t1 : -t1, u2 = side ? t2 : -t2;
+          const int pt = (u1 + 1) * 3 + (u2 + 1);
+          const int d0 = axis_comp(0, a, b, 1, u1, u2), d1 = axis_comp(1, a, b, 1, u1, u2),
+                    d2 = axis_comp(2, a, b, 1, u1, u2);
+          const float xq = xc + half_h * d0;
+          const float yq = yc + half_h * d1;
+          const float rl[3] = {half_h * d0, half_h * d1, half_h * d2};
+          const float rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
+          const float w = (u1 == 0 && u2 == 0) ? (16.f / 36.f) : (u1 == 0 || u2 == 0) ? (4.f / 36.f) : (1.f / 36.f);
+          point32(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, PF, fsum, tl, tr, amax);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < F; ++k) {
+        plus[p][k] = qpA[k];
+        if (p != 4) plus[8 - p][k] = qpB[k];
+      }
+    }
+    if (j >= 0) {
+      // face j-1/2 is complete: its sums in FP64 (each converted once); the
+      // a-difference of cell j-1 is exact in FP64
+      double fd[F], tld[3];
+#pragma unroll
+      for (int k = 0; k < F; ++k) fd[k] = (double)fsum[k];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) tld[m] = (double)tl[m];
+      if (j >= 1) {
+        const int cell = (axis_comp(2, a, b, j - 1, pb, pc) * N + axis_comp(1, a, b, j - 1, pb, pc)) * N +
+                         axis_comp(0, a, b, j - 1, pb, pc);
+        double* Da = D + (size_t)a * DQ * N3 + cell;
+#pragma unroll
+        for (int k = 0; k < F; ++k) Da[k * N3] = fd[k] - (double)fprev[k];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = tld[m] - (double)trprev[m];
+      }
+#pragma unroll
+      for (int k = 0; k < F; ++k) fprev[k] = fsum[k];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) trprev[m] = tr[m];
+      if (A.face_flux && (j == 0 || j == N)) {
+        // sub-grid boundary face: sums and the torque about the interior cell
+        const int f = 2 * a + (j == N ? 1 : 0);
+#pragma unroll
+        for (int k = 0; k < F; ++k) A.face_flux[face_index(s, f, k, pc, pb)] = fd[k];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = (j == N) ? tld[m] : (double)trprev[m];
+      }
+    }
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o2));
+  if ((tid & 31) == 0) red[tid >> 5] = amax;
+  __syncthreads();
+
+  // ---- 4. divergence + sources in FP64 --------------------------------
+  const double inv_h = 1.0 / hd;
+  const double om = A.P.omega;
+  for (int c = tid; c < N3; c += kThreadsMx) {
+    const int x = c % N, y = (c / N) % N, z = c / (N * N);
+    const int uc = ((z + G) * S + (y + G)) * S + (x + G);
+    double du[F];
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+      const double div = (D[(0 * DQ + k) * N3 + c] + D[(1 * DQ + k) * N3 + c]) + D[(2 * DQ + k) * N3 + c];
+      du[k] = -(div * inv_h);
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double tq =
+          (D[(0 * DQ + F + m) * N3 + c] + D[(1 * DQ + F + m) * N3 + c]) + D[(2 * DQ + F + m) * N3 + c];
+      du[ZX + m] = du[ZX + m] - tq * inv_h;
+    }
+    double uin[F];
+    io.own(sub, c, uc, uin);
+    const double sx = uin[SX], sy = uin[SY], sz = uin[SZ];
+    du[SX] = du[SX] + om * sy;
+    du[SY] = du[SY] - om * sx;
+    du[ZX] = du[ZX] + om * uin[ZY];
+    du[ZY] = du[ZY] - om * uin[ZX];
+    {
+      // spin source w(x_c) x s, w = -omega z_hat x x_c: removes the torque
+      // that the frame part s w_n of the momentum flux leaves in the face
+      // torques, so that sum (x_c x s + z)_z is conserved for omega != 0
+      const double xc = __dadd_rn(o[0], __dmul_rn(hd, x + 0.5));
+      const double yc = __dadd_rn(o[1], __dmul_rn(hd, y + 0.5));
+      const double wx = om * yc, wy = -(om * xc);
+      du[ZX] = du[ZX] + wy * sz;
+      du[ZY] = du[ZY] - wx * sz;
+      du[ZZ] = du[ZZ] + (wx * sy - wy * sx);
+    }
+    if (A.g) {
+      const double* gs = A.g + (size_t)s * 3 * N3;
+      const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];
+      const double rho = uin[RHO];
+      du[SX] = du[SX] + rho * gx;
+      du[SY] = du[SY] + rho * gy;
+      du[SZ] = du[SZ] + rho * gz;
+      du[EGAS] = du[EGAS] + ((sx * gx + sy * gy) + sz * gz);
+    }
+    io.store(sub, c, uc, du, uin);
+  }
+  if (tid == 0) {
+    float m = red[0];
+#pragma unroll
+    for (int w = 1; w < kThreadsMx / 32; ++w) m = fmaxf(m, red[w]);
+    io.amax(sub, (double)m);
+  }
+  __syncthreads();
+}
+
+}  // namespace hyd

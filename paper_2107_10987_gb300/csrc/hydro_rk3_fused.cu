@@ -1,0 +1,305 @@
+// hydro_rk3_fused.cu -- one whole SSP-RK3 time step (three hydro iterations,
+// Sec. IV-A.2) of a uniform mesh in mixed precision, as one persistent
+// cooperative launch.
+//
+// The separate-launch step (hydro_graph.cu) runs per stage a ghost fill, the
+// step kernel and the update, with the whole mesh finishing each launch
+// before the next starts.  Here, state X -> Y:
+//   stage 0  every sub-grid: dU0 = L(X), amax (static schedule);
+//            one grid-wide barrier; dt = cfl min h/amax (every CTA);
+//   stage 1  sub-grid s reads U1 = X + dt dU0 (with the tracer resync)
+//            computed on the fly and writes U2 = 3/4 X + 1/4 (U1 + dt L(U1))
+//            to an interior-only scratch;
+//   stage 2  sub-grid s reads U2 and writes U3 = 1/3 X + 2/3 (U2 + dt L(U2))
+//            into the interiors of Y.
+// Ghost cells are read straight from the neighbouring sub-grids' interiors
+// through the boundary map of hydro_fill_ghosts_uniform, so no ghost layer
+// is written and no separate update runs.  Stage-1 and stage-2 sub-grids come
+// from one work counter, all stage-1 ones first; a stage-2 sub-grid waits
+// until its 27 neighbours (itself included) have published U2.  Every unit a
+// CTA waits for was taken earlier by a CTA that never waits, so the waits
+// end; each is still bounded in time and reports HYDRO_ST_TIMEOUT.
+//
+// The per-cell arithmetic is the separate-launch step's own (the same
+// sub-grid body and rk3_cell with the same operands), so the interiors of Y
+// and dt equal its results bit for bit.  The ghost layers of Y are not
+// written, and dUdt holds the first stage's rates.
+#include "hydro_mixed_body.cuh"
+
+namespace hyd {
+
+struct FusedArgs {
+  StepArgs64 S;         // U = X (padded), dUdt = dU0 [n][F][N3], amax, scratch, status, ...
+  double* Y;            // padded output state (interiors written)
+  double* U2;           // [n][F][N3] second-stage state
+  double* dt_out;       // the step's dt
+  unsigned* sync;       // zero at launch: [0] barrier arrivals, [1] work counter,
+                        // [2] abort, [kSyncHead + s] U2 of sub-grid s published
+  int nbx, nby, nbz, bc;
+  double cfl, eta2, inv_gamma;
+  double alpha[3], beta[3];  // the stage coefficients of the update kernel
+  long long wait_ns;    // bound of every wait
+};
+constexpr int kSyncHead = 4;
+
+// Where the sub-grid's state comes from, per stage (see above).
+struct FusedIo {
+  const FusedArgs& A;
+  int stage;
+  double dt;
+  struct Sub {
+    int s, kx, ky, kz;
+  };
+  __device__ __forceinline__ Sub begin(int s) const {
+    return Sub{s, s % A.nbx, (s / A.nbx) % A.nby, s / (A.nbx * A.nby)};
+  }
+  // Stage input state of interior cell (os; oi compact, op padded index).
+  __device__ __forceinline__ void state(int os, int oi, int op, double u[F]) const {
+    if (stage == 0) {
+      const double* __restrict__ x = A.S.U + (size_t)os * F * S3 + op;
+#pragma unroll
+      for (int k = 0; k < F; ++k) u[k] = __ldg(x + (size_t)k * S3);
+    } else if (stage == 1) {
+      const double* __restrict__ x = A.S.U + (size_t)os * F * S3 + op;
+      const double* r = A.S.dUdt + (size_t)os * F * N3 + oi;
+      double xv[F], rv[F];
+#pragma unroll
+      for (int k = 0; k < F; ++k) {
+        xv[k] = __ldg(x + (size_t)k * S3);
+        rv[k] = __ldcg(r + (size_t)k * N3);
+      }
+      rk3_cell<true>(xv, xv, rv, dt, A.alpha[0], A.beta[0], A.eta2, A.inv_gamma, u);
+    } else {
+      const double* q = A.U2 + (size_t)os * F * N3 + oi;
+#pragma unroll
+      for (int k = 0; k < F; ++k) u[k] = __ldcg(q + (size_t)k * N3);
+    }
+  }
+  __device__ __forceinline__ void load(const Sub& q, int c, double u[F]) const {
+    const int nx = A.nbx * N, ny = A.nby * N, nz = A.nbz * N;
+    const int gx = bc_map(q.kx * N + c % S - G, nx, A.bc);
+    const int gy = bc_map(q.ky * N + (c / S) % S - G, ny, A.bc);
+    const int gz = bc_map(q.kz * N + c / (S * S) - G, nz, A.bc);
+    const int os = ((gz >> 3) * A.nby + (gy >> 3)) * A.nbx + (gx >> 3);
+    const int ix = gx & (N - 1), iy = gy & (N - 1), iz = gz & (N - 1);
+    state(os, (iz * N + iy) * N + ix, ((iz + G) * S + (iy + G)) * S + (ix + G), u);
+  }
+  __device__ __forceinline__ void own(const Sub& q, int c, int uc, double u[F]) const { state(q.s, c, uc, u); }
+  __device__ __forceinline__ void store(const Sub& q, int c, int uc, const double du[F], const double u[F]) const {
+    if (stage == 0) {
+      double* r = A.S.dUdt + (size_t)q.s * F * N3 + c;
+#pragma unroll
+      for (int k = 0; k < F; ++k) r[(size_t)k * N3] = du[k];
+      return;
+    }
+    const double* __restrict__ x = A.S.U + (size_t)q.s * F * S3 + uc;
+    double xv[F], un[F];
+#pragma unroll
+    for (int k = 0; k < F; ++k) xv[k] = __ldg(x + (size_t)k * S3);
+    rk3_cell<true>(u, xv, du, dt, A.alpha[stage], A.beta[stage], A.eta2, A.inv_gamma, un);
+    if (stage == 1) {
+      double* o = A.U2 + (size_t)q.s * F * N3 + c;
+#pragma unroll
+      for (int k = 0; k < F; ++k) o[(size_t)k * N3] = un[k];
+    } else {
+      double* o = A.Y + (size_t)q.s * F * S3 + uc;
+#pragma unroll
+      for (int k = 0; k < F; ++k) o[(size_t)k * S3] = un[k];
+    }
+  }
+  __device__ __forceinline__ void amax(const Sub& q, double m) const {
+    if (stage == 0) A.S.amax[q.s] = m;
+  }
+};
+
+// ---- bounded inter-CTA waits ---------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait until *p >= target.  Gives up (false) after limit_ns of polling, after
+// 2^26 polls whatever the clock says, or as soon as *abort is set.
+__device__ bool wait_geq(const unsigned* p, unsigned target, const unsigned* abort, long long limit_ns) {
+  if (ld_acquire(p) >= target) return true;
+  const unsigned long long t0 = global_ns();
+  for (long i = 0; i < (1l << 26); ++i) {
+    __nanosleep(128);
+    if (ld_acquire(p) >= target) return true;
+    if (ld_acquire(abort) != 0u) return false;
+    if ((long long)(global_ns() - t0) > limit_ns) return false;
+  }
+  return false;
+}
+
+template <bool kGate>
+__global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArgs A) {
+  extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [2][S3] smooth flags
+  __shared__ float red[kThreadsMx / 32];
+  __shared__ double dred[kThreadsMx / 32];
+  __shared__ int sh_unit, sh_ok;
+  const int tid = threadIdx.x;
+  const int n = A.S.n_sub;
+  double* __restrict__ D = A.S.scratch + (size_t)blockIdx.x * kScratchPerSub;
+  unsigned* arrive = A.sync;
+  unsigned* counter = A.sync + 1;
+  unsigned* abort = A.sync + 2;
+  unsigned* published = A.sync + kSyncHead;
+  const RowMap R = row_map(tid);
+
+  // ---- stage 0 --------------------------------------------------------
+  {
+    const FusedIo io{A, 0, 0.0};
+    for (int s = blockIdx.x; s < n; s += gridDim.x) mixed_subgrid<kGate>(A.S, io, s, R, Qf, red, D);
+  }
+
+  // ---- grid-wide barrier, then dt (the reduction of hydro_dt_kernel) ----
+  if (tid == 0) {
+    __threadfence();
+    atomicAdd(arrive, 1u);
+    const bool ok = wait_geq(arrive, gridDim.x, abort, A.wait_ns);
+    if (!ok) {
+      atomicOr(A.S.status, 2u);
+      atomicExch(abort, 1u);
+    }
+    sh_ok = ok;
+  }
+  __syncthreads();
+  if (!sh_ok) return;
+  double m = INFINITY;
+  for (int i = tid; i < n; i += kThreadsMx) m = fmin(m, A.S.h[i] / __ldcg(A.S.amax + i));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) dred[tid >> 5] = m;
+  __syncthreads();
+  m = dred[0];
+#pragma unroll
+  for (int w = 1; w < kThreadsMx / 32; ++w) m = fmin(m, dred[w]);
+  const double dt = A.cfl * m;
+  if (blockIdx.x == 0 && tid == 0) *A.dt_out = dt;
+
+  // ---- stages 1 and 2 from one work counter ---------------------------
+  for (;;) {
+    if (tid == 0) {
+      int u = (int)atomicAdd(counter, 1u);
+      if (ld_acquire(abort) != 0u) u = 2 * n;
+      sh_unit = u;
+    }
+    __syncthreads();
+    const int u = sh_unit;
+    if (u >= 2 * n) break;
+    const int stage = u < n ? 1 : 2;
+    const int s = stage == 1 ? u : u - n;
+    if (stage == 2) {
+      if (tid == 0) sh_ok = 1;
+      __syncthreads();
+      if (tid < 27) {
+        // neighbour (dx, dy, dz) in {-1, 0, 1}^3 under the boundary map
+        const int kx = s % A.nbx, ky = (s / A.nbx) % A.nby, kz = s / (A.nbx * A.nby);
+        int nx = kx + tid % 3 - 1, ny = ky + (tid / 3) % 3 - 1, nz = kz + tid / 9 - 1;
+        if (A.bc == 0) {
+          nx = (nx + A.nbx) % A.nbx;
+          ny = (ny + A.nby) % A.nby;
+          nz = (nz + A.nbz) % A.nbz;
+        } else {
+          nx = min(max(nx, 0), A.nbx - 1);
+          ny = min(max(ny, 0), A.nby - 1);
+          nz = min(max(nz, 0), A.nbz - 1);
+        }
+        if (!wait_geq(published + (nz * A.nby + ny) * A.nbx + nx, 1u, abort, A.wait_ns)) {
+          atomicOr(A.S.status, 2u);
+          atomicExch(abort, 1u);
+          sh_ok = 0;
+        }
+      }
+      __syncthreads();
+      if (!sh_ok) break;
+    }
+    mixed_subgrid<kGate>(A.S, FusedIo{A, stage, dt}, s, R, Qf, red, D);  // ends with a barrier
+    if (stage == 1 && tid == 0) {
+      __threadfence();
+      st_release(published + s, 1u);
+    }
+  }
+}
+
+size_t rk3_fused_sync_words(int n_sub) { return (size_t)kSyncHead + (size_t)n_sub; }
+
+// Opt in to the dynamic shared memory; the most CTAs of the kernel that can
+// be resident at once (the cooperative launch's limit).
+cudaError_t prepare_rk3_fused(int num_sms, int* max_grid) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int p0 = 0, p1 = 0;
+    cudaError_t e = cudaFuncSetAttribute(hydro_rk3_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMixedSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hydro_rk3_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kMixedSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, hydro_rk3_fused_kernel<false>, kThreadsMx,
+                                                        kMixedSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, hydro_rk3_fused_kernel<true>, kThreadsMx,
+                                                        kMixedSmemBytes);
+    if (e != cudaSuccess) return e;
+    per_sm = p0 < p1 ? p0 : p1;
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  *max_grid = per_sm * num_sms;
+  return cudaSuccess;
+}
+
+// sync must hold rk3_fused_sync_words(n_sub) words; it is cleared here.
+cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
+                             int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
+                             cudaStream_t st) {
+  int max_grid = 0;
+  cudaError_t e = prepare_rk3_fused(num_sms, &max_grid);
+  if (e != cudaSuccess) return e;
+  FusedArgs A;
+  A.S = S;
+  A.Y = Y;
+  A.U2 = U2;
+  A.dt_out = dt_out;
+  A.sync = sync;
+  A.nbx = nbx;
+  A.nby = nby;
+  A.nbz = nbz;
+  A.bc = bc;
+  A.cfl = cfl;
+  A.eta2 = eta2;
+  A.inv_gamma = 1.0 / gamma;
+  const double alpha[3] = {0.0, 0.75, 1.0 / 3.0}, beta[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int k = 0; k < 3; ++k) {
+    A.alpha[k] = alpha[k];
+    A.beta[k] = beta[k];
+  }
+  // a second plus 20 us per sub-grid: far above any stage's duration
+  A.wait_ns = 1000000000ll + 20000ll * (long long)S.n_sub;
+  e = cudaMemsetAsync(sync, 0, rk3_fused_sync_words(S.n_sub) * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(S.n_sub < max_grid ? S.n_sub : max_grid));
+  cfg.blockDim = dim3(kThreadsMx);
+  cfg.dynamicSmemBytes = kMixedSmemBytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (S.gate) return cudaLaunchKernelEx(&cfg, hydro_rk3_fused_kernel<true>, A);
+  return cudaLaunchKernelEx(&cfg, hydro_rk3_fused_kernel<false>, A);
+}
+
+}  // namespace hyd

@@ -206,10 +206,15 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
   }
   __syncthreads();
 
-  // this thread's row: axis a, transverse axes b < c at positions pb, pc
+  // this thread's row: axis a, transverse axes b < c at positions pb, pc.
+  // Warp w of the axis takes pb in [4w, 4w+4) x pc in [0, 8): with the cell
+  // strides (1, 14, 196) each half-warp's FP64 stencil loads then fall on 16
+  // (y rows) or 8 (x and z rows) distinct bank pairs, against 8 for all axes
+  // with pb running fastest.
+  static_assert(N == 8 && S == 14, "row-to-warp map assumes 8^3 interiors with 3-cell ghosts");
   const int a = tid / (N * N);
   const int r = tid % (N * N);
-  const int pb = r % N, pc = r / N;
+  const int pb = ((r >> 5) << 2) | (r & 3), pc = (r & 31) >> 2;
   const int b = (a == 0) ? 1 : 0;
   const int cx = (a == 2) ? 1 : 2;
   const int sa = axis_stride(a), sb = axis_stride(b), sc = axis_stride(cx);

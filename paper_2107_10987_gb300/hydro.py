@@ -55,7 +55,7 @@ class Batch(C.Structure):
 class RK3Desc(C.Structure):
     _fields_ = [("a", Batch), ("U_b", C.c_void_p), ("nbx", C.c_int), ("nby", C.c_int), ("nbz", C.c_int),
                 ("bc", C.c_int), ("dUdt", C.c_void_p), ("amax", C.c_void_p), ("dt", C.c_void_p), ("cfl", C.c_double),
-                ("amr", C.c_void_p), ("face_flux", C.c_void_p)]
+                ("amr", C.c_void_p), ("face_flux", C.c_void_p), ("fused", C.c_int)]
 
 
 _L = None
@@ -255,13 +255,16 @@ def hydro_step_static(ctx, batch: Batch, dt: float, dUdt, amax, status=None, str
                                     _stream(stream)), "hydro_step_static")
 
 
-def make_rk3_desc(Ua, Ub, origin, h, nb, bc, dUdt, amax, dt, cfl=0.4, g=None, mesh=None, face_flux=None) -> RK3Desc:
+def make_rk3_desc(Ua, Ub, origin, h, nb, bc, dUdt, amax, dt, cfl=0.4, g=None, mesh=None, face_flux=None,
+                  fused=False) -> RK3Desc:
     """Descriptor of one RK3 time step: of a uniform mesh of nb = (nbx, nby, nbz)
     sub-grids, or (mesh: an amr.AMRMesh, face_flux its work buffer) of an
-    adaptive mesh."""
+    adaptive mesh.  fused: the whole step as one persistent launch (uniform
+    mesh, mixed precision)."""
     nb = nb or (0, 0, 0)
     d = RK3Desc(make_batch(Ua, origin, h, g), _ptr(Ub), nb[0], nb[1], nb[2], bc, _ptr(dUdt), _ptr(amax), _ptr(dt),
-                float(cfl), C.addressof(mesh.desc) if mesh is not None else None, _ptr(face_flux))
+                float(cfl), C.addressof(mesh.desc) if mesh is not None else None, _ptr(face_flux),
+                1 if fused else 0)
     d._keep = (Ua, Ub, origin, h, g, dUdt, amax, dt, mesh, face_flux)
     return d
 

@@ -17,10 +17,12 @@ from . import hydro as H
 
 class UniformRun:
     def __init__(self, ctx, U, origin, h, nb, bc: int = H.HYDRO_BC_OUTFLOW, g=None, cfl: float = 0.4,
-                 device="cuda"):
+                 device="cuda", fused: bool = False):
         """U: [n][F][N][N][N] interiors or [n][F][S][S][S] padded states (array
         or tensor); origin [n][3]; h scalar or [n]; nb = (nbx, nby, nbz) or an
-        int; g: optional [n][3][N][N][N] gravitational acceleration."""
+        int; g: optional [n][3][N][N][N] gravitational acceleration; fused:
+        each time step as one persistent launch (mixed precision; the ghost
+        layers of the state buffers are then not maintained)."""
         self.ctx = ctx
         self.nb = (nb, nb, nb) if isinstance(nb, int) else tuple(nb)
         U = torch.as_tensor(U)
@@ -40,7 +42,7 @@ class UniformRun:
         self.dt = torch.empty(1, dtype=torch.float64, device=device)
         self.sums_buf = torch.empty(11, dtype=torch.float64, device=device)
         self.desc = H.make_rk3_desc(self.bufs[0], self.bufs[1], self.origin, self.h, self.nb, bc, self.dU, self.am,
-                                    self.dt, cfl, g=self.g)
+                                    self.dt, cfl, g=self.g, fused=fused)
         self.batches = (H.make_batch(self.bufs[0], self.origin, self.h, self.g),
                         H.make_batch(self.bufs[1], self.origin, self.h, self.g))
         self.parity = 0

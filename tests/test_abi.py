@@ -64,3 +64,34 @@ def test_kernels_compiled_for_sm103a():
     from paper_2107_10987_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
     assert os.path.exists(_build.LIB)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's field
+    offsets and size (a field added on one side only fails here)."""
+    import shutil
+    import subprocess
+    from paper_2107_10987_gb300 import amr, hydro as H
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [(H.Layout, "hydro_layout_t"), (H.Mode, "hydro_mode_t"), (H.Batch, "hydro_batch_t"),
+             (H.RK3Desc, "hydro_rk3_desc_t"), (amr.AMRDesc, "hydro_amr_t")]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hydro.h"', "int main(void) {"]
+    for cls, cname in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, val = ln.split()
+        got[(cname, field)] = int(val)
+    for cls, cname in pairs:
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
