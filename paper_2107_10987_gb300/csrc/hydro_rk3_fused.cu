@@ -6,19 +6,23 @@
 // step kernel and the update, with the whole mesh finishing each launch
 // before the next starts.  Here, state X -> Y:
 //   stage 0  every sub-grid: dU0 = L(X), amax (static schedule);
-//            one grid-wide barrier; dt = cfl min h/amax (every CTA);
-//   stage 1  sub-grid s reads U1 = X + dt dU0 (with the tracer resync)
-//            computed on the fly and writes U2 = 3/4 X + 1/4 (U1 + dt L(U1))
-//            to an interior-only scratch;
+//            one grid-wide barrier; dt = cfl min h/amax (every CTA); each
+//            CTA writes U1 = X + dt dU0 (with the tracer resync) of its
+//            stage-0 sub-grids into the interiors of Y and publishes them;
+//   stage 1  sub-grid s reads U1 and writes U2 = 3/4 X + 1/4 (U1 + dt L(U1))
+//            to an interior-only scratch and publishes it;
 //   stage 2  sub-grid s reads U2 and writes U3 = 1/3 X + 2/3 (U2 + dt L(U2))
 //            into the interiors of Y.
 // Ghost cells are read straight from the neighbouring sub-grids' interiors
 // through the boundary map of hydro_fill_ghosts_uniform, so no ghost layer
 // is written and no separate update runs.  Stage-1 and stage-2 sub-grids come
-// from one work counter, all stage-1 ones first; a stage-2 sub-grid waits
-// until its 27 neighbours (itself included) have published U2.  Every unit a
-// CTA waits for was taken earlier by a CTA that never waits, so the waits
-// end; each is still bounded in time and reports HYDRO_ST_TIMEOUT.
+// from one work counter, all stage-1 ones first; a sub-grid waits until its
+// 27 neighbours (itself included) have published its input (U1, U2).  U3
+// overwrites U1 in Y only after every reader of that U1 (the neighbours'
+// stage 1) has published.  Every unit a CTA waits for was taken earlier by a
+// CTA that never waits, and every U1 is written before its CTA takes a unit,
+// so the waits end; each is still bounded in time and reports
+// HYDRO_ST_TIMEOUT.
 //
 // The per-cell arithmetic is the separate-launch step's own (the same
 // sub-grid body and rk3_cell with the same operands), so the interiors of Y
@@ -33,8 +37,8 @@ struct FusedArgs {
   double* Y;            // padded output state (interiors written)
   double* U2;           // [n][F][N3] second-stage state
   double* dt_out;       // the step's dt
-  unsigned* sync;       // zero at launch: [0] barrier arrivals, [1] work counter,
-                        // [2] abort, [kSyncHead + s] U2 of sub-grid s published
+  unsigned* sync;       // zero at launch: [0] barrier arrivals, [1] work counter, [2] abort,
+                        // [kSyncHead + s] U2 of sub-grid s published, [kSyncHead + n + s] its U1
   int nbx, nby, nbz, bc;
   double cfl, eta2, inv_gamma;
   double alpha[3], beta[3];  // the stage coefficients of the update kernel
@@ -60,15 +64,9 @@ struct FusedIo {
 #pragma unroll
       for (int k = 0; k < F; ++k) u[k] = __ldg(x + (size_t)k * S3);
     } else if (stage == 1) {
-      const double* __restrict__ x = A.S.U + (size_t)os * F * S3 + op;
-      const double* r = A.S.dUdt + (size_t)os * F * N3 + oi;
-      double xv[F], rv[F];
+      const double* q = A.Y + (size_t)os * F * S3 + op;
 #pragma unroll
-      for (int k = 0; k < F; ++k) {
-        xv[k] = __ldg(x + (size_t)k * S3);
-        rv[k] = __ldcg(r + (size_t)k * N3);
-      }
-      rk3_cell<true>(xv, xv, rv, dt, A.alpha[0], A.beta[0], A.eta2, A.inv_gamma, u);
+      for (int k = 0; k < F; ++k) u[k] = __ldcg(q + (size_t)k * S3);
     } else {
       const double* q = A.U2 + (size_t)os * F * N3 + oi;
 #pragma unroll
@@ -140,6 +138,36 @@ __device__ bool wait_geq(const unsigned* p, unsigned target, const unsigned* abo
   return false;
 }
 
+// Threads 0..26 wait until flags[] of the 27 neighbours of sub-grid s (under
+// the boundary map, s itself included) are set; on a timeout the launch is
+// aborted.  Returns, to every thread, whether all were set.
+__device__ bool wait_neighbours(const FusedArgs& A, const unsigned* flags, int s, const unsigned* abort,
+                                int* sh_ok) {
+  const int tid = threadIdx.x;
+  if (tid == 0) *sh_ok = 1;
+  __syncthreads();
+  if (tid < 27) {
+    const int kx = s % A.nbx, ky = (s / A.nbx) % A.nby, kz = s / (A.nbx * A.nby);
+    int nx = kx + tid % 3 - 1, ny = ky + (tid / 3) % 3 - 1, nz = kz + tid / 9 - 1;
+    if (A.bc == 0) {
+      nx = (nx + A.nbx) % A.nbx;
+      ny = (ny + A.nby) % A.nby;
+      nz = (nz + A.nbz) % A.nbz;
+    } else {
+      nx = min(max(nx, 0), A.nbx - 1);
+      ny = min(max(ny, 0), A.nby - 1);
+      nz = min(max(nz, 0), A.nbz - 1);
+    }
+    if (!wait_geq(flags + (nz * A.nby + ny) * A.nbx + nx, 1u, abort, A.wait_ns)) {
+      atomicOr(A.S.status, 2u);
+      atomicExch(const_cast<unsigned*>(abort), 1u);
+      *sh_ok = 0;
+    }
+  }
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
 template <bool kGate>
 __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArgs A) {
   extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [2][S3] smooth flags
@@ -152,7 +180,8 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
   unsigned* arrive = A.sync;
   unsigned* counter = A.sync + 1;
   unsigned* abort = A.sync + 2;
-  unsigned* published = A.sync + kSyncHead;
+  unsigned* published = A.sync + kSyncHead;    // U2
+  unsigned* published1 = published + n;        // U1
   const RowMap R = row_map(tid);
 
   // ---- stage 0 --------------------------------------------------------
@@ -186,6 +215,30 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
   const double dt = A.cfl * m;
   if (blockIdx.x == 0 && tid == 0) *A.dt_out = dt;
 
+  // ---- U1 of this CTA's stage-0 sub-grids, into the interiors of Y -------
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    const double* __restrict__ x = A.S.U + (size_t)s * F * S3;
+    const double* r = A.S.dUdt + (size_t)s * F * N3;
+    double* y = A.Y + (size_t)s * F * S3;
+    for (int c = tid; c < N3; c += kThreadsMx) {
+      const int uc = (((c >> 6) + G) * S + (((c >> 3) & (N - 1)) + G)) * S + ((c & (N - 1)) + G);
+      double xv[F], rv[F], u1[F];
+#pragma unroll
+      for (int k = 0; k < F; ++k) {
+        xv[k] = __ldg(x + (size_t)k * S3 + uc);
+        rv[k] = r[(size_t)k * N3 + c];
+      }
+      rk3_cell<true>(xv, xv, rv, dt, A.alpha[0], A.beta[0], A.eta2, A.inv_gamma, u1);
+#pragma unroll
+      for (int k = 0; k < F; ++k) y[(size_t)k * S3 + uc] = u1[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(published1 + s, 1u);
+    }
+  }
+
   // ---- stages 1 and 2 from one work counter ---------------------------
   for (;;) {
     if (tid == 0) {
@@ -198,31 +251,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
     if (u >= 2 * n) break;
     const int stage = u < n ? 1 : 2;
     const int s = stage == 1 ? u : u - n;
-    if (stage == 2) {
-      if (tid == 0) sh_ok = 1;
-      __syncthreads();
-      if (tid < 27) {
-        // neighbour (dx, dy, dz) in {-1, 0, 1}^3 under the boundary map
-        const int kx = s % A.nbx, ky = (s / A.nbx) % A.nby, kz = s / (A.nbx * A.nby);
-        int nx = kx + tid % 3 - 1, ny = ky + (tid / 3) % 3 - 1, nz = kz + tid / 9 - 1;
-        if (A.bc == 0) {
-          nx = (nx + A.nbx) % A.nbx;
-          ny = (ny + A.nby) % A.nby;
-          nz = (nz + A.nbz) % A.nbz;
-        } else {
-          nx = min(max(nx, 0), A.nbx - 1);
-          ny = min(max(ny, 0), A.nby - 1);
-          nz = min(max(nz, 0), A.nbz - 1);
-        }
-        if (!wait_geq(published + (nz * A.nby + ny) * A.nbx + nx, 1u, abort, A.wait_ns)) {
-          atomicOr(A.S.status, 2u);
-          atomicExch(abort, 1u);
-          sh_ok = 0;
-        }
-      }
-      __syncthreads();
-      if (!sh_ok) break;
-    }
+    if (!wait_neighbours(A, stage == 1 ? published1 : published, s, abort, &sh_ok)) break;
     mixed_subgrid<kGate>(A.S, FusedIo{A, stage, dt}, s, R, Qf, red, D);  // ends with a barrier
     if (stage == 1 && tid == 0) {
       __threadfence();
@@ -231,7 +260,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
   }
 }
 
-size_t rk3_fused_sync_words(int n_sub) { return (size_t)kSyncHead + (size_t)n_sub; }
+size_t rk3_fused_sync_words(int n_sub) { return (size_t)kSyncHead + 2 * (size_t)n_sub; }
 
 // Opt in to the dynamic shared memory; the most CTAs of the kernel that can
 // be resident at once (the cooperative launch's limit).
