@@ -4,8 +4,11 @@ Workload: the Sedov-Taylor blast on a uniform octree level of 512 sub-grids
 of 8^3 cells (64^3 cells on [-1,1]^3), outflow boundaries, 10 FP64 fields,
 gamma = 5/3 -- the paper's pure-hydro benchmark problem (Sec. IV-A) at the
 sub-grid size 8^3.  One benchmark step is one full SSP-RK3 time step: three
-stages of (ghost fill, hydro_step, hydro_update) plus the CFL time step from
-the first stage's amax, all through the C ABI on the device.
+hydro stages (ghost fill, step, update) plus the CFL time step from the first
+stage's amax, all through the C ABI on the device.  The headline runs it in
+mixed precision as the fused step (hydro_rk3_step with the descriptor's
+fused flag: one persistent launch per time step); the same step as separate
+launches and the plain FP64 form are reported beside it.
 value = cells x time steps / s (the paper's "cells processed per second").
 
 --impl reference times the FP64 CPU oracle on the host cores instead (on a
@@ -144,10 +147,11 @@ class ClockSampler:
 # 15,552 point fluxes, face sums, divergence and sources.  Bytes: the padded
 # state read once and dU/dt written once.
 ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 260520}
-# DRAM bytes per hydro_step launch on this workload from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum), per precision form; None
-# until captured for the current kernel.
-TRAFFIC_PER_LAUNCH = {"fp64": 205798400.0, "mixed": 248572160.0}
+# DRAM bytes per launch on this workload from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum): the hydro_step launch of each precision form, and
+# the fused RK3 step (three stages per launch); None until captured for the
+# current kernel.
+TRAFFIC_PER_LAUNCH = {"fp64": 205798400.0, "mixed": 248572160.0, "fused": 833594880.0}
 
 
 def algorithmic_work():
@@ -186,11 +190,14 @@ def train_indicator(dev):
     return params, thr, ev
 
 
-def run_form(args, H, dev, precision, flush, indicator=None):
+def run_form(args, H, dev, precision, flush, indicator=None, fused=False):
     """Warm-up, then K timed RK3 steps of one precision form; returns timings
-    and the final state.  The launch sequence of a step is the one the C
-    ABI's graph captures (hydro_rk3_step): the first stage writes
-    the second state buffer, so no copy of the step's initial state is made."""
+    and the final state.  Separate launches: the sequence hydro_rk3_step
+    enqueues (per stage ghost fill, hydro_step, hydro_update; the first stage
+    writes the second state buffer, so no copy of the step's initial state is
+    made), issued entry point by entry point so that the step kernel can be
+    timed alone.  fused: hydro_rk3_step with the descriptor's fused flag (one
+    persistent launch per time step, mixed precision)."""
     import torch
     stream = torch.cuda.current_stream()
     ctx = H.Context(GAMMA, 0.0)
@@ -206,9 +213,18 @@ def run_form(args, H, dev, precision, flush, indicator=None):
     dt = torch.empty(1, dtype=torch.float64, device=dev)
     batches = [H.make_batch(Ua, origin, hv), H.make_batch(Ub, origin, hv)]
     cur = [0]
+    fdesc = H.make_rk3_desc(Ua, Ub, origin, hv, (NB, NB, NB), H.HYDRO_BC_OUTFLOW, dU, am, dt, 0.4, fused=True)
 
     def rk3_step(step_events=None):
         x = cur[0]
+        if fused:
+            if step_events is not None:
+                step_events[0][0].record(stream)
+            H.hydro_rk3_step(ctx, fdesc, x)
+            if step_events is not None:
+                step_events[0][1].record(stream)
+            cur[0] = 1 - x
+            return
         X, Y = batches[x], batches[1 - x]
         for k in range(3):
             B = X if k == 0 else Y
@@ -227,7 +243,7 @@ def run_form(args, H, dev, precision, flush, indicator=None):
         rk3_step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(3)]
+    kev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(1 if fused else 3)]
            for _ in range(args.steps)]
     for i in range(args.steps):
         flush.zero_()  # L2 flush between timed steps (outside the events)
@@ -240,7 +256,8 @@ def run_form(args, H, dev, precision, flush, indicator=None):
            "status": H.hydro_status(ctx), "rho": bufs[cur[0]][:, 0, 3:-3, 3:-3, 3:-3].clone(), "n": n}
 
     # the same step replayed as a captured CUDA graph (continuing the run)
-    desc = H.make_rk3_desc(bufs[cur[0]], bufs[1 - cur[0]], origin, hv, (NB, NB, NB), H.HYDRO_BC_OUTFLOW, dU, am, dt)
+    desc = H.make_rk3_desc(bufs[cur[0]], bufs[1 - cur[0]], origin, hv, (NB, NB, NB), H.HYDRO_BC_OUTFLOW, dU, am, dt,
+                           0.4, fused=fused)
     graph = H.hydro_rk3_graph_create(ctx, desc)
     gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
@@ -400,7 +417,7 @@ def polytrope_measure(args, H, dev, flush, indicator=None):
     cells = Ui.shape[0] * 512
     for name, prec in forms:
         ctx = context(name, prec)
-        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g)
+        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g, fused=not name.startswith("fp64"))
         steps = max(2, args.steps // 10) if name.startswith("fp64") else args.steps
         for _ in range(2):
             run.step(use_graph=True)
@@ -422,7 +439,7 @@ def polytrope_measure(args, H, dev, flush, indicator=None):
     acc = {"sub_grids": nb ** 3, "cells": nb ** 3 * 512, "steps": args.polytrope_steps}
     for name, prec in forms:
         ctx = context(name, prec)
-        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g)
+        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g, fused=not name.startswith("fp64"))
         c0 = run.sums()
         t = 0.0
         for _ in range(args.polytrope_steps):
@@ -456,11 +473,12 @@ def gpu_arm(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
-    launches_per_step = 10  # 3 x (ghost fill, step, update) + dt; no copies
-    forms = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED, "gated": H.HYDRO_PREC_MIXED,
-             "fp64_gated": H.HYDRO_PREC_FP64}
-    order = {"all": ["fp64", "fp64_gated", "gated", "mixed"],
-             "both": ["fp64", "mixed"]}.get(args.precision, [args.precision])
+    # precision and launch form of each measured form; the headline is last
+    forms = {"fp64": (H.HYDRO_PREC_FP64, False), "fp64_gated": (H.HYDRO_PREC_FP64, False),
+             "gated": (H.HYDRO_PREC_MIXED, True), "mixed_separate": (H.HYDRO_PREC_MIXED, False),
+             "mixed": (H.HYDRO_PREC_MIXED, True)}
+    order = {"all": ["fp64", "fp64_gated", "gated", "mixed_separate", "mixed"],
+             "both": ["fp64", "mixed_separate", "mixed"]}.get(args.precision, [args.precision])
     indicator = ind_eval = None
     if "gated" in order or "fp64_gated" in order:
         params, thr, ind_eval = train_indicator(dev)
@@ -470,14 +488,15 @@ def gpu_arm(args):
         if ws > 1:
             dist.barrier()
         ind = indicator if name in ("gated", "fp64_gated") else None
+        prec, fused = forms[name]
         if name == order[-1]:
             with ClockSampler(lr) as clk:
                 t0 = time.perf_counter()
-                res[name] = run_form(args, H, dev, forms[name], flush, ind)
+                res[name] = run_form(args, H, dev, prec, flush, ind, fused)
                 res[name]["wall"] = time.perf_counter() - t0
             res[name]["clocks"] = clk.summary()
         else:
-            res[name] = run_form(args, H, dev, forms[name], flush, ind)
+            res[name] = run_form(args, H, dev, prec, flush, ind, fused)
         res[name].update(max_over_ranks({k: res[name][k] for k in ("t_dev", "t_e2e", "t_graph")}, dev))
 
     if rk == 0:
@@ -486,10 +505,17 @@ def gpu_arm(args):
         head = order[-1]
         r = res[head]
         n = r["n"]
-        flops = work["fp64_flops_per_subgrid_stage"] * n
+        head_fused = forms[head][1]
+        flops = work["fp64_flops_per_subgrid_stage"] * n  # one stage of the mesh
         bytes_launch = work["bytes_per_subgrid_stage"] * n
-        peak = FP64_PEAK_TFLOPS if head == "fp64" else FP32_PEAK_TFLOPS
-        achieved = flops / r["kern_s"] / 1e12
+        # the timed kernel: the fused step does three stages per launch and
+        # reads the state once and writes the new state once (interiors)
+        k_flops = 3 * flops if head_fused else flops
+        k_bytes = 2 * n * 10 * N ** 3 * 8 if head_fused else bytes_launch
+        k_name = "hydro_rk3_fused_kernel (one launch per RK3 step)" if head_fused else f"hydro_step_{head} (avg launch)"
+        peak = FP64_PEAK_TFLOPS if head.startswith("fp64") else FP32_PEAK_TFLOPS
+        achieved = k_flops / r["kern_s"] / 1e12
+        traffic_key = "fused" if head_fused else ("fp64" if head.startswith("fp64") else "mixed")
         line = {
             "metric": METRIC, "value": job_rate(CELLS * args.steps, ws, r["t_dev"]), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["t_dev"] / args.steps,
@@ -500,6 +526,8 @@ def gpu_arm(args):
                        "sub_grids": n, "cells": CELLS,
                        "precision": "mixed: FP32 reconstruction/fluxes, FP64 dual-energy recovery, accumulation "
                                     "and update" if head != "fp64" else "fp64 (plain)",
+                       "launch": ("fused: one persistent launch per RK3 step" if head_fused
+                                  else "separate: ten launches per RK3 step"),
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MB write) between timed steps, outside the timed events"},
             "cell_stage_updates_per_s": 3 * job_rate(CELLS * args.steps, ws, r["t_dev"]),
@@ -507,19 +535,34 @@ def gpu_arm(args):
                              "ms_per_step": 1e3 * r["t_graph"] / args.steps,
                              "note": "the same RK3 step captured once into a CUDA graph (hydro_rk3_graph_*)"},
             "wall_s_timed_region": r["wall"],
-            "kernel_ms": {f"hydro_step_{head} (avg launch)": 1e3 * r["kern_s"]},
+            "kernel_ms": {k_name: 1e3 * r["kern_s"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": work.get("dram_bytes_per_launch_scaled", {}).get(head),
+                         "frac": achieved / peak,
+                         "traffic": work.get("dram_bytes_per_launch_scaled", {}).get(traffic_key),
                          "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flops x 2070 MHz (profiling recipe units)"
                                          if head != "fp64" else "nominal GB300 FP64 from the profiling recipe"),
                          "flops_counted": "algorithmic ops of the method (oracle count), each op one flop",
-                         "hbm_frac": (bytes_launch / r["kern_s"] / 1e9) / pk["hbm_gbs"] if "hbm_gbs" in pk else None},
+                         "hbm_frac": (k_bytes / r["kern_s"] / 1e9) / pk["hbm_gbs"] if "hbm_gbs" in pk else None},
             "e2e": {"value": job_rate(CELLS * args.steps, ws, r["t_e2e"]), "unit": UNIT,
                     "h2d_bytes_per_step": r["bytes_step"], "d2h_bytes_per_step": r["bytes_step"]},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": (1 if head_fused else 10) * args.steps,
             "clocks": r["clocks"],
             "device_status": r["status"],
         }
+        if "mixed_separate" in res and head != "mixed_separate":
+            m = res["mixed_separate"]
+            am = flops / m["kern_s"] / 1e12
+            line["separate_launches"] = {
+                "note": "the same mixed RK3 step as ten launches (per stage ghost fill, hydro_step, hydro_update; "
+                        "dt), hydro_rk3_step without the fused flag",
+                "value": job_rate(CELLS * args.steps, ws, m["t_dev"]), "ms_per_step": 1e3 * m["t_dev"] / args.steps,
+                "graph_replay": job_rate(CELLS * args.steps, ws, m["t_graph"]),
+                "e2e": job_rate(CELLS * args.steps, ws, m["t_e2e"]),
+                "kernel_ms": {"hydro_step_mixed (avg launch)": 1e3 * m["kern_s"]},
+                "roofline": {"bound": "alu", "achieved": am, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": am / FP32_PEAK_TFLOPS,
+                             "traffic": work.get("dram_bytes_per_launch_scaled", {}).get("mixed")},
+                "max_rel_density_diff_vs_fused": (m["rho"] - r["rho"]).abs().max().item() / r["rho"].abs().max().item()}
         if "fp64" in res and head != "fp64":
             f = res["fp64"]
             a64 = flops / f["kern_s"] / 1e12
@@ -638,7 +681,8 @@ def main():
     ap.add_argument("--polytrope-nb", type=int, default=16,
                     help="sub-grids per axis of the polytrope accuracy runs (32: the full 256^3 mesh)")
     ap.add_argument("--polytrope-steps", type=int, default=100)
-    ap.add_argument("--precision", default="all", choices=["all", "both", "mixed", "fp64", "gated", "fp64_gated"],
+    ap.add_argument("--precision", default="all",
+                    choices=["all", "both", "mixed", "mixed_separate", "fp64", "gated", "fp64_gated"],
                     help="all: time the plain FP64 form, the FP64 and mixed forms with the learned indicator, "
                          "then the mixed form (reported as value); both: FP64 then mixed")
     args = ap.parse_args()

@@ -309,6 +309,13 @@ int hydro_rk3_graph_create(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, hydro_gr
 /* Replay one time step on a stream (alternating a -> b and b -> a). */
 int hydro_rk3_graph_launch(hydro_graph_t* g, void* stream);
 
+/* Self-test of the fused step's bounded device wait: one thread waits for
+ * `seconds` (0 < seconds <= 1) on a flag that nothing sets, gives up and sets
+ * HYDRO_ST_TIMEOUT in the status word, as the fused step does when one of
+ * its waits expires.  Asynchronous; read the bit with hydro_status after a
+ * synchronise.  Errors: EINVAL, ENOMEM. */
+int hydro_selftest_wait(hydro_ctx_t* ctx, double seconds, void* stream);
+
 /* Which buffer holds the current state: 0 = a, 1 = b. */
 int hydro_rk3_graph_state(const hydro_graph_t* g);
 

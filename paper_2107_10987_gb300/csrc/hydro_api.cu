@@ -25,6 +25,7 @@ cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double*
                              cudaStream_t st);
 cudaError_t prepare_rk3_fused(int num_sms, int* max_grid);
 size_t rk3_fused_sync_words(int n_sub);
+cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long limit_ns, cudaStream_t st);
 cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
                         double* sums, cudaStream_t st);
 }  // namespace hyd
@@ -125,6 +126,16 @@ int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity,
   cudaError_t e = hyd::launch_rk3_fused(S, Y, c->u2, d->dt, reinterpret_cast<unsigned*>(c->sync), d->nbx, d->nby,
                                         d->nbz, d->bc, cfl, c->mode.de_eta2, c->gamma, c->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_rk3_step (fused)");
+  return HYDRO_OK;
+}
+
+extern "C" int hydro_selftest_wait(hydro_ctx_t* c, double seconds, void* stream) {
+  if (!c || !(seconds > 0.0 && seconds <= 1.0)) return HYDRO_EINVAL;
+  int rc = hydro_ctx_prepare_fused(c, 1);
+  if (rc) return rc;
+  cudaError_t e = hyd::launch_wait_selftest(reinterpret_cast<unsigned*>(c->sync), c->status,
+                                            (long long)(seconds * 1e9), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_selftest_wait");
   return HYDRO_OK;
 }
 

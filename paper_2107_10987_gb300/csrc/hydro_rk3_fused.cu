@@ -260,6 +260,20 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
   }
 }
 
+// Self-test of the bounded wait: thread 0 waits on a flag that nothing sets
+// (flag[0], abort flag[1], both zero) and reports the expiry in the status
+// word, as the fused step does.
+__global__ void hydro_wait_selftest_kernel(const unsigned* flag, unsigned* status, long long limit_ns) {
+  if (threadIdx.x == 0 && !wait_geq(flag, 1u, flag + 1, limit_ns)) atomicOr(status, 2u);
+}
+
+cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long limit_ns, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  hydro_wait_selftest_kernel<<<1, 32, 0, st>>>(words, status, limit_ns);
+  return cudaGetLastError();
+}
+
 size_t rk3_fused_sync_words(int n_sub) { return (size_t)kSyncHead + 2 * (size_t)n_sub; }
 
 // Opt in to the dynamic shared memory; the most CTAs of the kernel that can

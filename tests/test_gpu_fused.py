@@ -158,3 +158,24 @@ def test_fused_rejects_fp64_and_adaptive_meshes(H):
     assert lib.hydro_rk3_step(H._cp(ctx), C.byref(d), 0, None) == H.HYDRO_EUNSUP
     torch.cuda.synchronize()
     assert H.hydro_status(ctx) == 0
+
+
+def test_bounded_wait_reports_timeout(H):
+    """The fused step's wait, on a flag that nothing sets: it gives up after
+    its limit (10 ms here) and sets HYDRO_ST_TIMEOUT; the context stays
+    usable."""
+    import time
+    ctx = H.Context(GAMMA, 0.0)
+    assert H.hydro_status(ctx) == 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H.hydro_selftest_wait(ctx, 0.01)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    assert H.hydro_status(ctx) == H.HYDRO_ST_TIMEOUT
+    assert 0.009 < dt < 1.0, dt
+    # the context and the device still work: a fused step afterwards
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
+    U, o, h = blast_mesh(2, 2, 2)
+    run_pair(H, ctx, U, o, h, 2, H.HYDRO_BC_PERIODIC, steps=1)
+    assert H.hydro_status(ctx) == 0
