@@ -48,7 +48,10 @@ __device__ __forceinline__ void side32(const float q[F], int a, float xq, float 
   const float p = P.gm1 * eps;
   const float c2 = __fdividef(P.gamma * p, rho);
   const float c = c2 * rsqrtf(c2);
-  const float ux = vx + P.omega * yq, uy = vy - P.omega * xq;
+  // explicit FMAs: both sides of a point share omega * yq and omega * xq, and
+  // the compiler's own choice between a shared product and two contractions
+  // may differ between kernel instances
+  const float ux = __fmaf_rn(P.omega, yq, vx), uy = __fmaf_rn(-P.omega, xq, vy);
   const float un = (a == 0) ? ux : (a == 1) ? uy : vz;
   const float va = (a == 0) ? vx : (a == 1) ? vy : vz;
   U[RHO] = rho;

@@ -105,9 +105,10 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
     for (int k = 0; k < F; ++k) fsum[k] = 0.f;
     tl[0] = tl[1] = tl[2] = 0.f;
     tr[0] = tr[1] = tr[2] = 0.f;
-    // cell-centre coordinates of the left cell j - 1 (FP64 -> FP32 once)
-    const float xc = (float)(o[0] + hd * (axis_comp(0, a, b, j - 1, pb, pc) + 0.5)),
-                yc = (float)(o[1] + hd * (axis_comp(1, a, b, j - 1, pb, pc) + 0.5));
+    // cell-centre coordinates of the left cell j - 1 (FP64 -> FP32 once; an
+    // explicit FMA, so that every kernel instance rounds them alike)
+    const float xc = (float)fma(hd, axis_comp(0, a, b, j - 1, pb, pc) + 0.5, o[0]),
+                yc = (float)fma(hd, axis_comp(1, a, b, j - 1, pb, pc) + 0.5, o[1]);
 #pragma unroll 1
     for (int p = 0; p <= 4; ++p) {
       const int t1 = p / 3 - 1, t2 = p % 3 - 1;
@@ -195,32 +196,34 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
           (D[(0 * DQ + F + m) * N3 + c] + D[(1 * DQ + F + m) * N3 + c]) + D[(2 * DQ + F + m) * N3 + c];
       du[ZX + m] = du[ZX + m] - tq * inv_h;
     }
+    // The sources' products and sums are written as explicit FMAs and
+    // rounded operations, so that every kernel instance rounds them alike.
     double uin[F];
     io.own(sub, c, uc, uin);
     const double sx = uin[SX], sy = uin[SY], sz = uin[SZ];
-    du[SX] = du[SX] + om * sy;
-    du[SY] = du[SY] - om * sx;
-    du[ZX] = du[ZX] + om * uin[ZY];
-    du[ZY] = du[ZY] - om * uin[ZX];
+    du[SX] = fma(om, sy, du[SX]);
+    du[SY] = fma(-om, sx, du[SY]);
+    du[ZX] = fma(om, uin[ZY], du[ZX]);
+    du[ZY] = fma(-om, uin[ZX], du[ZY]);
     {
       // spin source w(x_c) x s, w = -omega z_hat x x_c: removes the torque
       // that the frame part s w_n of the momentum flux leaves in the face
       // torques, so that sum (x_c x s + z)_z is conserved for omega != 0
       const double xc = __dadd_rn(o[0], __dmul_rn(hd, x + 0.5));
       const double yc = __dadd_rn(o[1], __dmul_rn(hd, y + 0.5));
-      const double wx = om * yc, wy = -(om * xc);
-      du[ZX] = du[ZX] + wy * sz;
-      du[ZY] = du[ZY] - wx * sz;
-      du[ZZ] = du[ZZ] + (wx * sy - wy * sx);
+      const double wx = __dmul_rn(om, yc), wy = -__dmul_rn(om, xc);
+      du[ZX] = fma(wy, sz, du[ZX]);
+      du[ZY] = fma(-wx, sz, du[ZY]);
+      du[ZZ] = __dadd_rn(du[ZZ], fma(wx, sy, -__dmul_rn(wy, sx)));
     }
     if (A.g) {
       const double* gs = A.g + (size_t)s * 3 * N3;
       const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];
       const double rho = uin[RHO];
-      du[SX] = du[SX] + rho * gx;
-      du[SY] = du[SY] + rho * gy;
-      du[SZ] = du[SZ] + rho * gz;
-      du[EGAS] = du[EGAS] + ((sx * gx + sy * gy) + sz * gz);
+      du[SX] = fma(rho, gx, du[SX]);
+      du[SY] = fma(rho, gy, du[SY]);
+      du[SZ] = fma(rho, gz, du[SZ]);
+      du[EGAS] = __dadd_rn(du[EGAS], fma(sz, gz, fma(sy, gy, __dmul_rn(sx, gx))));
     }
     io.store(sub, c, uc, du, uin);
   }

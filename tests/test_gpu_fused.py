@@ -9,7 +9,8 @@ Meshes cover every neighbour case: cubic, ragged (3 x 2 x 5), a single
 sub-grid (its own neighbour on every side under periodic boundaries), rows
 of two and three, under both boundary conditions; the headline Sedov mesh; the
 rotating polytrope with gravity; the learned indicator's kernel; graph
-replay; and the configurations the fused form rejects."""
+replay; the configurations the fused form rejects; and the bounded wait's
+expiry."""
 import numpy as np
 import pytest
 
