@@ -151,7 +151,7 @@ ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 26
 # dram__bytes_write.sum): the hydro_step launch of each precision form, and
 # the fused RK3 step (three stages per launch); None until captured for the
 # current kernel.
-TRAFFIC_PER_LAUNCH = {"fp64": 205798400.0, "mixed": 248572160.0, "fused": 833594880.0}
+TRAFFIC_PER_LAUNCH = {"fp64": 204584192.0, "mixed": 254990848.0, "fused": 838170112.0}
 
 
 def algorithmic_work():

@@ -196,9 +196,27 @@ __device__ __forceinline__ void prolong_cell(const double* C, const double off[3
 // cells outside the domain (outflow: clamped positions) are prolonged one by
 // one afterwards.
 __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A) {
+  __shared__ int coarser;  // some neighbour position of the leaf lies inside a coarser leaf
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int l = A.leaf_level[s];
     if (l <= A.lmin) continue;  // no coarser leaves
+    // Every ghost cell of the leaf lies, after the boundary map, in one of
+    // the 27 positions around it at its level; a leaf none of whose positions
+    // is inside a coarser leaf (most of them) has nothing to prolong.
+    __syncthreads();  // the previous leaf's flag is no longer read
+    if (threadIdx.x == 0) coarser = 0;
+    __syncthreads();
+    if (threadIdx.x < 27) {
+      const int n = 1 << l, t = threadIdx.x;
+      const int q[3] = {A.leaf_ijk[3 * s] + t % 3 - 1, A.leaf_ijk[3 * s + 1] + (t / 3) % 3 - 1,
+                        A.leaf_ijk[3 * s + 2] + t / 9 - 1};
+      int w[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) w[d] = bc_amr(q[d], n, A.bc);
+      if (A.table[level_offset(l, A.lmin) + ((long)w[2] * n + w[1]) * n + w[0]] == -2) coarser = 1;
+    }
+    __syncthreads();
+    if (!coarser) continue;
     const int b[3] = {A.leaf_ijk[3 * s] * N, A.leaf_ijk[3 * s + 1] * N, A.leaf_ijk[3 * s + 2] * N};
     const int ncell = N << l, nc = ncell >> 1;
     double* dstb = A.U + (size_t)s * F * S3;

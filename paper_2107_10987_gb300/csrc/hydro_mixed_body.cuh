@@ -121,7 +121,8 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
         if (p != 4) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
       }
       if (j >= 0) {
-#pragma unroll 1
+        // both points of the pair unrolled: their chains interleave
+#pragma unroll
         for (int side = 0; side < 2; ++side) {
           if (p == 4 && side == 1) continue;
           const int u1 = side ? t1 : -t1, u2 = side ? t2 : -t2;
