@@ -166,10 +166,26 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
 // (exact equivalents of the FP64 comparisons; GB300 issues FP64 at 1/64 of
 // the FP32 rate).
 __device__ __forceinline__ double minmod64(double dp, double dm) {
-  if (__double_as_longlong(rmul(dp, dm)) <= 0LL) return 0.0;
-  const long long a = __double_as_longlong(dp) & 0x7fffffffffffffffLL;
-  const long long b = __double_as_longlong(dm) & 0x7fffffffffffffffLL;
+  const long long bp = __double_as_longlong(dp), bm = __double_as_longlong(dm);
+  const long long a = bp & 0x7fffffffffffffffLL, b = bm & 0x7fffffffffffffffLL;
+  // dp dm <= 0 when either is zero or the signs differ; with equal signs the
+  // product is positive unless it underflows to zero, which needs an operand
+  // below the normal range or |dp| |dm| < 2^-1074, i.e. biased exponents
+  // summing below 972: only then is the FP64 product itself consulted.
+  if (a == 0 || b == 0 || (bp ^ bm) < 0) return 0.0;
+  const int ep = (int)(a >> 52), em = (int)(b >> 52);
+  if ((ep == 0 || em == 0 || ep + em < 972) && __double_as_longlong(rmul(dp, dm)) <= 0LL) return 0.0;
   return a < b ? dp : dm;
+}
+
+// x * 0.25 exactly: a normal x whose quarter is still normal has its
+// exponent lowered by two; zeros, denormal results, inf and NaN take the
+// FP64 product.
+__device__ __forceinline__ double quarter64(double x) {
+  const long long bx = __double_as_longlong(x);
+  const int e = (int)((bx >> 52) & 0x7ff);
+  if (e > 2 && e < 0x7ff) return __longlong_as_double(bx - (2LL << 52));
+  return rmul(x, 0.25);
 }
 
 // Prolongation of one fine ghost cell from coarse cell C (padded pointer to
@@ -264,7 +280,7 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const double dp = rsub(q[st[d]], c), dm = rsub(c, q[-st[d]]);
-          t[d] = rmul(minmod64(dp, dm), 0.25);
+          t[d] = quarter64(minmod64(dp, dm));
         }
         double vx[2];
         if (need_x & 1) vx[0] = radd(c, -t[0]);
