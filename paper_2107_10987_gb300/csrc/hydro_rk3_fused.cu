@@ -19,9 +19,10 @@
 // from one work counter, all stage-1 ones first; a sub-grid waits until its
 // 27 neighbours (itself included) have published its input (U1, U2).  U3
 // overwrites U1 in Y only after every reader of that U1 (the neighbours'
-// stage 1) has published.  Every unit a CTA waits for was taken earlier by a
-// CTA that never waits, and every U1 is written before its CTA takes a unit,
-// so the waits end; each is still bounded in time and reports
+// stage 1) has published.  The waits end: every CTA writes its U1 before it
+// takes a unit, so a stage-1 unit waits only for CTAs that are not waiting,
+// and a stage-2 unit waits only for stage-1 units, all taken before it by
+// resident CTAs.  Each wait is still bounded in time and polls and reports
 // HYDRO_ST_TIMEOUT.
 //
 // The per-cell arithmetic is the separate-launch step's own (the same
