@@ -635,9 +635,20 @@ def cpu_baseline(budget_s: float):
         steps += 1
     dt = time.perf_counter() - t0
     cells = Ug[0].size
-    return {"value": cells * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{steps} RK3 steps of the central 4x4x4 sub-grids (32^3 cells) of the workload, "
-                      f"{dt:.1f} s, OpenMP over sub-grids on all host cores"}
+    out = {"value": cells * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{steps} RK3 steps of the central 4x4x4 sub-grids (32^3 cells) of the workload, "
+                     f"{dt:.1f} s, OpenMP over sub-grids on all host cores"}
+    # the same sample on one core, for a quarter of the budget
+    run1 = mesh.BoxRun(core.OracleParams(gamma=GAMMA), Ug, h, lo, "outflow", nthreads=1)
+    t0 = time.perf_counter()
+    steps1 = 0
+    while time.perf_counter() - t0 < budget_s / 4 or steps1 == 0:
+        run1.step(0.4)
+        steps1 += 1
+    dt1 = time.perf_counter() - t0
+    out["single_core"] = {"value": cells * steps1 / dt1, "unit": UNIT, "cores": 1,
+                          "sample": f"{steps1} RK3 steps of the same sample, {dt1:.1f} s"}
+    return out
 
 
 def reference_arm(args):
