@@ -382,7 +382,9 @@ def polytrope_measure(args, H, dev, flush, indicator=None):
     --polytrope-nb^3 sub-grids from the same initial state, and each reports
     the L1 density error against that state, the drift of the total angular
     momentum about z and of the mass.  With an indicator, the mixed form with
-    the learned smoothness indicator ("gated") runs beside them."""
+    the learned smoothness indicator ("gated") runs beside them.  The old
+    hydro module (fluxes at the face centres only) runs in both precisions
+    too: the paper's new-versus-old accuracy comparison."""
     import torch
     from paper_2107_10987_gb300 import workloads as W
     from paper_2107_10987_gb300.uniform import UniformRun
@@ -391,10 +393,13 @@ def polytrope_measure(args, H, dev, flush, indicator=None):
     forms = (("mixed", H.HYDRO_PREC_MIXED), ("fp64", H.HYDRO_PREC_FP64))
     if indicator is not None:
         forms = forms + (("gated", H.HYDRO_PREC_MIXED), ("fp64_gated", H.HYDRO_PREC_FP64))
+    # the old hydro module (fluxes at the face centres only, Sec. III-B), which
+    # the paper compares the new one with on a rotating star (Sec. VI)
+    forms = forms + (("mixed_old", H.HYDRO_PREC_MIXED), ("fp64_old", H.HYDRO_PREC_FP64))
 
     def context(name, prec):
         c = H.Context(GAMMA, omega)
-        H.hydro_set_mode(c, prec, 0.4)
+        H.hydro_set_mode(c, prec, 0.4, flux_points=1 if name.endswith("_old") else 9)
         if name in ("gated", "fp64_gated"):
             H.hydro_set_indicator(c, indicator[0], indicator[1])
         return c
@@ -429,6 +434,8 @@ def polytrope_measure(args, H, dev, flush, indicator=None):
         ctx.close()
         torch.cuda.empty_cache()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["cost_new_over_old_fp64"] = out["fp64"]["ms_per_step"] / out["fp64_old"]["ms_per_step"]
+    out["cost_new_over_old_mixed"] = out["mixed"]["ms_per_step"] / out["mixed_old"]["ms_per_step"]
     if indicator is not None:
         out["speedup_gated_vs_mixed"] = out["mixed"]["ms_per_step"] / out["gated"]["ms_per_step"]
         out["speedup_fp64_gated_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp64_gated"]["ms_per_step"]
@@ -455,6 +462,9 @@ def polytrope_measure(args, H, dev, flush, indicator=None):
         ctx.close()
         torch.cuda.empty_cache()
     acc["l1_mixed_over_fp64"] = acc["mixed"]["l1_density"] / acc["fp64"]["l1_density"]
+    # the paper's comparison: the old module's error over the new one's
+    acc["l1_old_over_new_fp64"] = acc["fp64_old"]["l1_density"] / acc["fp64"]["l1_density"]
+    acc["l1_old_over_new_mixed"] = acc["mixed_old"]["l1_density"] / acc["mixed"]["l1_density"]
     if indicator is not None:
         acc["l1_gated_over_fp64"] = acc["gated"]["l1_density"] / acc["fp64"]["l1_density"]
         acc["l1_fp64_gated_over_fp64"] = acc["fp64_gated"]["l1_density"] / acc["fp64"]["l1_density"]

@@ -79,13 +79,18 @@ typedef struct {
 
 /* Run-time options.  de_eta1: dual-energy selection threshold (eps from
  * E - KE where that exceeds de_eta1*E, else from tau^gamma); de_eta2: tracer
- * resync threshold (tau <- eps^(1/gamma) where eps > de_eta2*E).  Defaults:
- * FP64, cfl 0.4, eta1 1e-3, eta2 0.1. */
+ * resync threshold (tau <- eps^(1/gamma) where eps > de_eta2*E).
+ * flux_points: 9 (or 0) for the fluxes at the 9 points of every face summed
+ * with Simpson weights (the new hydro module, Sec. III-B), 1 for the flux at
+ * the face centre only (the old module the paper compares it with: the
+ * same reconstruction, fluxes only at the centres of cell faces).  Defaults:
+ * FP64, cfl 0.4, eta1 1e-3, eta2 0.1, 9 points. */
 typedef struct {
   int precision;   /* HYDRO_PREC_FP64 or HYDRO_PREC_MIXED */
   double cfl;
   double de_eta1;
   double de_eta2;
+  int flux_points; /* 9 (0 means 9) or 1 */
 } hydro_mode_t;
 
 /* A batch of leaf sub-grids (device pointers).  g may be NULL. */

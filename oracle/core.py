@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
 
 class _P(C.Structure):
     _fields_ = [("gamma", C.c_double), ("omega", C.c_double), ("eta1", C.c_double), ("eta2", C.c_double),
-                ("N", C.c_int), ("G", C.c_int), ("nf", C.c_int)]
+                ("N", C.c_int), ("G", C.c_int), ("nf", C.c_int), ("face_points", C.c_int)]
 
 
 @dataclass
@@ -43,9 +43,10 @@ class OracleParams:
     N: int = 8
     G: int = 3
     nf: int = 10
+    face_points: int = 9  # 1: flux at the face centres only (the old hydro module, Sec. III-B)
 
     def c(self) -> _P:
-        return _P(self.gamma, self.omega, self.eta1, self.eta2, self.N, self.G, self.nf)
+        return _P(self.gamma, self.omega, self.eta1, self.eta2, self.N, self.G, self.nf, self.face_points)
 
 
 _lib = None

@@ -95,6 +95,8 @@ struct Params {
   int N;          // interior cells per sub-grid edge
   int G;          // ghost depth (3 for the 5-point stencil)
   int nf;         // number of fields = 9 + species
+  int face_points;  // 9: flux at the 9 points of each face, Simpson sum (the new module);
+                    // 1: flux at the face centre only (the old module, Sec. III-B)
 };
 
 // Primitive recovery of one cell (Sec. III-B; dual energy after Bryan 1995).
@@ -356,6 +358,7 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
           T tl[3] = {T(0.0), T(0.0), T(0.0)}, tr[3] = {T(0.0), T(0.0), T(0.0)};
           for (int t1 = -1; t1 <= 1; ++t1)
             for (int t2 = -1; t2 <= 1; ++t2) {
+              if (P.face_points == 1 && (t1 != 0 || t2 != 0)) continue;
               int d[3];
               d[a] = 1;
               d[b] = t1;
@@ -371,7 +374,7 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
               point_flux(P, qL, qR, a, xq, Fq, aq);
               if (first) { am = aq; first = false; }
               else am = max_(am, aq);
-              const T w = T(nc_weight(t1, t2));
+              const T w = T(P.face_points == 1 ? 1.0 : nc_weight(t1, t2));
               for (int k = 0; k < nf; ++k) fsum[k] = fsum[k] + w * Fq[k];
               // torque of the momentum flux about each cell centre:
               // (x_q - x_c) x F_s with x_q - x_c = (h/2) d (left), (h/2)(d-2e_a) (right)
@@ -529,13 +532,14 @@ extern "C" {
 
 struct orc_params {
   double gamma, omega, eta1, eta2;
-  int N, G, nf;
+  int N, G, nf, face_points;
 };
 
 static orc::Params to_p(const orc_params* p) {
   orc::Params P;
   P.gamma = p->gamma; P.omega = p->omega; P.eta1 = p->eta1; P.eta2 = p->eta2;
   P.N = p->N; P.G = p->G; P.nf = p->nf;
+  P.face_points = p->face_points == 1 ? 1 : 9;
   return P;
 }
 

@@ -87,6 +87,7 @@ static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, dou
   A.P.gm1 = c->gamma - 1.0;
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
+  A.P.face_points = c->mode.flux_points == 1 ? 1 : 9;
   A.gate = c->gate_on ? 1 : 0;
   A.gate_w = c->gate_w;
   A.gate_logit_thr = (float)c->gate_logit_thr;
@@ -173,6 +174,7 @@ int hydro_create(const hydro_layout_t* L, double gamma, double omega, hydro_ctx_
   c->mode.cfl = 0.4;
   c->mode.de_eta1 = 1e-3;
   c->mode.de_eta2 = 0.1;
+  c->mode.flux_points = 9;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
@@ -189,7 +191,9 @@ int hydro_set_mode(hydro_ctx_t* c, const hydro_mode_t* m) {
   if (!(m->cfl > 0.0 && m->cfl <= 1.0) || !(m->de_eta1 > 0.0 && m->de_eta1 <= 1.0) ||
       !(m->de_eta2 > 0.0 && m->de_eta2 <= 1.0))
     return HYDRO_EINVAL;
+  if (m->flux_points != 0 && m->flux_points != 1 && m->flux_points != 9) return HYDRO_EINVAL;
   c->mode = *m;
+  if (c->mode.flux_points == 0) c->mode.flux_points = 9;
   return HYDRO_OK;
 }
 

@@ -109,8 +109,10 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
     // explicit FMA, so that every kernel instance rounds them alike)
     const float xc = (float)fma(hd, axis_comp(0, a, b, j - 1, pb, pc) + 0.5, o[0]),
                 yc = (float)fma(hd, axis_comp(1, a, b, j - 1, pb, pc) + 0.5, o[1]);
+    // the 9 face points as 4 mirrored pairs and the centre (p = 4); with one
+    // flux point per face (the old module) only the centre
 #pragma unroll 1
-    for (int p = 0; p <= 4; ++p) {
+    for (int p = A.P.face_points == 1 ? 4 : 0; p <= 4; ++p) {
       const int t1 = p / 3 - 1, t2 = p % 3 - 1;
       float qpA[F], qmA[F], qpB[F], qmB[F];
       if (kGate && smooth[cj]) {
@@ -133,7 +135,8 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
           const float yq = yc + half_h * d1;
           const float rl[3] = {half_h * d0, half_h * d1, half_h * d2};
           const float rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
-          const float w = (u1 == 0 && u2 == 0) ? (16.f / 36.f) : (u1 == 0 || u2 == 0) ? (4.f / 36.f) : (1.f / 36.f);
+          const float w = A.P.face_points == 1 ? 1.f
+                          : (u1 == 0 && u2 == 0) ? (16.f / 36.f) : (u1 == 0 || u2 == 0) ? (4.f / 36.f) : (1.f / 36.f);
           point32(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, PF, fsum, tl, tr, amax);
         }
       }

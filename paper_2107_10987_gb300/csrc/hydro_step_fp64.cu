@@ -280,8 +280,10 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
       tr[0] = tr[1] = tr[2] = 0.0;
       // left cell of face j-1/2 is (j-1) along a
       const int ci0 = axis_comp(0, a, b, j - 1, pb, pc), ci1 = axis_comp(1, a, b, j - 1, pb, pc);
+      // the 9 face points as 4 mirrored pairs and the centre (p = 4); with one
+      // flux point per face (the old module) only the centre
 #pragma unroll 1
-      for (int p = 0; p <= 4; ++p) {
+      for (int p = A.P.face_points == 1 ? 4 : 0; p <= 4; ++p) {
         const int t1 = p / 3 - 1, t2 = p % 3 - 1;  // point p; its mirror 8-p has (-t1,-t2)
         double qpA[F], qmA[F], qpB[F], qmB[F];
         if (kGate && smooth[cj]) {
@@ -306,7 +308,8 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
             const double rl[3] = {half_h * d0, half_h * d1, half_h * d2};
             // about the right cell the a-offset is d_a - 2 = -1
             const double rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
-            const double w = (u1 == 0 && u2 == 0) ? (16.0 / 36.0) : (u1 == 0 || u2 == 0) ? (4.0 / 36.0) : (1.0 / 36.0);
+            const double w = A.P.face_points == 1 ? 1.0
+                             : (u1 == 0 && u2 == 0) ? (16.0 / 36.0) : (u1 == 0 || u2 == 0) ? (4.0 / 36.0) : (1.0 / 36.0);
             point64(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, A.P, fsum, tl, tr, amax);
           }
         }
