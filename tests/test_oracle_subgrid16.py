@@ -1,0 +1,113 @@
+"""16^3 sub-grids in the oracle (the compile-time option of Sec. III-B, used
+for the best-performing runs of Sec. V), pinned to the 8^3 form (CPU only).
+
+On a uniform mesh the scheme does not depend on how the box is cut into
+sub-grids: every cell sees the same stencil, the same face points and the
+same sources.  So a box cut into 16^3 sub-grids must give the same rates as
+the same box cut into 8^3 sub-grids:
+  * bit for bit without rotation and gravity (no arithmetic depends on the
+    sub-grid origin there);
+  * to rounding with both (the cell centres are formed from other origins);
+  * over a whole RK3 step (dt from the largest signal speed, three stages).
+The cost side: each interior cell owns 3 (N+1)/N face evaluations (the
+faces between the ghost layer and the interior included), 3.375 at N = 8 and
+3.1875 at N = 16, and the PPM line evaluations and operations follow them.
+"""
+import numpy as np
+import pytest
+
+from paper_2107_10987_gb300 import workloads as W
+
+GAMMA = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_mod):
+    return oracle_mod.core
+
+
+def _box(n, seed, blast=True):
+    rng = np.random.default_rng(seed)
+    sh = (n, n, n)
+    rho = rng.uniform(0.5, 2.0, sh)
+    v = rng.uniform(-0.5, 0.5, (3,) + sh)
+    p = rng.uniform(0.2, 1.0, sh)
+    if blast:
+        p[n // 2 - 2:n // 2 + 2, n // 2 - 2:n // 2 + 2, n // 2 - 2:n // 2 + 2] = 50.0
+    z = rng.uniform(-0.05, 0.05, (3,) + sh)
+    return W.conserved_from_primitive(rho, v, p, GAMMA, z=z, species=0.3 * rho)
+
+
+def _rates(orc, N, Ug, h, lo, bc, omega=0.0, g=None):
+    from oracle import mesh
+    P = orc.OracleParams(gamma=GAMMA, omega=omega, N=N)
+    gs = None
+    if g is not None:
+        nb = Ug.shape[1] // N
+        gs = mesh.split(np.pad(g, ((0, 0), (3, 3), (3, 3), (3, 3))), N, 3)[:, :, 3:-3, 3:-3, 3:-3]
+        gs = np.ascontiguousarray(gs)
+        assert gs.shape[0] == nb ** 3
+    run = mesh.BoxRun(P, Ug, h, lo, bc, g=gs)
+    dU, am = run.rhs(Ug)
+    return mesh.join(dU, run.nbx, run.nby, run.nbz), float(am.max())
+
+
+@pytest.mark.parametrize("bc", ["periodic", "outflow"])
+def test_sixteen_equals_eight_bitwise(orc, bc):
+    Ug = _box(32, 3)
+    h, lo = 1.0 / 32, (-0.5, -0.5, -0.5)
+    d8, a8 = _rates(orc, 8, Ug, h, lo, bc)
+    d16, a16 = _rates(orc, 16, Ug, h, lo, bc)
+    assert d8.shape == d16.shape == (10, 32, 32, 32)
+    assert np.array_equal(d8.view(np.int64), d16.view(np.int64))
+    assert a8 == a16
+    # and the rates are not trivial: the blast and the spin act
+    assert np.abs(d8[0]).max() > 1.0 and np.abs(d8[6:9]).max() > 1e-3
+
+
+def test_sixteen_equals_eight_with_rotation_and_gravity(orc):
+    Ug = _box(32, 5)
+    rng = np.random.default_rng(7)
+    g = rng.uniform(-1.0, 1.0, (3, 32, 32, 32))
+    h, lo = 1.0 / 32, (-0.37, -0.61, -0.5)
+    d8, a8 = _rates(orc, 8, Ug, h, lo, "outflow", omega=0.4, g=g)
+    d16, a16 = _rates(orc, 16, Ug, h, lo, "outflow", omega=0.4, g=g)
+    scale = np.abs(d8).max(axis=(1, 2, 3))
+    err = np.abs(d16 - d8).max(axis=(1, 2, 3)) / scale
+    assert np.all(err <= 1e-13), err
+    assert a16 == pytest.approx(a8, rel=1e-15)
+    # the origins do enter: the frame sources differ from the omega = 0 rates
+    d0, _ = _rates(orc, 16, Ug, h, lo, "outflow", omega=0.0, g=g)
+    assert np.abs(d0[6:9] - d16[6:9]).max() > 1e-6 * scale[6:9].max()
+
+
+def test_sixteen_rk3_step_equals_eight(orc):
+    from oracle import mesh
+    Ug, h, lo = W.sedov_box(32, GAMMA)
+    runs = [mesh.BoxRun(orc.OracleParams(gamma=GAMMA, N=N), Ug, h, lo, "periodic") for N in (8, 16)]
+    dts = [r.step(0.4) for r in runs]
+    assert dts[0] == dts[1]
+    assert np.array_equal(runs[0].U.view(np.int64), runs[1].U.view(np.int64))
+
+
+def test_sixteen_halves_the_face_overhead(orc):
+    """Exact operation counts per interior cell: 3 (N+1) N^2 faces per
+    sub-grid, so 3 (N+1)/N per cell (3.375 at N = 8, 3.1875 at N = 16; the
+    part beyond 3 halves); the PPM evaluations follow the face points they
+    feed, and the total operations nearly so."""
+    out = {}
+    for N in (8, 16):
+        P = orc.OracleParams(gamma=GAMMA, N=N)
+        S = N + 6
+        rng = np.random.default_rng(11)
+        sh = (S, S, S)
+        U = W.conserved_from_primitive(rng.uniform(0.5, 2.0, sh), rng.uniform(-0.3, 0.3, (3,) + sh),
+                                       rng.uniform(0.2, 1.0, sh), GAMMA, species=0.3 * np.ones(sh))
+        c = orc.count_ops(P, U, np.zeros(3), 0.1)
+        out[N] = (c["ppm_calls"] / N ** 3, sum(c["step"].values()) / N ** 3)
+    for N in (8, 16):
+        faces = 3 * (N + 1) * N * N / N ** 3
+        # two sides of 9 points of 10 fields per face
+        assert out[N][0] == pytest.approx(faces * 2 * 9 * 10, rel=1e-12)
+    assert out[16][1] < out[8][1]
+    assert out[16][1] / out[8][1] == pytest.approx((17 / 16) / (9 / 8), rel=0.02)
