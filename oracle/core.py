@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
 
 class _P(C.Structure):
     _fields_ = [("gamma", C.c_double), ("omega", C.c_double), ("eta1", C.c_double), ("eta2", C.c_double),
-                ("N", C.c_int), ("G", C.c_int), ("nf", C.c_int), ("face_points", C.c_int)]
+                ("N", C.c_int), ("G", C.c_int), ("nf", C.c_int), ("face_points", C.c_int), ("contact", C.c_int)]
 
 
 @dataclass
@@ -44,9 +44,11 @@ class OracleParams:
     G: int = 3
     nf: int = 10
     face_points: int = 9  # 1: flux at the face centres only (the old hydro module, Sec. III-B)
+    contact: int = 0  # 1: PPM contact steepening of density and species (optional in Sec. III-B)
 
     def c(self) -> _P:
-        return _P(self.gamma, self.omega, self.eta1, self.eta2, self.N, self.G, self.nf, self.face_points)
+        return _P(self.gamma, self.omega, self.eta1, self.eta2, self.N, self.G, self.nf, self.face_points,
+                  self.contact)
 
 
 _lib = None
@@ -66,6 +68,10 @@ def lib():
         l.orc_primitives.argtypes = [C.POINTER(_P), dp, dp]
         l.orc_ppm_line.argtypes = [dp, dp, dp]
         l.orc_ppm_line.restype = C.c_int
+        l.orc_ppm_line_eta.argtypes = [dp, C.c_double, dp, dp]
+        l.orc_ppm_line_eta.restype = None
+        l.orc_contact_eta.argtypes = [C.POINTER(_P), dp, dp, dp]
+        l.orc_contact_eta.restype = C.c_double
         l.orc_point_flux.argtypes = [C.POINTER(_P), dp, dp, C.c_int, dp, dp, dp]
         l.orc_count_ops.argtypes = [C.POINTER(_P), dp, dp, C.c_double, C.POINTER(C.c_long)]
         ip = C.POINTER(C.c_int)
@@ -156,6 +162,25 @@ def ppm_line(s5) -> tuple[float, float, int]:
     qm = C.c_double()
     f = lib().orc_ppm_line(_dp(s), C.byref(qp), C.byref(qm))
     return qp.value, qm.value, f
+
+
+def ppm_line_eta(s5, eta: float) -> tuple[float, float]:
+    """PPM on five samples with the steepening weight eta applied before the
+    monotonicity fix-ups (eta = 0: plain PPM)."""
+    s = np.ascontiguousarray(s5, dtype=np.float64)
+    qp = C.c_double()
+    qm = C.c_double()
+    lib().orc_ppm_line_eta(_dp(s), float(eta), C.byref(qp), C.byref(qm))
+    return qp.value, qm.value
+
+
+def contact_eta(P: OracleParams, a5, rho2, p2) -> float:
+    """Steepening weight of a line: a5 the steepened field's samples, rho2/p2
+    density and pressure of the two neighbours (towards -d, towards +d)."""
+    a = np.ascontiguousarray(a5, dtype=np.float64)
+    r = np.ascontiguousarray(rho2, dtype=np.float64)
+    p = np.ascontiguousarray(p2, dtype=np.float64)
+    return lib().orc_contact_eta(C.byref(P.c()), _dp(a), _dp(r), _dp(p))
 
 
 def point_flux(P: OracleParams, qL, qR, axis: int, xq) -> tuple[np.ndarray, float]:

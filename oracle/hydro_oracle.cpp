@@ -10,7 +10,8 @@
 //     N^3 sub-grid with a 3-deep ghost layer;
 //   * primitives with the dual-energy selection of Bryan et al. (1995);
 //   * PPM (Colella & Woodward 1984) along the 13 lines through cell centres,
-//     giving left/right values at the 26 face, edge and vertex points;
+//     giving left/right values at the 26 face, edge and vertex points, with
+//     the optional contact-discontinuity steepening of that paper;
 //   * the Kurganov-Tadmor (2000) central flux at the 9 points of each face;
 //   * the Newton-Cotes (Simpson) face sum and the flux divergence;
 //   * rotating-frame, gravity and spin-torque sources;
@@ -97,6 +98,8 @@ struct Params {
   int nf;         // number of fields = 9 + species
   int face_points;  // 9: flux at the 9 points of each face, Simpson sum (the new module);
                     // 1: flux at the face centre only (the old module, Sec. III-B)
+  int contact;      // 1: PPM contact-discontinuity detection and steepening of the
+                    // density and species lines (optional in Sec. III-B); 0: off
 };
 
 // Primitive recovery of one cell (Sec. III-B; dual energy after Bryan 1995).
@@ -122,14 +125,17 @@ void primitives(const Params& P, const T* u, T* q) {
 //   Delta_j = 0 if delta_j*delta_{j-1} <= 0, else
 //             sgn(delta_j) min(2|delta_{j-1}|, 2|delta_j|, |delta_{j-1}+delta_j|/2)
 //   qp = (q0+q1)/2 - (Delta_1-Delta_0)/6,  qm = (q_{-1}+q0)/2 - (Delta_0-Delta_{-1})/6
+// then, with a steepening weight eta > 0 (contact_eta below), the blend of
+// both values with the limited-slope extrapolations from the neighbours
+// (Colella & Woodward 1984, discontinuity detection):
+//   qp <- (1-eta) qp + eta (q1 - Delta_1/2),  qm <- (1-eta) qm + eta (q-1 + Delta_-1/2),
 // then the monotonicity fix-ups, in this order: local extremum -> flatten;
 // overshoot towards -d -> qm = 3q0-2qp; overshoot towards +d -> qp = 3q0-2qm.
-// Contact steepening is off (optional in the method).
 // With uq (non-null), also returns the unlimited pair uq[0] = towards +d,
 // uq[1] = towards -d, from central slopes Delta_j = (delta_{j-1}+delta_j)/2
 // and no fix-ups (what the limiter would leave untouched).
 template <class T>
-void ppm_line(const T s[5], T& qp, T& qm, T* uq = nullptr) {
+void ppm_line(const T s[5], T& qp, T& qm, T* uq = nullptr, T eta = T(0.0)) {
   const T sixth = T(1.0 / 6.0);
   T dl[4];
   for (int j = 0; j < 4; ++j) dl[j] = s[j + 1] - s[j];  // delta_{j-2}
@@ -146,6 +152,11 @@ void ppm_line(const T s[5], T& qp, T& qm, T* uq = nullptr) {
   const T q0 = s[2];
   qp = T(0.5) * (q0 + s[3]) - (D[2] - D[1]) * sixth;
   qm = T(0.5) * (s[1] + q0) - (D[1] - D[0]) * sixth;
+  if (val(eta) > 0.0) {  // (not a counted comparison: eta is 0 with steepening off)
+    const T keep = T(1.0) - eta;
+    qp = keep * qp + eta * (s[3] - T(0.5) * D[2]);
+    qm = keep * qm + eta * (s[1] + T(0.5) * D[0]);
+  }
   if ((qp - q0) * (q0 - qm) <= T(0.0)) {
     qp = q0;
     qm = q0;
@@ -165,6 +176,39 @@ void ppm_line(const T s[5], T& qp, T& qm, T* uq = nullptr) {
   uq[0] = T(0.5) * (q0 + s[3]) - (Du[2] - Du[1]) * sixth;
   uq[1] = T(0.5) * (s[1] + q0) - (Du[1] - Du[0]) * sixth;
 }
+
+// Steepening weight of one line (Colella & Woodward 1984, discontinuity
+// detection, with their constants eps = 0.01, eta1 = 20, eta2 = 0.05, and
+// their contact criterion for gas dynamics with K0 = 0.1).  a[0..4] are the
+// five samples of the steepened field, rho/p the density and pressure of the
+// two neighbours on the same line (index 0: towards -d, 1: towards +d).
+//   The jump must be a contact, not a shock: the relative density jump,
+//   times gamma K0, at least the relative pressure jump:
+//     gamma K0 |rho_1 - rho_0| / min(rho) >= |p_1 - p_0| / min(p).
+//   With the second differences d2_m = (a_-2 + a_0) - 2a_-1 and
+//   d2_p = (a_0 + a_2) - 2a_1 (the 1/(6 h^2) of the nonuniform form cancels;
+//   each is summed symmetrically, so that a reversed line rounds alike):
+//     eta~ = 0 if d2_m d2_p > 0 (no inflection at the cell), or if
+//            |a_1 - a_-1| <= eps min(|a_1|, |a_-1|) (no jump to speak of),
+//     else eta~ = -(d2_p - d2_m) / (6 (a_1 - a_-1));
+//     eta = max(0, min(eta1 (eta~ - eta2), 1)).
+// The formula is free of the spacing, so it serves the diagonal lines as it
+// serves the axes.
+template <class T>
+T contact_eta(const Params& P, const T a[5], const T rho[2], const T p[2]) {
+  const T K0 = T(0.1), eps = T(0.01), eta1 = T(20.0), eta2 = T(0.05);
+  const T drho = abs_(rho[1] - rho[0]) / min_(rho[0], rho[1]);
+  const T dp = abs_(p[1] - p[0]) / min_(p[0], p[1]);
+  if ((T(P.gamma) * K0) * drho < dp) return T(0.0);
+  const T d2m = (a[0] + a[2]) - T(2.0) * a[1];
+  const T d2p = (a[2] + a[4]) - T(2.0) * a[3];
+  if (T(0.0) < d2m * d2p) return T(0.0);
+  const T jump = a[3] - a[1];
+  if (abs_(jump) <= eps * min_(abs_(a[3]), abs_(a[1]))) return T(0.0);
+  const T et = -(d2p - d2m) / (T(6.0) * jump);
+  return max_(T(0.0), min_(eta1 * (et - eta2), T(1.0)));
+}
+inline bool steepened_field(int k) { return k == RHO || k >= SP0; }
 
 // Significant limiter activity (the learned indicator's label): on a line
 // of field k through a cell, the limited pair differs from the unlimited one
@@ -265,6 +309,16 @@ int recon_point(const Params& P, const std::vector<T>& Q, int x, int y, int z, c
     vscale = std::fabs(val(Q[1 * S3 + c])) + std::fabs(val(Q[2 * S3 + c])) + std::fabs(val(Q[3 * S3 + c])) +
              std::sqrt(P.gamma * (P.gamma - 1.0) * eps / rho);
   }
+  // density and pressure of the two neighbours on the line (contact test)
+  T nrho[2] = {T(0.0), T(0.0)}, np_[2] = {T(0.0), T(0.0)};
+  if (P.contact && !unlimited) {
+    for (int e = 0; e < 2; ++e) {
+      const int m = 2 * e - 1;
+      const long cn = at(x + m * d[0], y + m * d[1], z + m * d[2]);
+      nrho[e] = Q[RHO * S3 + cn];
+      np_[e] = T(P.gamma - 1.0) * Q[4 * S3 + cn];
+    }
+  }
   int fl = 0;
   for (int k = 0; k < P.nf; ++k) {
     T s5[5];
@@ -274,19 +328,20 @@ int recon_point(const Params& P, const std::vector<T>& Q, int x, int y, int z, c
       out[k] = unlimited_plus(s5);
       continue;
     }
+    const T eta = (P.contact && steepened_field(k)) ? contact_eta(P, s5, nrho, np_) : T(0.0);
     if (want_flag && !spin_field(k)) {
       T uq[2];
-      ppm_line(s5, qp, qm, uq);
+      ppm_line(s5, qp, qm, uq, eta);
       const double scale = (k >= 1 && k <= 3) ? vscale : std::fabs(val(s5[2]));
       const double diff = std::max(std::fabs(val(qp) - val(uq[0])), std::fabs(val(qm) - val(uq[1])));
       if (diff > kLabelTol * scale) fl = 1;
     } else if constexpr (std::is_same<T, CD>::value) {
       const long before = g_ops.total();
-      ppm_line(s5, qp, qm);
+      ppm_line(s5, qp, qm, (T*)nullptr, eta);
       g_ppm_ops += g_ops.total() - before;
       g_ppm_calls += 1;
     } else {
-      ppm_line(s5, qp, qm);
+      ppm_line(s5, qp, qm, (T*)nullptr, eta);
     }
     out[k] = qp;
   }
@@ -532,7 +587,7 @@ extern "C" {
 
 struct orc_params {
   double gamma, omega, eta1, eta2;
-  int N, G, nf, face_points;
+  int N, G, nf, face_points, contact;
 };
 
 static orc::Params to_p(const orc_params* p) {
@@ -540,6 +595,7 @@ static orc::Params to_p(const orc_params* p) {
   P.gamma = p->gamma; P.omega = p->omega; P.eta1 = p->eta1; P.eta2 = p->eta2;
   P.N = p->N; P.G = p->G; P.nf = p->nf;
   P.face_points = p->face_points == 1 ? 1 : 9;
+  P.contact = p->contact ? 1 : 0;
   return P;
 }
 
@@ -610,6 +666,18 @@ int orc_ppm_line(const double* s5, double* qp, double* qm) {
   double uq[2];
   orc::ppm_line<double>(s5, *qp, *qm, uq);
   return (*qp != uq[0] || *qm != uq[1]) ? 1 : 0;
+}
+
+// PPM on one line with a given steepening weight eta (no unlimited pair).
+void orc_ppm_line_eta(const double* s5, double eta, double* qp, double* qm) {
+  orc::ppm_line<double>(s5, *qp, *qm, nullptr, eta);
+}
+
+// Steepening weight of one line: a5 the steepened field's five samples,
+// rho2/p2 the density and pressure of the neighbours (-d, +d).
+double orc_contact_eta(const orc_params* p, const double* a5, const double* rho2, const double* p2) {
+  const orc::Params P = to_p(p);
+  return orc::contact_eta<double>(P, a5, rho2, p2);
 }
 
 // Central flux at one quadrature point from primitive states qL, qR.
