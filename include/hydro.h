@@ -83,14 +83,23 @@ typedef struct {
  * flux_points: 9 (or 0) for the fluxes at the 9 points of every face summed
  * with Simpson weights (the new hydro module, Sec. III-B), 1 for the flux at
  * the face centre only (the old module the paper compares it with: the
- * same reconstruction, fluxes only at the centres of cell faces).  Defaults:
- * FP64, cfl 0.4, eta1 1e-3, eta2 0.1, 9 points. */
+ * same reconstruction, fluxes only at the centres of cell faces).
+ * contact: 1 turns on PPM contact-discontinuity detection and steepening of
+ * the density and species lines (optional in Sec. III-B; Colella & Woodward
+ * 1984: a line whose density jump is a contact, gamma K0 |drho|/min(rho) >=
+ * |dp|/min(p) over its two neighbours with K0 = 0.1, blends both interface
+ * values with the neighbours' limited extrapolations by a weight in [0,1]
+ * from its second differences, before the monotonicity fix-ups).  Not
+ * available with the learned indicator (hydro_step: EUNSUP) or in the fused
+ * RK3 step (EUNSUP).  Defaults: FP64, cfl 0.4, eta1 1e-3, eta2 0.1, 9
+ * points, contact 0. */
 typedef struct {
   int precision;   /* HYDRO_PREC_FP64 or HYDRO_PREC_MIXED */
   double cfl;
   double de_eta1;
   double de_eta2;
   int flux_points; /* 9 (0 means 9) or 1 */
+  int contact;     /* 0 or 1 */
 } hydro_mode_t;
 
 /* A batch of leaf sub-grids (device pointers).  g may be NULL. */
@@ -110,7 +119,8 @@ typedef struct {
 int hydro_create(const hydro_layout_t* layout, double gamma, double omega, hydro_ctx_t** out);
 
 /* Replace the run-time options.  Errors: EINVAL (unknown precision, cfl or
- * thresholds outside (0,1]). */
+ * thresholds outside (0,1], flux_points not in {0, 1, 9}, contact not in
+ * {0, 1}). */
 int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
 
 /* One stage of the semi-discrete operator on every sub-grid of the batch
@@ -131,7 +141,8 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
  * face-averaged fluxes and the 3 components of the momentum-flux torque
  * about the adjacent interior cell.
  * Errors: EINVAL (NULL ctx/batch/pointers, n_sub < 0, misaligned U, dt < 0),
- * ENOMEM, ECUDA.  n_sub == 0 is a no-op. */
+ * EUNSUP (contact steepening with the learned indicator on), ENOMEM, ECUDA.
+ * n_sub == 0 is a no-op. */
 int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, double* face_flux,
                void* stream);
 
@@ -302,7 +313,7 @@ typedef struct hydro_graph hydro_graph_t;
 /* Enqueue one time step on a stream: parity 0 advances a -> b, 1 advances
  * b -> a.  Ten launches (two with fused: a clear of the context's sync words
  * and the step).  Errors: EINVAL (inconsistent descriptor), EUNSUP (fused
- * with an adaptive mesh or in FP64), ENOMEM. */
+ * with an adaptive mesh, in FP64 or with contact steepening), ENOMEM. */
 int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
 
 /* Capture the two directions of hydro_rk3_step once into CUDA graphs

@@ -88,6 +88,7 @@ static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, dou
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
   A.P.face_points = c->mode.flux_points == 1 ? 1 : 9;
+  A.P.contact = c->mode.contact ? 1 : 0;
   A.gate = c->gate_on ? 1 : 0;
   A.gate_w = c->gate_w;
   A.gate_logit_thr = (float)c->gate_logit_thr;
@@ -111,7 +112,7 @@ int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
 }
 
 int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st) {
-  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED) return HYDRO_EUNSUP;
+  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED || c->mode.contact) return HYDRO_EUNSUP;
   if (d->bc != HYDRO_BC_PERIODIC && d->bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
   if (!aligned16(d->a.U) || !aligned16(d->U_b) || !aligned16(d->dUdt)) return HYDRO_EINVAL;
   int rc = hydro_ctx_prepare_fused(c, d->a.n_sub);
@@ -175,6 +176,7 @@ int hydro_create(const hydro_layout_t* L, double gamma, double omega, hydro_ctx_
   c->mode.de_eta1 = 1e-3;
   c->mode.de_eta2 = 0.1;
   c->mode.flux_points = 9;
+  c->mode.contact = 0;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
@@ -192,6 +194,7 @@ int hydro_set_mode(hydro_ctx_t* c, const hydro_mode_t* m) {
       !(m->de_eta2 > 0.0 && m->de_eta2 <= 1.0))
     return HYDRO_EINVAL;
   if (m->flux_points != 0 && m->flux_points != 1 && m->flux_points != 9) return HYDRO_EINVAL;
+  if (m->contact != 0 && m->contact != 1) return HYDRO_EINVAL;
   c->mode = *m;
   if (c->mode.flux_points == 0) c->mode.flux_points = 9;
   return HYDRO_OK;
@@ -205,6 +208,7 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   if (!B->U || !B->origin || !B->h || !dUdt || !amax) return HYDRO_EINVAL;
   if (!aligned16(B->U) || !aligned16(dUdt)) return HYDRO_EINVAL;
   const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
+  if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;
   int rc = ensure_status(c);
   if (rc) return rc;
   const int slots = step_slots(c, mixed);

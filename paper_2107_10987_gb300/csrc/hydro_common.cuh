@@ -36,6 +36,7 @@ __device__ __forceinline__ size_t face_index(int s, int f, int q, int pc, int pb
 struct StepParams {
   double gamma, gm1, omega, eta1;
   int face_points;  // 9: Simpson sum of the 9 face points; 1: the face centre only
+  int contact;      // 1: PPM contact steepening of the density and species lines
 };
 
 // Arguments of the step kernels (device pointers; layouts as in hydro.h).

@@ -12,12 +12,20 @@ __device__ __forceinline__ float slope32(float a, float b) {
   return (a * b <= 0.f) ? 0.f : copysignf(m, b);
 }
 
-// PPM on one line in FP32 (branch-free form of the same limiter).
-__device__ __forceinline__ void ppm32(float s0, float s1, float s2, float s3, float s4, float& qp, float& qm) {
+// PPM on one line in FP32 (branch-free form of the same limiter).  kSteep:
+// the contact-steepening blend with weight eta before the fix-ups (as ppm64).
+template <bool kSteep = false>
+__device__ __forceinline__ void ppm32(float s0, float s1, float s2, float s3, float s4, float& qp, float& qm,
+                                      float eta = 0.f) {
   const float sixth = 1.f / 6.f;
   const float D0 = slope32(s1 - s0, s2 - s1), D1 = slope32(s2 - s1, s3 - s2), D2 = slope32(s3 - s2, s4 - s3);
-  const float p = 0.5f * (s2 + s3) - (D2 - D1) * sixth;
-  const float m = 0.5f * (s1 + s2) - (D1 - D0) * sixth;
+  float p = 0.5f * (s2 + s3) - (D2 - D1) * sixth;
+  float m = 0.5f * (s1 + s2) - (D1 - D0) * sixth;
+  if (kSteep) {
+    const float keep = 1.f - eta;
+    p = keep * p + eta * (s3 - 0.5f * D2);
+    m = keep * m + eta * (s1 + 0.5f * D0);
+  }
   const bool ext = (p - s2) * (s2 - m) <= 0.f;
   const float dq = p - m;
   const float lhs = dq * (s2 - 0.5f * (p + m));
@@ -33,6 +41,37 @@ __device__ __forceinline__ void line10f(const float* __restrict__ Q, int c, int 
   for (int k = 0; k < F; ++k) {
     const float* q = Q + k * S3 + c;
     ppm32(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+  }
+}
+
+// Contact-steepening weight of one line in FP32 (contact_eta64's definition).
+__device__ __forceinline__ float contact_eta32(float a0, float a1, float a2, float a3, float a4) {
+  const float d2m = (a0 + a2) - 2.f * a1, d2p = (a2 + a4) - 2.f * a3;
+  const float jump = a3 - a1;
+  const float et = (d2m - d2p) / (6.f * jump);
+  const bool off = d2m * d2p > 0.f || fabsf(jump) <= 0.01f * fminf(fabsf(a3), fabsf(a1));
+  return off ? 0.f : fminf(fmaxf(20.f * (et - 0.05f), 0.f), 1.f);
+}
+
+// line10f with contact steepening of the density and species lines (the
+// gas-dynamics contact test of line10c over the two neighbours; gamma_k0 =
+// gamma K0, gm1 = gamma - 1).
+__device__ __forceinline__ void line10fc(const float* __restrict__ Q, int c, int st, float gamma_k0, float gm1,
+                                         float qp[F], float qm[F]) {
+  const float r0 = Q[RHO * S3 + c - st], r1 = Q[RHO * S3 + c + st];
+  const float p0 = gm1 * Q[EGAS * S3 + c - st], p1 = gm1 * Q[EGAS * S3 + c + st];
+  const float drho = fabsf(r1 - r0) / fminf(r0, r1);
+  const float dp = fabsf(p1 - p0) / fminf(p0, p1);
+  const bool contact = !(gamma_k0 * drho < dp);
+#pragma unroll
+  for (int k = 0; k < F; ++k) {
+    const float* q = Q + k * S3 + c;
+    if (k == RHO || k >= SP0) {
+      const float eta = contact ? contact_eta32(q[-2 * st], q[-st], q[0], q[st], q[2 * st]) : 0.f;
+      ppm32<true>(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k], eta);
+    } else {
+      ppm32(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+    }
   }
 }
 

@@ -61,7 +61,8 @@ __device__ __forceinline__ RowMap row_map(int tid) {
 // Qf: the CTA's dynamic shared memory; red: [kThreadsMx / 32] floats of
 // shared memory; D: the CTA's scratch (kScratchPerSub doubles).  Ends with
 // a barrier, so the next sub-grid may reuse all of them.
-template <bool kGate, class Io>
+// kContact: contact steepening of the density and species lines (line10fc).
+template <bool kGate, bool kContact = false, class Io>
 __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io, int s, const RowMap& R, float* Qf,
                                               float* red, double* __restrict__ D) {
   uint8_t* smooth = reinterpret_cast<uint8_t*>(Qf + F * S3);
@@ -118,6 +119,10 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
       if (kGate && smooth[cj]) {
         line10u(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
         if (p != 4) line10u(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+      } else if (kContact) {
+        const float gk0 = PF.gamma * 0.1f;
+        line10fc(Qf, cj, sa + t1 * sb + t2 * sc, gk0, PF.gm1, qpA, qmA);
+        if (p != 4) line10fc(Qf, cj, sa - t1 * sb - t2 * sc, gk0, PF.gm1, qpB, qmB);
       } else {
         line10f(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
         if (p != 4) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);

@@ -76,14 +76,23 @@ __device__ __forceinline__ double slope64(double a, double b) {
 }
 
 // PPM on the five samples s0..s4 of one line: qp = value at the +d end of the
-// centre cell, qm = value at its -d end (limited, monotonised).
+// centre cell, qm = value at its -d end (limited, monotonised).  kSteep: blend
+// both interface values with the neighbours' limited extrapolations by the
+// contact-steepening weight eta before the fix-ups (Colella & Woodward 1984):
+//   qp <- (1-eta) qp + eta (s3 - D2/2),  qm <- (1-eta) qm + eta (s1 + D0/2).
+template <bool kSteep = false>
 __device__ __forceinline__ void ppm64(double s0, double s1, double s2, double s3, double s4, double& qp,
-                                      double& qm) {
+                                      double& qm, double eta = 0.0) {
   const double sixth = 1.0 / 6.0;
   const double d0 = rsub(s1, s0), d1 = rsub(s2, s1), d2 = rsub(s3, s2), d3 = rsub(s4, s3);
   const double D0 = slope64(d0, d1), D1 = slope64(d1, d2), D2 = slope64(d2, d3);
   double p = rsub(rmul(0.5, radd(s2, s3)), rmul(rsub(D2, D1), sixth));
   double m = rsub(rmul(0.5, radd(s1, s2)), rmul(rsub(D1, D0), sixth));
+  if (kSteep && eta > 0.0) {
+    const double keep = rsub(1.0, eta);
+    p = radd(rmul(keep, p), rmul(eta, rsub(s3, rmul(0.5, D2))));
+    m = radd(rmul(keep, m), rmul(eta, radd(s1, rmul(0.5, D0))));
+  }
   if (nonpositive(rmul(rsub(p, s2), rsub(s2, m)))) {
     p = s2;
     m = s2;
@@ -108,6 +117,50 @@ __device__ __forceinline__ void line10(const double* __restrict__ Q, int c, int 
   for (int k = 0; k < F; ++k) {
     const double* q = Q + k * S3 + c;
     ppm64(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+  }
+}
+
+// Contact-steepening weight of one line from the five samples a0..a4 of the
+// steepened field (Colella & Woodward 1984 discontinuity detection; their
+// constants eps = 0.01, eta1 = 20, eta2 = 0.05): second differences
+// d- = (a0 + a2) - 2 a1 and d+ = (a2 + a4) - 2 a3; no weight without an
+// inflection (d- d+ > 0) or with a jump a3 - a1 of at most eps min(|a3|, |a1|);
+// else eta~ = -(d+ - d-) / (6 (a3 - a1)) and eta = max(0, min(20 (eta~ - 0.05), 1)).
+// Every operation explicitly rounded, in the oracle's order, and the minima
+// and maxima as the same comparisons: the oracle's bits.
+__device__ __forceinline__ double contact_eta64(double a0, double a1, double a2, double a3, double a4) {
+  const double d2m = rsub(radd(a0, a2), rmul(2.0, a1));
+  const double d2p = rsub(radd(a2, a4), rmul(2.0, a3));
+  if (rmul(d2m, d2p) > 0.0) return 0.0;
+  const double jump = rsub(a3, a1);
+  const double f3 = fabs(a3), f1 = fabs(a1);
+  if (fabs(jump) <= rmul(0.01, f3 < f1 ? f3 : f1)) return 0.0;
+  const double et = -rsub(d2p, d2m) / rmul(6.0, jump);
+  const double v = rmul(20.0, rsub(et, 0.05));
+  const double m = v < 1.0 ? v : 1.0;
+  return 0.0 > m ? 0.0 : m;
+}
+
+// line10 with contact steepening of the density and species lines.  The line
+// is a contact, not a shock, where Colella & Woodward's gas-dynamics test
+// holds over its two neighbours (K0 = 0.1):
+//   gamma K0 |rho+ - rho-| / min(rho) >= |p+ - p-| / min(p),  p = (gamma-1) eps.
+__device__ __forceinline__ void line10c(const double* __restrict__ Q, int c, int st, const StepParams& P,
+                                        double qp[F], double qm[F]) {
+  const double r0 = Q[RHO * S3 + c - st], r1 = Q[RHO * S3 + c + st];
+  const double p0 = rmul(P.gm1, Q[EGAS * S3 + c - st]), p1 = rmul(P.gm1, Q[EGAS * S3 + c + st]);
+  const double drho = fabs(rsub(r1, r0)) / (r0 < r1 ? r0 : r1);
+  const double dp = fabs(rsub(p1, p0)) / (p0 < p1 ? p0 : p1);
+  const bool contact = !(rmul(rmul(P.gamma, 0.1), drho) < dp);
+#pragma unroll
+  for (int k = 0; k < F; ++k) {
+    const double* q = Q + k * S3 + c;
+    if (k == RHO || k >= SP0) {
+      const double eta = contact ? contact_eta64(q[-2 * st], q[-st], q[0], q[st], q[2 * st]) : 0.0;
+      ppm64<true>(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k], eta);
+    } else {
+      ppm64(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+    }
   }
 }
 
@@ -188,8 +241,9 @@ constexpr long kWaitPolls = 1L << 24;
 
 // kGate: the learned smoothness indicator is on (A.gate): its decisions per
 // reconstructed cell follow the primitives in shared memory ([S3] bytes of
-// flags and [S3] of predictions after the state).
-template <bool kGate>
+// flags and [S3] of predictions after the state).  kContact: contact
+// steepening (A.P.contact; not combined with the indicator).
+template <bool kGate, bool kContact = false>
 __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs64 A) {
   extern __shared__ __align__(128) double Q[];  // [F][S3], then the indicator's flags
   uint8_t* smooth = reinterpret_cast<uint8_t*>(Q + F * S3);
@@ -289,6 +343,9 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
         if (kGate && smooth[cj]) {
           line10u(Q, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
           if (p != 4) line10u(Q, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        } else if (kContact) {
+          line10c(Q, cj, sa + t1 * sb + t2 * sc, A.P, qpA, qmA);
+          if (p != 4) line10c(Q, cj, sa - t1 * sb - t2 * sc, A.P, qpB, qmB);
         } else {
           line10(Q, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
           if (p != 4) line10(Q, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
@@ -425,6 +482,9 @@ cudaError_t prepare_step_fp64() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(hydro_step_fp64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)step_fp64_smem_bytes(true));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)step_fp64_smem_bytes(false));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -436,6 +496,8 @@ cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (A.gate)
     hydro_step_fp64_kernel<true><<<grid, kThreads64, step_fp64_smem_bytes(true), st>>>(A);
+  else if (A.P.contact)
+    hydro_step_fp64_kernel<false, true><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);
   else
     hydro_step_fp64_kernel<false><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);
   return cudaGetLastError();

@@ -34,15 +34,16 @@ struct StepIo {
 };
 
 // kGate: the learned smoothness indicator is on (A.gate); the kernel without
-// it carries none of the indicator's registers.
-template <bool kGate>
+// it carries none of the indicator's registers.  kContact: contact
+// steepening (A.P.contact; not combined with the indicator).
+template <bool kGate, bool kContact = false>
 __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArgs64 A) {
   extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [2][S3] smooth flags
   __shared__ float red[kThreadsMx / 32];
   double* __restrict__ D = A.scratch + (size_t)blockIdx.x * kScratchPerSub;
   const RowMap R = row_map(threadIdx.x);
   const StepIo io{A};
-  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) mixed_subgrid<kGate>(A, io, s, R, Qf, red, D);
+  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) mixed_subgrid<kGate, kContact>(A, io, s, R, Qf, red, D);
 }
 
 size_t step_mixed_smem_bytes() { return kMixedSmemBytes; }
@@ -57,6 +58,9 @@ cudaError_t prepare_step_mixed() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)step_mixed_smem_bytes());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)step_mixed_smem_bytes());
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -68,6 +72,8 @@ cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (A.gate)
     hydro_step_mixed_kernel<true><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+  else if (A.P.contact)
+    hydro_step_mixed_kernel<false, true><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   else
     hydro_step_mixed_kernel<false><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   return cudaGetLastError();

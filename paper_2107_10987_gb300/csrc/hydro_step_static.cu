@@ -98,6 +98,7 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
   A.P.face_points = c->mode.flux_points == 1 ? 1 : 9;
+  A.P.contact = c->mode.contact ? 1 : 0;
   A.gate = 0;
   A.gate_w = nullptr;
   A.gate_logit_thr = 0.f;

@@ -1,0 +1,256 @@
+"""PPM contact steepening (hydro_mode_t.contact = 1; the option Sec. III-B
+names, after Colella & Woodward 1984) in the step kernels, through the C ABI,
+against the oracle's steepening (pinned in test_oracle_contact.py):
+  * FP64 step: <= 1e-12 per field on contact-rich random sub-grids with and
+    without rotation and gravity.  The kernel computes the steepening
+    weights with the oracle's explicitly rounded operations, so its
+    decisions (contact test, inflection, jump floor) are the oracle's;
+  * mixed step: within the mixed-precision budget, on sub-grids whose
+    density takes the exact values 1, 1/2 and 1/4 at a level pressure:
+    there every steepening decision is exact in FP32 as in FP64, so the
+    comparison measures the FP32 arithmetic and not a decision that a
+    rounding flips on a borderline line;
+  * three RK3 steps of an advected contact: FP64 within 1e-12 of the oracle;
+  * conservation on a periodic mesh, and the rates differ from the
+    unsteepened ones;
+  * the mode's checks: contact outside {0, 1}, the indicator together with
+    steepening, and the fused step with steepening are rejected.
+The last test prints the step times with and without steepening.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2107_10987_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GAMMA = 5.0 / 3.0
+S = 14
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2107_10987_gb300 import _build, hydro
+    _build.build()
+    return hydro
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_mod):
+    return oracle_mod.core
+
+
+def contact_subgrids(n, seed, exact=False):
+    """Padded sub-grids [n][10][S][S][S] full of density contacts.
+    exact=False: two density levels with 5 % noise, pressure 1 +- 2 %, and
+    every fourth sub-grid with a pressure jump (1 to 10) across a plane, so
+    that the contact test also refuses lines.  exact=True: density levels 1,
+    1/2 and 1/4, pressure exactly 1, species exactly half the density."""
+    rng = np.random.default_rng(seed)
+    sh = (S, S, S)
+    out = np.empty((n, 10) + sh)
+    for i in range(n):
+        if exact:
+            rho = rng.choice([1.0, 0.5, 0.25], size=sh)
+            p = np.ones(sh)
+            frac = np.full(sh, 0.5)
+        else:
+            rho = np.where(rng.random(sh) < 0.5, 1.0, 0.3) * rng.uniform(0.95, 1.05, sh)
+            p = rng.uniform(0.98, 1.02, sh)
+            if i % 4 == 3:
+                p = np.where(np.arange(S)[None, None, :] < S // 2, 10.0, 1.0) * p
+            frac = rng.uniform(0.4, 0.6, sh)
+        v = rng.uniform(-0.3, 0.3, (3,) + sh)
+        z = rng.uniform(-0.01, 0.01, (3,) + sh)
+        out[i] = W.conserved_from_primitive(rho, v, p, GAMMA, z=z, species=frac * rho)
+    return out
+
+
+def gpu_step(H, ctx, U, origin, h, g=None):
+    dev = torch.device("cuda")
+    n = U.shape[0]
+    Ut = torch.tensor(U, device=dev)
+    ot = torch.tensor(np.broadcast_to(origin, (n, 3)).copy(), device=dev)
+    ht = torch.tensor(np.broadcast_to(h, (n,)).copy(), device=dev)
+    gt = torch.tensor(g, device=dev) if g is not None else None
+    dU = torch.full((n, 10, 8, 8, 8), np.nan, dtype=torch.float64, device=dev)
+    am = torch.full((n,), np.nan, dtype=torch.float64, device=dev)
+    H.hydro_step(ctx, H.make_batch(Ut, ot, ht, gt), 0.0, dU, am)
+    torch.cuda.synchronize()
+    return dU.cpu().numpy(), am.cpu().numpy()
+
+
+@pytest.mark.parametrize("omega,gravity", [(0.0, False), (0.3, True)])
+def test_fp64_contact_step_matches_oracle(H, orc, omega, gravity):
+    from oracle.compare import max_rel_error
+    n = 96
+    U = contact_subgrids(n, 61)
+    rng = np.random.default_rng(62)
+    origin = rng.uniform(-1, 1, (n, 3))
+    h = rng.uniform(0.01, 0.1, n)
+    g = rng.uniform(-1, 1, (n, 3, 8, 8, 8)) if gravity else None
+    ctx = H.Context(GAMMA, omega)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=1)
+    dU, am = gpu_step(H, ctx, U, origin, h, g)
+    assert H.hydro_status(ctx) == 0
+    P = orc.OracleParams(gamma=GAMMA, omega=omega, contact=1)
+    ref, amo, _ = orc.step(P, U, origin, h, g)
+    assert np.all(np.isfinite(dU))
+    assert max_rel_error(dU, ref, h.max()) <= 1e-12
+    assert np.allclose(am, amo, rtol=1e-14, atol=0)
+    # steepening acts on this data: the unsteepened oracle differs
+    ref0, _, _ = orc.step(orc.OracleParams(gamma=GAMMA, omega=omega), U, origin, h, g)
+    assert max_rel_error(ref0, ref, h.max()) > 1e-3
+
+
+def test_mixed_contact_step_within_budget(H, orc):
+    from oracle.compare import field_scales, mixed_budget
+    n = 96
+    U = contact_subgrids(n, 71, exact=True)
+    rng = np.random.default_rng(72)
+    origin = rng.uniform(-1, 1, (n, 3))
+    h = rng.uniform(0.01, 0.1, n)
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, contact=1)
+    dU, am = gpu_step(H, ctx, U, origin, h)
+    assert H.hydro_status(ctx) == 0
+    P = orc.OracleParams(gamma=GAMMA, contact=1)
+    ref, amo, _, faces = orc.step(P, U, origin, h, faces=True)
+    pert, _, _ = orc.step(P, U.astype(np.float32).astype(np.float64), origin, h)
+    budget, _ = mixed_budget(ref, pert, faces, h, U, amo)
+    sc = field_scales(ref, h.max())[None, :, None, None, None]
+    err = (np.abs(dU - ref) / sc).max(axis=(0, 2, 3, 4))
+    assert np.all(np.isfinite(dU))
+    assert np.all(err <= budget), (err, budget)
+    assert np.allclose(am, amo, rtol=1e-6, atol=0)
+    ref0, _, _ = orc.step(orc.OracleParams(gamma=GAMMA), U, origin, h)
+    d0 = (np.abs(ref0 - ref) / sc).max(axis=(0, 2, 3, 4))
+    assert d0[0] > 100 * budget[0] and d0[9] > 100 * budget[9], (d0, budget)
+
+
+def _advected_contact(nx=32):
+    x = np.arange(nx)
+    rho_x = np.where((x >= nx // 4) & (x < 3 * nx // 4), 1.0, 0.5)
+    sh = (8, 8, nx)
+    rho = np.broadcast_to(rho_x, sh)
+    v = np.stack([np.full(sh, 1.0), np.full(sh, 0.1), np.zeros(sh)])
+    Ug = W.conserved_from_primitive(rho, v, np.ones(sh), GAMMA, species=0.3 * rho)
+    return Ug, 1.0 / nx
+
+
+def test_contact_rk3_steps_match_oracle(H):
+    from oracle import core, mesh
+    from oracle.compare import max_rel_error
+    from paper_2107_10987_gb300.uniform import UniformRun
+    Ug, h = _advected_contact()
+    nbx = Ug.shape[3] // 8
+    sub = np.stack([Ug[:, :, :, 8 * k:8 * k + 8] for k in range(nbx)])
+    origin = np.array([[8 * k * h, 0.0, 0.0] for k in range(nbx)])
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=1)
+    run = UniformRun(ctx, sub, origin, h, (nbx, 1, 1), H.HYDRO_BC_PERIODIC)
+    ref = mesh.BoxRun(core.OracleParams(gamma=GAMMA, contact=1), Ug, h, (0.0, 0.0, 0.0), "periodic")
+    for _ in range(3):
+        run.step()
+        dt_ref = ref.step(0.4)
+        assert run.last_dt() == pytest.approx(dt_ref, rel=1e-14)
+    got = run.interior().cpu().numpy()
+    want = np.stack([ref.U[:, :, :, 8 * k:8 * k + 8] for k in range(nbx)])
+    assert max_rel_error(got, want, h) <= 1e-12
+    assert H.hydro_status(ctx) == 0
+    run.close()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_contact_conserves_on_periodic_mesh(H, mixed):
+    from oracle import mesh
+    rng = np.random.default_rng(81)
+    n = 16
+    sh = (n, n, n)
+    # three levels: with two, every cell equals one of its line neighbours and
+    # the extremum flattening takes both values to the cell's, steepened or not
+    rho = rng.choice([1.0, 0.6, 0.3], size=sh)
+    v = rng.uniform(-0.3, 0.3, (3,) + sh)
+    Ug = W.conserved_from_primitive(rho, v, np.ones(sh), GAMMA, species=0.5 * rho)
+    h = 1.0 / n
+    U = torch.tensor(mesh.split(mesh.pad_box(Ug, 3, "periodic"), 8, 3), device="cuda")
+    o = torch.tensor(mesh.origins(2, 2, 2, 8, h, (0.0, 0.0, 0.0)), device="cuda")
+    hh = torch.full((8,), h, dtype=torch.float64, device="cuda")
+    out = {}
+    for contact in (0, 1):
+        ctx = H.Context(GAMMA, 0.0)
+        H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED if mixed else H.HYDRO_PREC_FP64, contact=contact)
+        dU = torch.empty((8, 10, 8, 8, 8), dtype=torch.float64, device="cuda")
+        am = torch.empty(8, dtype=torch.float64, device="cuda")
+        H.hydro_step(ctx, H.make_batch(U, o, hh), 0.0, dU, am)
+        torch.cuda.synchronize()
+        assert H.hydro_status(ctx) == 0
+        out[contact] = dU.cpu().numpy()
+    d = out[1]
+    tot = d.sum(axis=(0, 2, 3, 4))
+    scale = np.abs(d).sum(axis=(0, 2, 3, 4))
+    for k in (0, 1, 2, 3, 4, 5, 9):
+        assert abs(tot[k]) <= 1e-12 * scale[k], (k, tot[k], scale[k])
+    assert np.abs(out[1][:, 0] - out[0][:, 0]).max() > 1e-3 * np.abs(out[0][:, 0]).max()
+
+
+def test_contact_mode_checks(H):
+    import ctypes as C
+    from oracle import gate
+    from paper_2107_10987_gb300.uniform import UniformRun
+    ctx = H.Context(GAMMA, 0.0)
+    for bad in (2, -1):
+        with pytest.raises(H.HydroError):
+            H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=bad)
+    # the fused step does not steepen
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, contact=1)
+    U = contact_subgrids(8, 3)
+    o, h = W.uniform_mesh(2)
+    run = UniformRun(ctx, U, o, h, 2, H.HYDRO_BC_PERIODIC, fused=True)
+    assert H._lib().hydro_rk3_step(H._cp(ctx), C.byref(run.desc), 0, None) == H.HYDRO_EUNSUP
+    # nor together with the learned indicator
+    theta = torch.tensor(np.random.default_rng(5).normal(0, 0.3, gate.NPARAM).astype(np.float32), device="cuda")
+    H.hydro_set_indicator(ctx, theta, 0.5)
+    with pytest.raises(H.HydroError):
+        gpu_step(H, ctx, U, np.asarray(o), np.full(8, h))
+    H.hydro_set_indicator(ctx, None)
+    dU, _ = gpu_step(H, ctx, U, np.asarray(o), np.full(8, h))
+    assert np.all(np.isfinite(dU))
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    run.close()
+
+
+def test_contact_step_cost(H):
+    """Step kernel time with and without steepening on 512 sub-grids of the
+    Sedov mesh (CUDA events, after warm-up; printed for the record)."""
+    Ug, h, lo = W.sedov_box(64, GAMMA)
+    from oracle import mesh
+    U = torch.tensor(mesh.split(mesh.pad_box(Ug, 3, "outflow"), 8, 3), device="cuda")
+    o = torch.tensor(mesh.origins(8, 8, 8, 8, h, lo), device="cuda")
+    hh = torch.full((512,), h, dtype=torch.float64, device="cuda")
+    dU = torch.empty((512, 10, 8, 8, 8), dtype=torch.float64, device="cuda")
+    am = torch.empty(512, dtype=torch.float64, device="cuda")
+    B = H.make_batch(U, o, hh)
+    times = {}
+    for prec, name in ((H.HYDRO_PREC_FP64, "fp64"), (H.HYDRO_PREC_MIXED, "mixed")):
+        for contact in (0, 1):
+            ctx = H.Context(GAMMA, 0.0)
+            H.hydro_set_mode(ctx, prec, contact=contact)
+            for _ in range(3):
+                H.hydro_step(ctx, B, 0.0, dU, am)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(10):
+                H.hydro_step(ctx, B, 0.0, dU, am)
+            e1.record()
+            torch.cuda.synchronize()
+            times[name, contact] = e0.elapsed_time(e1) / 10
+            assert H.hydro_status(ctx) == 0
+    print("\ncontact steepening, step kernel ms on 512 sub-grids: " +
+          ", ".join(f"{k[0]} contact={k[1]}: {v:.3f}" for k, v in times.items()))
+    assert all(v > 0 for v in times.values())

@@ -5,7 +5,8 @@ option Sec. III-B names, from Colella & Woodward 1984), pinned (CPU only):
   * each condition of the detection on its own: an inflection is required,
     a jump below 1 % of the values is left alone, a shock (large pressure
     jump) is left alone, and eta is clamped to [0, 1];
-  * mirror symmetry and scale invariance of the line;
+  * mirror symmetry and scale invariance of the line; no change on lines of
+    two values (every cell is then an extremum and is flattened);
   * on smooth data (16 cells per wavelength) nothing changes, bit for bit;
   * behaviour: an advected density contact stays sharper, the species
     follow the density, and the Sod density error near the contact falls;
@@ -119,6 +120,22 @@ def test_mirror_and_scale(orc):
         assert _eta(orc, 8.0 * a, 0.25 * rho, 4.0 * p) == eta
         assert orc.ppm_line_eta(8.0 * a, eta) == (8.0 * qp, 8.0 * qm)
     assert seen > 300
+
+
+def test_two_level_lines_are_flattened_either_way(orc):
+    """On a line of two values every cell equals one of its neighbours, so
+    the cell is a local extremum of its interface values with or without the
+    blend, and the extremum fix-up takes both to the cell value: steepening
+    changes nothing there (it acts on intermediate values, as in a smeared
+    contact)."""
+    import itertools
+    for a in itertools.product((0.4, 1.0), repeat=5):
+        a = np.array(a)
+        eta = _eta(orc, a)
+        assert orc.ppm_line_eta(a, eta) == orc.ppm_line_eta(a, 0.0) == (a[2], a[2]), (a, eta)
+    # while a third value in the middle is steepened
+    a = np.array([0.4, 0.4, 0.7, 1.0, 1.0])
+    assert _eta(orc, a) == 1.0 and orc.ppm_line_eta(a, 1.0) == (1.0, 0.4)
 
 
 def _x_box(orc, rho_x, ny=8, p=1.0, vx=0.0, frac=0.3):
