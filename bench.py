@@ -190,18 +190,19 @@ def train_indicator(dev):
     return params, thr, ev
 
 
-def run_form(args, H, dev, precision, flush, indicator=None, fused=False):
+def run_form(args, H, dev, precision, flush, indicator=None, fused=False, contact=False):
     """Warm-up, then K timed RK3 steps of one precision form; returns timings
     and the final state.  Separate launches: the sequence hydro_rk3_step
     enqueues (per stage ghost fill, hydro_step, hydro_update; the first stage
     writes the second state buffer, so no copy of the step's initial state is
     made), issued entry point by entry point so that the step kernel can be
     timed alone.  fused: hydro_rk3_step with the descriptor's fused flag (one
-    persistent launch per time step, mixed precision)."""
+    persistent launch per time step, mixed precision).  contact: PPM contact
+    steepening on (hydro_mode_t.contact)."""
     import torch
     stream = torch.cuda.current_stream()
     ctx = H.Context(GAMMA, 0.0)
-    H.hydro_set_mode(ctx, precision, 0.4)
+    H.hydro_set_mode(ctx, precision, 0.4, contact=1 if contact else 0)
     if indicator is not None:
         H.hydro_set_indicator(ctx, indicator[0], indicator[1])
     Ua, origin, hv, _ = make_state(dev)
@@ -370,6 +371,29 @@ def amr_measure(args, H, dev, flush, precision, steps, indicator=None):
     out["status"] = H.hydro_status(ctx)
     run.close()
     ctx.close()
+    return out
+
+
+def contact_measure(args, H, dev, flush, res):
+    """PPM contact steepening (hydro_mode_t.contact = 1) on the same Sedov
+    mesh: the mixed and the FP64 RK3 step as separate launches (the fused
+    step does not steepen), each beside the same form without steepening
+    from this run (res: mixed_separate, fp64) when that was measured.
+    Values are this GPU's (the block runs on rank 0)."""
+    out = {"note": "separate launches (ghost fill, hydro_step, hydro_update per stage; dt); the step kernel "
+                   "steepens the density and species lines"}
+    for name, prec, plain in (("mixed", H.HYDRO_PREC_MIXED, "mixed_separate"), ("fp64", H.HYDRO_PREC_FP64, "fp64")):
+        r = run_form(args, H, dev, prec, flush, contact=True)
+        ent = {"value": CELLS * args.steps / r["t_dev"], "ms_per_step": 1e3 * r["t_dev"] / args.steps,
+               "graph_replay": CELLS * args.steps / r["t_graph"], "kernel_ms": 1e3 * r["kern_s"],
+               "device_status": r["status"]}
+        if plain in res:
+            p = res[plain]
+            ent["step_cost_vs_unsteepened"] = r["t_dev"] / p["t_dev"]
+            ent["kernel_cost_vs_unsteepened"] = r["kern_s"] / p["kern_s"]
+            ent["max_rel_density_diff_vs_unsteepened"] = ((r["rho"] - p["rho"]).abs().max().item() /
+                                                          p["rho"].abs().max().item())
+        out[name] = ent
     return out
 
 
@@ -613,6 +637,11 @@ def gpu_arm(args):
                                                                 max(2, args.steps // 5), indicator)
         if args.polytrope:
             line["rotating_polytrope"] = polytrope_measure(args, H, dev, flush, indicator)
+        if args.contact:
+            try:
+                line["contact_steepening"] = contact_measure(args, H, dev, flush, res)
+            except Exception as e:  # an optional block: it never costs the headline line
+                line["contact_steepening"] = {"error": f"{type(e).__name__}: {e}"}
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -699,6 +728,8 @@ def main():
     ap.add_argument("--no-amr", dest="amr", action="store_false", help="skip the batched adaptive-mesh measurement")
     ap.add_argument("--no-polytrope", dest="polytrope", action="store_false",
                     help="skip the rotating-polytrope measurement")
+    ap.add_argument("--no-contact", dest="contact", action="store_false",
+                    help="skip the contact-steepening measurement")
     ap.add_argument("--polytrope-nb", type=int, default=16,
                     help="sub-grids per axis of the polytrope accuracy runs (32: the full 256^3 mesh)")
     ap.add_argument("--polytrope-steps", type=int, default=100)
