@@ -312,7 +312,8 @@ typedef struct hydro_graph hydro_graph_t;
 
 /* Enqueue one time step on a stream: parity 0 advances a -> b, 1 advances
  * b -> a.  Ten launches (two with fused: a clear of the context's sync words
- * and the step).  Errors: EINVAL (inconsistent descriptor), EUNSUP (fused
+ * and the step).  Errors: EINVAL (inconsistent descriptor, or state
+ * buffers a.U and U_b that overlap), EUNSUP (fused
  * with an adaptive mesh, in FP64 or with contact steepening), ENOMEM. */
 int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
 

@@ -231,8 +231,13 @@ int hydro_autotune_step(hydro_ctx_t* c, const hydro_batch_t* B, double* dUdt, do
   int rc = hydro_ctx_prepare(c, B->n_sub);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HYDRO_ECUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ee = cudaEventCreate(&e0);
+  if (ee == cudaSuccess) ee = cudaEventCreate(&e1);
+  if (ee != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(ee, "hydro_autotune_step");
+  }
   // candidates: whole rounds of the batch over 1, 1.5 and 2 CTAs per SM
   // (mixed), or 1 CTA per SM and the smallest grid with the same number of
   // rounds (FP64); three timed launches each after one warm-up

@@ -51,9 +51,12 @@ static int rk3_enqueue(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, 
 }
 
 static bool desc_ok(const hydro_rk3_desc_t* d) {
-  if (!(d && d->a.U && d->U_b && d->a.origin && d->a.h && d->dUdt && d->amax && d->dt && d->a.n_sub > 0 &&
-        d->a.U != d->U_b))
+  if (!(d && d->a.U && d->U_b && d->a.origin && d->a.h && d->dUdt && d->amax && d->dt && d->a.n_sub > 0))
     return false;
+  // the two state buffers may not overlap: each stage reads one and writes the other
+  const size_t bytes = (size_t)d->a.n_sub * hyd::F * hyd::S3 * sizeof(double);
+  const char *a = (const char*)d->a.U, *b = (const char*)d->U_b;
+  if (a < b + bytes && b < a + bytes) return false;
   if (d->amr) return d->face_flux != nullptr;
   return (long)d->nbx * d->nby * d->nbz == d->a.n_sub;
 }
