@@ -99,3 +99,36 @@ def test_clock_sampler_summary_and_missing_tool():
         with bench.ClockSampler(0) as c2:
             pass
         assert c2.summary()["samples"] == 0
+
+
+def test_contact_block_reports_cost_against_unsteepened(monkeypatch):
+    """The contact-steepening block: each precision's RK3 step with
+    steepening on, as run_form reports it, against the same form without it
+    from the run; a form measured without its unsteepened partner reports
+    no ratio.  run_form itself (GPU) is replaced by a stand-in."""
+    import types
+
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    calls = []
+
+    def fake_run_form(args, H, dev, prec, flush, indicator=None, fused=False, contact=False):
+        calls.append((prec, fused, contact))
+        return {"t_dev": 0.030 if prec == 0 else 0.015, "t_graph": 0.014, "kern_s": 0.0005, "status": 0,
+                "rho": torch.full((4,), 1.1), "n": 512}
+
+    monkeypatch.setattr(bench, "run_form", fake_run_form)
+    H = types.SimpleNamespace(HYDRO_PREC_MIXED=1, HYDRO_PREC_FP64=0)
+    args = types.SimpleNamespace(steps=20)
+    res = {"mixed_separate": {"t_dev": 0.012, "kern_s": 0.0004, "rho": torch.ones(4)}}
+    out = bench.contact_measure(args, H, None, None, res)
+    assert calls == [(1, False, True), (0, False, True)]
+    m, f = out["mixed"], out["fp64"]
+    assert m["value"] == pytest.approx(bench.CELLS * 20 / 0.015)
+    assert m["ms_per_step"] == pytest.approx(0.75)
+    assert m["step_cost_vs_unsteepened"] == pytest.approx(1.25)
+    assert m["kernel_cost_vs_unsteepened"] == pytest.approx(1.25)
+    assert m["max_rel_density_diff_vs_unsteepened"] == pytest.approx(0.1, rel=1e-6)
+    assert "step_cost_vs_unsteepened" not in f and f["device_status"] == 0
+    json.dumps(out)
