@@ -1,6 +1,7 @@
 """Oracle of the adaptive-mesh plumbing between stages (test infrastructure).
 
-Octree leaves (level l, i, j, k) on [-1, 1]^3, 8^3 cells each; 2:1 balanced
+Octree leaves (level l, i, j, k) on [-1, 1]^3, N^3 cells each (N = 8 by
+default, 16 for the larger sub-grids of Sec. III-B); 2:1 balanced
 across faces, edges and vertices (octree of Sec. III-B).  Readings (the paper
 defers the mesh operations to the method paper):
 
@@ -30,12 +31,12 @@ import numpy as np
 
 from . import core
 
-N, G = 8, 3
-S = N + 2 * G
+G = 3
 
 
 class Octree:
-    def __init__(self, level, ijk):
+    def __init__(self, level, ijk, N: int = 8):
+        self.N = int(N)
         self.level = [int(v) for v in level]
         self.ijk = [tuple(int(v) for v in t) for t in np.asarray(ijk)]
         self.leaf = {(l,) + c: s for s, (l, c) in enumerate(zip(self.level, self.ijk))}
@@ -43,6 +44,7 @@ class Octree:
     def find(self, l, g):
         """Leaf of level l holding global cell g: ('leaf', s, local) or
         ('refined',) or ('coarse',)."""
+        N = self.N
         key = (l, g[0] // N, g[1] // N, g[2] // N)
         if key in self.leaf:
             return ("leaf", self.leaf[key], (g[0] % N, g[1] % N, g[2] % N))
@@ -60,6 +62,7 @@ def _clamp(g, n):
 
 def fill_ghosts(tree: Octree, U: np.ndarray) -> np.ndarray:
     """Both passes; U [n][F][S][S][S] (interiors valid) -> new array."""
+    N = tree.N
     U = U.copy()
     n = U.shape[0]
     todo = []
@@ -117,6 +120,7 @@ def fill_ghosts(tree: Octree, U: np.ndarray) -> np.ndarray:
 def flux_correct(tree: Octree, dU: np.ndarray, faces: np.ndarray, h) -> np.ndarray:
     """Coarse-fine correction of dU/dt [n][F][N][N][N] from the boundary-face
     sums [n][6][F+3][N][N] of every leaf."""
+    N = tree.N
     dU = dU.copy()
     nf = dU.shape[1]
     for s in range(dU.shape[0]):
@@ -173,6 +177,7 @@ def flux_correct(tree: Octree, dU: np.ndarray, faces: np.ndarray, h) -> np.ndarr
 def rk3_step(P: core.OracleParams, tree: Octree, U: np.ndarray, origin, h, cfl: float = 0.4):
     """One SSP-RK3 step of the whole mesh (ghost fill, step with face sums,
     correction, update, three times; dt from the first stage)."""
+    assert P.N == tree.N
     U0 = U.copy()
     Us = U
     dt = None

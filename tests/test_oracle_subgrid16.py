@@ -111,3 +111,73 @@ def test_sixteen_halves_the_face_overhead(orc):
         assert out[N][0] == pytest.approx(faces * 2 * 9 * 10, rel=1e-12)
     assert out[16][1] < out[8][1]
     assert out[16][1] / out[8][1] == pytest.approx((17 / 16) / (9 / 8), rel=0.02)
+
+
+def _octree_cut(level, ijk):
+    """The 8^3 cut of a 16^3-leaf octree: each leaf (l, i, j, k) becomes the
+    eight leaves (l+1, 2i+dx, 2j+dy, 2k+dz) of the same cell width; returns
+    their levels, indices and, per new leaf, (parent, octant offset in cells)."""
+    lv, ix, src = [], [], []
+    for s, (l, c) in enumerate(zip(level, ijk)):
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    lv.append(l + 1)
+                    ix.append((2 * c[0] + dx, 2 * c[1] + dy, 2 * c[2] + dz))
+                    src.append((s, (8 * dx, 8 * dy, 8 * dz)))
+    return np.array(lv), np.array(ix), src
+
+
+def _leaf_state(level, ijk, N):
+    """Interiors from a smooth field plus a pressure jump, padded with
+    unfilled ghosts: U [n][10][S][S][S], origins, widths."""
+    S = N + 6
+    n = len(level)
+    U = np.zeros((n, 10, S, S, S))
+    origin = np.zeros((n, 3))
+    h = np.zeros(n)
+    for s in range(n):
+        l = int(level[s])
+        w = 2.0 / 2 ** l
+        h[s] = w / N
+        origin[s] = -1.0 + np.asarray(ijk[s], dtype=np.float64) * w
+        X, Y, Z = W.cell_centres((N, N, N), tuple(origin[s]), h[s])
+        rho = 1.0 + 0.3 * np.sin(3 * X) * np.cos(2 * Y) + 0.2 * Z
+        p = np.where(X + 0.5 * Y < -0.3, 2.0, 1.0)
+        v = np.stack([0.2 * np.cos(Y), -0.1 * X, 0.05 * np.ones_like(X)])
+        z = np.stack([0.01 * Y, 0.0 * X, -0.01 * X])
+        U[s][:, 3:-3, 3:-3, 3:-3] = W.conserved_from_primitive(rho, v, p, GAMMA, z=z, species=0.3 * rho)
+    return U, origin, h
+
+
+@pytest.mark.slow
+def test_adaptive_sixteen_equals_eight(orc):
+    """An adaptive mesh of 16^3 leaves (seven at level 1, one octant refined
+    into eight at level 2) against its 8^3 cut: the two-pass ghost fill, the
+    coarse-fine flux correction and a whole RK3 step give the same bits."""
+    from oracle import amr
+    lev16 = [1] * 7 + [2] * 8
+    ijk16 = [c for c in np.ndindex(2, 2, 2) if c != (0, 0, 0)] + list(np.ndindex(2, 2, 2))
+    ijk16 = [(c[2], c[1], c[0]) for c in ijk16]
+    t16 = amr.Octree(lev16, ijk16, N=16)
+    U16, o16, h16 = _leaf_state(lev16, ijk16, 16)
+    lev8, ijk8, src = _octree_cut(lev16, ijk16)
+    t8 = amr.Octree(lev8, ijk8, N=8)
+    U8, o8, h8 = _leaf_state(lev8, ijk8, 8)
+    # the cut's interiors are the parents' octants, bit for bit
+    for s, (p, (ox, oy, oz)) in enumerate(src):
+        want = U16[p][:, 3 + oz:11 + oz, 3 + oy:11 + oy, 3 + ox:11 + ox]
+        assert np.array_equal(U8[s][:, 3:-3, 3:-3, 3:-3], want)
+    out = {}
+    for name, tree, U, o, h, N in (("16", t16, U16, o16, h16, 16), ("8", t8, U8, o8, h8, 8)):
+        P = orc.OracleParams(gamma=GAMMA, N=N)
+        Un, dt = amr.rk3_step(P, tree, amr.fill_ghosts(tree, U), o, h)
+        out[name] = (Un, dt)
+    assert out["16"][1] == out["8"][1]
+    U16n, U8n = out["16"][0], out["8"][0]
+    for s, (p, (ox, oy, oz)) in enumerate(src):
+        a = U8n[s][:, 3:-3, 3:-3, 3:-3]
+        b = U16n[p][:, 3 + oz:11 + oz, 3 + oy:11 + oy, 3 + ox:11 + ox]
+        assert np.array_equal(a.view(np.int64), b.view(np.int64)), s
+    # the step did something at the coarse-fine faces: the state moved
+    assert np.abs(U16n[:, 0, 3:-3, 3:-3, 3:-3] - U16[:, 0, 3:-3, 3:-3, 3:-3]).max() > 1e-3
