@@ -131,6 +131,35 @@ def random_subgrids(n_sub: int, seed: int, gamma: float = 5.0 / 3.0, N: int = 8,
     return out
 
 
+def contact_subgrids(n_sub: int, seed: int, gamma: float = 5.0 / 3.0, exact: bool = False, N: int = 8, G: int = 3):
+    """Ghost-padded sub-grids [n_sub][NF][S][S][S] full of density contacts
+    (the data PPM contact steepening acts on).  exact=False: two density
+    levels (1 and 0.3) with 5 % noise, pressure 1 +- 2 %, species fraction
+    0.4-0.6, and every fourth sub-grid with a pressure jump (1 to 10) across
+    a plane, so that the contact test also meets shocks.  exact=True: density
+    levels 1, 1/2 and 1/4, pressure exactly 1, species exactly half the
+    density (values exact in FP32).  Velocities |v_i| <= 0.3, small spin."""
+    rng = np.random.default_rng(seed)
+    S = N + 2 * G
+    sh = (S, S, S)
+    out = np.empty((n_sub, NF) + sh)
+    for i in range(n_sub):
+        if exact:
+            rho = rng.choice([1.0, 0.5, 0.25], size=sh)
+            p = np.ones(sh)
+            frac = np.full(sh, 0.5)
+        else:
+            rho = np.where(rng.random(sh) < 0.5, 1.0, 0.3) * rng.uniform(0.95, 1.05, sh)
+            p = rng.uniform(0.98, 1.02, sh)
+            if i % 4 == 3:
+                p = np.where(np.arange(S)[None, None, :] < S // 2, 10.0, 1.0) * p
+            frac = rng.uniform(0.4, 0.6, sh)
+        v = rng.uniform(-0.3, 0.3, (3,) + sh)
+        z = rng.uniform(-0.01, 0.01, (3,) + sh)
+        out[i] = conserved_from_primitive(rho, v, p, gamma, z=z, species=frac * rho)
+    return out
+
+
 def uniform_mesh(nb: int, N: int = 8, L: float = 2.0):
     """Uniform octree level: nb^3 sub-grids of N^3 on [-L/2, L/2]^3.
     Returns (origins [n_sub][3], h); sub-grid s = (kz*nb + ky)*nb + kx."""

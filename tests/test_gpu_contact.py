@@ -26,7 +26,6 @@ from paper_2107_10987_gb300 import workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 GAMMA = 5.0 / 3.0
-S = 14
 
 
 @pytest.fixture(scope="module")
@@ -44,29 +43,7 @@ def orc(oracle_mod):
 
 
 def contact_subgrids(n, seed, exact=False):
-    """Padded sub-grids [n][10][S][S][S] full of density contacts.
-    exact=False: two density levels with 5 % noise, pressure 1 +- 2 %, and
-    every fourth sub-grid with a pressure jump (1 to 10) across a plane, so
-    that the contact test also refuses lines.  exact=True: density levels 1,
-    1/2 and 1/4, pressure exactly 1, species exactly half the density."""
-    rng = np.random.default_rng(seed)
-    sh = (S, S, S)
-    out = np.empty((n, 10) + sh)
-    for i in range(n):
-        if exact:
-            rho = rng.choice([1.0, 0.5, 0.25], size=sh)
-            p = np.ones(sh)
-            frac = np.full(sh, 0.5)
-        else:
-            rho = np.where(rng.random(sh) < 0.5, 1.0, 0.3) * rng.uniform(0.95, 1.05, sh)
-            p = rng.uniform(0.98, 1.02, sh)
-            if i % 4 == 3:
-                p = np.where(np.arange(S)[None, None, :] < S // 2, 10.0, 1.0) * p
-            frac = rng.uniform(0.4, 0.6, sh)
-        v = rng.uniform(-0.3, 0.3, (3,) + sh)
-        z = rng.uniform(-0.01, 0.01, (3,) + sh)
-        out[i] = W.conserved_from_primitive(rho, v, p, GAMMA, z=z, species=frac * rho)
-    return out
+    return W.contact_subgrids(n, seed, GAMMA, exact=exact)
 
 
 def gpu_step(H, ctx, U, origin, h, g=None):

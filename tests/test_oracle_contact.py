@@ -245,3 +245,28 @@ def test_conservation_and_cut_with_steepening(orc):
     diff = np.abs(rates[8, 1] - rates[8, 0]).max(axis=(1, 2, 3))
     assert diff[0] > 1e-3 * np.abs(rates[8, 0][0]).max()
     assert diff[9] > 1e-3 * np.abs(rates[8, 0][9]).max()
+
+
+def test_steepening_with_the_smoothness_mask(orc):
+    """With the learned indicator's mask: cells marked smooth take the
+    unlimited formula and are not steepened, the others are.  So an empty
+    mask gives the steepened step and a full mask the unsteepened masked
+    step, bit for bit."""
+    n = 6
+    U = W.contact_subgrids(n, 5, GAMMA)
+    rng = np.random.default_rng(6)
+    origin = rng.uniform(-1, 1, (n, 3))
+    h = rng.uniform(0.01, 0.1, n)
+    P1 = orc.OracleParams(gamma=GAMMA, contact=1)
+    P0 = orc.OracleParams(gamma=GAMMA)
+    none = np.zeros((n, 14, 14, 14), dtype=np.uint8)
+    full = np.ones((n, 14, 14, 14), dtype=np.uint8)
+    d1, a1, _ = orc.step(P1, U, origin, h)
+    m1, b1 = orc.step_masked(P1, U, origin, h, none)
+    assert np.array_equal(d1.view(np.int64), m1.view(np.int64)) and np.array_equal(a1, b1)
+    f1, _ = orc.step_masked(P1, U, origin, h, full)
+    f0, _ = orc.step_masked(P0, U, origin, h, full)
+    assert np.array_equal(f1.view(np.int64), f0.view(np.int64))
+    # and steepening does act where the mask is empty
+    d0, _, _ = orc.step(P0, U, origin, h)
+    assert np.abs(d1 - d0).max() > 1e-3 * np.abs(d0).max()
