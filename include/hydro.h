@@ -4,8 +4,9 @@
  * The library evaluates, for every leaf sub-grid of an adaptive octree, the
  * per-sub-grid step of the fully three-dimensional reconstruction scheme of
  * Octo-Tiger's hydro module (arXiv 2107.10987, Sec. III-B): PPM reconstruction
- * (Colella & Woodward 1984) along the 13 lines through cell centres to the 26
- * face, edge and vertex points of each cell, the Kurganov-Tadmor (2000)
+ * (Colella & Woodward 1984, with its optional contact steepening) along the
+ * 13 lines through cell centres to the 26 face, edge and vertex points of
+ * each cell, the Kurganov-Tadmor (2000)
  * central flux at the 9 points of every face, the Newton-Cotes (Simpson)
  * face sum, the flux divergence, rotating-frame and spin-torque sources
  * (rotating frame: Sec. I), and the maximum signal speed for the CFL time
