@@ -8,7 +8,9 @@ a wrong sign, a transposed index or direction) fails at least one of them:
   * conservation (linear, angular) -> flux sharing, face signs, the spin torque
   * permutation symmetry          -> axis-specific slips (p e_a, transverse order)
   * flux sign / consistency       -> the dissipation sign, the pressure terms
-  * 1-D reduction                 -> quadrature weights, the face sum
+  * 1-D reduction                 -> the face sum of a 1-D flow (weights summing to 1)
+  * transverse quadratic          -> the distribution of the face weights (Simpson,
+                                     exact to cubic order) on both transverse axes
   * RK3 polynomial                -> the stage coefficients
   * dual energy                   -> selection and resync thresholds
 The analytic solutions (Sod, Sedov) are in test_oracle_analytic.py.
@@ -348,3 +350,79 @@ def test_operation_counts_are_stable(orc):
     c = orc.count_ops(P(orc), U, np.zeros(3), 0.1)
     assert c["step"]["sqrt"] == 2 * 3 * 9 * N * N * (N + 1)  # one sqrt per side per point
     assert c["step"]["div"] == 3 * S ** 3 + 2 * 3 * 9 * N * N * (N + 1)
+
+
+@pytest.mark.parametrize("ax", [0, 1, 2])
+def test_face_quadrature_transverse_quadratic(orc, ax):
+    """The face sum of Sec. III-B ("Newtonian quadrature") on data that vary
+    quadratically along one axis ax only, f(x) = a + b x_ax + c x_ax^2, with a
+    uniform velocity normal to ax and a uniform pressure, seen on the faces
+    whose normal is one of the other two axes (ax is then transverse to
+    them).  No limiter acts, both sides of every quadrature point hold the
+    same state, and the three point values across a face along ax lie on
+    the quadratic g(s) = f(y_c + s) + c h^2 (1 - 4 s^2/h^2)/12 (the
+    closed-form reconstruction pinned above).  The face average of the
+    fluxes is then the exact mean of g and of its first moment over the
+    face, which a 3-point rule reproduces only with the Simpson weights
+    (exact to cubic order):
+        mean g        = f(y_c) + 5 c h^2 / 36,
+        mean s g(s)   = f'(y_c) h^2 / 12.
+    Weights (1,2,1)/4 give c h^2/6 and f' h^2/8; the centre alone c h^2/12
+    and 0; a weight table transposed between the two transverse axes, or
+    not summing to 1, fails the pressure and uniform terms."""
+    h = 0.05
+    origin = np.array([-0.35, 0.2, -0.1])
+    origin[ax] = 0.6  # every stored cell at x_ax > 0.45: f is monotone there
+    a0, b0, c0 = 1.0, 0.5, 2.0
+    idx = np.arange(S) - G
+    yc_all = origin[ax] + (idx + 0.5) * h
+    avg1 = a0 + b0 * yc_all + c0 * (yc_all ** 2 + h * h / 12.0)  # exact cell averages
+    shp = [1, 1, 1]
+    shp[2 - ax] = S  # array order is [z][y][x]
+    rho = np.broadcast_to(avg1.reshape(shp), (S, S, S))
+    vel = np.array([0.3, -0.45, 0.7])
+    vel[ax] = 0.0
+    p = 1.0
+    U = W.conserved_from_primitive(rho, np.stack([np.full((S, S, S), c) for c in vel]), np.full((S, S, S), p),
+                                   GAMMA, species=0.3 * rho)
+    dU, am, _, faces = orc.step(P(orc), U[None], origin, h, faces=True)
+    eps = p / (GAMMA - 1.0)
+    tau = eps ** (1.0 / GAMMA)
+    for a in range(3):
+        if a == ax:
+            continue
+        b = 1 if a == 0 else 0
+        cax = 1 if a == 2 else 2
+        ua = vel[a]
+        e_a = np.eye(3)[a]
+        e_ax = np.eye(3)[ax]
+        for side in (0, 1):
+            f = faces[0, 2 * a + side]  # [F+3][pc][pb]
+            for pc in range(N):
+                for pb in range(N):
+                    i_ax = pb if ax == b else pc
+                    y = origin[ax] + (i_ax + 0.5) * h
+                    mean_g = a0 + b0 * y + c0 * y * y + 5.0 * c0 * h * h / 36.0
+                    m1 = (b0 + 2.0 * c0 * y) * h * h / 12.0
+                    want = np.zeros(13)
+                    want[0] = ua * mean_g
+                    want[1:4] = ua * vel * mean_g
+                    want[1 + a] += p
+                    want[4] = ua * (eps + p + 0.5 * vel @ vel * mean_g)
+                    want[5] = ua * tau
+                    want[9] = 0.3 * ua * mean_g
+                    # torque about the adjacent interior cell: the mean of
+                    # (x_q - x_c) x F_s, lever (h/2) e_a (upper face, cell on
+                    # its left) or -(h/2) e_a (lower face) plus the offset in
+                    # the face; the pressure part has zero mean moment
+                    lever = 0.5 * h if side == 1 else -0.5 * h
+                    want[10:13] = ua * (lever * mean_g * np.cross(e_a, vel) + m1 * np.cross(e_ax, vel))
+                    got = f[:, pc, pb]
+                    sc = np.array([abs(want[0])] + [np.abs(want[1:4]).max()] * 3 + [abs(want[4]), abs(want[5])]
+                                  + [0.0] * 3 + [abs(want[9])] + [h * np.abs(want[1:4]).max()] * 3)
+                    sc[6:9] = 1.0  # no spin: its fluxes vanish
+                    assert np.all(np.abs(got - want) <= 1e-13 * sc), (a, side, pc, pb, got - want)
+    # the rates of this stationary, uniformly moving state: only the ax-faces
+    # (which see f vary along their normal) contribute; the faces pinned
+    # above cancel in pairs
+    assert np.all(np.isfinite(dU))
