@@ -91,9 +91,8 @@ typedef struct {
  * |dp|/min(p) over its two neighbours with K0 = 0.1, blends both interface
  * values with the neighbours' limited extrapolations by a weight in [0,1]
  * from its second differences, before the monotonicity fix-ups).  Not
- * available with the learned indicator (hydro_step: EUNSUP) or in the fused
- * RK3 step (EUNSUP).  Defaults: FP64, cfl 0.4, eta1 1e-3, eta2 0.1, 9
- * points, contact 0. */
+ * available together with the learned indicator (EUNSUP).  Defaults: FP64,
+ * cfl 0.4, eta1 1e-3, eta2 0.1, 9 points, contact 0. */
 typedef struct {
   int precision;   /* HYDRO_PREC_FP64 or HYDRO_PREC_MIXED */
   double cfl;
@@ -133,9 +132,9 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
  * semi-discrete operator does not depend on it (it is accepted for the
  * interface's sake and must be finite and >= 0).  dUdt and amax are written
  * completely.  Alignment: U, dUdt 16-byte aligned.  Precision follows the
- * context's mode: HYDRO_PREC_FP64 matches the FP64 oracle to 1e-12 (per-field
- * normalised error); HYDRO_PREC_MIXED to the FP32 error budget stated in the
- * tests (about 1e-6).
+ * context's mode: HYDRO_PREC_FP64 matches the FP64 oracle to 1e-12 (error of
+ * each field normalised by its largest value in the sub-grid); HYDRO_PREC_MIXED
+ * to the FP32 error budget stated in the tests (about 1e-6).
  * face_flux (nullable): the sub-grid boundary faces' sums for coarse-fine
  * flux correction, [n_sub][6][F+3][N][N]: face slot 2a (lower) / 2a+1
  * (upper) of axis a; per face cell [c][b] (b < c the transverse axes) the F
@@ -147,14 +146,49 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
 int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, double* face_flux,
                void* stream);
 
+/* Sub-grid decompositions of the step kernels (launch shape; the results do
+ * not depend on it, bit for bit):
+ *   HYDRO_DECOMP_ROWS    one thread per row of cells along each axis (192
+ *                        threads per sub-grid, two CTAs per SM in mixed
+ *                        precision); the edge lines of a cell are
+ *                        reconstructed in two axis sweeps and the vertex lines
+ *                        in three (27 line evaluations per cell).  The FP64
+ *                        kernels and the learned indicator use it; the
+ *                        default.
+ *   HYDRO_DECOMP_PLANES  mixed precision: the sub-grid swept plane by plane
+ *                        along z by 768 threads (one CTA per SM), each of the
+ *                        13 lines through a cell reconstructed once, the
+ *                        primitives in a ring of six planes staged from
+ *                        global memory one step ahead, the per-axis flux
+ *                        differences kept on chip.
+ *   HYDRO_DECOMP_AUTO    the autotuner's choice, else the default. */
+#define HYDRO_DECOMP_AUTO 0
+#define HYDRO_DECOMP_ROWS 1
+#define HYDRO_DECOMP_PLANES 2
+
 /* Autotuner of the step's launch shape for this batch size and the context's
- * precision: times hydro_step (one warm-up, three timed launches each) with
- * persistent grids of 1, 1.5 and 2 CTAs per SM where they fit, and the
- * smallest grid that keeps the number of rounds over the batch, and keeps
- * the fastest for later steps of this context (*slots_out, nullable).
- * Overwrites dUdt and amax; synchronises the stream.  Not in the paper. */
+ * precision: times hydro_step (one warm-up, three timed launches each) over
+ * the candidate decompositions and persistent grids -- the row sweep with 1,
+ * 1.5 and 2 CTAs per SM where they fit and the smallest grid that keeps the
+ * number of rounds over the batch; in mixed precision without the indicator
+ * also the plane sweep with 1 CTA per SM and its balanced grid -- and keeps
+ * the fastest for later steps of this context (*slots_out: its CTAs,
+ * nullable; hydro_get_launch gives both).  Overwrites dUdt and amax;
+ * synchronises the stream.  Not in the paper. */
 int hydro_autotune_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double* dUdt, double* amax, int* slots_out,
                         void* stream);
+
+/* Fix the launch shape of this context's steps in its current precision:
+ * the decomposition (HYDRO_DECOMP_*; mixed precision only, the FP64 kernels
+ * have rows alone) and the number of persistent CTAs of hydro_step (0: the
+ * decomposition's default, one or two per SM).  The fused RK3 step runs the
+ * decomposition with as many CTAs as can be resident.  Not in the paper.
+ * Errors: EINVAL (unknown decomposition, ctas < 0), EUNSUP (PLANES in FP64). */
+int hydro_set_launch(hydro_ctx_t* ctx, int decomposition, int ctas);
+
+/* The launch shape the context's next step will use in its current
+ * precision: *decomposition (ROWS or PLANES) and *ctas (either nullable). */
+int hydro_get_launch(const hydro_ctx_t* ctx, int* decomposition, int* ctas);
 
 /* SSP-RK3 stage update of the interior cells (ghosts are not touched):
  *   U_new <- alpha_k U0 + beta_k (U + dt dUdt), (alpha, beta) = (0,1), (3/4,1/4),
@@ -177,13 +211,6 @@ int hydro_update(hydro_ctx_t* ctx, const hydro_batch_t* B, const double* U0, con
 int hydro_dt(hydro_ctx_t* ctx, const double* amax, const double* h, int n_sub, double cfl, double* dt_out,
              void* stream);
 
-/* Ghost fill of a uniform mesh of nbx x nby x nbz sub-grids (sub-grid
- * s = (kz*nby + ky)*nbx + kx, all at one refinement level): every ghost cell
- * copies the cell of the same global position from the neighbouring
- * sub-grid's interior; at the domain boundary the position is wrapped
- * (HYDRO_BC_PERIODIC) or clamped to the nearest interior cell
- * (HYDRO_BC_OUTFLOW).  Ghost exchange between leaf sub-grids, Sec. IV-A.2.
- * Requires B->n_sub == nbx*nby*nbz.  Pure copies (bitwise). */
 /* Interior cells between a compact array and the batch's padded state.  The
  * compact layout holds only the N^3 interior cells of every sub-grid,
  * interior[n_sub][F][N][N][N] FP64 (x fastest; 40,960 bytes per sub-grid
@@ -203,9 +230,15 @@ int hydro_dt(hydro_ctx_t* ctx, const double* amax, const double* h, int n_sub, d
 int hydro_scatter_interior(hydro_ctx_t* ctx, const hydro_batch_t* B, const double* interior, void* stream);
 int hydro_gather_interior(hydro_ctx_t* ctx, const hydro_batch_t* B, double* interior, void* stream);
 
+/* Ghost fill of a uniform mesh of nbx x nby x nbz sub-grids (sub-grid
+ * s = (kz*nby + ky)*nbx + kx, all at one refinement level): every ghost cell
+ * copies the cell of the same global position from the neighbouring
+ * sub-grid's interior; at the domain boundary the position is wrapped
+ * (HYDRO_BC_PERIODIC) or clamped to the nearest interior cell
+ * (HYDRO_BC_OUTFLOW).  Ghost exchange between leaf sub-grids, Sec. IV-A.2.
+ * Requires B->n_sub == nbx*nby*nbz.  Pure copies (bitwise). */
 int hydro_fill_ghosts_uniform(hydro_ctx_t* ctx, const hydro_batch_t* B, int nbx, int nby, int nbz, int bc,
                               void* stream);
-
 
 /* Global conservation sums over the interior cells of the batch, FP64:
  * sums[k] = sum_s sum_cells U[s][k] h_s^3 for k < F, and
@@ -217,12 +250,15 @@ int hydro_conserved_sums(hydro_ctx_t* ctx, const hydro_batch_t* B, double* sums,
  * entry point exists for callers that cannot call cudaMalloc, such as a host
  * code that gives all device memory to its own pool allocator, or a time
  * loop that cannot afford the device-wide synchronisation an allocation may
- * cause.  It computes exactly what hydro_step computes (FP64 mode only), with
+ * cause.  It computes exactly what hydro_step computes (FP64 mode only, with
+ * the context's flux points, contact steepening and learned indicator), with
  * the same kernel, but takes its scratch from a fixed array compiled into
  * the library: HYDRO_STATIC_MAX_SUB slots of 159,744 bytes (30.7 MB), held by
  * every GPU that loads the library until the process exits.
  *   - B->n_sub above HYDRO_STATIC_MAX_SUB returns HYDRO_ERANGE (split the
- *     batch); n_sub == 0 is a no-op.  Other argument errors as hydro_step.
+ *     batch); n_sub == 0 is a no-op; a mixed-precision context returns
+ *     HYDRO_EUNSUP.  Other argument errors as hydro_step (EINVAL, and
+ *     EUNSUP for contact steepening with the indicator on).
  *   - status: optional device word (caller-owned); it is set to zero, then
  *     receives this call's HYDRO_ST_* bits.  NULL: the bits go to an internal
  *     word nobody reads.
@@ -300,7 +336,8 @@ typedef struct {
   /* Nonzero: the whole time step as one persistent launch (uniform mesh and
    * HYDRO_PREC_MIXED only; otherwise the step returns EUNSUP).  Ghost cells
    * are read from the neighbouring sub-grids' interiors instead of being
-   * filled, stages 1 and 2 apply their update inside the launch, and a
+   * filled (in the context's decomposition, hydro_set_launch), stages 1 and
+   * 2 apply their update inside the launch, and a
    * sub-grid's third stage starts as soon as its 27 neighbours have finished
    * their second (bounded waits; HYDRO_ST_TIMEOUT if one expires).  The
    * interiors of the new state and *dt equal the separate launches' bit for
@@ -314,8 +351,8 @@ typedef struct hydro_graph hydro_graph_t;
 /* Enqueue one time step on a stream: parity 0 advances a -> b, 1 advances
  * b -> a.  Ten launches (two with fused: a clear of the context's sync words
  * and the step).  Errors: EINVAL (inconsistent descriptor, or state
- * buffers a.U and U_b that overlap), EUNSUP (fused
- * with an adaptive mesh, in FP64 or with contact steepening), ENOMEM. */
+ * buffers a.U and U_b that overlap), EUNSUP (fused with an adaptive mesh or
+ * in FP64; contact steepening with the indicator), ENOMEM. */
 int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
 
 /* Capture the two directions of hydro_rk3_step once into CUDA graphs

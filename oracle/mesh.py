@@ -49,6 +49,14 @@ def join(sub: np.ndarray, nbx: int, nby: int, nbz: int) -> np.ndarray:
     return out
 
 
+def unjoin(Ug: np.ndarray, N: int) -> np.ndarray:
+    """[nf][nz][ny][nx] -> [n_sub][nf][N][N][N] (the inverse of join)."""
+    nf, nz, ny, nx = Ug.shape
+    nbz, nby, nbx = nz // N, ny // N, nx // N
+    v = Ug.reshape(nf, nbz, N, nby, N, nbx, N).transpose(1, 3, 5, 0, 2, 4, 6)
+    return np.ascontiguousarray(v.reshape(nbz * nby * nbx, nf, N, N, N))
+
+
 def interior(sub_padded: np.ndarray, G: int) -> np.ndarray:
     return sub_padded[:, :, G:-G, G:-G, G:-G]
 

@@ -11,7 +11,7 @@
 
 namespace hyd {
 cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st);
-cudaError_t launch_step_mixed(const StepArgs64& A, int grid, cudaStream_t st);
+cudaError_t launch_step_mixed(const StepArgs64& A, int grid, int planes, cudaStream_t st);
 cudaError_t prepare_step_fp64();
 cudaError_t prepare_step_mixed();
 cudaError_t launch_update(const double* U, double* Uout, const double* U0, const double* dUdt, double dt,
@@ -22,8 +22,8 @@ cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, i
 cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, cudaStream_t st);
 cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
                              int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
-                             cudaStream_t st);
-cudaError_t prepare_rk3_fused(int num_sms, int* max_grid);
+                             int planes, cudaStream_t st);
+cudaError_t prepare_rk3_fused(int num_sms, int planes, int* max_grid);
 size_t rk3_fused_sync_words(int n_sub);
 cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long limit_ns, cudaStream_t st);
 cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
@@ -63,11 +63,21 @@ static int ensure_buf(double** buf, size_t* have, size_t need, const char* what)
   return HYDRO_OK;
 }
 
+// The sub-grid decomposition a step of this context runs: the row sweep
+// unless the plane sweep was chosen (by hydro_set_launch or the autotuner;
+// mixed precision without the learned indicator only).
+static int eff_decomp(const hydro_ctx* c) {
+  if (c->mode.precision != HYDRO_PREC_MIXED || c->gate_on) return HYDRO_DECOMP_ROWS;
+  return c->decomp == HYDRO_DECOMP_PLANES ? HYDRO_DECOMP_PLANES : HYDRO_DECOMP_ROWS;
+}
+
 static int step_slots(const hydro_ctx* c, bool mixed) {
-  // persistent CTAs: one per SM for FP64 (219 KB of shared memory each), two
-  // per SM in mixed precision (110 KB each), unless the autotuner chose fewer
+  // persistent CTAs: one per SM for FP64 (219 KB of shared memory each) and
+  // for the plane sweep (190 KB, 672 threads), two per SM for the mixed row
+  // sweep (110 KB each), unless the autotuner or the caller chose another
   if (c->slots_tuned[mixed ? 1 : 0] > 0) return c->slots_tuned[mixed ? 1 : 0];
-  return mixed ? 2 * c->num_sms : c->num_sms;
+  if (!mixed || eff_decomp(c) == HYDRO_DECOMP_PLANES) return c->num_sms;
+  return 2 * c->num_sms;
 }
 
 static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, double* dUdt, double* amax,
@@ -106,13 +116,14 @@ int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
   rc = ensure_buf(&c->sync, &c->sync_bytes, (words * sizeof(unsigned) + 7) / 8 * 8, "cudaMalloc(fused sync words)");
   if (rc) return rc;
   int max_grid = 0;
-  cudaError_t e = hyd::prepare_rk3_fused(c->num_sms, &max_grid);
+  cudaError_t e = hyd::prepare_rk3_fused(c->num_sms, 0, &max_grid);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_ctx_prepare_fused");
   return HYDRO_OK;
 }
 
 int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st) {
-  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED || c->mode.contact) return HYDRO_EUNSUP;
+  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED) return HYDRO_EUNSUP;
+  if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;
   if (d->bc != HYDRO_BC_PERIODIC && d->bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
   if (!aligned16(d->a.U) || !aligned16(d->U_b) || !aligned16(d->dUdt)) return HYDRO_EINVAL;
   int rc = hydro_ctx_prepare_fused(c, d->a.n_sub);
@@ -126,7 +137,8 @@ int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity,
   const hyd::StepArgs64 S = step_args(c, &X, d->dUdt, d->amax, nullptr);
   const double cfl = d->cfl > 0.0 ? d->cfl : c->mode.cfl;
   cudaError_t e = hyd::launch_rk3_fused(S, Y, c->u2, d->dt, reinterpret_cast<unsigned*>(c->sync), d->nbx, d->nby,
-                                        d->nbz, d->bc, cfl, c->mode.de_eta2, c->gamma, c->num_sms, st);
+                                        d->nbz, d->bc, cfl, c->mode.de_eta2, c->gamma, c->num_sms,
+                                        eff_decomp(c) == HYDRO_DECOMP_PLANES, st);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_rk3_step (fused)");
   return HYDRO_OK;
 }
@@ -217,7 +229,7 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
   const hyd::StepArgs64 A = step_args(c, B, dUdt, amax, face_flux);
-  cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, (cudaStream_t)stream)
+  cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, eff_decomp(c) == HYDRO_DECOMP_PLANES, (cudaStream_t)stream)
                         : hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
   return HYDRO_OK;
@@ -238,20 +250,39 @@ int hydro_autotune_step(hydro_ctx_t* c, const hydro_batch_t* B, double* dUdt, do
     if (e0) cudaEventDestroy(e0);
     return cuda_fail(ee, "hydro_autotune_step");
   }
-  // candidates: whole rounds of the batch over 1, 1.5 and 2 CTAs per SM
-  // (mixed), or 1 CTA per SM and the smallest grid with the same number of
-  // rounds (FP64); three timed launches each after one warm-up
-  int cand[4], nc = 0;
-  const int maxs = mixed ? 2 * c->num_sms : c->num_sms;
-  const int per[3] = {c->num_sms, (3 * c->num_sms) / 2, 2 * c->num_sms};
-  for (int i = 0; i < 3; ++i)
-    if (per[i] <= maxs) cand[nc++] = per[i];
-  const int rounds = (B->n_sub + maxs - 1) / maxs;
-  cand[nc++] = (B->n_sub + rounds - 1) / rounds;  // balanced: same rounds, fewer idle CTAs in the last one
+  // candidates (decomposition, persistent CTAs), three timed launches each
+  // after one warm-up:
+  //   row sweep: whole rounds of the batch over 1, 1.5 and 2 CTAs per SM
+  //     (mixed) or 1 (FP64), and the smallest grid with the same number of
+  //     rounds as the largest;
+  //   plane sweep (mixed without the indicator): 1 CTA per SM and the
+  //     smallest grid with the same number of rounds.
+  struct Cand {
+    int decomp, ctas;
+  };
+  Cand cand[8];
+  int nc = 0;
+  const bool planes_ok = mixed && !c->gate_on;
+  {
+    const int maxs = mixed ? 2 * c->num_sms : c->num_sms;
+    const int per[3] = {c->num_sms, (3 * c->num_sms) / 2, 2 * c->num_sms};
+    for (int i = 0; i < 3; ++i)
+      if (per[i] <= maxs) cand[nc++] = {HYDRO_DECOMP_ROWS, per[i]};
+    const int rounds = (B->n_sub + maxs - 1) / maxs;
+    cand[nc++] = {HYDRO_DECOMP_ROWS, (B->n_sub + rounds - 1) / rounds};
+  }
+  if (planes_ok) {
+    const int maxs = c->num_sms;
+    cand[nc++] = {HYDRO_DECOMP_PLANES, maxs};
+    const int rounds = (B->n_sub + maxs - 1) / maxs;
+    cand[nc++] = {HYDRO_DECOMP_PLANES, (B->n_sub + rounds - 1) / rounds};
+  }
+  const int decomp0 = c->decomp;
   float best = 1e30f;
-  int best_s = maxs;
+  Cand best_c = cand[0];
   for (int i = 0; i < nc && rc == HYDRO_OK; ++i) {
-    c->slots_tuned[idx] = cand[i];
+    c->decomp = cand[i].decomp;
+    c->slots_tuned[idx] = cand[i].ctas;
     rc = hydro_step(c, B, 0.0, dUdt, amax, nullptr, stream);
     if (rc) break;
     cudaEventRecord(e0, st);
@@ -262,14 +293,40 @@ int hydro_autotune_step(hydro_ctx_t* c, const hydro_batch_t* B, double* dUdt, do
     cudaEventElapsedTime(&ms, e0, e1);
     if (rc == HYDRO_OK && ms < best) {
       best = ms;
-      best_s = cand[i];
+      best_c = cand[i];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->slots_tuned[idx] = rc == HYDRO_OK ? best_s : 0;
+  if (rc == HYDRO_OK) {
+    c->decomp = mixed ? best_c.decomp : decomp0;
+    c->slots_tuned[idx] = best_c.ctas;
+  } else {
+    c->decomp = decomp0;
+    c->slots_tuned[idx] = 0;
+  }
   if (slots_out) *slots_out = c->slots_tuned[idx];
   return rc;
+}
+
+int hydro_set_launch(hydro_ctx_t* c, int decomposition, int ctas) {
+  if (!c || ctas < 0) return HYDRO_EINVAL;
+  if (decomposition != HYDRO_DECOMP_AUTO && decomposition != HYDRO_DECOMP_ROWS &&
+      decomposition != HYDRO_DECOMP_PLANES)
+    return HYDRO_EINVAL;
+  const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
+  if (!mixed && decomposition == HYDRO_DECOMP_PLANES) return HYDRO_EUNSUP;
+  if (mixed) c->decomp = decomposition;
+  c->slots_tuned[mixed ? 1 : 0] = ctas;
+  return HYDRO_OK;
+}
+
+int hydro_get_launch(const hydro_ctx_t* c, int* decomposition, int* ctas) {
+  if (!c) return HYDRO_EINVAL;
+  const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
+  if (decomposition) *decomposition = eff_decomp(c);
+  if (ctas) *ctas = step_slots(c, mixed);
+  return HYDRO_OK;
 }
 
 int hydro_update(hydro_ctx_t* c, const hydro_batch_t* B, const double* U0, const double* dUdt, double dt,

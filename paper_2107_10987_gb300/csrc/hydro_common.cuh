@@ -2,6 +2,8 @@
 // kernels of the GB300 hydro library (sm_103a).
 #pragma once
 #include <cstdint>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 namespace hyd {
@@ -167,6 +169,28 @@ __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// ---- host: once-per-device set-up -------------------------------------
+// Function attributes (the dynamic shared-memory opt-in) belong to each
+// device's context, so a set-up step runs once per device: bit d of *mask
+// records that fn() succeeded with device d current.  Serialised by one
+// process-wide mutex.
+inline std::mutex& device_setup_mutex() {
+  static std::mutex m;
+  return m;
+}
+template <class Fn>
+cudaError_t once_per_device(unsigned long long* mask, Fn fn) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(device_setup_mutex());
+  if (*mask & (1ull << dev)) return cudaSuccess;
+  e = fn();
+  if (e == cudaSuccess) *mask |= 1ull << dev;
+  return e;
 }
 
 }  // namespace hyd

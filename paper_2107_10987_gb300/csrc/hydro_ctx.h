@@ -12,7 +12,8 @@ struct hydro_ctx {
   hydro_mode_t mode;
   int device;
   int num_sms;
-  int slots_tuned[2];    // persistent CTAs chosen by hydro_autotune_step (0: default), [fp64, mixed]
+  int slots_tuned[2];    // persistent CTAs chosen by hydro_autotune_step or hydro_set_launch (0: default), [fp64, mixed]
+  int decomp;            // mixed-precision sub-grid decomposition, HYDRO_DECOMP_* (AUTO: planes)
   unsigned* status;      // device word
   double* scratch;       // step scratch
   size_t scratch_bytes;

@@ -263,13 +263,12 @@ int hydro_gate_data(hydro_ctx_t* c, const hydro_batch_t* B, float* X, uint8_t* y
   if (B->n_sub == 0) return HYDRO_OK;
   if (!B->U) return HYDRO_EINVAL;
   const size_t smem = (size_t)hyd::F * hyd::S3 * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(hyd::hydro_gate_data_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return HYDRO_ECUDA;
-    attr = true;
-  }
+  static unsigned long long attr = 0;
+  if (hyd::once_per_device(&attr, [smem] {
+        return cudaFuncSetAttribute(hyd::hydro_gate_data_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+      }) != cudaSuccess)
+    return HYDRO_ECUDA;
   hyd::GateDataArgs A{B->U, X, y, B->n_sub, c->mode.de_eta1, (float)c->gamma, (float)(c->gamma - 1.0)};
   const int grid = B->n_sub < 2 * c->num_sms ? B->n_sub : 2 * c->num_sms;
   hyd::hydro_gate_data_kernel<<<grid, 256, smem, (cudaStream_t)stream>>>(A);
@@ -295,13 +294,12 @@ int hydro_mlp_loss_grad(const float* params, const float* X, const float* y, int
   float* work = static_cast<float*>(work_v);
   if (!params || !X || !y || !grad || !work || n <= 0) return HYDRO_EINVAL;
   if (work_bytes < hydro_mlp_work_bytes(n)) return HYDRO_EINVAL;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(hyd::hydro_mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)hyd::mlp_grad_smem()) != cudaSuccess)
-      return HYDRO_ECUDA;
-    attr = true;
-  }
+  static unsigned long long attr = 0;
+  if (hyd::once_per_device(&attr, [] {
+        return cudaFuncSetAttribute(hyd::hydro_mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)hyd::mlp_grad_smem());
+      }) != cudaSuccess)
+    return HYDRO_ECUDA;
   const int tiles = (n + hyd::kTile - 1) / hyd::kTile;
   cudaStream_t st = (cudaStream_t)stream;
   hyd::hydro_mlp_grad_kernel<<<tiles, hyd::kTile, hyd::mlp_grad_smem(), st>>>(params, X, y, n, w1, w0, 1.f / n,

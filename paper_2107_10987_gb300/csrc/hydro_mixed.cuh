@@ -7,31 +7,45 @@
 
 namespace hyd {
 
+// ---- PPM on one line, FP32 ------------------------------------------------
+// Every operation below is written out as an explicitly rounded or fused
+// intrinsic, for two reasons: every kernel that inlines these functions then
+// computes the same bits (the compiler has no contraction left to choose),
+// and the line operator is exactly symmetric under reversal of the line --
+// ppm32 on (s4, s3, s2, s1, s0) returns (qm, qp) of ppm32 on (s0, ..., s4)
+// bit for bit -- so a line may be evaluated in either orientation.
+// (Negation, |x|, min, 2x and x/2 are exact; a + b, a - b, a*b and fma round
+// symmetrically.)
+
+// MC slope of two one-sided differences: 0 where they differ in sign, else
+// the sign of b times min(2|a|, 2|b|, |a + b|/2).
 __device__ __forceinline__ float slope32(float a, float b) {
-  const float m = fminf(fminf(2.f * fabsf(a), 2.f * fabsf(b)), 0.5f * fabsf(a + b));
-  return (a * b <= 0.f) ? 0.f : copysignf(m, b);
+  const float m = fminf(__fmul_rn(2.f, fminf(fabsf(a), fabsf(b))), __fmul_rn(0.5f, fabsf(__fadd_rn(a, b))));
+  return (__fmul_rn(a, b) <= 0.f) ? 0.f : copysignf(m, b);
 }
 
-// PPM on one line in FP32 (branch-free form of the same limiter).  kSteep:
-// the contact-steepening blend with weight eta before the fix-ups (as ppm64).
+// PPM on one line in FP32 (branch-free form of the limiter).  kSteep: the
+// contact-steepening blend with weight eta before the fix-ups (as ppm64).
 template <bool kSteep = false>
 __device__ __forceinline__ void ppm32(float s0, float s1, float s2, float s3, float s4, float& qp, float& qm,
                                       float eta = 0.f) {
   const float sixth = 1.f / 6.f;
-  const float D0 = slope32(s1 - s0, s2 - s1), D1 = slope32(s2 - s1, s3 - s2), D2 = slope32(s3 - s2, s4 - s3);
-  float p = 0.5f * (s2 + s3) - (D2 - D1) * sixth;
-  float m = 0.5f * (s1 + s2) - (D1 - D0) * sixth;
+  const float d0 = __fsub_rn(s1, s0), d1 = __fsub_rn(s2, s1), d2 = __fsub_rn(s3, s2), d3 = __fsub_rn(s4, s3);
+  const float D0 = slope32(d0, d1), D1 = slope32(d1, d2), D2 = slope32(d2, d3);
+  float p = __fmaf_rn(-sixth, __fsub_rn(D2, D1), __fmul_rn(0.5f, __fadd_rn(s2, s3)));
+  float m = __fmaf_rn(-sixth, __fsub_rn(D1, D0), __fmul_rn(0.5f, __fadd_rn(s1, s2)));
   if (kSteep) {
-    const float keep = 1.f - eta;
-    p = keep * p + eta * (s3 - 0.5f * D2);
-    m = keep * m + eta * (s1 + 0.5f * D0);
+    const float keep = __fsub_rn(1.f, eta);
+    p = __fmaf_rn(eta, __fmaf_rn(-0.5f, D2, s3), __fmul_rn(keep, p));
+    m = __fmaf_rn(eta, __fmaf_rn(0.5f, D0, s1), __fmul_rn(keep, m));
   }
-  const bool ext = (p - s2) * (s2 - m) <= 0.f;
-  const float dq = p - m;
-  const float lhs = dq * (s2 - 0.5f * (p + m));
-  const float rhs = dq * dq * sixth;
-  const float m2 = (lhs > rhs) ? 3.f * s2 - 2.f * p : m;
-  const float p2 = (lhs < -rhs) ? 3.f * s2 - 2.f * m : p;
+  const bool ext = __fmul_rn(__fsub_rn(p, s2), __fsub_rn(s2, m)) <= 0.f;
+  const float dq = __fsub_rn(p, m);
+  const float lhs = __fmul_rn(dq, __fmaf_rn(-0.5f, __fadd_rn(p, m), s2));
+  const float rhs = __fmul_rn(__fmul_rn(dq, dq), sixth);
+  const float s2x3 = __fmul_rn(3.f, s2);
+  const float m2 = (lhs > rhs) ? __fmaf_rn(-2.f, p, s2x3) : m;
+  const float p2 = (lhs < -rhs) ? __fmaf_rn(-2.f, m, s2x3) : p;
   qp = ext ? s2 : p2;
   qm = ext ? s2 : m2;
 }
@@ -44,13 +58,24 @@ __device__ __forceinline__ void line10f(const float* __restrict__ Q, int c, int 
   }
 }
 
-// Contact-steepening weight of one line in FP32 (contact_eta64's definition).
+// Contact-steepening weight of one line in FP32 (contact_eta64's definition;
+// symmetric under reversal of the line).
 __device__ __forceinline__ float contact_eta32(float a0, float a1, float a2, float a3, float a4) {
-  const float d2m = (a0 + a2) - 2.f * a1, d2p = (a2 + a4) - 2.f * a3;
-  const float jump = a3 - a1;
-  const float et = (d2m - d2p) / (6.f * jump);
-  const bool off = d2m * d2p > 0.f || fabsf(jump) <= 0.01f * fminf(fabsf(a3), fabsf(a1));
-  return off ? 0.f : fminf(fmaxf(20.f * (et - 0.05f), 0.f), 1.f);
+  const float d2m = __fsub_rn(__fadd_rn(a0, a2), __fmul_rn(2.f, a1)),
+              d2p = __fsub_rn(__fadd_rn(a2, a4), __fmul_rn(2.f, a3));
+  const float jump = __fsub_rn(a3, a1);
+  const float et = __fdiv_rn(__fsub_rn(d2m, d2p), __fmul_rn(6.f, jump));
+  const bool off = __fmul_rn(d2m, d2p) > 0.f || fabsf(jump) <= __fmul_rn(0.01f, fminf(fabsf(a3), fabsf(a1)));
+  return off ? 0.f : fminf(fmaxf(__fmul_rn(20.f, __fsub_rn(et, 0.05f)), 0.f), 1.f);
+}
+
+// The gas-dynamics contact test of a line over its two neighbours (density
+// r0, r1 and pressure p0, p1; gamma_k0 = gamma K0): the density jump is a
+// contact unless gamma K0 |drho|/min(rho) < |dp|/min(p).  Symmetric.
+__device__ __forceinline__ bool contact_line32(float r0, float r1, float p0, float p1, float gamma_k0) {
+  const float drho = __fdiv_rn(fabsf(__fsub_rn(r1, r0)), fminf(r0, r1));
+  const float dp = __fdiv_rn(fabsf(__fsub_rn(p1, p0)), fminf(p0, p1));
+  return !(__fmul_rn(gamma_k0, drho) < dp);
 }
 
 // line10f with contact steepening of the density and species lines (the
@@ -58,11 +83,9 @@ __device__ __forceinline__ float contact_eta32(float a0, float a1, float a2, flo
 // gamma K0, gm1 = gamma - 1).
 __device__ __forceinline__ void line10fc(const float* __restrict__ Q, int c, int st, float gamma_k0, float gm1,
                                          float qp[F], float qm[F]) {
-  const float r0 = Q[RHO * S3 + c - st], r1 = Q[RHO * S3 + c + st];
-  const float p0 = gm1 * Q[EGAS * S3 + c - st], p1 = gm1 * Q[EGAS * S3 + c + st];
-  const float drho = fabsf(r1 - r0) / fminf(r0, r1);
-  const float dp = fabsf(p1 - p0) / fminf(p0, p1);
-  const bool contact = !(gamma_k0 * drho < dp);
+  const bool contact = contact_line32(Q[RHO * S3 + c - st], Q[RHO * S3 + c + st],
+                                      __fmul_rn(gm1, Q[EGAS * S3 + c - st]), __fmul_rn(gm1, Q[EGAS * S3 + c + st]),
+                                      gamma_k0);
 #pragma unroll
   for (int k = 0; k < F; ++k) {
     const float* q = Q + k * S3 + c;
@@ -79,63 +102,111 @@ struct StepParamsF {
   float gamma, gm1, omega;
 };
 
-__device__ __forceinline__ void side32(const float q[F], int a, float xq, float yq, const StepParamsF& P, float U[F],
-                                       float Fl[F], float& spd) {
-  const float rho = q[RHO], vx = q[1], vy = q[2], vz = q[3], eps = q[4];
-  const float ek = (0.5f * rho) * (vx * vx + vy * vy + vz * vz);
-  const float E = eps + ek;
-  const float p = P.gm1 * eps;
-  const float c2 = __fdividef(P.gamma * p, rho);
-  const float c = c2 * rsqrtf(c2);
-  // explicit FMAs: both sides of a point share omega * yq and omega * xq, and
-  // the compiler's own choice between a shared product and two contractions
-  // may differ between kernel instances
-  const float ux = __fmaf_rn(P.omega, yq, vx), uy = __fmaf_rn(-P.omega, xq, vy);
-  const float un = (a == 0) ? ux : (a == 1) ? uy : vz;
-  const float va = (a == 0) ? vx : (a == 1) ? vy : vz;
-  U[RHO] = rho;
-  U[SX] = rho * vx;
-  U[SY] = rho * vy;
-  U[SZ] = rho * vz;
-  U[EGAS] = E;
-#pragma unroll
-  for (int k = TAU; k < F; ++k) U[k] = q[k];
-#pragma unroll
-  for (int k = 0; k < F; ++k) Fl[k] = U[k] * un;
-  Fl[SX + a] += p;
-  Fl[EGAS] += p * va;
-  spd = fabsf(un) + c;
+// ---- Kurganov-Tadmor flux at one quadrature point, FP32 --------------------
+// A side's state at the point: density, velocity, energy E = eps + rho|v|^2/2,
+// pressure p = (gamma-1) eps, sound speed, the rotating-frame advection
+// velocity normal to the face (u = v - omega z_hat x x_q) and |u_n| + c.
+struct Side32 {
+  float rho, vx, vy, vz, E, p, un, va, spd;
+};
+template <class Q>
+__device__ __forceinline__ Side32 side32(const Q& q, int a, float xq, float yq, const StepParamsF& P) {
+  Side32 s;
+  s.rho = q(RHO);
+  s.vx = q(SX);
+  s.vy = q(SY);
+  s.vz = q(SZ);
+  const float eps = q(EGAS);
+  const float v2 = __fmaf_rn(s.vz, s.vz, __fmaf_rn(s.vy, s.vy, __fmul_rn(s.vx, s.vx)));
+  s.E = __fmaf_rn(__fmul_rn(0.5f, s.rho), v2, eps);
+  s.p = __fmul_rn(P.gm1, eps);
+  const float c2 = __fdividef(__fmul_rn(P.gamma, s.p), s.rho);
+  const float c = __fmul_rn(c2, rsqrtf(c2));
+  const float ux = __fmaf_rn(P.omega, yq, s.vx), uy = __fmaf_rn(-P.omega, xq, s.vy);
+  s.un = (a == 0) ? ux : (a == 1) ? uy : s.vz;
+  s.va = (a == 0) ? s.vx : (a == 1) ? s.vy : s.vz;
+  s.spd = __fadd_rn(fabsf(s.un), c);
+  return s;
 }
 
-__device__ __forceinline__ void point32(const float qL[F], const float qR[F], int a, float xq, float yq, float w,
-                                        const float rl[3], const float rr[3], const StepParamsF& P, float fsum[F],
-                                        float tl[3], float tr[3], float& amax) {
-  float UL[F], FL[F], UR[F], FR[F], sL, sR;
-  side32(qL, a, xq, yq, P, UL, FL, sL);
-  side32(qR, a, xq, yq, P, UR, FR, sR);
-  const float aq = fmaxf(sL, sR);
+// Conserved component k of a side and its physical flux along axis a.
+template <class Q>
+__device__ __forceinline__ void cons_flux32(const Q& q, const Side32& s, int a, int k, float& u, float& f) {
+  if (k == RHO) {
+    u = s.rho;
+    f = __fmul_rn(u, s.un);
+  } else if (k <= SZ) {
+    u = __fmul_rn(s.rho, k == SX ? s.vx : (k == SY ? s.vy : s.vz));
+    f = (k - SX == a) ? __fmaf_rn(u, s.un, s.p) : __fmul_rn(u, s.un);
+  } else if (k == EGAS) {
+    u = s.E;
+    f = __fmaf_rn(u, s.un, __fmul_rn(s.p, s.va));
+  } else {
+    u = q(k);
+    f = __fmul_rn(u, s.un);
+  }
+}
+
+// One quadrature point of a face of axis a: F_q = (F_L + F_R)/2 - a_q (U_R -
+// U_L)/2 with a_q = max(|u_n| + c) of the two sides, added to the face
+// group's sums G[k] += w F_q[k], and its momentum-flux torques about the
+// left and right cell centres, TL += (w h/2) dL x F_s and TR += (w h/2) dR x
+// F_s, with the levers (h/2) dL and (h/2) dR, dL = d, dR = d - 2 e_a.
+// ql(k), qr(k): the reconstructed primitives of the two sides (read when
+// needed).  wh = w h/2.
+template <class QL, class QR>
+__device__ __forceinline__ void point32(const QL& ql, const QR& qr, int a, float xq, float yq, float w, float wh,
+                                        const float dL[3], const float dR[3], const StepParamsF& P, float G[F],
+                                        float TL[3], float TR[3], float& amax) {
+  const Side32 L = side32(ql, a, xq, yq, P);
+  const Side32 R = side32(qr, a, xq, yq, P);
+  const float aq = fmaxf(L.spd, R.spd);
   amax = fmaxf(amax, aq);
-  float Fq[F];
+  const float ha = __fmul_rn(0.5f, aq);
+  float fs[3];
 #pragma unroll
   for (int k = 0; k < F; ++k) {
-    Fq[k] = 0.5f * (FL[k] + FR[k]) - (0.5f * aq) * (UR[k] - UL[k]);
-    fsum[k] += w * Fq[k];
+    float uL, fL, uR, fR;
+    cons_flux32(ql, L, a, k, uL, fL);
+    cons_flux32(qr, R, a, k, uR, fR);
+    const float fq = __fmaf_rn(-ha, __fsub_rn(uR, uL), __fmul_rn(0.5f, __fadd_rn(fL, fR)));
+    G[k] = __fmaf_rn(w, fq, G[k]);
+    if (k >= SX && k <= SZ) fs[k - SX] = fq;
   }
-  const float fx = Fq[SX], fy = Fq[SY], fz = Fq[SZ];
-  tl[0] += w * (rl[1] * fz - rl[2] * fy);
-  tl[1] += w * (rl[2] * fx - rl[0] * fz);
-  tl[2] += w * (rl[0] * fy - rl[1] * fx);
-  tr[0] += w * (rr[1] * fz - rr[2] * fy);
-  tr[1] += w * (rr[2] * fx - rr[0] * fz);
-  tr[2] += w * (rr[0] * fy - rr[1] * fx);
+  const float cl[3] = {__fsub_rn(__fmul_rn(dL[1], fs[2]), __fmul_rn(dL[2], fs[1])),
+                       __fsub_rn(__fmul_rn(dL[2], fs[0]), __fmul_rn(dL[0], fs[2])),
+                       __fsub_rn(__fmul_rn(dL[0], fs[1]), __fmul_rn(dL[1], fs[0]))};
+  const float cr[3] = {__fsub_rn(__fmul_rn(dR[1], fs[2]), __fmul_rn(dR[2], fs[1])),
+                       __fsub_rn(__fmul_rn(dR[2], fs[0]), __fmul_rn(dR[0], fs[2])),
+                       __fsub_rn(__fmul_rn(dR[0], fs[1]), __fmul_rn(dR[1], fs[0]))};
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    TL[m] = __fmaf_rn(wh, cl[m], TL[m]);
+    TR[m] = __fmaf_rn(wh, cr[m], TR[m]);
+  }
+}
+
+// The 9 points of a face in their summation order: point n has offsets
+// (u1, u2) along the face's two transverse axes b < c,
+//   (1,1), (-1,-1), (1,0), (-1,0), (1,-1), (-1,1), (0,1), (0,-1), (0,0),
+// summed in three groups of three, (G0 + G1) + G2, each group a fused chain
+// from zero.  With one point per face (the old module) only the last, the
+// centre, with weight 1.  (u + 1 packed two bits per point.)
+__device__ __forceinline__ int face_u1(int n) { return ((86562 >> (2 * n)) & 3) - 1; }
+__device__ __forceinline__ int face_u2(int n) { return ((75858 >> (2 * n)) & 3) - 1; }
+// Newton-Cotes (Simpson) weight of a point, (1,4,1)x(1,4,1)/36, or 1 with
+// one point per face.
+__device__ __forceinline__ float face_w(int u1, int u2, int face_points) {
+  return face_points == 1 ? 1.f : (u1 == 0 && u2 == 0) ? (16.f / 36.f) : (u1 == 0 || u2 == 0) ? (4.f / 36.f) : (1.f / 36.f);
 }
 
 // Unlimited interface value towards +d (the 4-point formula the PPM
 // interface value reduces to when no limiter acts): used on cells the
 // learned indicator marks smooth.
 __device__ __forceinline__ void unlimited32(float s0, float s1, float s2, float s3, float s4, float& qp, float& qm) {
-  qp = (7.f / 12.f) * (s2 + s3) - (1.f / 12.f) * (s1 + s4);
-  qm = (7.f / 12.f) * (s1 + s2) - (1.f / 12.f) * (s0 + s3);
+  const float a = 7.f / 12.f, b = 1.f / 12.f;
+  qp = __fmaf_rn(a, __fadd_rn(s2, s3), -__fmul_rn(b, __fadd_rn(s1, s4)));
+  qm = __fmaf_rn(a, __fadd_rn(s1, s2), -__fmul_rn(b, __fadd_rn(s0, s3)));
 }
 
 // Lines of a cell the indicator marks smooth: the unlimited formula for all

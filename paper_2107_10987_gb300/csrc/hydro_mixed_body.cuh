@@ -26,8 +26,19 @@ namespace hyd {
 constexpr int kThreadsMx = NROW;  // 192
 
 // Dynamic shared memory of one CTA: FP32 primitives [F][S3], then two
-// [S3] byte arrays of smooth flags (learned indicator).
-constexpr size_t kMixedSmemBytes = (size_t)F * S3 * sizeof(float) + 2 * S3;
+// [S3] byte arrays of smooth flags (learned indicator), then the FP32 cell-
+// centre coordinates x_c, y_c of the reconstructed cells (sub_coords).
+constexpr size_t kMixedSmemBytes = (size_t)F * S3 * sizeof(float) + 2 * S3 + 2 * (N + 2) * sizeof(float);
+
+// The FP32 x and y cell-centre coordinates of the cells -1 .. N of a
+// sub-grid, x_c = fl(o + h (i + 1/2)) (an FP64 fma rounded once to FP32),
+// coord[a * (N + 2) + i + 1]: computed once per sub-grid instead of at every
+// quadrature point (the FP64 pipe is 1/64 of the FP32 rate).  Threads
+// 0 .. 2(N+2)-1 write; the caller's next barrier publishes them.
+__device__ __forceinline__ void sub_coords(float* coord, double hd, const double* origin) {
+  const int t = threadIdx.x;
+  if (t < 2 * (N + 2)) coord[t] = (float)fma(hd, (t % (N + 2) - 1) + 0.5, origin[t / (N + 2)]);
+}
 
 // This thread's row: axis a, transverse axes b < cx at positions pb, pc.
 // Warp w of the axis takes pb in [4w, 4w+4) x pc in [0, 8).  With the cell
@@ -52,6 +63,57 @@ __device__ __forceinline__ RowMap row_map(int tid) {
   return R;
 }
 
+// The end of one interior cell (x, y, z) of sub-grid s (compact index c,
+// padded index uc): dU/dt from its per-axis differences of face sums,
+// D_a[q] = Fbar_a(i+1/2) - Fbar_a(i-1/2) for the F fluxes and the torque
+// differences for q >= F (FP64), summed as (D_x + D_y) + D_z: s01(q) gives
+// D_x + D_y, d2(q) gives D_z.  Then the rotating-frame, spin and gravity
+// sources, and io.store.  Every operation is explicitly rounded or fused,
+// so that both sub-grid decompositions and every kernel give the same bits.
+template <class Io, class S01, class D2>
+__device__ __forceinline__ void finish_cell(const StepArgs64& A, const Io& io, const typename Io::Sub& sub, int s,
+                                            int x, int y, int z, const S01& s01, const D2& d2, double hd,
+                                            double inv_h, const double o[3]) {
+  const int c = (z * N + y) * N + x;
+  const int uc = ((z + G) * S + (y + G)) * S + (x + G);
+  const double om = A.P.omega;
+  double du[F];
+#pragma unroll
+  for (int k = 0; k < F; ++k) du[k] = -__dmul_rn(__dadd_rn(s01(k), d2(k)), inv_h);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) du[ZX + m] = __dsub_rn(du[ZX + m], __dmul_rn(__dadd_rn(s01(F + m), d2(F + m)), inv_h));
+  // The sources' products and sums are written as explicit FMAs and
+  // rounded operations, so that every kernel instance rounds them alike.
+  double uin[F];
+  io.own(sub, c, uc, uin);
+  const double sx = uin[SX], sy = uin[SY], sz = uin[SZ];
+  du[SX] = fma(om, sy, du[SX]);
+  du[SY] = fma(-om, sx, du[SY]);
+  du[ZX] = fma(om, uin[ZY], du[ZX]);
+  du[ZY] = fma(-om, uin[ZX], du[ZY]);
+  {
+    // spin source w(x_c) x s, w = -omega z_hat x x_c: removes the torque
+    // that the frame part s w_n of the momentum flux leaves in the face
+    // torques, so that sum (x_c x s + z)_z is conserved for omega != 0
+    const double xc = __dadd_rn(o[0], __dmul_rn(hd, x + 0.5));
+    const double yc = __dadd_rn(o[1], __dmul_rn(hd, y + 0.5));
+    const double wx = __dmul_rn(om, yc), wy = -__dmul_rn(om, xc);
+    du[ZX] = fma(wy, sz, du[ZX]);
+    du[ZY] = fma(-wx, sz, du[ZY]);
+    du[ZZ] = __dadd_rn(du[ZZ], fma(wx, sy, -__dmul_rn(wy, sx)));
+  }
+  if (A.g) {
+    const double* gs = A.g + (size_t)s * 3 * N3;
+    const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];
+    const double rho = uin[RHO];
+    du[SX] = fma(rho, gx, du[SX]);
+    du[SY] = fma(rho, gy, du[SY]);
+    du[SZ] = fma(rho, gz, du[SZ]);
+    du[EGAS] = __dadd_rn(du[EGAS], fma(sz, gz, fma(sy, gy, __dmul_rn(sx, gx))));
+  }
+  io.store(sub, c, uc, du, uin);
+}
+
 // One sub-grid s.  Io supplies the state and takes the results:
 //   typename Io::Sub io.begin(s)                    per-sub-grid context
 //   io.load(sub, c, u)        conserved state u[F] of padded cell c
@@ -66,10 +128,14 @@ template <bool kGate, bool kContact = false, class Io>
 __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io, int s, const RowMap& R, float* Qf,
                                               float* red, double* __restrict__ D) {
   uint8_t* smooth = reinterpret_cast<uint8_t*>(Qf + F * S3);
+  float* coord = reinterpret_cast<float*>(smooth + 2 * S3);
   const int tid = threadIdx.x;
   const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega};
   const int a = R.a, b = R.b, pb = R.pb, pc = R.pc, sa = R.sa, sb = R.sb, sc = R.sc;
   const typename Io::Sub sub = io.begin(s);
+  const double hd = A.h[s];
+  const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
+  sub_coords(coord, hd, o);
 
   // ---- 1-2. load the FP64 state, recover primitives, store FP32 ---------
   bool bad = false;
@@ -89,38 +155,42 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
     gate_phase<float, kThreadsMx>(Qf, PF.gm1, A.gate_w, A.gate_logit_thr, A.gate_zero_smooth, smooth, smooth + S3);
 
   // ---- 3. row sweep in FP32 --------------------------------------------
-  const double hd = A.h[s];
   const float h = (float)hd, half_h = 0.5f * h;
-  const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
   float amax = 0.f;
   float plus[9][F];
-  // the previous face's FP32 sums (their FP64 values are these converted: exact)
-  float fprev[F], trprev[3];
+  // the previous face's sums and right-cell torques, converted to FP64 once
+  // (exact conversions of the FP32 sums)
+  double fprev[F], trprev[3];
   const int c0 = ((axis_comp(2, a, b, 0, pb, pc) + G) * S + (axis_comp(1, a, b, 0, pb, pc) + G)) * S +
                  (axis_comp(0, a, b, 0, pb, pc) + G);
+  const int npt = A.P.face_points;
 #pragma unroll 1
   for (int j = -1; j <= N; ++j) {
     const int cj = c0 + j * sa;
-    float fsum[F], tl[3], tr[3];
+    // face j-1/2: completed groups S (fluxes, left and right torques) and the
+    // group being summed, G
+    float Sf[F], Stl[3], Str[3], Gf[F], Gtl[3], Gtr[3];
+    bool first = true;
 #pragma unroll
-    for (int k = 0; k < F; ++k) fsum[k] = 0.f;
-    tl[0] = tl[1] = tl[2] = 0.f;
-    tr[0] = tr[1] = tr[2] = 0.f;
+    for (int k = 0; k < F; ++k) Gf[k] = 0.f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) Gtl[m] = Gtr[m] = 0.f;
     // cell-centre coordinates of the left cell j - 1 (FP64 -> FP32 once; an
     // explicit FMA, so that every kernel instance rounds them alike)
-    const float xc = (float)fma(hd, axis_comp(0, a, b, j - 1, pb, pc) + 0.5, o[0]),
-                yc = (float)fma(hd, axis_comp(1, a, b, j - 1, pb, pc) + 0.5, o[1]);
+    const float xc = coord[axis_comp(0, a, b, j - 1, pb, pc) + 1],
+                yc = coord[(N + 2) + axis_comp(1, a, b, j - 1, pb, pc) + 1];
     // the 9 face points as 4 mirrored pairs and the centre (p = 4); with one
-    // flux point per face (the old module) only the centre
+    // flux point per face (the old module) only the centre.  Pair p's two
+    // points are points 2p and 2p + 1 of the face's summation order.
 #pragma unroll 1
-    for (int p = A.P.face_points == 1 ? 4 : 0; p <= 4; ++p) {
+    for (int p = npt == 1 ? 4 : 0; p <= 4; ++p) {
       const int t1 = p / 3 - 1, t2 = p % 3 - 1;
       float qpA[F], qmA[F], qpB[F], qmB[F];
       if (kGate && smooth[cj]) {
         line10u(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
         if (p != 4) line10u(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
       } else if (kContact) {
-        const float gk0 = PF.gamma * 0.1f;
+        const float gk0 = __fmul_rn(PF.gamma, 0.1f);
         line10fc(Qf, cj, sa + t1 * sb + t2 * sc, gk0, PF.gm1, qpA, qmA);
         if (p != 4) line10fc(Qf, cj, sa - t1 * sb - t2 * sc, gk0, PF.gm1, qpB, qmB);
       } else {
@@ -128,21 +198,35 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
         if (p != 4) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
       }
       if (j >= 0) {
-        // both points of the pair unrolled: their chains interleave
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
           if (p == 4 && side == 1) continue;
-          const int u1 = side ? t1 : -t1, u2 = side ? t2 : -t2;
+          const int n = 2 * p + side;  // the point's place in the summation order
+          const int u1 = face_u1(n), u2 = face_u2(n);
           const int pt = (u1 + 1) * 3 + (u2 + 1);
-          const int d0 = axis_comp(0, a, b, 1, u1, u2), d1 = axis_comp(1, a, b, 1, u1, u2),
-                    d2 = axis_comp(2, a, b, 1, u1, u2);
-          const float xq = xc + half_h * d0;
-          const float yq = yc + half_h * d1;
-          const float rl[3] = {half_h * d0, half_h * d1, half_h * d2};
-          const float rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
-          const float w = A.P.face_points == 1 ? 1.f
-                          : (u1 == 0 && u2 == 0) ? (16.f / 36.f) : (u1 == 0 || u2 == 0) ? (4.f / 36.f) : (1.f / 36.f);
-          point32(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, PF, fsum, tl, tr, amax);
+          const float dL[3] = {(float)axis_comp(0, a, b, 1, u1, u2), (float)axis_comp(1, a, b, 1, u1, u2),
+                               (float)axis_comp(2, a, b, 1, u1, u2)};
+          const float dR[3] = {a == 0 ? -1.f : dL[0], a == 1 ? -1.f : dL[1], a == 2 ? -1.f : dL[2]};
+          const float xq = __fmaf_rn(half_h, dL[0], xc), yq = __fmaf_rn(half_h, dL[1], yc);
+          const float w = face_w(u1, u2, npt);
+          const float* qr = side ? qmB : qmA;
+          point32([&](int k) { return plus[pt][k]; }, [&](int k) { return qr[k]; }, a, xq, yq, w,
+                  __fmul_rn(w, half_h), dL, dR, PF, Gf, Gtl, Gtr, amax);
+          if (n % 3 == 2) {
+            // a group is complete: S = G0, then (S + G1), then (S + G2)
+#pragma unroll
+            for (int k = 0; k < F; ++k) {
+              Sf[k] = first ? Gf[k] : __fadd_rn(Sf[k], Gf[k]);
+              Gf[k] = 0.f;
+            }
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+              Stl[m] = first ? Gtl[m] : __fadd_rn(Stl[m], Gtl[m]);
+              Str[m] = first ? Gtr[m] : __fadd_rn(Str[m], Gtr[m]);
+              Gtl[m] = Gtr[m] = 0.f;
+            }
+            first = false;
+          }
         }
       }
 #pragma unroll
@@ -156,29 +240,29 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
       // a-difference of cell j-1 is exact in FP64
       double fd[F], tld[3];
 #pragma unroll
-      for (int k = 0; k < F; ++k) fd[k] = (double)fsum[k];
+      for (int k = 0; k < F; ++k) fd[k] = (double)Sf[k];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) tld[m] = (double)tl[m];
+      for (int m = 0; m < 3; ++m) tld[m] = (double)Stl[m];
       if (j >= 1) {
         const int cell = (axis_comp(2, a, b, j - 1, pb, pc) * N + axis_comp(1, a, b, j - 1, pb, pc)) * N +
                          axis_comp(0, a, b, j - 1, pb, pc);
         double* Da = D + (size_t)a * DQ * N3 + cell;
 #pragma unroll
-        for (int k = 0; k < F; ++k) Da[k * N3] = fd[k] - (double)fprev[k];
+        for (int k = 0; k < F; ++k) Da[k * N3] = __dsub_rn(fd[k], fprev[k]);
 #pragma unroll
-        for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = tld[m] - (double)trprev[m];
+        for (int m = 0; m < 3; ++m) Da[(F + m) * N3] = __dsub_rn(tld[m], trprev[m]);
       }
 #pragma unroll
-      for (int k = 0; k < F; ++k) fprev[k] = fsum[k];
+      for (int k = 0; k < F; ++k) fprev[k] = fd[k];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) trprev[m] = tr[m];
+      for (int m = 0; m < 3; ++m) trprev[m] = (double)Str[m];
       if (A.face_flux && (j == 0 || j == N)) {
         // sub-grid boundary face: sums and the torque about the interior cell
         const int f = 2 * a + (j == N ? 1 : 0);
 #pragma unroll
         for (int k = 0; k < F; ++k) A.face_flux[face_index(s, f, k, pc, pb)] = fd[k];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = (j == N) ? tld[m] : (double)trprev[m];
+        for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = j == N ? tld[m] : trprev[m];
       }
     }
   }
@@ -189,52 +273,12 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
 
   // ---- 4. divergence + sources in FP64 --------------------------------
   const double inv_h = 1.0 / hd;
-  const double om = A.P.omega;
   for (int c = tid; c < N3; c += kThreadsMx) {
     const int x = c % N, y = (c / N) % N, z = c / (N * N);
-    const int uc = ((z + G) * S + (y + G)) * S + (x + G);
-    double du[F];
-#pragma unroll
-    for (int k = 0; k < F; ++k) {
-      const double div = (D[(0 * DQ + k) * N3 + c] + D[(1 * DQ + k) * N3 + c]) + D[(2 * DQ + k) * N3 + c];
-      du[k] = -(div * inv_h);
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const double tq =
-          (D[(0 * DQ + F + m) * N3 + c] + D[(1 * DQ + F + m) * N3 + c]) + D[(2 * DQ + F + m) * N3 + c];
-      du[ZX + m] = du[ZX + m] - tq * inv_h;
-    }
-    // The sources' products and sums are written as explicit FMAs and
-    // rounded operations, so that every kernel instance rounds them alike.
-    double uin[F];
-    io.own(sub, c, uc, uin);
-    const double sx = uin[SX], sy = uin[SY], sz = uin[SZ];
-    du[SX] = fma(om, sy, du[SX]);
-    du[SY] = fma(-om, sx, du[SY]);
-    du[ZX] = fma(om, uin[ZY], du[ZX]);
-    du[ZY] = fma(-om, uin[ZX], du[ZY]);
-    {
-      // spin source w(x_c) x s, w = -omega z_hat x x_c: removes the torque
-      // that the frame part s w_n of the momentum flux leaves in the face
-      // torques, so that sum (x_c x s + z)_z is conserved for omega != 0
-      const double xc = __dadd_rn(o[0], __dmul_rn(hd, x + 0.5));
-      const double yc = __dadd_rn(o[1], __dmul_rn(hd, y + 0.5));
-      const double wx = __dmul_rn(om, yc), wy = -__dmul_rn(om, xc);
-      du[ZX] = fma(wy, sz, du[ZX]);
-      du[ZY] = fma(-wx, sz, du[ZY]);
-      du[ZZ] = __dadd_rn(du[ZZ], fma(wx, sy, -__dmul_rn(wy, sx)));
-    }
-    if (A.g) {
-      const double* gs = A.g + (size_t)s * 3 * N3;
-      const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];
-      const double rho = uin[RHO];
-      du[SX] = fma(rho, gx, du[SX]);
-      du[SY] = fma(rho, gy, du[SY]);
-      du[SZ] = fma(rho, gz, du[SZ]);
-      du[EGAS] = __dadd_rn(du[EGAS], fma(sz, gz, fma(sy, gy, __dmul_rn(sx, gx))));
-    }
-    io.store(sub, c, uc, du, uin);
+    finish_cell(
+        A, io, sub, s, x, y, z,
+        [&](int q) { return __dadd_rn(D[(0 * DQ + q) * N3 + c], D[(1 * DQ + q) * N3 + c]); },
+        [&](int q) { return D[(2 * DQ + q) * N3 + c]; }, hd, inv_h, o);
   }
   if (tid == 0) {
     float m = red[0];

@@ -29,7 +29,7 @@
 // sub-grid body and rk3_cell with the same operands), so the interiors of Y
 // and dt equal its results bit for bit.  The ghost layers of Y are not
 // written, and dUdt holds the first stage's rates.
-#include "hydro_mixed_body.cuh"
+#include "hydro_mixed_planes.cuh"
 
 namespace hyd {
 
@@ -58,31 +58,35 @@ struct FusedIo {
   __device__ __forceinline__ Sub begin(int s) const {
     return Sub{s, s % A.nbx, (s / A.nbx) % A.nby, s / (A.nbx * A.nby)};
   }
-  // Stage input state of interior cell (os; oi compact, op padded index).
-  __device__ __forceinline__ void state(int os, int oi, int op, double u[F]) const {
+  // Stage input state of interior cell (os; oi compact, op padded index):
+  // fields f0 .. f0 + nf - 1 into u[0 .. nf-1].
+  __device__ __forceinline__ void state(int os, int oi, int op, double* u, int f0 = 0, int nf = F) const {
     if (stage == 0) {
       const double* __restrict__ x = A.S.U + (size_t)os * F * S3 + op;
 #pragma unroll
-      for (int k = 0; k < F; ++k) u[k] = __ldg(x + (size_t)k * S3);
+      for (int k = 0; k < nf; ++k) u[k] = __ldg(x + (size_t)(f0 + k) * S3);
     } else if (stage == 1) {
       const double* q = A.Y + (size_t)os * F * S3 + op;
 #pragma unroll
-      for (int k = 0; k < F; ++k) u[k] = __ldcg(q + (size_t)k * S3);
+      for (int k = 0; k < nf; ++k) u[k] = __ldcg(q + (size_t)(f0 + k) * S3);
     } else {
       const double* q = A.U2 + (size_t)os * F * N3 + oi;
 #pragma unroll
-      for (int k = 0; k < F; ++k) u[k] = __ldcg(q + (size_t)k * N3);
+      for (int k = 0; k < nf; ++k) u[k] = __ldcg(q + (size_t)(f0 + k) * N3);
     }
   }
-  __device__ __forceinline__ void load(const Sub& q, int c, double u[F]) const {
+  // Padded cell c of sub-grid q: its source sub-grid and cell under the
+  // uniform mesh's boundary map, fields f0 .. f0 + nf - 1.
+  __device__ __forceinline__ void load_fields(const Sub& q, int c, int f0, int nf, double* u) const {
     const int nx = A.nbx * N, ny = A.nby * N, nz = A.nbz * N;
     const int gx = bc_map(q.kx * N + c % S - G, nx, A.bc);
     const int gy = bc_map(q.ky * N + (c / S) % S - G, ny, A.bc);
     const int gz = bc_map(q.kz * N + c / (S * S) - G, nz, A.bc);
     const int os = ((gz >> 3) * A.nby + (gy >> 3)) * A.nbx + (gx >> 3);
     const int ix = gx & (N - 1), iy = gy & (N - 1), iz = gz & (N - 1);
-    state(os, (iz * N + iy) * N + ix, ((iz + G) * S + (iy + G)) * S + (ix + G), u);
+    state(os, (iz * N + iy) * N + ix, ((iz + G) * S + (iy + G)) * S + (ix + G), u, f0, nf);
   }
+  __device__ __forceinline__ void load(const Sub& q, int c, double u[F]) const { load_fields(q, c, 0, F, u); }
   __device__ __forceinline__ void own(const Sub& q, int c, int uc, double u[F]) const { state(q.s, c, uc, u); }
   __device__ __forceinline__ void store(const Sub& q, int c, int uc, const double du[F], const double u[F]) const {
     if (stage == 0) {
@@ -169,26 +173,57 @@ __device__ bool wait_neighbours(const FusedArgs& A, const unsigned* flags, int s
   return *sh_ok != 0;
 }
 
-template <bool kGate>
-__global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArgs A) {
-  extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [2][S3] smooth flags
-  __shared__ float red[kThreadsMx / 32];
-  __shared__ double dred[kThreadsMx / 32];
+// The sub-grid bodies the fused step can run, with their launch shapes: the
+// row sweep (two CTAs of kThreadsMx threads per SM, per-CTA scratch of flux
+// differences; with or without the learned indicator and contact
+// steepening) and the plane sweep (one CTA of kThreadsPl threads per SM).
+template <bool kGate, bool kContact>
+struct RowBody {
+  static constexpr int kThreads = kThreadsMx, kMinBlocks = 2;
+  static constexpr size_t kRed = (kMixedSmemBytes + 15) / 16 * 16;
+  static constexpr size_t kSmem = kRed + sizeof(float) * (kThreadsMx / 32);
+  RowMap R;
+  float* Qf;
+  float* red;
+  double* D;
+  __device__ RowBody(const StepArgs64& S, unsigned char* sm)
+      : R(row_map(threadIdx.x)), Qf(reinterpret_cast<float*>(sm)), red(reinterpret_cast<float*>(sm + kRed)),
+        D(S.scratch + (size_t)blockIdx.x * kScratchPerSub) {}
+  template <class Io>
+  __device__ __forceinline__ void run(const StepArgs64& S, const Io& io, int s) const {
+    mixed_subgrid<kGate, kContact>(S, io, s, R, Qf, red, D);
+  }
+};
+template <bool kContact>
+struct PlaneBody {
+  static constexpr int kThreads = kThreadsPl, kMinBlocks = 1;
+  static constexpr size_t kSmem = kPlaneSmemBytes;
+  unsigned char* sm;
+  __device__ PlaneBody(const StepArgs64&, unsigned char* p) : sm(p) {}
+  template <class Io>
+  __device__ __forceinline__ void run(const StepArgs64& S, const Io& io, int s) const {
+    mixed_subgrid_planes<kContact>(S, io, s, sm);
+  }
+};
+
+template <class Body>
+__global__ void __launch_bounds__(Body::kThreads, Body::kMinBlocks) hydro_rk3_fused_kernel(FusedArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double dred[Body::kThreads / 32];
   __shared__ int sh_unit, sh_ok;
   const int tid = threadIdx.x;
   const int n = A.S.n_sub;
-  double* __restrict__ D = A.S.scratch + (size_t)blockIdx.x * kScratchPerSub;
+  const Body body(A.S, smem_raw);
   unsigned* arrive = A.sync;
   unsigned* counter = A.sync + 1;
   unsigned* abort = A.sync + 2;
   unsigned* published = A.sync + kSyncHead;    // U2
   unsigned* published1 = published + n;        // U1
-  const RowMap R = row_map(tid);
 
   // ---- stage 0 --------------------------------------------------------
   {
     const FusedIo io{A, 0, 0.0};
-    for (int s = blockIdx.x; s < n; s += gridDim.x) mixed_subgrid<kGate>(A.S, io, s, R, Qf, red, D);
+    for (int s = blockIdx.x; s < n; s += gridDim.x) body.run(A.S, io, s);
   }
 
   // ---- grid-wide barrier, then dt (the reduction of hydro_dt_kernel) ----
@@ -205,14 +240,14 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
   __syncthreads();
   if (!sh_ok) return;
   double m = INFINITY;
-  for (int i = tid; i < n; i += kThreadsMx) m = fmin(m, A.S.h[i] / __ldcg(A.S.amax + i));
+  for (int i = tid; i < n; i += Body::kThreads) m = fmin(m, A.S.h[i] / __ldcg(A.S.amax + i));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) dred[tid >> 5] = m;
   __syncthreads();
   m = dred[0];
 #pragma unroll
-  for (int w = 1; w < kThreadsMx / 32; ++w) m = fmin(m, dred[w]);
+  for (int w = 1; w < Body::kThreads / 32; ++w) m = fmin(m, dred[w]);
   const double dt = A.cfl * m;
   if (blockIdx.x == 0 && tid == 0) *A.dt_out = dt;
 
@@ -221,7 +256,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
     const double* __restrict__ x = A.S.U + (size_t)s * F * S3;
     const double* r = A.S.dUdt + (size_t)s * F * N3;
     double* y = A.Y + (size_t)s * F * S3;
-    for (int c = tid; c < N3; c += kThreadsMx) {
+    for (int c = tid; c < N3; c += Body::kThreads) {
       const int uc = (((c >> 6) + G) * S + (((c >> 3) & (N - 1)) + G)) * S + ((c & (N - 1)) + G);
       double xv[F], rv[F], u1[F];
 #pragma unroll
@@ -253,7 +288,7 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_rk3_fused_kernel(FusedArg
     const int stage = u < n ? 1 : 2;
     const int s = stage == 1 ? u : u - n;
     if (!wait_neighbours(A, stage == 1 ? published1 : published, s, abort, &sh_ok)) break;
-    mixed_subgrid<kGate>(A.S, FusedIo{A, stage, dt}, s, R, Qf, red, D);  // ends with a barrier
+    body.run(A.S, FusedIo{A, stage, dt}, s);  // ends with a barrier
     if (stage == 1 && tid == 0) {
       __threadfence();
       st_release(published + s, 1u);
@@ -277,38 +312,74 @@ cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long li
 
 size_t rk3_fused_sync_words(int n_sub) { return (size_t)kSyncHead + 2 * (size_t)n_sub; }
 
-// Opt in to the dynamic shared memory; the most CTAs of the kernel that can
-// be resident at once (the cooperative launch's limit).
-cudaError_t prepare_rk3_fused(int num_sms, int* max_grid) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    int p0 = 0, p1 = 0;
-    cudaError_t e = cudaFuncSetAttribute(hydro_rk3_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kMixedSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(hydro_rk3_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kMixedSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, hydro_rk3_fused_kernel<false>, kThreadsMx,
-                                                        kMixedSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, hydro_rk3_fused_kernel<true>, kThreadsMx,
-                                                        kMixedSmemBytes);
-    if (e != cudaSuccess) return e;
-    per_sm = p0 < p1 ? p0 : p1;
-    if (per_sm > 2) per_sm = 2;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  }
-  *max_grid = per_sm * num_sms;
+// The fused kernel instances: [decomposition: 0 rows, 1 planes][variant:
+// 0 plain, 1 learned indicator (rows only), 2 contact steepening].
+template <class Body>
+static cudaError_t fused_attr(int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(hydro_rk3_fused_kernel<Body>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Body::kSmem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, hydro_rk3_fused_kernel<Body>, Body::kThreads,
+                                                      Body::kSmem);
+  return e;
+}
+
+// Opt in to the dynamic shared memory (once per device); the most CTAs of
+// the decomposition's kernels that can be resident at once (the cooperative
+// launch's limit).
+cudaError_t prepare_rk3_fused(int num_sms, int planes, int* max_grid) {
+  static unsigned long long done = 0;
+  static int per_sm_dev[64][2];
+  cudaError_t e = once_per_device(&done, [] {
+    int dev = 0, p[5] = {0, 0, 0, 0, 0};
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = fused_attr<RowBody<false, false>>(&p[0]);
+    if (r == cudaSuccess) r = fused_attr<RowBody<true, false>>(&p[1]);
+    if (r == cudaSuccess) r = fused_attr<RowBody<false, true>>(&p[2]);
+    if (r == cudaSuccess) r = fused_attr<PlaneBody<false>>(&p[3]);
+    if (r == cudaSuccess) r = fused_attr<PlaneBody<true>>(&p[4]);
+    if (r != cudaSuccess) return r;
+    int rows = p[0] < p[1] ? p[0] : p[1];
+    rows = rows < p[2] ? rows : p[2];
+    if (rows > 2) rows = 2;
+    int pl = p[3] < p[4] ? p[3] : p[4];
+    if (pl > 1) pl = 1;
+    if (rows < 1 || pl < 1) return cudaErrorInvalidConfiguration;
+    per_sm_dev[dev][0] = rows;
+    per_sm_dev[dev][1] = pl;
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  *max_grid = per_sm_dev[dev][planes ? 1 : 0] * num_sms;
   return cudaSuccess;
 }
 
+template <class Body>
+static cudaError_t launch_fused(const FusedArgs& A, int max_grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A.S.n_sub < max_grid ? A.S.n_sub : max_grid));
+  cfg.blockDim = dim3(Body::kThreads);
+  cfg.dynamicSmemBytes = Body::kSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, hydro_rk3_fused_kernel<Body>, A);
+}
+
 // sync must hold rk3_fused_sync_words(n_sub) words; it is cleared here.
+// planes: the plane-sweep body (no learned indicator); otherwise the row
+// sweep.
 cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
                              int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
-                             cudaStream_t st) {
+                             int planes, cudaStream_t st) {
   int max_grid = 0;
-  cudaError_t e = prepare_rk3_fused(num_sms, &max_grid);
+  cudaError_t e = prepare_rk3_fused(num_sms, planes, &max_grid);
   if (e != cudaSuccess) return e;
   FusedArgs A;
   A.S = S;
@@ -332,18 +403,11 @@ cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double*
   A.wait_ns = 1000000000ll + 20000ll * (long long)S.n_sub;
   e = cudaMemsetAsync(sync, 0, rk3_fused_sync_words(S.n_sub) * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(S.n_sub < max_grid ? S.n_sub : max_grid));
-  cfg.blockDim = dim3(kThreadsMx);
-  cfg.dynamicSmemBytes = kMixedSmemBytes;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (S.gate) return cudaLaunchKernelEx(&cfg, hydro_rk3_fused_kernel<true>, A);
-  return cudaLaunchKernelEx(&cfg, hydro_rk3_fused_kernel<false>, A);
+  if (planes && !S.gate)
+    return S.P.contact ? launch_fused<PlaneBody<true>>(A, max_grid, st) : launch_fused<PlaneBody<false>>(A, max_grid, st);
+  if (S.gate) return launch_fused<RowBody<true, false>>(A, max_grid, st);
+  if (S.P.contact) return launch_fused<RowBody<false, true>>(A, max_grid, st);
+  return launch_fused<RowBody<false, false>>(A, max_grid, st);
 }
 
 }  // namespace hyd

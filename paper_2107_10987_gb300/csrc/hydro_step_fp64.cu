@@ -472,11 +472,11 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
 
 size_t step_fp64_smem_bytes(bool gate = false) { return (size_t)F * S3 * sizeof(double) + (gate ? 2 * S3 : 0); }
 
-// Opt in to the kernel's dynamic shared memory once per process (no
+// Opt in to the kernel's dynamic shared memory once per device (no
 // allocation; call before any stream capture).
 cudaError_t prepare_step_fp64() {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static unsigned long long done = 0;
+  return once_per_device(&done, [] {
     cudaError_t e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)step_fp64_smem_bytes(false));
     if (e == cudaSuccess)
@@ -485,10 +485,8 @@ cudaError_t prepare_step_fp64() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)step_fp64_smem_bytes(false));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  return cudaSuccess;
+    return e;
+  });
 }
 
 cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {

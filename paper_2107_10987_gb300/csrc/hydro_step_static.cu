@@ -20,6 +20,7 @@
 // device code and looks the array's address up with cudaGetSymbolAddress
 // (the host-side name of the array is only a stand-in, not a device
 // address).  Make that first call before any stream capture.
+#include <cmath>
 #include <mutex>
 
 #include "hydro.h"
@@ -69,12 +70,13 @@ int addrs_for_current_device(DeviceAddrs* out) {
 extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, double* amax,
                                  uint32_t* status, void* stream) {
   if (!c || !B) return HYDRO_EINVAL;
-  if (B->n_sub < 0 || !(dt >= 0.0) || dt > 1e300) return HYDRO_EINVAL;
+  if (B->n_sub < 0 || !std::isfinite(dt) || dt < 0.0) return HYDRO_EINVAL;
   if (B->n_sub > HYDRO_STATIC_MAX_SUB) return HYDRO_ERANGE;
   if (B->n_sub == 0) return HYDRO_OK;
   if (!B->U || !B->origin || !B->h || !dUdt || !amax) return HYDRO_EINVAL;
   if ((((uintptr_t)B->U) & 15u) || (((uintptr_t)dUdt) & 15u)) return HYDRO_EINVAL;
   if (c->mode.precision != HYDRO_PREC_FP64) return HYDRO_EUNSUP;
+  if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;  // as hydro_step
   DeviceAddrs a;
   int rc = addrs_for_current_device(&a);
   if (rc) return rc;
@@ -99,10 +101,12 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.P.eta1 = c->mode.de_eta1;
   A.P.face_points = c->mode.flux_points == 1 ? 1 : 9;
   A.P.contact = c->mode.contact ? 1 : 0;
-  A.gate = 0;
-  A.gate_w = nullptr;
-  A.gate_logit_thr = 0.f;
-  A.gate_zero_smooth = 0;
+  // the learned indicator as the context has it (its parameters are the
+  // context's own device copy, made by hydro_set_indicator)
+  A.gate = c->gate_on ? 1 : 0;
+  A.gate_w = c->gate_w;
+  A.gate_logit_thr = (float)c->gate_logit_thr;
+  A.gate_zero_smooth = c->gate_zero_smooth;
   if (hyd::launch_step_fp64(A, B->n_sub, st) != cudaSuccess) return HYDRO_ECUDA;
   return HYDRO_OK;
 }

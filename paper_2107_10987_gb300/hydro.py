@@ -19,13 +19,15 @@ HYDRO_STATIC_MAX_SUB = 192
 HYDRO_ST_NONPHYS, HYDRO_ST_TIMEOUT = 0x1, 0x2
 HYDRO_PREC_FP64, HYDRO_PREC_MIXED = 0, 1
 HYDRO_BC_PERIODIC, HYDRO_BC_OUTFLOW = 0, 1
+HYDRO_DECOMP_AUTO, HYDRO_DECOMP_ROWS, HYDRO_DECOMP_PLANES = 0, 1, 2
 
 EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydro_dt", "hydro_fill_ghosts_uniform",
            "hydro_conserved_sums", "hydro_status", "hydro_strerror", "hydro_last_cuda_error", "hydro_destroy",
            "hydro_step_static", "hydro_rk3_step", "hydro_rk3_graph_create", "hydro_rk3_graph_launch",
            "hydro_rk3_graph_state", "hydro_rk3_graph_destroy", "hydro_gate_data", "hydro_mlp_forward",
            "hydro_mlp_work_bytes", "hydro_mlp_loss_grad", "hydro_mlp_adam", "hydro_set_indicator",
-           "hydro_fill_ghosts_amr", "hydro_flux_correct_amr", "hydro_autotune_step", "hydro_selftest_wait")
+           "hydro_fill_ghosts_amr", "hydro_flux_correct_amr", "hydro_autotune_step", "hydro_selftest_wait",
+           "hydro_set_launch", "hydro_get_launch")
 HYDRO_ST_MESH = 0x4
 HYDRO_GATE_NPARAM, HYDRO_GATE_NIN = 2849, 54
 
@@ -108,6 +110,8 @@ def _lib(load: bool = True):
         L.hydro_set_indicator.argtypes = [vp, vp, dp, vp]
         L.hydro_fill_ghosts_amr.argtypes = [vp, C.POINTER(Batch), vp, vp]
         L.hydro_autotune_step.argtypes = [vp, C.POINTER(Batch), vp, vp, C.POINTER(C.c_int), vp]
+        L.hydro_set_launch.argtypes = [vp, ip, ip]
+        L.hydro_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.hydro_flux_correct_amr.argtypes = [vp, C.POINTER(Batch), vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("hydro_strerror", "hydro_last_cuda_error", "hydro_destroy", "hydro_rk3_graph_destroy",
@@ -353,8 +357,21 @@ def hydro_flux_correct_amr(ctx, batch: Batch, mesh, face_flux, dUdt, stream=None
 
 
 def hydro_autotune_step(ctx, batch: Batch, dUdt, amax, stream=None) -> int:
-    """Pick and keep the fastest persistent grid for this batch; returns it."""
+    """Pick and keep the fastest decomposition and persistent grid for this batch;
+    returns the grid (hydro_get_launch gives both)."""
     out = C.c_int()
     _check(_lib().hydro_autotune_step(_cp(ctx), C.byref(batch), _ptr(dUdt), _ptr(amax), C.byref(out),
                                       _stream(stream)), "hydro_autotune_step")
     return out.value
+
+
+def hydro_set_launch(ctx, decomposition=HYDRO_DECOMP_AUTO, ctas=0):
+    """Fix the step's decomposition (HYDRO_DECOMP_*) and persistent CTAs (0: default)."""
+    _check(_lib().hydro_set_launch(_cp(ctx), int(decomposition), int(ctas)), "hydro_set_launch")
+
+
+def hydro_get_launch(ctx):
+    """(decomposition, ctas) of the context's next step."""
+    d, n = C.c_int(), C.c_int()
+    _check(_lib().hydro_get_launch(_cp(ctx), C.byref(d), C.byref(n)), "hydro_get_launch")
+    return d.value, n.value

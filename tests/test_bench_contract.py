@@ -113,19 +113,20 @@ def test_contact_block_reports_cost_against_unsteepened(monkeypatch):
     import bench
     calls = []
 
-    def fake_run_form(args, H, dev, prec, flush, indicator=None, fused=False, contact=False):
-        calls.append((prec, fused, contact))
+    def fake_run_form(args, H, dev, prec, flush, indicator=None, fused=False, contact=False, workload="polytrope",
+                      steps=None, state=None):
+        calls.append((prec, fused, contact, workload))
         return {"t_dev": 0.030 if prec == 0 else 0.015, "t_graph": 0.014, "kern_s": 0.0005, "status": 0,
-                "rho": torch.full((4,), 1.1), "n": 512}
+                "rho": torch.full((4,), 1.1), "n": 512, "cells": 512 * 512, "steps": 20}
 
     monkeypatch.setattr(bench, "run_form", fake_run_form)
     H = types.SimpleNamespace(HYDRO_PREC_MIXED=1, HYDRO_PREC_FP64=0)
     args = types.SimpleNamespace(steps=20)
-    res = {"mixed_separate": {"t_dev": 0.012, "kern_s": 0.0004, "rho": torch.ones(4)}}
+    res = {"mixed_separate": {"t_dev": 0.012, "kern_s": 0.0004, "rho": torch.ones(4), "steps": 20}}
     out = bench.contact_measure(args, H, None, None, res)
-    assert calls == [(1, False, True), (0, False, True)]
+    assert calls == [(1, False, True, "sedov"), (0, False, True, "sedov")]
     m, f = out["mixed"], out["fp64"]
-    assert m["value"] == pytest.approx(bench.CELLS * 20 / 0.015)
+    assert m["value"] == pytest.approx(512 * 512 * 20 / 0.015)
     assert m["ms_per_step"] == pytest.approx(0.75)
     assert m["step_cost_vs_unsteepened"] == pytest.approx(1.25)
     assert m["kernel_cost_vs_unsteepened"] == pytest.approx(1.25)

@@ -79,7 +79,7 @@ def test_single_level_octree_equals_uniform_ghost_fill(H, bc):
 
 def test_amr_faces_and_flux_correction(H, oracle_mod):
     from oracle import amr, core
-    from oracle.compare import max_rel_error
+    from oracle.compare import max_rel_error, rate_floor
     from paper_2107_10987_gb300.amr import AMRMesh
     lev, ijk, U, o, h = small()
     tree = amr.Octree(lev, ijk)
@@ -108,12 +108,12 @@ def test_amr_faces_and_flux_correction(H, oracle_mod):
     # and on the GPU's own step results
     H.hydro_flux_correct_amr(ctx, B, mesh, ff, dU)
     torch.cuda.synchronize()
-    assert max_rel_error(dU.cpu().numpy(), dUc, h.max()) <= 1e-12
+    assert max_rel_error(dU.cpu().numpy(), dUc, h, rate_floor(Uf, amo, h)) <= 1e-12
 
 
 def test_amr_rk3_steps_match_oracle_and_conserve(H, oracle_mod):
     from oracle import amr, core
-    from oracle.compare import max_rel_error
+    from oracle.compare import max_rel_error, state_floor
     from paper_2107_10987_gb300.amr import AMRRun
     lev, ijk, U, o, h = small()
     tree = amr.Octree(lev, ijk)
@@ -131,7 +131,8 @@ def test_amr_rk3_steps_match_oracle_and_conserve(H, oracle_mod):
     torch.cuda.synchronize()
     got = run.U.cpu().numpy()[:, :, 3:-3, 3:-3, 3:-3]
     assert run.dt.item() == pytest.approx(dto, rel=1e-14)
-    assert max_rel_error(got, Uo[:, :, 3:-3, 3:-3, 3:-3], h.max()) <= 1e-12
+    _, am0, _ = core.step(P, amr.fill_ghosts(tree, U), o, h)
+    assert max_rel_error(got, Uo[:, :, 3:-3, 3:-3, 3:-3], h, state_floor(U, am0)) <= 1e-12
     sums1 = torch.empty(11, dtype=torch.float64, device="cuda")
     H.hydro_conserved_sums(ctx, H.make_batch(run.U, run.origin, run.h), sums1)
     torch.cuda.synchronize()
@@ -186,7 +187,7 @@ def test_batched_4096_leaf_mesh(H, mixed, oracle_mod):
     assert torch.equal(dU_lv[inv], dU_all) and torch.equal(am_lv[inv], am_all)
     # the whole-mesh launch against the oracle on 48 seeded leaves of every level
     from oracle import core
-    from oracle.compare import field_scales, max_rel_error, mixed_budget
+    from oracle.compare import max_rel_error, mixed_worst, rate_floor
     rng = np.random.default_rng(77)
     idx = np.unique(np.concatenate([rng.choice(np.flatnonzero(lev == l), 12, replace=False) for l in np.unique(lev)]))
     ti = torch.tensor(idx, device="cuda")
@@ -196,11 +197,10 @@ def test_batched_4096_leaf_mesh(H, mixed, oracle_mod):
     ref, amo, _, faces = core.step(P, Us, o_s, h_s, faces=True)
     got = dU_all[ti].cpu().numpy()
     if not mixed:
-        assert max_rel_error(got, ref, h_s.max()) <= 1e-12
+        assert max_rel_error(got, ref, h_s, rate_floor(Us, amo, h_s)) <= 1e-12
         assert np.allclose(am_all[ti].cpu().numpy(), amo, rtol=1e-14, atol=0)
     else:
         pert, _, _ = core.step(P, Us.astype(np.float32).astype(np.float64), o_s, h_s)
-        budget, _ = mixed_budget(ref, pert, faces, h_s, Us, amo)
-        sc = field_scales(ref, h_s.max())[None, :, None, None, None]
-        err = (np.abs(got - ref) / sc).max(axis=(0, 2, 3, 4))
-        assert np.all(err <= budget), (err, budget)
+        worst = mixed_worst(got, ref, pert, faces, h_s, Us, amo)
+        print("AMR shell mixed: largest err/budget", worst)
+        assert worst <= 1.0

@@ -13,8 +13,10 @@ against the oracle's steepening (pinned in test_oracle_contact.py):
   * three RK3 steps of an advected contact: FP64 within 1e-12 of the oracle;
   * conservation on a periodic mesh, and the rates differ from the
     unsteepened ones;
-  * the mode's checks: contact outside {0, 1}, the indicator together with
-    steepening, and the fused step with steepening are rejected.
+  * the mode's checks: contact outside {0, 1} and the indicator together
+    with steepening are rejected, in the separate and the fused step (the
+    fused step's steepening itself is held to the separate launches bit for
+    bit in test_gpu_planes.py).
 The last test prints the step times with and without steepening.
 """
 import numpy as np
@@ -62,7 +64,7 @@ def gpu_step(H, ctx, U, origin, h, g=None):
 
 @pytest.mark.parametrize("omega,gravity", [(0.0, False), (0.3, True)])
 def test_fp64_contact_step_matches_oracle(H, orc, omega, gravity):
-    from oracle.compare import max_rel_error
+    from oracle.compare import max_rel_error, rate_floor
     n = 96
     U = contact_subgrids(n, 61)
     rng = np.random.default_rng(62)
@@ -76,15 +78,15 @@ def test_fp64_contact_step_matches_oracle(H, orc, omega, gravity):
     P = orc.OracleParams(gamma=GAMMA, omega=omega, contact=1)
     ref, amo, _ = orc.step(P, U, origin, h, g)
     assert np.all(np.isfinite(dU))
-    assert max_rel_error(dU, ref, h.max()) <= 1e-12
+    assert max_rel_error(dU, ref, h, rate_floor(U, amo, h, omega, g)) <= 1e-12
     assert np.allclose(am, amo, rtol=1e-14, atol=0)
     # steepening acts on this data: the unsteepened oracle differs
     ref0, _, _ = orc.step(orc.OracleParams(gamma=GAMMA, omega=omega), U, origin, h, g)
-    assert max_rel_error(ref0, ref, h.max()) > 1e-3
+    assert max_rel_error(ref0, ref, h) > 1e-3
 
 
 def test_mixed_contact_step_within_budget(H, orc):
-    from oracle.compare import field_scales, mixed_budget
+    from oracle.compare import mixed_budget, mixed_error, mixed_worst
     n = 96
     U = contact_subgrids(n, 71, exact=True)
     rng = np.random.default_rng(72)
@@ -97,15 +99,16 @@ def test_mixed_contact_step_within_budget(H, orc):
     P = orc.OracleParams(gamma=GAMMA, contact=1)
     ref, amo, _, faces = orc.step(P, U, origin, h, faces=True)
     pert, _, _ = orc.step(P, U.astype(np.float32).astype(np.float64), origin, h)
-    budget, _ = mixed_budget(ref, pert, faces, h, U, amo)
-    sc = field_scales(ref, h.max())[None, :, None, None, None]
-    err = (np.abs(dU - ref) / sc).max(axis=(0, 2, 3, 4))
     assert np.all(np.isfinite(dU))
-    assert np.all(err <= budget), (err, budget)
+    worst = mixed_worst(dU, ref, pert, faces, h, U, amo)
+    print("mixed contact step: largest err/budget", worst)
+    assert worst <= 1.0
     assert np.allclose(am, amo, rtol=1e-6, atol=0)
+    # steepening is far above the budget on this data (density and species)
+    budget, _ = mixed_budget(ref, pert, faces, h, U, amo)
     ref0, _, _ = orc.step(orc.OracleParams(gamma=GAMMA), U, origin, h)
-    d0 = (np.abs(ref0 - ref) / sc).max(axis=(0, 2, 3, 4))
-    assert d0[0] > 100 * budget[0] and d0[9] > 100 * budget[9], (d0, budget)
+    d0 = mixed_error(ref0, ref, h)
+    assert d0[:, 0].max() > 100 * budget[:, 0].max() and d0[:, 9].max() > 100 * budget[:, 9].max(), (d0, budget)
 
 
 def _advected_contact(nx=32):
@@ -120,7 +123,7 @@ def _advected_contact(nx=32):
 
 def test_contact_rk3_steps_match_oracle(H):
     from oracle import core, mesh
-    from oracle.compare import max_rel_error
+    from oracle.compare import max_rel_error, state_floor
     from paper_2107_10987_gb300.uniform import UniformRun
     Ug, h = _advected_contact()
     nbx = Ug.shape[3] // 8
@@ -130,13 +133,15 @@ def test_contact_rk3_steps_match_oracle(H):
     H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=1)
     run = UniformRun(ctx, sub, origin, h, (nbx, 1, 1), H.HYDRO_BC_PERIODIC)
     ref = mesh.BoxRun(core.OracleParams(gamma=GAMMA, contact=1), Ug, h, (0.0, 0.0, 0.0), "periodic")
+    _, am0 = ref.rhs(ref.U)
+    U0 = ref._sub(ref.U)
     for _ in range(3):
         run.step()
         dt_ref = ref.step(0.4)
         assert run.last_dt() == pytest.approx(dt_ref, rel=1e-14)
     got = run.interior().cpu().numpy()
     want = np.stack([ref.U[:, :, :, 8 * k:8 * k + 8] for k in range(nbx)])
-    assert max_rel_error(got, want, h) <= 1e-12
+    assert max_rel_error(got, want, h, state_floor(U0, am0)) <= 1e-12
     assert H.hydro_status(ctx) == 0
     run.close()
 
@@ -182,17 +187,17 @@ def test_contact_mode_checks(H):
     for bad in (2, -1):
         with pytest.raises(H.HydroError):
             H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=bad)
-    # the fused step does not steepen
+    # steepening does not combine with the learned indicator, in the
+    # separate step or the fused one
     H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, contact=1)
     U = contact_subgrids(8, 3)
     o, h = W.uniform_mesh(2)
     run = UniformRun(ctx, U, o, h, 2, H.HYDRO_BC_PERIODIC, fused=True)
-    assert H._lib().hydro_rk3_step(H._cp(ctx), C.byref(run.desc), 0, None) == H.HYDRO_EUNSUP
-    # nor together with the learned indicator
     theta = torch.tensor(np.random.default_rng(5).normal(0, 0.3, gate.NPARAM).astype(np.float32), device="cuda")
     H.hydro_set_indicator(ctx, theta, 0.5)
     with pytest.raises(H.HydroError):
         gpu_step(H, ctx, U, np.asarray(o), np.full(8, h))
+    assert H._lib().hydro_rk3_step(H._cp(ctx), C.byref(run.desc), 0, None) == H.HYDRO_EUNSUP
     H.hydro_set_indicator(ctx, None)
     dU, _ = gpu_step(H, ctx, U, np.asarray(o), np.full(8, h))
     assert np.all(np.isfinite(dU))

@@ -107,7 +107,7 @@ def test_gated_step_matches_masked_oracle(H, oracle_mod, fp64):
     step then matches the oracle's masked step: the FP64 form to 1e-12, the
     mixed form within the mixed-precision budget."""
     from oracle import core, gate
-    from oracle.compare import field_scales, max_rel_error
+    from oracle.compare import max_rel_error, mixed_worst, rate_floor
     # smooth data only: seeded random parameters also gate cells at jumps,
     # where the unlimited formula may leave density or energy negative
     U = W.random_subgrids(10, 8, GAMMA, smooth=True)
@@ -148,23 +148,23 @@ def test_gated_step_matches_masked_oracle(H, oracle_mod, fp64):
     got = dU.cpu().numpy()
     assert 0.02 < mask.sum() / (n * 1000) < 0.98
     if fp64:
-        assert max_rel_error(got, ref, 0.05) <= 1e-12
+        assert max_rel_error(got, ref, 0.05, rate_floor(U, amo, 0.05)) <= 1e-12
         assert np.allclose(am.cpu().numpy(), amo, rtol=1e-14, atol=0)
         return
-    sc = field_scales(ref, 0.05)[None, :, None, None, None]
-    err = (np.abs(got - ref) / sc).max(axis=(0, 2, 3, 4))
-    sens = (np.abs(pert - ref) / sc).max(axis=(0, 2, 3, 4))
-    assert np.all(err <= 8 * sens + 4e-7), (err, sens)
+    # the masked oracle exports no face sums: the budget's flux terms come
+    # from the states and signal speeds alone
+    worst = mixed_worst(got, ref, pert, None, 0.05, U, amo)
+    print("gated mixed step: largest err/budget", worst)
+    assert worst <= 1.0
     # the indicator off again: the plain mixed step
     H.hydro_set_indicator(ctx, None)
     H.hydro_step(ctx, B, 0.0, dU, am)
     torch.cuda.synchronize()
-    plain, _, _ = core.step(P, U, origin, 0.05)
+    plain, amp, _, faces = core.step(P, U, origin, 0.05, faces=True)
     plain_p, _, _ = core.step(P, U.astype(np.float32).astype(np.float64), origin, 0.05)
-    sc = field_scales(plain, 0.05)[None, :, None, None, None]
-    err = (np.abs(dU.cpu().numpy() - plain) / sc).max(axis=(0, 2, 3, 4))
-    sens = (np.abs(plain_p - plain) / sc).max(axis=(0, 2, 3, 4))
-    assert np.all(err <= 8 * sens + 4e-7), (err, sens)
+    worst = mixed_worst(dU.cpu().numpy(), plain, plain_p, faces, 0.05, U, amp)
+    print("plain mixed step after the indicator: largest err/budget", worst)
+    assert worst <= 1.0
 
 
 def test_training_gain_on_held_out_runs(H):

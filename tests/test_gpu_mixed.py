@@ -60,16 +60,15 @@ def gpu_step(H, ctx, U, origin, h, g=None):
 
 
 def check_budget(orc, P, U, origin, h, g, dU, am):
-    from oracle.compare import field_scales, mixed_budget
+    from oracle.compare import mixed_worst
     ref, amo, _, faces = orc.step(P, U, origin, h, g, faces=True)
     pert, _, _ = orc.step(P, U.astype(np.float32).astype(np.float64), origin, h, g)
-    budget, sens = mixed_budget(ref, pert, faces, h, U, amo)
-    sc = field_scales(ref, np.max(h))[None, :, None, None, None]
-    err = (np.abs(dU - ref) / sc).max(axis=(0, 2, 3, 4))
     assert np.all(np.isfinite(dU))
-    assert np.all(err <= budget), (err, budget)
+    worst = mixed_worst(dU, ref, pert, faces, h, U, amo)
+    print("mixed step: largest err/budget", worst)
+    assert worst <= 1.0
     assert np.allclose(am, amo, rtol=1e-6, atol=0)
-    return err, sens
+    return worst
 
 
 @pytest.mark.parametrize("omega,gravity,smooth", [(0.0, False, False), (0.37, True, False), (0.2, True, True),

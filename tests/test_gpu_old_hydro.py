@@ -44,7 +44,7 @@ def step(H, ctx, U, origin, h, g=None):
 @pytest.mark.parametrize("mixed", [False, True])
 def test_old_module_step_matches_oracle(H, oracle_mod, mixed):
     from oracle import core
-    from oracle.compare import field_scales, max_rel_error, mixed_budget
+    from oracle.compare import max_rel_error, mixed_worst, rate_floor
     n = 160
     U = W.random_subgrids(n, 41, GAMMA, smooth=mixed)
     rng = np.random.default_rng(43)
@@ -60,17 +60,16 @@ def test_old_module_step_matches_oracle(H, oracle_mod, mixed):
     assert H.hydro_status(ctx) == 0
     assert np.all(np.isfinite(dU))
     if not mixed:
-        assert max_rel_error(dU, ref, h.max()) <= 1e-12
+        assert max_rel_error(dU, ref, h, rate_floor(U, amo, h, omega, g)) <= 1e-12
         assert np.allclose(am, amo, rtol=1e-14, atol=0)
     else:
         pert, _, _ = core.step(P, U.astype(np.float32).astype(np.float64), origin, h, g)
-        budget, _ = mixed_budget(ref, pert, faces, h, U, amo)
-        sc = field_scales(ref, h.max())[None, :, None, None, None]
-        err = (np.abs(dU - ref) / sc).max(axis=(0, 2, 3, 4))
-        assert np.all(err <= budget), (err, budget)
+        worst = mixed_worst(dU, ref, pert, faces, h, U, amo)
+        print("old module mixed: largest err/budget", worst)
+        assert worst <= 1.0
     # and the new module gives other rates on the same data
     ref9, _, _ = core.step(core.OracleParams(gamma=GAMMA, omega=omega), U, origin, h, g)
-    assert max_rel_error(ref9, ref, h.max()) > 1e-6
+    assert max_rel_error(ref9, ref, h) > 1e-6
 
 
 def test_old_module_fused_equals_separate(H):

@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerance: the plain FP64 path must match the oracle to <= 1e-12 relative
-error per field, the error of each field normalised by that field's largest
-|value| over the compared set (a pure relative error is undefined where
-dU/dt ~ 0).  The PPM/limiter arithmetic of the kernel is rounded exactly as
+error per sub-grid and field, the error of each field normalised by that
+field's largest |value| in the sub-grid (a pure relative error is undefined
+where dU/dt ~ 0; oracle/compare.py adds the floor for rates that are a
+rounding-level residual of large flux terms).  The PPM/limiter arithmetic of the kernel is rounded exactly as
 the oracle's, so limiter decisions agree; the remaining differences come
 from FMA contraction and summation order in the fluxes (~1e-16 relative).
 """
@@ -33,9 +34,34 @@ def orc(oracle_mod):
     return oracle_mod.core
 
 
-def rel_err(got, want, h=1.0):
+def rel_err(got, want, h=1.0, floor=None):
     from oracle.compare import max_rel_error
-    return max_rel_error(got, want, h)
+    return max_rel_error(got, want, h, floor)
+
+
+def rate_floor(U, amax, h, omega=0.0, g=None):
+    from oracle.compare import rate_floor as rf
+    return rf(U, amax, h, omega, g)
+
+
+def box_states(Ug, bc, rel_to=None):
+    """Interior states of a joined box as [n_sub][F][8][8][8], and with
+    rel_to = (P, h, lo) also the state floor of its first stage."""
+    from oracle import mesh
+    from oracle.compare import state_floor
+    sub = mesh.unjoin(Ug, 8)
+    if rel_to is None:
+        return sub
+    P, h, lo = rel_to
+    nbz, nby, nbx = (n // 8 for n in Ug.shape[1:])
+    pad = mesh.split(mesh.pad_box(Ug, 3, bc), 8, 3)
+    _, am, _ = orc_step(P, pad, mesh.origins(nbx, nby, nbz, 8, h, lo), h)
+    return sub, state_floor(pad, am)
+
+
+def orc_step(P, U, o, h):
+    from oracle import core
+    return core.step(P, U, o, h)
 
 
 def gpu_step(H, ctx, U, origin, h, g=None):
@@ -57,7 +83,7 @@ def test_step_sedov_subgrid(H, orc):
     ctx = H.Context(GAMMA, 0.0)
     dU, am = gpu_step(H, ctx, U[None], np.array(lo), h)
     dUo, amo, _ = orc.step(orc.OracleParams(gamma=GAMMA), U[None], np.array(lo), h)
-    assert rel_err(dU, dUo, h) <= TOL
+    assert rel_err(dU, dUo, h, rate_floor(U[None], amo, h)) <= TOL
     assert am[0] == pytest.approx(amo[0], rel=1e-14)
     assert H.hydro_status(ctx) == 0
 
@@ -75,7 +101,7 @@ def test_step_random_batch(H, orc, omega, gravity, smooth):
     dU, am = gpu_step(H, ctx, U, origin, h, g)
     dUo, amo, _ = orc.step(orc.OracleParams(gamma=GAMMA, omega=omega), U, origin, h, g)
     assert np.all(np.isfinite(dU))
-    assert rel_err(dU, dUo, h) <= TOL
+    assert rel_err(dU, dUo, h, rate_floor(U, amo, h, omega, g)) <= TOL
     assert np.allclose(am, amo, rtol=1e-14, atol=0)
 
 
@@ -190,10 +216,12 @@ def test_full_rk3_step_config1(H, orc):
     Ug, h, lo = W.sedov_box(8, GAMMA)
     ctx = H.Context(GAMMA, 0.0)
     got, t, _ = run_rk3_gpu(H, ctx, Ug, h, lo, "periodic", (1, 1, 1), steps=1)
-    run = mesh.BoxRun(orc.OracleParams(gamma=GAMMA), Ug, h, lo, "periodic")
+    P = orc.OracleParams(gamma=GAMMA)
+    _, fl = box_states(Ug, "periodic", (P, h, lo))
+    run = mesh.BoxRun(P, Ug, h, lo, "periodic")
     run.step(0.4)
     assert t == run.t
-    assert rel_err(got[None], run.U[None], h) <= TOL
+    assert rel_err(box_states(got, "periodic"), box_states(run.U, "periodic"), h, fl) <= TOL
 
 
 def test_rk3_steps_uniform_mesh_outflow(H, orc):
@@ -202,11 +230,14 @@ def test_rk3_steps_uniform_mesh_outflow(H, orc):
     Ug, h, lo = W.sedov_box(16, GAMMA)
     ctx = H.Context(GAMMA, 0.0)
     got, t, _ = run_rk3_gpu(H, ctx, Ug, h, lo, "outflow", (2, 2, 2), steps=5)
-    run = mesh.BoxRun(orc.OracleParams(gamma=GAMMA), Ug, h, lo, "outflow")
+    P = orc.OracleParams(gamma=GAMMA)
+    _, fl = box_states(Ug, "outflow", (P, h, lo))
+    run = mesh.BoxRun(P, Ug, h, lo, "outflow")
     for _ in range(5):
         run.step(0.4)
     assert t == pytest.approx(run.t, rel=1e-13)
-    assert rel_err(got[None], run.U[None], h) <= 1e-11  # five steps of accumulated rounding
+    # five steps of accumulated rounding
+    assert rel_err(box_states(got, "outflow"), box_states(run.U, "outflow"), h, fl) <= 1e-11
 
 
 def test_sedov_64_shock_radius(H):
@@ -243,7 +274,7 @@ def test_bench_size_sampled_parity(H, orc):
     dU, am = gpu_step(H, ctx, sub, o, h)
     pick = np.array([0, 7, 63, 219, 292, 300, 365, 511])
     dUo, amo, _ = orc.step(orc.OracleParams(gamma=GAMMA), sub[pick], o[pick], h)
-    assert rel_err(dU[pick], dUo, h) <= TOL
+    assert rel_err(dU[pick], dUo, h, rate_floor(sub[pick], amo, h)) <= TOL
     assert np.allclose(am[pick], amo, rtol=1e-14, atol=0)
 
 

@@ -2,10 +2,11 @@
 ambient density 1e-10) on the GPU, through the C ABI.
 
 * parity: one RK3 step from the initial state, FP64 path against the oracle
-  (<= 1e-12 per field, normalised by the field's largest |value|); one stage
-  on a state evolved for 10 steps, FP64 against the oracle and the mixed
-  form within its budget (oracle.compare.mixed_budget: 8 sens + 8 eps32 R
-  + 4e-7, sens = the oracle's own change on FP32-rounded inputs, R the
+  (<= 1e-12 per sub-grid and field, normalised by the field's largest
+  |value| in that sub-grid, oracle.compare); one stage on a state evolved
+  for 10 steps, FP64 against the oracle and the mixed form within its
+  budget (oracle.compare.mixed_budget: 8 sens + 8 eps32 R + 4e-7 per
+  sub-grid, sens = the oracle's own change on FP32-rounded inputs, R the
   face-flux terms of each rate over its scale);
 * accuracy at 64^3 over 100 RK3 steps, FP64 and mixed forms side by side:
   the L1 density error against the initial state (Sec. VI's measure with an
@@ -82,23 +83,25 @@ class PolyRun:
 
 def test_polytrope_rk3_step_fp64_matches_oracle(H, oracle_mod):
     from oracle import mesh
-    from oracle.compare import max_rel_error
+    from oracle.compare import max_rel_error, state_floor
     nb = 4
     run = PolyRun(H, nb, H.HYDRO_PREC_FP64)
     run.step(1)
     Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
     ref = mesh.BoxRun(oracle_mod.core.OracleParams(gamma=GAMMA, omega=OMEGA), mesh.join(Ui, nb, nb, nb), h,
                       (-1, -1, -1), "outflow", g=g)
+    _, am0 = ref.rhs(ref.U)
+    U0 = ref._sub(ref.U)
     ref.step(0.4)
     assert run.t == pytest.approx(ref.t, rel=1e-14)
-    got = mesh.join(run.interior(), nb, nb, nb)
-    assert max_rel_error(got[None], ref.U[None], h) <= 1e-12
+    got = run.interior()
+    assert max_rel_error(got, mesh.unjoin(ref.U, 8), h, state_floor(U0, am0)) <= 1e-12
     assert H.hydro_status(run.ctx) == 0
 
 
 def test_polytrope_stage_on_evolved_state(H, oracle_mod):
     """FP64 and mixed single stages on the same evolved, ghost-filled state."""
-    from oracle.compare import field_scales, max_rel_error, mixed_budget
+    from oracle.compare import max_rel_error, mixed_worst, rate_floor
     core = oracle_mod.core
     nb = 4
     run = PolyRun(H, nb, H.HYDRO_PREC_FP64)
@@ -116,14 +119,13 @@ def test_polytrope_stage_on_evolved_state(H, oracle_mod):
         torch.cuda.synchronize()
         got = run.dU.cpu().numpy()
         if prec == H.HYDRO_PREC_FP64:
-            assert max_rel_error(got, ref, h) <= 1e-12
+            assert max_rel_error(got, ref, h, rate_floor(Us, amo, h, OMEGA, g)) <= 1e-12
             assert np.allclose(run.am.cpu().numpy(), amo, rtol=1e-14, atol=0)
         else:
             pert, _, _ = core.step(P, Us.astype(np.float32).astype(np.float64), o, h, g)
-            budget, sens = mixed_budget(ref, pert, faces, h, Us, amo)
-            sc = field_scales(ref, h)[None, :, None, None, None]
-            err = (np.abs(got - ref) / sc).max(axis=(0, 2, 3, 4))
-            assert np.all(err <= budget), (err, budget)
+            worst = mixed_worst(got, ref, pert, faces, h, Us, amo)
+            print("polytrope evolved stage, mixed: largest err/budget", worst)
+            assert worst <= 1.0
     assert H.hydro_status(run.ctx) == 0
 
 
@@ -160,7 +162,7 @@ def test_full_size_sampled_parity(H, oracle_mod):
     """The full rotating-polytrope mesh (32,768 sub-grids, 256^3 cells, 7.2 GB
     of padded state) in one launch of each form, as the benchmark runs it;
     48 seeded sub-grids (and the first and last) against the oracle."""
-    from oracle.compare import field_scales, max_rel_error, mixed_budget
+    from oracle.compare import max_rel_error, mixed_worst, rate_floor
     core = oracle_mod.core
     nb = 32
     Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
@@ -188,12 +190,11 @@ def test_full_size_sampled_parity(H, oracle_mod):
         torch.cuda.synchronize()
         got = dU[torch.tensor(idx, device=dev)].cpu().numpy()
         if prec == H.HYDRO_PREC_FP64:
-            assert max_rel_error(got, ref, h) <= 1e-12
+            assert max_rel_error(got, ref, h, rate_floor(Us, amo, h, OMEGA, g[idx])) <= 1e-12
             assert np.allclose(am.cpu().numpy()[idx], amo, rtol=1e-14, atol=0)
         else:
             pert, _, _ = core.step(P, Us.astype(np.float32).astype(np.float64), o[idx], h, g[idx])
-            budget, _ = mixed_budget(ref, pert, faces, h, Us, amo)
-            sc = field_scales(ref, h)[None, :, None, None, None]
-            err = (np.abs(got - ref) / sc).max(axis=(0, 2, 3, 4))
-            assert np.all(err <= budget), (err, budget)
+            worst = mixed_worst(got, ref, pert, faces, h, Us, amo)
+            print("polytrope 256^3 sampled, mixed: largest err/budget", worst)
+            assert worst <= 1.0
     assert H.hydro_status(ctx) == 0
