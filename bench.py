@@ -565,6 +565,44 @@ def polytrope_measure(args, H, dev, flush, indicator=None):
     return out
 
 
+def subgrid16_measure(args, H, dev, flush):
+    """The headline's rotating polytrope at 256^3 cut into 4,096 sub-grids of
+    16^3 (the paper's best-performing sub-grid size, Sec. V): RK3 steps as
+    separate launches replayed from a CUDA graph (the step kernels run the
+    octants of each sub-grid in place; the fused step is 8^3 only), mixed
+    precision and plain FP64."""
+    import torch
+    from paper_2107_10987_gb300 import workloads as W
+    from paper_2107_10987_gb300.uniform import UniformRun
+    stream = torch.cuda.current_stream()
+    omega = WORKLOADS["polytrope"]["omega"]
+    nb = 16
+    Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA, N=16)
+    cells = Ui.shape[0] * 16 ** 3
+    out = {"workload": "rotating n=1.5 polytrope, 4,096 sub-grids of 16^3 (256^3 on [-1,1]^3), as the headline"}
+    for name, prec in (("mixed", H.HYDRO_PREC_MIXED), ("fp64", H.HYDRO_PREC_FP64)):
+        ctx = H.Context(GAMMA, omega, N=16)
+        H.hydro_set_mode(ctx, prec, 0.4)
+        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g)
+        steps = max(2, args.steps // 10) if name == "fp64" else args.steps
+        for _ in range(2):
+            run.step(use_graph=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            run.step(use_graph=True)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t = float(np.mean([a.elapsed_time(b) for a, b in ev])) / 1e3
+        out[name] = {"value": cells / t, "ms_per_step": 1e3 * t, "steps_timed": steps, "status": H.hydro_status(ctx)}
+        run.close()
+        del run
+        ctx.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -715,6 +753,11 @@ def gpu_arm(args):
                         "state (Sec. VI's measure with an absolute value)",
                 "l1_fp64": acc["fp64"]["l1_density"], "l1_mixed": acc["mixed"]["l1_density"],
                 "l1_mixed_over_fp64": acc["l1_mixed_over_fp64"]}
+        if args.subgrid16 and wl == "polytrope":
+            line["subgrid16"] = subgrid16_measure(args, H, dev, flush)
+            line["subgrid16"]["vs_8cubed_separate_launches"] = (
+                line["separate_launches"]["ms_per_step"] / line["subgrid16"]["mixed"]["ms_per_step"]
+                if "separate_launches" in line else None)
         if args.sedov:
             line["sedov_512"], sres = sedov_measure(args, H, dev, flush)
         else:
@@ -848,6 +891,8 @@ def main():
                     help="skip the contact-steepening measurement")
     ap.add_argument("--no-sedov", dest="sedov", action="store_false",
                     help="skip the 512-sub-grid Sedov measurement")
+    ap.add_argument("--no-subgrid16", dest="subgrid16", action="store_false",
+                    help="skip the 16^3-sub-grid measurement")
     ap.add_argument("--workload", default="polytrope", choices=sorted(WORKLOADS),
                     help="the headline workload (polytrope: 32,768 sub-grids; sedov: 512 sub-grids)")
     ap.add_argument("--polytrope-nb", type=int, default=16,

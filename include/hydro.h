@@ -13,7 +13,8 @@
  * step; plus the SSP-RK3 stage update with the dual-energy tracer resync of
  * Bryan et al. (1995) (three hydro iterations per step: Sec. IV-A.2).
  *
- * Data layout (all FP64, C order, x fastest):
+ * Data layout (all FP64, C order, x fastest; N = 8 or 16 interior cells per
+ * sub-grid edge, fixed per context):
  *   U     [n_sub][F][S][S][S]  cell averages with G = 3 ghost layers,
  *                              S = N + 2G, F = 9 + n_species fields in the order
  *                              rho, s_x, s_y, s_z, E, tau, z_x, z_y, z_z, species...
@@ -69,9 +70,15 @@ extern "C" {
 
 typedef struct hydro_ctx hydro_ctx_t;
 
-/* Sub-grid layout.  N is the number of interior cells per edge (8; the paper's
- * default sub-grid, Sec. III-B), ghost the ghost depth (must be 3: the 5-cell
- * PPM stencil plus the face-adjacent ghost row), n_species >= 1. */
+/* Sub-grid layout.  N is the number of interior cells per edge: 8 (the
+ * paper's default sub-grid, Sec. III-B) or 16 (its compile-time alternative,
+ * the best-performing configuration of Sec. V); ghost the ghost depth (must
+ * be 3: the 5-cell PPM stencil plus the face-adjacent ghost row),
+ * n_species >= 1.  With N = 16 the step kernels process each sub-grid as its
+ * eight 8^3 octants, each read in place from its 14^3 window of the padded
+ * array (no copy); the mesh kernels work on the 16^3 layout.  Not available
+ * with N = 16: the fused RK3 step, hydro_step_static and hydro_gate_data
+ * (EUNSUP). */
 typedef struct {
   int N;
   int ghost;
@@ -114,8 +121,8 @@ typedef struct {
 /* Create a context for a field layout, ratio of specific heats gamma > 1 and
  * frame angular velocity omega (about +z).  Allocates nothing on the device
  * until the first call that needs scratch.  *out is set on success.
- * Errors: EINVAL (N not in {8}, ghost != 3, n_species outside [1,7], gamma <= 1,
- * non-finite omega, out == NULL). */
+ * Errors: EINVAL (N not in {8, 16}, ghost != 3, n_species < 1, gamma <= 1,
+ * non-finite omega, out == NULL), EUNSUP (n_species other than 1). */
 int hydro_create(const hydro_layout_t* layout, double gamma, double omega, hydro_ctx_t** out);
 
 /* Replace the run-time options.  Errors: EINVAL (unknown precision, cfl or

@@ -62,16 +62,18 @@ class AMRRun:
         from . import workloads as W
         self.ctx = ctx
         self.mesh = AMRMesh(level, ijk, bc, device)
-        o, h = W.amr_geometry(level, ijk)
+        N = getattr(ctx, "N", 8)  # the leaves' edge (8 or 16)
+        o, h = W.amr_geometry(level, ijk, N)
         n = len(level)
         self.origin = torch.tensor(o, device=device)
         self.h = torch.tensor(h, device=device)
-        self.bufs = (torch.as_tensor(U, device=device).clone(), torch.zeros((n, 10, 14, 14, 14), dtype=torch.float64,
+        Sp = N + 6
+        self.bufs = (torch.as_tensor(U, device=device).clone(), torch.zeros((n, 10, Sp, Sp, Sp), dtype=torch.float64,
                                                                             device=device))
-        self.dU = torch.empty((n, 10, 8, 8, 8), dtype=torch.float64, device=device)
+        self.dU = torch.empty((n, 10, N, N, N), dtype=torch.float64, device=device)
         self.am = torch.empty(n, dtype=torch.float64, device=device)
         self.dt = torch.empty(1, dtype=torch.float64, device=device)
-        self.faces = torch.empty((n, 6, 13, 8, 8), dtype=torch.float64, device=device)
+        self.faces = torch.empty((n, 6, 13, N, N), dtype=torch.float64, device=device)
         self.desc = H.make_rk3_desc(self.bufs[0], self.bufs[1], self.origin, self.h, None, bc, self.dU, self.am,
                                     self.dt, cfl, mesh=self.mesh, face_flux=self.faces)
         self.parity = 0

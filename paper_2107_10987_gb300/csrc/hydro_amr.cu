@@ -1,5 +1,6 @@
 // hydro_amr.cu -- ghost fill and coarse-fine flux correction on an adaptive
-// octree of 8^3 sub-grids (2:1 balanced across faces, edges and vertices).
+// octree of NN^3 sub-grids, NN = 8 or 16 (2:1 balanced across faces, edges
+// and vertices).
 //
 // Leaves are found through dense per-level tables (hydro_amr_t): at level l
 // entry ((k 2^l) + j) 2^l + i is the leaf index at that sub-grid position,
@@ -43,10 +44,19 @@ __device__ __forceinline__ long level_offset(int l, int lmin) {
   return off;
 }
 
+// The leaf (or -1 / -2) holding global cell (gx, gy, gz) of level l, for
+// leaves of NN^3 cells.
+template <int NN>
 __device__ __forceinline__ int lookup(const AMRArgs& A, int l, int gx, int gy, int gz) {
   if (l < A.lmin || l > A.lmax) return -3;
   const int n = 1 << l;
-  return A.table[level_offset(l, A.lmin) + ((long)(gz >> 3) * n + (gy >> 3)) * n + (gx >> 3)];
+  return A.table[level_offset(l, A.lmin) + ((long)(gz / NN) * n + (gy / NN)) * n + (gx / NN)];
+}
+
+// Boundary-face value [s][f][q][pc][pb] of leaves of NN^3 cells.
+template <int NN>
+__device__ __forceinline__ size_t face_index_nn(int s, int f, int q, int pc, int pb) {
+  return ((((size_t)s * 6 + f) * DQ + q) * NN + pc) * NN + pb;
 }
 
 __device__ __forceinline__ int bc_amr(int g, int n, int bc) {
@@ -74,14 +84,16 @@ __device__ __forceinline__ int rel_pos(int p, int base, int n, int bc, int lo, i
 // only path) before their stores.
 constexpr int kAmrBatch = 2;
 
+template <int NN>
 __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
   __shared__ int nb[27];   // level l:   relative position (-1..1)^3
   __shared__ int nbf[64];  // level l+1: relative position (-1..2)^3 from 2p
   const int tid = threadIdx.x;
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int l = A.leaf_level[s];
     const int pi[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
-    const int n = 1 << l, ncell = N << l;
+    const int n = 1 << l, ncell = NN << l;
     __syncthreads();  // the previous leaf's tables are no longer read
     if (tid < 27) {
       const int q[3] = {pi[0] + tid % 3 - 1, pi[1] + (tid / 3) % 3 - 1, pi[2] + tid / 9 - 1};
@@ -106,44 +118,44 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
       nbf[i] = inside ? A.table[level_offset(l + 1, A.lmin) + ((long)w[2] * nf + w[1]) * nf + w[0]] : -3;
     }
     __syncthreads();
-    double* dst = A.U + (size_t)s * F * S3;
-    for (int c0 = tid; c0 < S3; c0 += kAmrBatch * blockDim.x) {
+    double* dst = A.U + (size_t)s * F * LS3;
+    for (int c0 = tid; c0 < LS3; c0 += kAmrBatch * blockDim.x) {
       double v[kAmrBatch][F];
       bool put[kAmrBatch];
 #pragma unroll
       for (int j = 0; j < kAmrBatch; ++j) {
         const int c = c0 + j * blockDim.x;
-        const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
-        put[j] = c < S3 && !((unsigned)lx < (unsigned)N && (unsigned)ly < (unsigned)N && (unsigned)lz < (unsigned)N);
+        const int lx = c % LS - G, ly = (c / LS) % LS - G, lz = c / (LS * LS) - G;
+        put[j] = c < LS3 && !((unsigned)lx < (unsigned)NN && (unsigned)ly < (unsigned)NN && (unsigned)lz < (unsigned)NN);
         if (!put[j]) continue;
-        const int g[3] = {bc_amr(pi[0] * N + lx, ncell, A.bc), bc_amr(pi[1] * N + ly, ncell, A.bc),
-                          bc_amr(pi[2] * N + lz, ncell, A.bc)};
-        const int r[3] = {rel_pos(g[0] >> 3, pi[0], n, A.bc, -1, 3), rel_pos(g[1] >> 3, pi[1], n, A.bc, -1, 3),
-                          rel_pos(g[2] >> 3, pi[2], n, A.bc, -1, 3)};
+        const int g[3] = {bc_amr(pi[0] * NN + lx, ncell, A.bc), bc_amr(pi[1] * NN + ly, ncell, A.bc),
+                          bc_amr(pi[2] * NN + lz, ncell, A.bc)};
+        const int r[3] = {rel_pos(g[0] >> LSH, pi[0], n, A.bc, -1, 3), rel_pos(g[1] >> LSH, pi[1], n, A.bc, -1, 3),
+                          rel_pos(g[2] >> LSH, pi[2], n, A.bc, -1, 3)};
         const int t = nb[((r[2] + 1) * 3 + (r[1] + 1)) * 3 + (r[0] + 1)];
         if (t >= 0) {
           const double* src =
-              A.U + (size_t)t * F * S3 + (((g[2] & 7) + G) * S + ((g[1] & 7) + G)) * S + ((g[0] & 7) + G);
+              A.U + (size_t)t * F * LS3 + (((g[2] & LM) + G) * LS + ((g[1] & LM) + G)) * LS + ((g[0] & LM) + G);
 #pragma unroll
-          for (int k = 0; k < F; ++k) v[j][k] = __ldg(src + (size_t)k * S3);
+          for (int k = 0; k < F; ++k) v[j][k] = __ldg(src + (size_t)k * LS3);
         } else if (t == -1) {
           const double* kid[8];
           bool ok = true;
 #pragma unroll
           for (int d = 0; d < 8; ++d) {
             const int f[3] = {2 * g[0] + (d & 1), 2 * g[1] + ((d >> 1) & 1), 2 * g[2] + (d >> 2)};
-            const int rf[3] = {rel_pos(f[0] >> 3, 2 * pi[0], 2 * n, A.bc, -1, 4),
-                               rel_pos(f[1] >> 3, 2 * pi[1], 2 * n, A.bc, -1, 4),
-                               rel_pos(f[2] >> 3, 2 * pi[2], 2 * n, A.bc, -1, 4)};
+            const int rf[3] = {rel_pos(f[0] >> LSH, 2 * pi[0], 2 * n, A.bc, -1, 4),
+                               rel_pos(f[1] >> LSH, 2 * pi[1], 2 * n, A.bc, -1, 4),
+                               rel_pos(f[2] >> LSH, 2 * pi[2], 2 * n, A.bc, -1, 4)};
             const int tf = nbf[((rf[2] + 1) * 4 + (rf[1] + 1)) * 4 + (rf[0] + 1)];
             ok &= tf >= 0;
-            kid[d] = A.U + (size_t)(tf < 0 ? s : tf) * F * S3 + (((f[2] & 7) + G) * S + ((f[1] & 7) + G)) * S +
-                     ((f[0] & 7) + G);
+            kid[d] = A.U + (size_t)(tf < 0 ? s : tf) * F * LS3 + (((f[2] & LM) + G) * LS + ((f[1] & LM) + G)) * LS +
+                     ((f[0] & LM) + G);
           }
           if (!ok) atomicOr(A.status, 4u);
 #pragma unroll
           for (int k = 0; k < F; ++k) {
-            const size_t o = (size_t)k * S3;
+            const size_t o = (size_t)k * LS3;
             const double acc = radd(radd(radd(__ldg(kid[0] + o), __ldg(kid[1] + o)), radd(__ldg(kid[2] + o), __ldg(kid[3] + o))),
                                     radd(radd(__ldg(kid[4] + o), __ldg(kid[5] + o)), radd(__ldg(kid[6] + o), __ldg(kid[7] + o))));
             v[j][k] = rmul(acc, 0.125);
@@ -156,7 +168,7 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
       for (int j = 0; j < kAmrBatch; ++j)
         if (put[j])
 #pragma unroll
-          for (int k = 0; k < F; ++k) dst[(size_t)k * S3 + c0 + j * blockDim.x] = v[j][k];
+          for (int k = 0; k < F; ++k) dst[(size_t)k * LS3 + c0 + j * blockDim.x] = v[j][k];
     }
   }
 }
@@ -190,18 +202,20 @@ __device__ __forceinline__ double quarter64(double x) {
 
 // Prolongation of one fine ghost cell from coarse cell C (padded pointer to
 // field 0): U_C + s_x o_x + s_y o_y + s_z o_z, all ten fields.
+template <int NN>
 __device__ __forceinline__ void prolong_cell(const double* C, const double off[3], double* dst) {
-  const int st[3] = {1, S, S * S};
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
+  const int st[3] = {1, LS, LS * LS};
 #pragma unroll
   for (int k = 0; k < F; ++k) {
-    const double* q = C + (size_t)k * S3;
+    const double* q = C + (size_t)k * LS3;
     double v = q[0];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
       v = radd(v, rmul(minmod64(dp, dm), off[d]));
     }
-    dst[(size_t)k * S3] = v;
+    dst[(size_t)k * LS3] = v;
   }
 }
 
@@ -211,7 +225,9 @@ __device__ __forceinline__ void prolong_cell(const double* C, const double off[3
 // leaf's ghost cells (the same values as prolonging child by child).  Ghost
 // cells outside the domain (outflow: clamped positions) are prolonged one by
 // one afterwards.
+template <int NN>
 __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A) {
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
   __shared__ int coarser;  // some neighbour position of the leaf lies inside a coarser leaf
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int l = A.leaf_level[s];
@@ -233,12 +249,14 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
     }
     __syncthreads();
     if (!coarser) continue;
-    const int b[3] = {A.leaf_ijk[3 * s] * N, A.leaf_ijk[3 * s + 1] * N, A.leaf_ijk[3 * s + 2] * N};
-    const int ncell = N << l, nc = ncell >> 1;
-    double* dstb = A.U + (size_t)s * F * S3;
-    for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+    const int b[3] = {A.leaf_ijk[3 * s] * NN, A.leaf_ijk[3 * s + 1] * NN, A.leaf_ijk[3 * s + 2] * NN};
+    const int ncell = NN << l, nc = ncell >> 1;
+    double* dstb = A.U + (size_t)s * F * LS3;
+    // the coarse block covering the leaf's padded region: NN/2 + 4 cells an axis
+    constexpr int LB = NN / 2 + 4;
+    for (int i = threadIdx.x; i < LB * LB * LB; i += blockDim.x) {
       int C[3], Cw[3];
-      const int ii[3] = {i & 7, (i >> 3) & 7, i >> 6};
+      const int ii[3] = {i % LB, (i / LB) % LB, i / (LB * LB)};
       bool out = false;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -255,26 +273,26 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
 #pragma unroll
       for (int dch = 0; dch < 8; ++dch) {
         const int f[3] = {2 * C[0] + (dch & 1) - b[0], 2 * C[1] + ((dch >> 1) & 1) - b[1], 2 * C[2] + (dch >> 2) - b[2]};
-        const bool in = f[0] >= -G && f[0] < N + G && f[1] >= -G && f[1] < N + G && f[2] >= -G && f[2] < N + G;
-        const bool interior = (unsigned)f[0] < (unsigned)N && (unsigned)f[1] < (unsigned)N && (unsigned)f[2] < (unsigned)N;
+        const bool in = f[0] >= -G && f[0] < NN + G && f[1] >= -G && f[1] < NN + G && f[2] >= -G && f[2] < NN + G;
+        const bool interior = (unsigned)f[0] < (unsigned)NN && (unsigned)f[1] < (unsigned)NN && (unsigned)f[2] < (unsigned)NN;
         if (in && !interior) mask |= 1 << dch;
       }
       if (!mask) continue;
-      const int tc = lookup(A, l - 1, Cw[0], Cw[1], Cw[2]);
+      const int tc = lookup<NN>(A, l - 1, Cw[0], Cw[1], Cw[2]);
       if (tc == -2) atomicOr(A.status, 4u);  // two levels coarser: not 2:1 balanced
       if (tc < 0) continue;                  // refined at level l-1: pass 1 filled these
       const double* Cp =
-          A.U + (size_t)tc * F * S3 + (((Cw[2] & 7) + G) * S + ((Cw[1] & 7) + G)) * S + ((Cw[0] & 7) + G);
+          A.U + (size_t)tc * F * LS3 + (((Cw[2] & LM) + G) * LS + ((Cw[1] & LM) + G)) * LS + ((Cw[0] & LM) + G);
       // per field: the quarter slopes t_d = s_d / 4 once (the child offsets are
       // +-1/4, and -(s/4) = s * (-1/4) exactly), then the children's values
       // ((c +- t_x) +- t_y) +- t_z as a tree of partial sums -- the same
       // additions, in the same order, as prolonging child by child
-      const int st[3] = {1, S, S * S};
+      const int st[3] = {1, LS, LS * LS};
       const int need_x = ((mask & 0x55) ? 1 : 0) | ((mask & 0xaa) ? 2 : 0);  // children with x offset -, +
-      double* dst0 = dstb + ((2 * C[2] - b[2] + G) * S + (2 * C[1] - b[1] + G)) * S + (2 * C[0] - b[0] + G);
+      double* dst0 = dstb + ((2 * C[2] - b[2] + G) * LS + (2 * C[1] - b[1] + G)) * LS + (2 * C[0] - b[0] + G);
 #pragma unroll 1
       for (int k = 0; k < F; ++k) {
-        const double* q = Cp + (size_t)k * S3;
+        const double* q = Cp + (size_t)k * LS3;
         const double c = q[0];
         double t[3];
 #pragma unroll
@@ -297,7 +315,7 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
             for (int iz = 0; iz < 2; ++iz) {
               const int dch = ix + 2 * iy + 4 * iz;
               if (!(mask & (1 << dch))) continue;
-              dst0[(size_t)k * S3 + (iz * S + iy) * S + ix] = radd(vxy, iz ? t[2] : -t[2]);
+              dst0[(size_t)k * LS3 + (iz * LS + iy) * LS + ix] = radd(vxy, iz ? t[2] : -t[2]);
             }
           }
         }
@@ -305,52 +323,54 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
     }
     if (A.bc == 0) continue;
     // outflow: ghost cells outside the domain, clamped, one by one
-    for (int c = threadIdx.x; c < S3; c += blockDim.x) {
-      const int lx = c % S - G, ly = (c / S) % S - G, lz = c / (S * S) - G;
+    for (int c = threadIdx.x; c < LS3; c += blockDim.x) {
+      const int lx = c % LS - G, ly = (c / LS) % LS - G, lz = c / (LS * LS) - G;
       const int gx = b[0] + lx, gy = b[1] + ly, gz = b[2] + lz;
       if (gx >= 0 && gx < ncell && gy >= 0 && gy < ncell && gz >= 0 && gz < ncell) continue;
       const int cx = bc_amr(gx, ncell, 1), cy = bc_amr(gy, ncell, 1), cz = bc_amr(gz, ncell, 1);
-      if (lookup(A, l, cx, cy, cz) != -2) continue;
+      if (lookup<NN>(A, l, cx, cy, cz) != -2) continue;
       const int px = cx >> 1, py = cy >> 1, pz = cz >> 1;
-      const int tc = lookup(A, l - 1, px, py, pz);
+      const int tc = lookup<NN>(A, l - 1, px, py, pz);
       if (tc < 0) {
         atomicOr(A.status, 4u);
         continue;
       }
-      const double* Cp = A.U + (size_t)tc * F * S3 + (((pz & 7) + G) * S + ((py & 7) + G)) * S + ((px & 7) + G);
+      const double* Cp = A.U + (size_t)tc * F * LS3 + (((pz & LM) + G) * LS + ((py & LM) + G)) * LS + ((px & LM) + G);
       const double off[3] = {(cx & 1) ? 0.25 : -0.25, (cy & 1) ? 0.25 : -0.25, (cz & 1) ? 0.25 : -0.25};
-      prolong_cell(Cp, off, dstb + c);
+      prolong_cell<NN>(Cp, off, dstb + c);
     }
   }
 }
 
 // One thread per interior cell of a leaf; the cell's faces on the leaf
 // boundary that border finer leaves are corrected in the order x-, x+, y-, ...
+template <int NN>
 __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, const double* h, const double* faces,
                                                                  double* dUdt) {
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int l = A.leaf_level[s];
     const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
     const int n = 1 << l;
     const double hc = h[s];
-    for (int cell = threadIdx.x; cell < N3; cell += blockDim.x) {
-      const int cl[3] = {cell & 7, (cell >> 3) & 7, cell >> 6};
+    for (int cell = threadIdx.x; cell < LN3; cell += blockDim.x) {
+      const int cl[3] = {cell % NN, (cell / NN) % NN, cell / (NN * NN)};
       double du[F];
       bool touched = false;
       for (int a = 0; a < 3; ++a) {
         const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
         for (int side = 0; side < 2; ++side) {
-          if (cl[a] != (side ? N - 1 : 0)) continue;
+          if (cl[a] != (side ? NN - 1 : 0)) continue;
           int nb[3] = {ijk[0], ijk[1], ijk[2]};
           nb[a] += side ? 1 : -1;
           if (nb[a] < 0 || nb[a] >= n) {
             if (A.bc != 0) continue;
             nb[a] = (nb[a] + n) % n;
           }
-          if (lookup(A, l, nb[0] * N, nb[1] * N, nb[2] * N) != -1) continue;
+          if (lookup<NN>(A, l, nb[0] * NN, nb[1] * NN, nb[2] * NN) != -1) continue;
           if (!touched) {
 #pragma unroll
-            for (int k = 0; k < F; ++k) du[k] = dUdt[((size_t)s * F + k) * N3 + cell];
+            for (int k = 0; k < F; ++k) du[k] = dUdt[((size_t)s * F + k) * LN3 + cell];
             touched = true;
           }
           const double sgn = side ? 1.0 : -1.0;
@@ -362,19 +382,19 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
           for (int dc = 0; dc < 2; ++dc)
             for (int db = 0; db < 2; ++db) {
               int gf[3];
-              gf[a] = side ? (ijk[a] + 1) * 2 * N : ijk[a] * 2 * N - 1;
-              gf[b] = 2 * (ijk[b] * N + pb) + db;
-              gf[c] = 2 * (ijk[c] * N + pc) + dc;
-              const int nf = N << (l + 1);
+              gf[a] = side ? (ijk[a] + 1) * 2 * NN : ijk[a] * 2 * NN - 1;
+              gf[b] = 2 * (ijk[b] * NN + pb) + db;
+              gf[c] = 2 * (ijk[c] * NN + pc) + dc;
+              const int nf = NN << (l + 1);
               if (gf[a] < 0 || gf[a] >= nf) gf[a] = (gf[a] + nf) % nf;  // periodic wrap
-              const int o = lookup(A, l + 1, gf[0], gf[1], gf[2]);
+              const int o = lookup<NN>(A, l + 1, gf[0], gf[1], gf[2]);
               if (o < 0) {
                 ok = false;
                 continue;
               }
-              const int loc[3] = {gf[0] & 7, gf[1] & 7, gf[2] & 7};
-              const double* ff = faces + face_index(o, 2 * a + (side ? 0 : 1), 0, loc[c], loc[b]);
-              const size_t qs = (size_t)N * N;  // stride between quantities
+              const int loc[3] = {gf[0] & LM, gf[1] & LM, gf[2] & LM};
+              const double* ff = faces + face_index_nn<NN>(o, 2 * a + (side ? 0 : 1), 0, loc[c], loc[b]);
+              const size_t qs = (size_t)NN * NN;  // stride between quantities
               double r[3];
               r[a] = rmul(0.75 * sgn, hc);
               r[b] = rmul(db ? 0.25 : -0.25, hc);
@@ -391,8 +411,8 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
             atomicOr(A.status, 4u);
             continue;
           }
-          const double* own = faces + face_index(s, 2 * a + side, 0, pc, pb);
-          const size_t qs = (size_t)N * N;
+          const double* own = faces + face_index_nn<NN>(s, 2 * a + side, 0, pc, pb);
+          const size_t qs = (size_t)NN * NN;
           const double coef = -(sgn / hc);
           double corr[F];
 #pragma unroll
@@ -406,7 +426,7 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
       }
       if (touched) {
 #pragma unroll
-        for (int k = 0; k < F; ++k) dUdt[((size_t)s * F + k) * N3 + cell] = du[k];
+        for (int k = 0; k < F; ++k) dUdt[((size_t)s * F + k) * LN3 + cell] = du[k];
       }
     }
   }
@@ -447,8 +467,13 @@ int hydro_fill_ghosts_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_am
   const int cap = c->num_sms * 8;
   const int grid = B->n_sub < cap ? B->n_sub : cap;
   cudaStream_t st = (cudaStream_t)stream;
-  hyd::hydro_ghost_amr_kernel<<<grid, 256, 0, st>>>(A);
-  hyd::hydro_ghost_amr_prolong_kernel<<<grid, 256, 0, st>>>(A);
+  if (c->N == 16) {
+    hyd::hydro_ghost_amr_kernel<16><<<grid, 256, 0, st>>>(A);
+    hyd::hydro_ghost_amr_prolong_kernel<16><<<grid, 256, 0, st>>>(A);
+  } else {
+    hyd::hydro_ghost_amr_kernel<8><<<grid, 256, 0, st>>>(A);
+    hyd::hydro_ghost_amr_prolong_kernel<8><<<grid, 256, 0, st>>>(A);
+  }
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 
@@ -462,7 +487,10 @@ int hydro_flux_correct_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_a
   hyd::AMRArgs A = amr_args(c, B, M);
   const int cap = c->num_sms * 8;
   const int grid = B->n_sub < cap ? B->n_sub : cap;
-  hyd::hydro_flux_correct_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(A, B->h, face_flux, dUdt);
+  if (c->N == 16)
+    hyd::hydro_flux_correct_kernel<16><<<grid, 256, 0, (cudaStream_t)stream>>>(A, B->h, face_flux, dUdt);
+  else
+    hyd::hydro_flux_correct_kernel<8><<<grid, 256, 0, (cudaStream_t)stream>>>(A, B->h, face_flux, dUdt);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 

@@ -10,16 +10,17 @@
 #include "hydro_ctx.h"
 
 namespace hyd {
-cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st);
-cudaError_t launch_step_mixed(const StepArgs64& A, int grid, int planes, cudaStream_t st);
+cudaError_t launch_step_fp64(const StepArgs64& A, int grid, int nn, cudaStream_t st);
+cudaError_t launch_step_mixed(const StepArgs64& A, int grid, int planes, int nn, cudaStream_t st);
 cudaError_t prepare_step_fp64();
 cudaError_t prepare_step_mixed();
 cudaError_t launch_update(const double* U, double* Uout, const double* U0, const double* dUdt, double dt,
                           const double* dt_dev, int stage, double eta2, double gamma, int n_sub, bool mixed,
-                          int num_sms, cudaStream_t st);
+                          int num_sms, int nn, cudaStream_t st);
 cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, double* out, cudaStream_t st);
-cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, cudaStream_t st);
-cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, cudaStream_t st);
+cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, int nn,
+                                 cudaStream_t st);
+cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, int nn, cudaStream_t st);
 cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
                              int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
                              int planes, cudaStream_t st);
@@ -27,7 +28,7 @@ cudaError_t prepare_rk3_fused(int num_sms, int planes, int* max_grid);
 size_t rk3_fused_sync_words(int n_sub);
 cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long limit_ns, cudaStream_t st);
 cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
-                        double* sums, cudaStream_t st);
+                        double* sums, int nn, cudaStream_t st);
 }  // namespace hyd
 
 
@@ -39,6 +40,18 @@ static int cuda_fail(cudaError_t e, const char* where) {
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Cells of a padded sub-grid of the context's layout, and the 8^3 tiles the
+// step kernels process for n_sub sub-grids (one per 8^3 sub-grid, eight
+// octants per 16^3 sub-grid).
+static size_t padded_cells(const hydro_ctx* c) {
+  const size_t s = (size_t)c->N + 2 * hyd::G;
+  return s * s * s;
+}
+static int step_units(const hydro_ctx* c, int n_sub) {
+  const int t = c->N / hyd::N;
+  return n_sub * t * t * t;
+}
 
 static int ensure_status(hydro_ctx* c) {
   if (c->status) return HYDRO_OK;
@@ -122,7 +135,7 @@ int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
 }
 
 int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st) {
-  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED) return HYDRO_EUNSUP;
+  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED || c->N != hyd::N) return HYDRO_EUNSUP;
   if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;
   if (d->bc != HYDRO_BC_PERIODIC && d->bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
   if (!aligned16(d->a.U) || !aligned16(d->U_b) || !aligned16(d->dUdt)) return HYDRO_EINVAL;
@@ -157,7 +170,8 @@ int hydro_ctx_prepare(hydro_ctx* c, int n_sub) {
   int rc = ensure_status(c);
   if (rc) return rc;
   const int slots = 2 * c->num_sms;  // the most any launch uses
-  const int grid = n_sub < slots ? n_sub : slots;
+  const int units = step_units(c, n_sub);
+  const int grid = units < slots ? units : slots;
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
@@ -172,7 +186,7 @@ extern "C" {
 int hydro_create(const hydro_layout_t* L, double gamma, double omega, hydro_ctx_t** out) {
   if (!L || !out) return HYDRO_EINVAL;
   *out = nullptr;
-  if (L->N != hyd::N || L->ghost != hyd::G || L->n_species < 1) return HYDRO_EINVAL;
+  if ((L->N != 8 && L->N != 16) || L->ghost != hyd::G || L->n_species < 1) return HYDRO_EINVAL;
   if (L->n_species != 1) return HYDRO_EUNSUP;
   if (!(gamma > 1.0) || !std::isfinite(gamma) || !std::isfinite(omega)) return HYDRO_EINVAL;
   hydro_ctx* c = new (std::nothrow) hydro_ctx();
@@ -224,13 +238,15 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   int rc = ensure_status(c);
   if (rc) return rc;
   const int slots = step_slots(c, mixed);
-  const int grid = B->n_sub < slots ? B->n_sub : slots;
+  const int units = step_units(c, B->n_sub);
+  const int grid = units < slots ? units : slots;
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
   const hyd::StepArgs64 A = step_args(c, B, dUdt, amax, face_flux);
-  cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, eff_decomp(c) == HYDRO_DECOMP_PLANES, (cudaStream_t)stream)
-                        : hyd::launch_step_fp64(A, grid, (cudaStream_t)stream);
+  cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, eff_decomp(c) == HYDRO_DECOMP_PLANES, c->N,
+                                                  (cudaStream_t)stream)
+                        : hyd::launch_step_fp64(A, grid, c->N, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
   return HYDRO_OK;
 }
@@ -268,14 +284,16 @@ int hydro_autotune_step(hydro_ctx_t* c, const hydro_batch_t* B, double* dUdt, do
     const int per[3] = {c->num_sms, (3 * c->num_sms) / 2, 2 * c->num_sms};
     for (int i = 0; i < 3; ++i)
       if (per[i] <= maxs) cand[nc++] = {HYDRO_DECOMP_ROWS, per[i]};
-    const int rounds = (B->n_sub + maxs - 1) / maxs;
-    cand[nc++] = {HYDRO_DECOMP_ROWS, (B->n_sub + rounds - 1) / rounds};
+    const int units = step_units(c, B->n_sub);
+    const int rounds = (units + maxs - 1) / maxs;
+    cand[nc++] = {HYDRO_DECOMP_ROWS, (units + rounds - 1) / rounds};
   }
   if (planes_ok) {
     const int maxs = c->num_sms;
     cand[nc++] = {HYDRO_DECOMP_PLANES, maxs};
-    const int rounds = (B->n_sub + maxs - 1) / maxs;
-    cand[nc++] = {HYDRO_DECOMP_PLANES, (B->n_sub + rounds - 1) / rounds};
+    const int units = step_units(c, B->n_sub);
+    const int rounds = (units + maxs - 1) / maxs;
+    cand[nc++] = {HYDRO_DECOMP_PLANES, (units + rounds - 1) / rounds};
   }
   const int decomp0 = c->decomp;
   float best = 1e30f;
@@ -339,12 +357,12 @@ int hydro_update(hydro_ctx_t* c, const hydro_batch_t* B, const double* U0, const
   double* out = U_out ? U_out : B->U;
   if (out != B->U) {
     // out of place: the two state buffers may not overlap
-    const size_t bytes = (size_t)B->n_sub * hyd::F * hyd::S3 * sizeof(double);
+    const size_t bytes = (size_t)B->n_sub * hyd::F * padded_cells(c) * sizeof(double);
     const char *a = (const char*)B->U, *b = (const char*)out;
     if (a < b + bytes && b < a + bytes) return HYDRO_EINVAL;
   }
   cudaError_t e = hyd::launch_update(B->U, out, U0, dUdt, dt, dt_dev, stage, c->mode.de_eta2, c->gamma, B->n_sub,
-                                     c->mode.precision == HYDRO_PREC_MIXED, c->num_sms, (cudaStream_t)stream);
+                                     c->mode.precision == HYDRO_PREC_MIXED, c->num_sms, c->N, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_update");
   return HYDRO_OK;
 }
@@ -363,7 +381,7 @@ int hydro_fill_ghosts_uniform(hydro_ctx_t* c, const hydro_batch_t* B, int nbx, i
   if (!c || !B || !B->U) return HYDRO_EINVAL;
   if (nbx <= 0 || nby <= 0 || nbz <= 0 || (long)nbx * nby * nbz != B->n_sub) return HYDRO_EINVAL;
   if (bc != HYDRO_BC_PERIODIC && bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
-  cudaError_t e = hyd::launch_ghost_uniform(B->U, nbx, nby, nbz, bc, c->num_sms, (cudaStream_t)stream);
+  cudaError_t e = hyd::launch_ghost_uniform(B->U, nbx, nby, nbz, bc, c->num_sms, c->N, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_fill_ghosts_uniform");
   return HYDRO_OK;
 }
@@ -396,7 +414,7 @@ static int interior_copy(hydro_ctx_t* c, const hydro_batch_t* B, const double* I
   if (!B->U || !I) return HYDRO_EINVAL;
   double* Id = device_view(I);
   if (!Id || !aligned16(Id)) return HYDRO_EINVAL;
-  cudaError_t e = hyd::launch_interior(B->U, Id, B->n_sub, scatter, c->num_sms, (cudaStream_t)stream);
+  cudaError_t e = hyd::launch_interior(B->U, Id, B->n_sub, scatter, c->num_sms, c->N, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, scatter ? "hydro_scatter_interior" : "hydro_gather_interior");
   return HYDRO_OK;
 }
@@ -414,7 +432,7 @@ int hydro_conserved_sums(hydro_ctx_t* c, const hydro_batch_t* B, double* sums, v
   int rc = ensure_buf(&c->part, &c->part_bytes, (size_t)B->n_sub * (hyd::F + 1) * sizeof(double),
                       "cudaMalloc(sum partials)");
   if (rc) return rc;
-  cudaError_t e = hyd::launch_sums(B->U, B->origin, B->h, B->n_sub, c->part, sums, (cudaStream_t)stream);
+  cudaError_t e = hyd::launch_sums(B->U, B->origin, B->h, B->n_sub, c->part, sums, c->N, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_conserved_sums");
   return HYDRO_OK;
 }

@@ -35,6 +35,60 @@ __device__ __forceinline__ size_t face_index(int s, int f, int q, int pc, int pb
   return ((((size_t)s * 6 + f) * DQ + q) * N + pc) * N + pb;
 }
 
+// ---- sub-grid layouts and their 8^3 tiles ----------------------------------
+// A sub-grid has NN^3 interior cells (NN = 8, the paper's default, or 16)
+// and G ghost layers, stored [F][NN+2G]^3.  The step kernels work on 8^3
+// tiles: the whole sub-grid (NN = 8), or one of the eight octants of a 16^3
+// sub-grid, whose 14^3 window of the padded array -- the octant and its
+// G-deep surround of neighbouring octants' interior cells and ghost cells --
+// is a padded 8^3 sub-grid in place.  Work unit u = s * kTiles + octant,
+// octant = (oz * 2 + oy) * 2 + ox.
+template <int NN>
+struct Tile {
+  static_assert(NN == 8 || NN == 16, "8^3 or 16^3 sub-grids");
+  static constexpr int kN = NN, kS = NN + 2 * G, kS3 = kS * kS * kS, kN3 = NN * NN * NN;
+  static constexpr int kTiles = (NN / N) * (NN / N) * (NN / N);
+  int s;     // the sub-grid
+  int o[3];  // the tile's cell offsets in the sub-grid (0, or N for the upper octants)
+  __device__ __forceinline__ explicit Tile(int u) {
+    s = u / kTiles;
+    const int t = u % kTiles;
+    o[0] = (t & 1) * N;
+    o[1] = ((t >> 1) & 1) * N;
+    o[2] = ((t >> 2) & 1) * N;
+  }
+  // index in the sub-grid's padded array of tile-padded cell (x, y, z) in [0, S)^3
+  __device__ __forceinline__ int pad(int x, int y, int z) const {
+    return ((z + o[2]) * kS + (y + o[1])) * kS + (x + o[0]);
+  }
+  __device__ __forceinline__ int pad(int c) const {
+    return NN == N ? c : pad(c % S, (c / S) % S, c / (S * S));
+  }
+  // index in the sub-grid's compact NN^3 array of tile interior cell c (an 8^3 index)
+  __device__ __forceinline__ int cell(int c) const {
+    return NN == N ? c : (((c / (N * N)) + o[2]) * kN + ((c / N) % N + o[1])) * kN + (c % N + o[0]);
+  }
+  // whether face slot f (2a: lower, 2a + 1: upper face of axis a) of the tile
+  // is a face of the sub-grid
+  __device__ __forceinline__ bool outer(int f) const {
+    return (f & 1) ? o[f >> 1] + N == kN : o[f >> 1] == 0;
+  }
+  // index of boundary-face value q of sub-grid face f at the tile's face cell
+  // (pc, pb) (b < c the face's transverse axes): [n][6][DQ][NN][NN]
+  __device__ __forceinline__ size_t face(int f, int q, int pc, int pb) const {
+    const int a = f >> 1, b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    return ((((size_t)s * 6 + f) * DQ + q) * kN + (pc + o[c])) * kN + (pb + o[b]);
+  }
+};
+
+// Largest of the non-negative doubles in *p and v, atomically (IEEE order of
+// non-negative doubles is the order of their bit patterns): the amax of a
+// sub-grid whose tiles run on different CTAs.  The result does not depend on
+// the order of the updates.
+__device__ __forceinline__ void atomic_max_nonneg(double* p, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+
 struct StepParams {
   double gamma, gm1, omega, eta1;
   int face_points;  // 9: Simpson sum of the 9 face points; 1: the face centre only

@@ -260,6 +260,7 @@ extern "C" {
 
 int hydro_gate_data(hydro_ctx_t* c, const hydro_batch_t* B, float* X, uint8_t* y, void* stream) {
   if (!c || !B || B->n_sub < 0 || (!X && !y)) return HYDRO_EINVAL;
+  if (c->N != hyd::N) return HYDRO_EUNSUP;
   if (B->n_sub == 0) return HYDRO_OK;
   if (!B->U) return HYDRO_EINVAL;
   const size_t smem = (size_t)hyd::F * hyd::S3 * sizeof(float);

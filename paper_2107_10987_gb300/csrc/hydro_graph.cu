@@ -50,11 +50,12 @@ static int rk3_enqueue(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, 
   return HYDRO_OK;
 }
 
-static bool desc_ok(const hydro_rk3_desc_t* d) {
+static bool desc_ok(const hydro_ctx_t* ctx, const hydro_rk3_desc_t* d) {
   if (!(d && d->a.U && d->U_b && d->a.origin && d->a.h && d->dUdt && d->amax && d->dt && d->a.n_sub > 0))
     return false;
   // the two state buffers may not overlap: each stage reads one and writes the other
-  const size_t bytes = (size_t)d->a.n_sub * hyd::F * hyd::S3 * sizeof(double);
+  const size_t sp = (size_t)ctx->N + 2 * hyd::G;
+  const size_t bytes = (size_t)d->a.n_sub * hyd::F * sp * sp * sp * sizeof(double);
   const char *a = (const char*)d->a.U, *b = (const char*)d->U_b;
   if (a < b + bytes && b < a + bytes) return false;
   if (d->amr) return d->face_flux != nullptr;
@@ -64,12 +65,12 @@ static bool desc_ok(const hydro_rk3_desc_t* d) {
 extern "C" {
 
 int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream) {
-  if (!ctx || !desc_ok(d) || (parity != 0 && parity != 1)) return HYDRO_EINVAL;
+  if (!ctx || !desc_ok(ctx, d) || (parity != 0 && parity != 1)) return HYDRO_EINVAL;
   return rk3_enqueue(ctx, d, parity, (cudaStream_t)stream);
 }
 
 int hydro_rk3_graph_create(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, hydro_graph_t** out) {
-  if (!ctx || !out || !desc_ok(d)) return HYDRO_EINVAL;
+  if (!ctx || !out || !desc_ok(ctx, d)) return HYDRO_EINVAL;
   *out = nullptr;
   hydro_graph* g = new (std::nothrow) hydro_graph();
   if (!g) return HYDRO_ENOMEM;

@@ -30,14 +30,18 @@ constexpr int kThreadsMx = NROW;  // 192
 // centre coordinates x_c, y_c of the reconstructed cells (sub_coords).
 constexpr size_t kMixedSmemBytes = (size_t)F * S3 * sizeof(float) + 2 * S3 + 2 * (N + 2) * sizeof(float);
 
-// The FP32 x and y cell-centre coordinates of the cells -1 .. N of a
-// sub-grid, x_c = fl(o + h (i + 1/2)) (an FP64 fma rounded once to FP32),
-// coord[a * (N + 2) + i + 1]: computed once per sub-grid instead of at every
-// quadrature point (the FP64 pipe is 1/64 of the FP32 rate).  Threads
-// 0 .. 2(N+2)-1 write; the caller's next barrier publishes them.
-__device__ __forceinline__ void sub_coords(float* coord, double hd, const double* origin) {
+// The FP32 x and y cell-centre coordinates of the cells -1 .. N of a tile
+// (cell offsets offx, offy in its sub-grid), x_c = fl(o + h (off + i + 1/2))
+// (an FP64 fma rounded once to FP32), coord[a * (N + 2) + i + 1]: computed
+// once per tile instead of at every quadrature point (the FP64 pipe is 1/64
+// of the FP32 rate).  Threads 0 .. 2(N+2)-1 write; the caller's next barrier
+// publishes them.
+__device__ __forceinline__ void sub_coords(float* coord, double hd, double ox, double oy, int offx, int offy) {
   const int t = threadIdx.x;
-  if (t < 2 * (N + 2)) coord[t] = (float)fma(hd, (t % (N + 2) - 1) + 0.5, origin[t / (N + 2)]);
+  if (t < 2 * (N + 2)) {
+    const bool y = t >= N + 2;
+    coord[t] = (float)fma(hd, (t % (N + 2) - 1 + (y ? offy : offx)) + 0.5, y ? oy : ox);
+  }
 }
 
 // This thread's row: axis a, transverse axes b < cx at positions pb, pc.
@@ -63,17 +67,18 @@ __device__ __forceinline__ RowMap row_map(int tid) {
   return R;
 }
 
-// The end of one interior cell (x, y, z) of sub-grid s (compact index c,
-// padded index uc): dU/dt from its per-axis differences of face sums,
+// The end of one interior cell (x, y, z) of a tile (its compact index c and
+// padded index uc are the tile's; offx, offy: the tile's cell offsets in its
+// sub-grid): dU/dt from its per-axis differences of face sums,
 // D_a[q] = Fbar_a(i+1/2) - Fbar_a(i-1/2) for the F fluxes and the torque
 // differences for q >= F (FP64), summed as (D_x + D_y) + D_z: s01(q) gives
 // D_x + D_y, d2(q) gives D_z.  Then the rotating-frame, spin and gravity
 // sources, and io.store.  Every operation is explicitly rounded or fused,
 // so that both sub-grid decompositions and every kernel give the same bits.
 template <class Io, class S01, class D2>
-__device__ __forceinline__ void finish_cell(const StepArgs64& A, const Io& io, const typename Io::Sub& sub, int s,
-                                            int x, int y, int z, const S01& s01, const D2& d2, double hd,
-                                            double inv_h, const double o[3]) {
+__device__ __forceinline__ void finish_cell(const StepArgs64& A, const Io& io, const typename Io::Sub& sub,
+                                            int offx, int offy, int x, int y, int z, const S01& s01, const D2& d2,
+                                            double hd, double inv_h, const double o[3]) {
   const int c = (z * N + y) * N + x;
   const int uc = ((z + G) * S + (y + G)) * S + (x + G);
   const double om = A.P.omega;
@@ -95,16 +100,16 @@ __device__ __forceinline__ void finish_cell(const StepArgs64& A, const Io& io, c
     // spin source w(x_c) x s, w = -omega z_hat x x_c: removes the torque
     // that the frame part s w_n of the momentum flux leaves in the face
     // torques, so that sum (x_c x s + z)_z is conserved for omega != 0
-    const double xc = __dadd_rn(o[0], __dmul_rn(hd, x + 0.5));
-    const double yc = __dadd_rn(o[1], __dmul_rn(hd, y + 0.5));
+    const double xc = __dadd_rn(o[0], __dmul_rn(hd, (x + offx) + 0.5));
+    const double yc = __dadd_rn(o[1], __dmul_rn(hd, (y + offy) + 0.5));
     const double wx = __dmul_rn(om, yc), wy = -__dmul_rn(om, xc);
     du[ZX] = fma(wy, sz, du[ZX]);
     du[ZY] = fma(-wx, sz, du[ZY]);
     du[ZZ] = __dadd_rn(du[ZZ], fma(wx, sy, -__dmul_rn(wy, sx)));
   }
   if (A.g) {
-    const double* gs = A.g + (size_t)s * 3 * N3;
-    const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];
+    double gx, gy, gz;
+    io.grav(sub, c, gx, gy, gz);
     const double rho = uin[RHO];
     du[SX] = fma(rho, gx, du[SX]);
     du[SY] = fma(rho, gy, du[SY]);
@@ -114,12 +119,18 @@ __device__ __forceinline__ void finish_cell(const StepArgs64& A, const Io& io, c
   io.store(sub, c, uc, du, uin);
 }
 
-// One sub-grid s.  Io supplies the state and takes the results:
-//   typename Io::Sub io.begin(s)                    per-sub-grid context
+// One 8^3 tile (a sub-grid, or an octant of a 16^3 sub-grid) of work unit s.
+// Io supplies the state and takes the results; all cell indices are the
+// tile's own (padded 14^3, interior 8^3):
+//   typename Io::Sub io.begin(s)                    per-unit context
+//   io.sidx(sub), io.offx(sub), io.offy(sub)  the sub-grid (for h, origin)
+//                             and the tile's x and y cell offsets in it
 //   io.load(sub, c, u)        conserved state u[F] of padded cell c
 //   io.own(sub, c, uc, u)     conserved state of interior cell c (padded index uc)
 //   io.store(sub, c, uc, du, u)  dU/dt of interior cell c; u is its state from own()
-//   io.amax(sub, m)           the sub-grid's maximum signal speed (thread 0)
+//   io.grav(sub, c, gx, gy, gz)  gravity at interior cell c
+//   io.face(sub, f, q, pc, pb, v)  boundary-face value (tile face f)
+//   io.amax(sub, m)           the tile's maximum signal speed (thread 0)
 // Qf: the CTA's dynamic shared memory; red: [kThreadsMx / 32] floats of
 // shared memory; D: the CTA's scratch (kScratchPerSub doubles).  Ends with
 // a barrier, so the next sub-grid may reuse all of them.
@@ -133,9 +144,10 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
   const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega};
   const int a = R.a, b = R.b, pb = R.pb, pc = R.pc, sa = R.sa, sb = R.sb, sc = R.sc;
   const typename Io::Sub sub = io.begin(s);
-  const double hd = A.h[s];
-  const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
-  sub_coords(coord, hd, o);
+  const int si = io.sidx(sub), offx = io.offx(sub), offy = io.offy(sub);
+  const double hd = A.h[si];
+  const double o[3] = {A.origin[3 * si + 0], A.origin[3 * si + 1], A.origin[3 * si + 2]};
+  sub_coords(coord, hd, o[0], o[1], offx, offy);
 
   // ---- 1-2. load the FP64 state, recover primitives, store FP32 ---------
   bool bad = false;
@@ -257,12 +269,12 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
 #pragma unroll
       for (int m = 0; m < 3; ++m) trprev[m] = (double)Str[m];
       if (A.face_flux && (j == 0 || j == N)) {
-        // sub-grid boundary face: sums and the torque about the interior cell
+        // tile boundary face: sums and the torque about the interior cell
         const int f = 2 * a + (j == N ? 1 : 0);
 #pragma unroll
-        for (int k = 0; k < F; ++k) A.face_flux[face_index(s, f, k, pc, pb)] = fd[k];
+        for (int k = 0; k < F; ++k) io.face(sub, f, k, pc, pb, fd[k]);
 #pragma unroll
-        for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = j == N ? tld[m] : trprev[m];
+        for (int m = 0; m < 3; ++m) io.face(sub, f, F + m, pc, pb, j == N ? tld[m] : trprev[m]);
       }
     }
   }
@@ -276,7 +288,7 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
   for (int c = tid; c < N3; c += kThreadsMx) {
     const int x = c % N, y = (c / N) % N, z = c / (N * N);
     finish_cell(
-        A, io, sub, s, x, y, z,
+        A, io, sub, offx, offy, x, y, z,
         [&](int q) { return __dadd_rn(D[(0 * DQ + q) * N3 + c], D[(1 * DQ + q) * N3 + c]); },
         [&](int q) { return D[(2 * DQ + q) * N3 + c]; }, hd, inv_h, o);
   }

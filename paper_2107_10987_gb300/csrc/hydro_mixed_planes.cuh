@@ -121,7 +121,7 @@ __device__ __forceinline__ void plane_line(const float* __restrict__ ring, int i
   }
 }
 
-// One sub-grid s as a plane sweep; Io as for mixed_subgrid, plus
+// One 8^3 tile (work unit s) as a plane sweep; Io as for mixed_subgrid, plus
 //   io.load_fields(sub, c, f0, nf, u)   fields f0 .. f0+nf-1 of padded cell c
 // (nf <= 5).  sm: the CTA's dynamic shared memory (kPlaneSmemBytes).  Ends
 // with a barrier.  Must be called by all kThreadsPl threads.
@@ -140,9 +140,10 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega};
   const typename Io::Sub sub = io.begin(s);
-  const double hd = A.h[s];
+  const int si = io.sidx(sub), offx = io.offx(sub), offy = io.offy(sub);
+  const double hd = A.h[si];
   const float h = (float)hd, half_h = 0.5f * h;
-  const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
+  const double o[3] = {A.origin[3 * si + 0], A.origin[3 * si + 1], A.origin[3 * si + 2]};
   const double inv_h = 1.0 / hd;
   const int npt = A.P.face_points;
   float amax = 0.f;
@@ -157,7 +158,7 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
     for (int f = 0; f < F; ++f) dst[f * kPl] = pq[f];
   };
 
-  sub_coords(coord, hd, o);
+  sub_coords(coord, hd, o[0], o[1], offx, offy);
 
   // dU/dt of plane p (its z-differences from the face sums of p - 1/2 and
   // p + 1/2, the x- plus y-differences from phase C, finish_cell), on the
@@ -169,7 +170,7 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
     const double* zu = zsum + (size_t)((p + 1) % 3) * 16 * N * N + c2;  // face p+1/2: upper face of p
     const double* zl = zsum + (size_t)(p % 3) * 16 * N * N + c2;        // face p-1/2: lower face of p
     finish_cell(
-        A, io, sub, s, c2 % N, c2 / N, p, [&](int q) { return a01[q * N * N]; },
+        A, io, sub, offx, offy, c2 % N, c2 / N, p, [&](int q) { return a01[q * N * N]; },
         [&](int q) { return __dsub_rn(zu[q * N * N], zl[(q < F ? q : q + 3) * N * N]); }, hd, inv_h, o);
   };
 
@@ -361,10 +362,9 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
           }
           if (f >= 0) {
 #pragma unroll
-            for (int q = 0; q < F; ++q) A.face_flux[face_index(s, f, q, pc, pb)] = dst[q * dstride];
+            for (int q = 0; q < F; ++q) io.face(sub, f, q, pc, pb, dst[q * dstride]);
 #pragma unroll
-            for (int m = 0; m < 3; ++m)
-              A.face_flux[face_index(s, f, F + m, pc, pb)] = dst[(upper ? F + m : F + 3 + m) * dstride];
+            for (int m = 0; m < 3; ++m) io.face(sub, f, F + m, pc, pb, dst[(upper ? F + m : F + 3 + m) * dstride]);
           }
         }
       }

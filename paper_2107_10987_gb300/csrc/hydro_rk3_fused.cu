@@ -58,6 +58,17 @@ struct FusedIo {
   __device__ __forceinline__ Sub begin(int s) const {
     return Sub{s, s % A.nbx, (s / A.nbx) % A.nby, s / (A.nbx * A.nby)};
   }
+  __device__ __forceinline__ int sidx(const Sub& q) const { return q.s; }
+  __device__ __forceinline__ int offx(const Sub&) const { return 0; }
+  __device__ __forceinline__ int offy(const Sub&) const { return 0; }
+  __device__ __forceinline__ void grav(const Sub& q, int c, double& gx, double& gy, double& gz) const {
+    const double* gs = A.S.g + (size_t)q.s * 3 * N3 + c;
+    gx = gs[0];
+    gy = gs[N3];
+    gz = gs[2 * N3];
+  }
+  // the fused step exports no boundary faces (uniform meshes only)
+  __device__ __forceinline__ void face(const Sub&, int, int, int, int, double) const {}
   // Stage input state of interior cell (os; oi compact, op padded index):
   // fields f0 .. f0 + nf - 1 into u[0 .. nf-1].
   __device__ __forceinline__ void state(int os, int oi, int op, double* u, int f0 = 0, int nf = F) const {

@@ -242,9 +242,12 @@ constexpr long kWaitPolls = 1L << 24;
 // kGate: the learned smoothness indicator is on (A.gate): its decisions per
 // reconstructed cell follow the primitives in shared memory ([S3] bytes of
 // flags and [S3] of predictions after the state).  kContact: contact
-// steepening (A.P.contact; not combined with the indicator).
-template <bool kGate, bool kContact = false>
+// steepening (A.P.contact; not combined with the indicator).  NN: the
+// sub-grids' edge (8, or 16: each 8^3 octant tile is a work unit staged from
+// its 14^3 window of the 22^3 array, Tile<NN>).
+template <bool kGate, bool kContact = false, int NN = N>
 __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs64 A) {
+  using T = Tile<NN>;
   extern __shared__ __align__(128) double Q[];  // [F][S3], then the indicator's flags
   uint8_t* smooth = reinterpret_cast<uint8_t*>(Q + F * S3);
   __shared__ __align__(8) uint64_t bar;
@@ -274,14 +277,33 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
   const int sa = axis_stride(a), sb = axis_stride(b), sc = axis_stride(cx);
 
   uint32_t phase = 0;
-  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
-    // ---- 1. stage the sub-grid into shared memory (bulk TMA) ------------
-    if (tid == 0) {
-      fence_proxy_async();
-      mbar_expect_tx(&bar, (uint32_t)(F * S3 * sizeof(double)));
-      const double* src = A.U + (size_t)s * F * S3;
+  for (int u = blockIdx.x; u < A.n_sub * T::kTiles; u += gridDim.x) {
+    const T tile(u);
+    const int s = tile.s;
+    // ---- 1. stage the tile into shared memory (bulk TMA) ----------------
+    // 8^3 sub-grid: one copy per field of its contiguous padded block; 16^3
+    // octant: one copy per (field, z, y) row of its 14^3 window (112 bytes,
+    // 16-byte aligned: the octant offsets are 0 or 8 cells), issued by the
+    // 32 lanes of warp 0 after lane 0 has announced the total.
+    if (tid < 32) {
+      if (tid == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&bar, (uint32_t)(F * S3 * sizeof(double)));
+      }
+      __syncwarp();
+      const double* src = A.U + (size_t)s * F * T::kS3;
+      if (NN == N) {
+        if (tid == 0)
 #pragma unroll 1
-      for (int k = 0; k < F; ++k) bulk_g2s(Q + k * S3, src + (size_t)k * S3, S3 * sizeof(double), &bar);
+          for (int k = 0; k < F; ++k) bulk_g2s(Q + k * S3, src + (size_t)k * S3, S3 * sizeof(double), &bar);
+      } else {
+#pragma unroll 1
+        for (int r = tid; r < F * S * S; r += 32) {
+          const int k = r / (S * S), z = (r / S) % S, y = r % S;
+          bulk_g2s(Q + k * S3 + (z * S + y) * S, src + (size_t)k * T::kS3 + tile.pad(0, y, z), S * sizeof(double),
+                   &bar);
+        }
+      }
     }
     if (!mbar_wait_bounded(&bar, phase, kWaitPolls)) {
       atomicOr(A.status, 2u);
@@ -315,6 +337,7 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
                                      smooth + S3);
 
     // ---- 3. row sweep ------------------------------------------------------
+    const int ox = tile.o[0], oy = tile.o[1];
     const double h = A.h[s];
     const double half_h = 0.5 * h;
     const double o[3] = {A.origin[3 * s + 0], A.origin[3 * s + 1], A.origin[3 * s + 2]};
@@ -333,7 +356,7 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
       tl[0] = tl[1] = tl[2] = 0.0;
       tr[0] = tr[1] = tr[2] = 0.0;
       // left cell of face j-1/2 is (j-1) along a
-      const int ci0 = axis_comp(0, a, b, j - 1, pb, pc), ci1 = axis_comp(1, a, b, j - 1, pb, pc);
+      const int ci0 = axis_comp(0, a, b, j - 1, pb, pc) + ox, ci1 = axis_comp(1, a, b, j - 1, pb, pc) + oy;
       // the 9 face points as 4 mirrored pairs and the centre (p = 4); with one
       // flux point per face (the old module) only the centre
 #pragma unroll 1
@@ -394,13 +417,13 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
         trprev[1] = tr[1];
         trprev[2] = tr[2];
       }
-      if (A.face_flux && (j == 0 || j == N)) {
+      if (A.face_flux && (j == 0 || j == N) && tile.outer(2 * a + (j == N ? 1 : 0))) {
         // sub-grid boundary face: sums and the torque about the interior cell
         const int f = 2 * a + (j == N ? 1 : 0);
 #pragma unroll
-        for (int k = 0; k < F; ++k) A.face_flux[face_index(s, f, k, pc, pb)] = fsum[k];
+        for (int k = 0; k < F; ++k) A.face_flux[tile.face(f, k, pc, pb)] = fsum[k];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) A.face_flux[face_index(s, f, F + m, pc, pb)] = (j == N) ? tl[m] : tr[m];
+        for (int m = 0; m < 3; ++m) A.face_flux[tile.face(f, F + m, pc, pb)] = (j == N) ? tl[m] : tr[m];
       }
     }
     // block-wide amax; order the generic-proxy shared-memory accesses of this
@@ -413,11 +436,12 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
     // ---- 4. divergence + sources, one thread per interior cell -----------
     const double inv_h = 1.0 / h;
     const double om = A.P.omega;
-    const double* Us = A.U + (size_t)s * F * S3;
-    double* dU = A.dUdt + (size_t)s * F * N3;
+    const double* Us = A.U + (size_t)s * F * T::kS3;
+    double* dU = A.dUdt + (size_t)s * F * T::kN3;
     for (int c = tid; c < N3; c += kThreads64) {
       const int x = c % N, y = (c / N) % N, z = c / (N * N);
-      const int uc = ((z + G) * S + (y + G)) * S + (x + G);
+      const int uc = tile.pad(x + G, y + G, z + G);  // in the sub-grid's padded array
+      const int cs = tile.cell(c);                   // in its compact NN^3 array
       double du[F];
 #pragma unroll
       for (int k = 0; k < F; ++k) {
@@ -430,39 +454,42 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
             (D[(0 * DQ + F + m) * N3 + c] + D[(1 * DQ + F + m) * N3 + c]) + D[(2 * DQ + F + m) * N3 + c];
         du[ZX + m] = du[ZX + m] - tq * inv_h;
       }
-      const double sx = Us[SX * S3 + uc], sy = Us[SY * S3 + uc], sz = Us[SZ * S3 + uc];
+      const double sx = Us[SX * T::kS3 + uc], sy = Us[SY * T::kS3 + uc], sz = Us[SZ * T::kS3 + uc];
       du[SX] = du[SX] + om * sy;
       du[SY] = du[SY] - om * sx;
-      du[ZX] = du[ZX] + om * Us[ZY * S3 + uc];
-      du[ZY] = du[ZY] - om * Us[ZX * S3 + uc];
+      du[ZX] = du[ZX] + om * Us[ZY * T::kS3 + uc];
+      du[ZY] = du[ZY] - om * Us[ZX * T::kS3 + uc];
       {
         // spin source w(x_c) x s, w = -omega z_hat x x_c: removes the torque
         // that the frame part s w_n of the momentum flux leaves in the face
         // torques, so that sum (x_c x s + z)_z is conserved for omega != 0
-        const double xc = __dadd_rn(o[0], __dmul_rn(h, x + 0.5));
-        const double yc = __dadd_rn(o[1], __dmul_rn(h, y + 0.5));
+        const double xc = __dadd_rn(o[0], __dmul_rn(h, (x + ox) + 0.5));
+        const double yc = __dadd_rn(o[1], __dmul_rn(h, (y + oy) + 0.5));
         const double wx = om * yc, wy = -(om * xc);
         du[ZX] = du[ZX] + wy * sz;
         du[ZY] = du[ZY] - wx * sz;
         du[ZZ] = du[ZZ] + (wx * sy - wy * sx);
       }
       if (A.g) {
-        const double* gs = A.g + (size_t)s * 3 * N3;
-        const double gx = gs[c], gy = gs[N3 + c], gz = gs[2 * N3 + c];
-        const double rho = Us[RHO * S3 + uc];
+        const double* gs = A.g + (size_t)s * 3 * T::kN3 + cs;
+        const double gx = gs[0], gy = gs[T::kN3], gz = gs[2 * T::kN3];
+        const double rho = Us[RHO * T::kS3 + uc];
         du[SX] = du[SX] + rho * gx;
         du[SY] = du[SY] + rho * gy;
         du[SZ] = du[SZ] + rho * gz;
         du[EGAS] = du[EGAS] + ((sx * gx + sy * gy) + sz * gz);
       }
 #pragma unroll
-      for (int k = 0; k < F; ++k) dU[k * N3 + c] = du[k];
+      for (int k = 0; k < F; ++k) dU[k * T::kN3 + cs] = du[k];
     }
     if (tid == 0) {
       double m = red[0];
 #pragma unroll
       for (int w = 1; w < kThreads64 / 32; ++w) m = fmax(m, red[w]);
-      A.amax[s] = m;
+      if (T::kTiles == 1)
+        A.amax[s] = m;
+      else
+        atomic_max_nonneg(A.amax + s, m);  // cleared before the launch
     }
     __syncthreads();  // scratch and red reused by the next sub-grid
   }
@@ -474,30 +501,50 @@ size_t step_fp64_smem_bytes(bool gate = false) { return (size_t)F * S3 * sizeof(
 
 // Opt in to the kernel's dynamic shared memory once per device (no
 // allocation; call before any stream capture).
+template <int NN>
+static cudaError_t fp64_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false, false, NN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_fp64_smem_bytes(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(hydro_step_fp64_kernel<true, false, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_fp64_smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false, true, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_fp64_smem_bytes(false));
+  return e;
+}
+
 cudaError_t prepare_step_fp64() {
   static unsigned long long done = 0;
   return once_per_device(&done, [] {
-    cudaError_t e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_fp64_smem_bytes(false));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(hydro_step_fp64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)step_fp64_smem_bytes(true));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)step_fp64_smem_bytes(false));
-    return e;
+    cudaError_t e = fp64_attrs<8>();
+    return e == cudaSuccess ? fp64_attrs<16>() : e;
   });
 }
 
-cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st) {
+template <int NN>
+static void launch_fp64_nn(const StepArgs64& A, int grid, cudaStream_t st) {
+  if (A.gate)
+    hydro_step_fp64_kernel<true, false, NN><<<grid, kThreads64, step_fp64_smem_bytes(true), st>>>(A);
+  else if (A.P.contact)
+    hydro_step_fp64_kernel<false, true, NN><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);
+  else
+    hydro_step_fp64_kernel<false, false, NN><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);
+}
+
+// nn: the sub-grids' edge (8 or 16); grid: persistent CTAs over the
+// A.n_sub * (nn/8)^3 tiles.  With 16^3 sub-grids the amax of a sub-grid is
+// the atomic maximum over its tiles, cleared here first.
+cudaError_t launch_step_fp64(const StepArgs64& A, int grid, int nn, cudaStream_t st) {
   cudaError_t e = prepare_step_fp64();
   if (e != cudaSuccess) return e;
-  if (A.gate)
-    hydro_step_fp64_kernel<true><<<grid, kThreads64, step_fp64_smem_bytes(true), st>>>(A);
-  else if (A.P.contact)
-    hydro_step_fp64_kernel<false, true><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);
-  else
-    hydro_step_fp64_kernel<false><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);
+  if (nn == 16) {
+    e = cudaMemsetAsync(A.amax, 0, (size_t)A.n_sub * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    launch_fp64_nn<16>(A, grid, st);
+  } else {
+    launch_fp64_nn<8>(A, grid, st);
+  }
   return cudaGetLastError();
 }
 

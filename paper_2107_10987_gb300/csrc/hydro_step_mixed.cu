@@ -8,100 +8,129 @@
 
 namespace hyd {
 
-// Padded state in, dU/dt and amax out.  Holds a reference to the kernel's
-// parameters, so its pointers stay in the parameter bank (no registers).
+// Padded state in, dU/dt and amax out, for the 8^3 tiles of NN^3 sub-grids
+// (Tile).  Holds a reference to the kernel's parameters, so its pointers
+// stay in the parameter bank (no registers).
+template <int NN>
 struct StepIo {
+  using T = Tile<NN>;
   const StepArgs64& A;
-  struct Sub {
-    int s;
-  };
-  __device__ __forceinline__ Sub begin(int s) const { return Sub{s}; }
-  __device__ __forceinline__ void load(const Sub& q, int c, double u[F]) const {
-    const double* __restrict__ Us = A.U + (size_t)q.s * F * S3;
-#pragma unroll
-    for (int k = 0; k < F; ++k) u[k] = __ldg(Us + (size_t)k * S3 + c);
-  }
+  using Sub = T;
+  __device__ __forceinline__ Sub begin(int u) const { return T(u); }
+  __device__ __forceinline__ int sidx(const Sub& q) const { return q.s; }
+  __device__ __forceinline__ int offx(const Sub& q) const { return q.o[0]; }
+  __device__ __forceinline__ int offy(const Sub& q) const { return q.o[1]; }
+  __device__ __forceinline__ void load(const Sub& q, int c, double u[F]) const { load_fields(q, c, 0, F, u); }
   __device__ __forceinline__ void load_fields(const Sub& q, int c, int f0, int nf, double* u) const {
-    const double* __restrict__ Us = A.U + (size_t)q.s * F * S3 + (size_t)f0 * S3 + c;
+    const double* __restrict__ Us = A.U + (size_t)q.s * F * T::kS3 + (size_t)f0 * T::kS3 + q.pad(c);
 #pragma unroll
-    for (int k = 0; k < nf; ++k) u[k] = __ldg(Us + (size_t)k * S3);
+    for (int k = 0; k < nf; ++k) u[k] = __ldg(Us + (size_t)k * T::kS3);
   }
   // only the fields the sources read (rho, s, z_x, z_y)
   __device__ __forceinline__ void own(const Sub& q, int, int uc, double u[F]) const {
-    const double* __restrict__ Us = A.U + (size_t)q.s * F * S3;
+    const double* __restrict__ Us = A.U + (size_t)q.s * F * T::kS3 + q.pad(uc);
 #pragma unroll
-    for (int k = 0; k < F; ++k) u[k] = (k <= SZ || k == ZX || k == ZY) ? __ldg(Us + (size_t)k * S3 + uc) : 0.0;
+    for (int k = 0; k < F; ++k) u[k] = (k <= SZ || k == ZX || k == ZY) ? __ldg(Us + (size_t)k * T::kS3) : 0.0;
   }
   __device__ __forceinline__ void store(const Sub& q, int c, int, const double du[F], const double*) const {
-    double* dU = A.dUdt + (size_t)q.s * F * N3;
+    double* dU = A.dUdt + (size_t)q.s * F * T::kN3 + q.cell(c);
 #pragma unroll
-    for (int k = 0; k < F; ++k) dU[k * N3 + c] = du[k];
+    for (int k = 0; k < F; ++k) dU[(size_t)k * T::kN3] = du[k];
   }
-  __device__ __forceinline__ void amax(const Sub& q, double m) const { A.amax[q.s] = m; }
+  __device__ __forceinline__ void grav(const Sub& q, int c, double& gx, double& gy, double& gz) const {
+    const double* gs = A.g + (size_t)q.s * 3 * T::kN3 + q.cell(c);
+    gx = gs[0];
+    gy = gs[T::kN3];
+    gz = gs[2 * T::kN3];
+  }
+  __device__ __forceinline__ void face(const Sub& q, int f, int k, int pc, int pb, double v) const {
+    if (q.outer(f)) A.face_flux[q.face(f, k, pc, pb)] = v;
+  }
+  __device__ __forceinline__ void amax(const Sub& q, double m) const {
+    if (T::kTiles == 1)
+      A.amax[q.s] = m;
+    else
+      atomic_max_nonneg(A.amax + q.s, m);  // cleared before the launch
+  }
 };
 
 // kGate: the learned smoothness indicator is on (A.gate); the kernel without
 // it carries none of the indicator's registers.  kContact: contact
 // steepening (A.P.contact; not combined with the indicator).
-template <bool kGate, bool kContact = false>
+template <bool kGate, bool kContact = false, int NN = N>
 __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArgs64 A) {
   extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [2][S3] smooth flags
   __shared__ float red[kThreadsMx / 32];
   double* __restrict__ D = A.scratch + (size_t)blockIdx.x * kScratchPerSub;
   const RowMap R = row_map(threadIdx.x);
-  const StepIo io{A};
-  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) mixed_subgrid<kGate, kContact>(A, io, s, R, Qf, red, D);
+  const StepIo<NN> io{A};
+  const int units = A.n_sub * Tile<NN>::kTiles;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) mixed_subgrid<kGate, kContact>(A, io, u, R, Qf, red, D);
 }
 
 // The plane sweep: one CTA of kThreadsPl threads per SM (no indicator).
-template <bool kContact>
+template <bool kContact, int NN = N>
 __global__ void __launch_bounds__(kThreadsPl, 1) hydro_step_mixed_planes_kernel(StepArgs64 A) {
   extern __shared__ __align__(128) unsigned char sm[];
-  const StepIo io{A};
-  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) mixed_subgrid_planes<kContact>(A, io, s, sm);
+  const StepIo<NN> io{A};
+  const int units = A.n_sub * Tile<NN>::kTiles;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) mixed_subgrid_planes<kContact>(A, io, u, sm);
 }
 
 size_t step_mixed_smem_bytes() { return kMixedSmemBytes; }
+
+template <int NN>
+static cudaError_t mixed_attrs() {
+  const int rows = (int)step_mixed_smem_bytes(), planes = (int)kPlaneSmemBytes;
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, false, NN>, at, rows);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true, false, NN>, at, rows);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, true, NN>, at, rows);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<false, NN>, at, planes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<true, NN>, at, planes);
+  return e;
+}
 
 // Opt in to the kernels' dynamic shared memory once per device (no
 // allocation; call before any stream capture).
 cudaError_t prepare_step_mixed() {
   static unsigned long long done = 0;
   return once_per_device(&done, [] {
-    cudaError_t e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_mixed_smem_bytes());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)step_mixed_smem_bytes());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)step_mixed_smem_bytes());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kPlaneSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kPlaneSmemBytes);
-    return e;
+    cudaError_t e = mixed_attrs<8>();
+    return e == cudaSuccess ? mixed_attrs<16>() : e;
   });
 }
 
-// planes: the plane-sweep decomposition (grid: CTAs, at most one per SM);
-// the learned indicator always runs in the row sweep.
-cudaError_t launch_step_mixed(const StepArgs64& A, int grid, int planes, cudaStream_t st) {
-  cudaError_t e = prepare_step_mixed();
-  if (e != cudaSuccess) return e;
+template <int NN>
+static void launch_mixed_nn(const StepArgs64& A, int grid, int planes, cudaStream_t st) {
   if (planes && !A.gate) {
     if (A.P.contact)
-      hydro_step_mixed_planes_kernel<true><<<grid, kThreadsPl, kPlaneSmemBytes, st>>>(A);
+      hydro_step_mixed_planes_kernel<true, NN><<<grid, kThreadsPl, kPlaneSmemBytes, st>>>(A);
     else
-      hydro_step_mixed_planes_kernel<false><<<grid, kThreadsPl, kPlaneSmemBytes, st>>>(A);
+      hydro_step_mixed_planes_kernel<false, NN><<<grid, kThreadsPl, kPlaneSmemBytes, st>>>(A);
   } else if (A.gate) {
-    hydro_step_mixed_kernel<true><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+    hydro_step_mixed_kernel<true, false, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   } else if (A.P.contact) {
-    hydro_step_mixed_kernel<false, true><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+    hydro_step_mixed_kernel<false, true, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   } else {
-    hydro_step_mixed_kernel<false><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+    hydro_step_mixed_kernel<false, false, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+  }
+}
+
+// planes: the plane-sweep decomposition (grid: CTAs, at most one per SM);
+// the learned indicator always runs in the row sweep.  nn: the sub-grids'
+// edge (8 or 16); the persistent CTAs loop over A.n_sub * (nn/8)^3 tiles,
+// and with 16^3 sub-grids the amax of a sub-grid is the atomic maximum over
+// its tiles, cleared here first.
+cudaError_t launch_step_mixed(const StepArgs64& A, int grid, int planes, int nn, cudaStream_t st) {
+  cudaError_t e = prepare_step_mixed();
+  if (e != cudaSuccess) return e;
+  if (nn == 16) {
+    e = cudaMemsetAsync(A.amax, 0, (size_t)A.n_sub * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    launch_mixed_nn<16>(A, grid, planes, st);
+  } else {
+    launch_mixed_nn<8>(A, grid, planes, st);
   }
   return cudaGetLastError();
 }

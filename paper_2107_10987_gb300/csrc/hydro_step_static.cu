@@ -28,7 +28,7 @@
 #include "hydro_ctx.h"
 
 namespace hyd {
-cudaError_t launch_step_fp64(const StepArgs64& A, int grid, cudaStream_t st);
+cudaError_t launch_step_fp64(const StepArgs64& A, int grid, int nn, cudaStream_t st);
 }
 
 namespace {
@@ -75,7 +75,7 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   if (B->n_sub == 0) return HYDRO_OK;
   if (!B->U || !B->origin || !B->h || !dUdt || !amax) return HYDRO_EINVAL;
   if ((((uintptr_t)B->U) & 15u) || (((uintptr_t)dUdt) & 15u)) return HYDRO_EINVAL;
-  if (c->mode.precision != HYDRO_PREC_FP64) return HYDRO_EUNSUP;
+  if (c->mode.precision != HYDRO_PREC_FP64 || c->N != hyd::N) return HYDRO_EUNSUP;
   if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;  // as hydro_step
   DeviceAddrs a;
   int rc = addrs_for_current_device(&a);
@@ -107,6 +107,6 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.gate_w = c->gate_w;
   A.gate_logit_thr = (float)c->gate_logit_thr;
   A.gate_zero_smooth = c->gate_zero_smooth;
-  if (hyd::launch_step_fp64(A, B->n_sub, st) != cudaSuccess) return HYDRO_ECUDA;
+  if (hyd::launch_step_fp64(A, B->n_sub, hyd::N, st) != cudaSuccess) return HYDRO_ECUDA;
   return HYDRO_OK;
 }

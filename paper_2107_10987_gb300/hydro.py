@@ -155,7 +155,7 @@ class Context:
 
     def __init__(self, gamma: float = 5.0 / 3.0, omega: float = 0.0, N: int = 8, ghost: int = 3, n_species: int = 1):
         self.ptr = hydro_create(Layout(N, ghost, n_species), gamma, omega)
-        self.gamma, self.omega = gamma, omega
+        self.gamma, self.omega, self.N = gamma, omega, N
 
     def close(self):
         if self.ptr:

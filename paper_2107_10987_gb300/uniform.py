@@ -19,8 +19,9 @@ class UniformRun:
     def __init__(self, ctx, U, origin, h, nb, bc: int = H.HYDRO_BC_OUTFLOW, g=None, cfl: float = 0.4,
                  device="cuda", fused: bool = False):
         """U: [n][F][N][N][N] interiors or [n][F][S][S][S] padded states (array
-        or tensor); origin [n][3]; h scalar or [n]; nb = (nbx, nby, nbz) or an
-        int; g: optional [n][3][N][N][N] gravitational acceleration; fused:
+        or tensor; N the context's sub-grid edge, 8 or 16, S = N + 6); origin
+        [n][3]; h scalar or [n]; nb = (nbx, nby, nbz) or an int; g: optional
+        [n][3][N][N][N] gravitational acceleration; fused:
         each time step as one persistent launch (mixed precision; the ghost
         layers of the state buffers are then not maintained)."""
         self.ctx = ctx
@@ -28,16 +29,18 @@ class UniformRun:
         U = torch.as_tensor(U)
         n = U.shape[0]
         assert n == self.nb[0] * self.nb[1] * self.nb[2]
-        a = torch.zeros((n, 10, 14, 14, 14), dtype=torch.float64, device=device)
+        self.N = N = getattr(ctx, "N", 8)  # the sub-grids' edge (8 or 16)
+        Sp = N + 6
+        a = torch.zeros((n, 10, Sp, Sp, Sp), dtype=torch.float64, device=device)
         self.bufs = (a, torch.zeros_like(a))
         self.origin = torch.as_tensor(np.asarray(origin, dtype=np.float64)).to(device).contiguous()
         self.h = torch.as_tensor(np.broadcast_to(np.asarray(h, dtype=np.float64), (n,)).copy()).to(device)
         self.g = torch.as_tensor(g).to(device).contiguous() if g is not None else None
-        if U.shape[-1] == 8:
+        if U.shape[-1] == N:
             H.hydro_scatter_interior(ctx, H.make_batch(a, self.origin, self.h), U.to(device).contiguous())
         else:
             a.copy_(U)
-        self.dU = torch.empty((n, 10, 8, 8, 8), dtype=torch.float64, device=device)
+        self.dU = torch.empty((n, 10, N, N, N), dtype=torch.float64, device=device)
         self.am = torch.empty(n, dtype=torch.float64, device=device)
         self.dt = torch.empty(1, dtype=torch.float64, device=device)
         self.sums_buf = torch.empty(11, dtype=torch.float64, device=device)
@@ -75,7 +78,7 @@ class UniformRun:
 
     def interior(self) -> torch.Tensor:
         """The current interiors, [n][F][N][N][N] (a new tensor)."""
-        out = torch.empty((self.n, 10, 8, 8, 8), dtype=torch.float64, device=self.U.device)
+        out = torch.empty((self.n, 10, self.N, self.N, self.N), dtype=torch.float64, device=self.U.device)
         H.hydro_gather_interior(self.ctx, self.batches[self.parity], out)
         return out
 

@@ -48,7 +48,7 @@ def test_host_side_argument_checks(lib):
     from paper_2107_10987_gb300 import hydro as H
     out = C.c_void_p()
     assert lib.hydro_create(None, 5 / 3, 0.0, C.byref(out)) == H.HYDRO_EINVAL
-    assert lib.hydro_create(C.byref(H.Layout(16, 3, 1)), 5 / 3, 0.0, C.byref(out)) == H.HYDRO_EINVAL
+    assert lib.hydro_create(C.byref(H.Layout(12, 3, 1)), 5 / 3, 0.0, C.byref(out)) == H.HYDRO_EINVAL
     assert lib.hydro_create(C.byref(H.Layout(8, 2, 1)), 5 / 3, 0.0, C.byref(out)) == H.HYDRO_EINVAL
     assert lib.hydro_create(C.byref(H.Layout(8, 3, 0)), 5 / 3, 0.0, C.byref(out)) == H.HYDRO_EINVAL
     assert lib.hydro_create(C.byref(H.Layout(8, 3, 2)), 5 / 3, 0.0, C.byref(out)) == H.HYDRO_EUNSUP
