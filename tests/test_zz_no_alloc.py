@@ -7,6 +7,8 @@ same FP64 step kernel with its scratch in a fixed array of the library.  This
 file is collected last so that a run stopping at the first failure has run
 everything else before it.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -77,12 +79,17 @@ def test_static_step_matches_hydro_step_on_two_calls_in_a_row(H, variant):
         assert status.item() == 0, call  # cleared by the call, no fault bits
         if call == 1:
             # the entry point allocates nothing: an already warmed-up call
-            # leaves the free memory as it was
+            # leaves the device's free memory and torch's pool as they were
+            # (unreferenced tensors of earlier tests collected first, so that
+            # no deallocation lands between the two readings)
+            gc.collect()
+            torch.cuda.synchronize()
             free0 = torch.cuda.mem_get_info()[0]
-            alloc0 = torch.cuda.memory_allocated()
+            res0, alloc0 = torch.cuda.memory_reserved(), torch.cuda.memory_allocated()
             H.hydro_step_static(ctx, B, 0.0, dU, am, status=status)
             torch.cuda.synchronize()
             assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_reserved() == res0
             assert torch.cuda.memory_allocated() == alloc0
             assert bool((_bits(dU) == _bits(dU_ref)).all())
     assert H.hydro_status(ctx) == 0
