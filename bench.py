@@ -54,6 +54,10 @@ WORKLOADS = {
                   "desc": "rotating n=1.5 polytrope, 32,768 sub-grids of 8^3 (256^3 on [-1,1]^3), static gravity "
                           "field input, rotating frame omega=0.2, ambient rho 1e-10, outflow, 10 FP64 fields, "
                           "one step = one full RK3 time step (3 stages)"},
+    "polytrope128": {"nb": 16, "omega": 0.2,
+                     "desc": "rotating n=1.5 polytrope cut at 128^3: 4,096 sub-grids of 8^3 on [-1,1]^3 (h = 1/64), "
+                             "static gravity field input, rotating frame omega=0.2, ambient rho 1e-10, outflow; the "
+                             "headline's workload at an eighth of its size, for profiler captures"},
     "sedov": {"nb": 8, "omega": 0.0,
               "desc": "Sedov blast, uniform octree level of 512 sub-grids of 8^3 (64^3 on [-1,1]^3), outflow, "
                       "10 FP64 fields, one step = one full RK3 time step (3 stages)"},
@@ -171,9 +175,10 @@ ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 26
 # fused RK3 step (three stages per launch).  Captures on the 256^3 polytrope
 # are taken on its 128^3 cut (4,096 sub-grids) and scaled by 8 (traffic
 # grows with the sub-grids processed).  None until captured for the current
-# kernel.
-TRAFFIC_PER_LAUNCH = {"fp64_sedov": 204584192.0, "mixed_sedov": 254990848.0, "fused_sedov": 838170112.0,
-                      "fp64_polytrope": None, "mixed_polytrope": None, "fused_polytrope": None}
+# kernel (the Sedov figures were taken on earlier builds of the kernels).
+TRAFFIC_PER_LAUNCH = {"fp64_sedov": None, "mixed_sedov": None, "fused_sedov": None,
+                      "fp64_polytrope": None, "mixed_polytrope": None,
+                      "fused_polytrope": 8 * (3738083e3 + 3519702e3)}
 
 
 def algorithmic_work():
@@ -188,7 +193,7 @@ def host_state(workload: str):
     from paper_2107_10987_gb300 import workloads as W
     if workload not in _HOST_STATES:
         nb = WORKLOADS[workload]["nb"]
-        if workload == "polytrope":
+        if workload.startswith("polytrope"):
             Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
         else:
             Ug, h, lo = W.sedov_box(nb * N, GAMMA)
@@ -793,7 +798,7 @@ def oracle_sample(workload: str):
     from paper_2107_10987_gb300 import workloads as W
     nb = WORKLOADS[workload]["nb"]
     k0 = nb // 2 - 2
-    if workload == "polytrope":
+    if workload.startswith("polytrope"):
         o, h = W.uniform_mesh(nb, N)
         lo = tuple(o[(k0 * nb + k0) * nb + k0])
         model = W.polytrope_model(1.5, 0.5)
