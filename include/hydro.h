@@ -95,7 +95,8 @@ typedef struct {
  * contact: 1 turns on PPM contact-discontinuity detection and steepening of
  * the density and species lines (optional in Sec. III-B; Colella & Woodward
  * 1984: a line whose density jump is a contact, gamma K0 |drho|/min(rho) >=
- * |dp|/min(p) over its two neighbours with K0 = 0.1, blends both interface
+ * |dp|/min(p) over its two neighbours with K0 = 0.1 (evaluated as gamma K0
+ * |drho| min(p) >= |dp| min(rho)), blends both interface
  * values with the neighbours' limited extrapolations by a weight in [0,1]
  * from its second differences, before the monotonicity fix-ups).  Not
  * available together with the learned indicator (EUNSUP).  Defaults: FP64,

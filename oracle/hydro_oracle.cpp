@@ -183,8 +183,10 @@ void ppm_line(const T s[5], T& qp, T& qm, T* uq = nullptr, T eta = T(0.0)) {
 // five samples of the steepened field, rho/p the density and pressure of the
 // two neighbours on the same line (index 0: towards -d, 1: towards +d).
 //   The jump must be a contact, not a shock: the relative density jump,
-//   times gamma K0, at least the relative pressure jump:
-//     gamma K0 |rho_1 - rho_0| / min(rho) >= |p_1 - p_0| / min(p).
+//   times gamma K0, at least the relative pressure jump,
+//     gamma K0 |rho_1 - rho_0| / min(rho) >= |p_1 - p_0| / min(p),
+//   taken multiplied through by the two (positive) minima:
+//     gamma K0 |rho_1 - rho_0| min(p) >= |p_1 - p_0| min(rho).
 //   With the second differences d2_m = (a_-2 + a_0) - 2a_-1 and
 //   d2_p = (a_0 + a_2) - 2a_1 (the 1/(6 h^2) of the nonuniform form cancels;
 //   each is summed symmetrically, so that a reversed line rounds alike):
@@ -197,9 +199,8 @@ void ppm_line(const T s[5], T& qp, T& qm, T* uq = nullptr, T eta = T(0.0)) {
 template <class T>
 T contact_eta(const Params& P, const T a[5], const T rho[2], const T p[2]) {
   const T K0 = T(0.1), eps = T(0.01), eta1 = T(20.0), eta2 = T(0.05);
-  const T drho = abs_(rho[1] - rho[0]) / min_(rho[0], rho[1]);
-  const T dp = abs_(p[1] - p[0]) / min_(p[0], p[1]);
-  if ((T(P.gamma) * K0) * drho < dp) return T(0.0);
+  const T drho = abs_(rho[1] - rho[0]), dp = abs_(p[1] - p[0]);
+  if (((T(P.gamma) * K0) * drho) * min_(p[0], p[1]) < dp * min_(rho[0], rho[1])) return T(0.0);
   const T d2m = (a[0] + a[2]) - T(2.0) * a[1];
   const T d2p = (a[2] + a[4]) - T(2.0) * a[3];
   if (T(0.0) < d2m * d2p) return T(0.0);

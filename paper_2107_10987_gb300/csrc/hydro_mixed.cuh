@@ -50,11 +50,81 @@ __device__ __forceinline__ void ppm32(float s0, float s1, float s2, float s3, fl
   qm = ext ? s2 : m2;
 }
 
+// ---- Two lanes per instruction ---------------------------------------------
+// Blackwell's packed FP32 add, multiply and fma (FADD2/FMUL2/FFMA2) round
+// each of their two lanes exactly as the scalar intrinsics do.  The step
+// kernels are bound by instruction issue, so the hot arithmetic below runs
+// two independent evaluations per instruction -- two fields of one line, or
+// the same quantities at two quadrature points -- and gives, lane by lane,
+// the bits of the scalar form.  a - b is fma(b, -1, a): one rounding of the
+// exact a - b, as the scalar subtraction.  Minima, |x|, comparisons and
+// selects have no packed form and run per lane.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 abs2(float2 a) { return f2(fabsf(a.x), fabsf(a.y)); }
+
+// slope32 on two lanes.
+__device__ __forceinline__ float2 slope32x2(float2 a, float2 b) {
+  const float2 t = mul2(f2(2.f), f2(fminf(fabsf(a.x), fabsf(b.x)), fminf(fabsf(a.y), fabsf(b.y))));
+  const float2 u = mul2(f2(0.5f), abs2(add2(a, b)));
+  const float2 ab = mul2(a, b);
+  return f2(ab.x <= 0.f ? 0.f : copysignf(fminf(t.x, u.x), b.x), ab.y <= 0.f ? 0.f : copysignf(fminf(t.y, u.y), b.y));
+}
+
+// ppm32 on two lanes (two fields of a line, or two lines); eta per lane.
+template <bool kSteep = false>
+__device__ __forceinline__ void ppm32x2(float2 s0, float2 s1, float2 s2, float2 s3, float2 s4, float2& qp, float2& qm,
+                                        float2 eta = make_float2(0.f, 0.f)) {
+  const float2 msixth = f2(-(1.f / 6.f)), half = f2(0.5f);
+  const float2 d0 = sub2(s1, s0), d1 = sub2(s2, s1), d2 = sub2(s3, s2), d3 = sub2(s4, s3);
+  const float2 D0 = slope32x2(d0, d1), D1 = slope32x2(d1, d2), D2 = slope32x2(d2, d3);
+  float2 p = fma2(msixth, sub2(D2, D1), mul2(half, add2(s2, s3)));
+  float2 m = fma2(msixth, sub2(D1, D0), mul2(half, add2(s1, s2)));
+  if (kSteep) {
+    const float2 keep = sub2(f2(1.f), eta);
+    p = fma2(eta, fma2(f2(-0.5f), D2, s3), mul2(keep, p));
+    m = fma2(eta, fma2(half, D0, s1), mul2(keep, m));
+  }
+  const float2 e = mul2(sub2(p, s2), sub2(s2, m));
+  const float2 dq = sub2(p, m);
+  const float2 lhs = mul2(dq, fma2(f2(-0.5f), add2(p, m), s2));
+  const float2 rhs = mul2(mul2(dq, dq), f2(1.f / 6.f));
+  const float2 s2x3 = mul2(f2(3.f), s2);
+  const float2 mc = fma2(f2(-2.f), p, s2x3), pc = fma2(f2(-2.f), m, s2x3);
+  qp.x = e.x <= 0.f ? s2.x : (lhs.x < -rhs.x ? pc.x : p.x);
+  qp.y = e.y <= 0.f ? s2.y : (lhs.y < -rhs.y ? pc.y : p.y);
+  qm.x = e.x <= 0.f ? s2.x : (lhs.x > rhs.x ? mc.x : m.x);
+  qm.y = e.y <= 0.f ? s2.y : (lhs.y > rhs.y ? mc.y : m.y);
+}
+
+// The five samples of fields fa and fb along a line (stride st through cell
+// c of the padded FP32 array Q), as pairs.
+struct Samples2 {
+  float2 s[5];
+};
+__device__ __forceinline__ Samples2 samples2(const float* __restrict__ Q, int c, int st, int fa, int fb) {
+  const float* qa = Q + fa * S3 + c;
+  const float* qb = Q + fb * S3 + c;
+  Samples2 r;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) r.s[m] = f2(qa[(m - 2) * st], qb[(m - 2) * st]);
+  return r;
+}
+
 __device__ __forceinline__ void line10f(const float* __restrict__ Q, int c, int st, float qp[F], float qm[F]) {
 #pragma unroll
-  for (int k = 0; k < F; ++k) {
-    const float* q = Q + k * S3 + c;
-    ppm32(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
+  for (int k = 0; k < F; k += 2) {
+    const Samples2 v = samples2(Q, c, st, k, k + 1);
+    float2 p, m;
+    ppm32x2(v.s[0], v.s[1], v.s[2], v.s[3], v.s[4], p, m);
+    qp[k] = p.x;
+    qp[k + 1] = p.y;
+    qm[k] = m.x;
+    qm[k + 1] = m.y;
   }
 }
 
@@ -71,11 +141,12 @@ __device__ __forceinline__ float contact_eta32(float a0, float a1, float a2, flo
 
 // The gas-dynamics contact test of a line over its two neighbours (density
 // r0, r1 and pressure p0, p1; gamma_k0 = gamma K0): the density jump is a
-// contact unless gamma K0 |drho|/min(rho) < |dp|/min(p).  Symmetric.
+// contact unless gamma K0 |drho|/min(rho) < |dp|/min(p), taken multiplied
+// through by the two positive minima: gamma K0 |drho| min(p) < |dp| min(rho).
+// Symmetric.
 __device__ __forceinline__ bool contact_line32(float r0, float r1, float p0, float p1, float gamma_k0) {
-  const float drho = __fdiv_rn(fabsf(__fsub_rn(r1, r0)), fminf(r0, r1));
-  const float dp = __fdiv_rn(fabsf(__fsub_rn(p1, p0)), fminf(p0, p1));
-  return !(__fmul_rn(gamma_k0, drho) < dp);
+  const float drho = fabsf(__fsub_rn(r1, r0)), dp = fabsf(__fsub_rn(p1, p0));
+  return !(__fmul_rn(__fmul_rn(gamma_k0, drho), fminf(p0, p1)) < __fmul_rn(dp, fminf(r0, r1)));
 }
 
 // line10f with contact steepening of the density and species lines (the
@@ -83,18 +154,32 @@ __device__ __forceinline__ bool contact_line32(float r0, float r1, float p0, flo
 // gamma K0, gm1 = gamma - 1).
 __device__ __forceinline__ void line10fc(const float* __restrict__ Q, int c, int st, float gamma_k0, float gm1,
                                          float qp[F], float qm[F]) {
+  static_assert(RHO == 0 && SP0 == F - 1, "the steepened fields are the first and the last");
   const bool contact = contact_line32(Q[RHO * S3 + c - st], Q[RHO * S3 + c + st],
                                       __fmul_rn(gm1, Q[EGAS * S3 + c - st]), __fmul_rn(gm1, Q[EGAS * S3 + c + st]),
                                       gamma_k0);
+  {
+    // density and species, steepened, as one pair
+    const Samples2 v = samples2(Q, c, st, RHO, SP0);
+    const float2 eta = contact ? f2(contact_eta32(v.s[0].x, v.s[1].x, v.s[2].x, v.s[3].x, v.s[4].x),
+                                    contact_eta32(v.s[0].y, v.s[1].y, v.s[2].y, v.s[3].y, v.s[4].y))
+                               : f2(0.f);
+    float2 p, m;
+    ppm32x2<true>(v.s[0], v.s[1], v.s[2], v.s[3], v.s[4], p, m, eta);
+    qp[RHO] = p.x;
+    qp[SP0] = p.y;
+    qm[RHO] = m.x;
+    qm[SP0] = m.y;
+  }
 #pragma unroll
-  for (int k = 0; k < F; ++k) {
-    const float* q = Q + k * S3 + c;
-    if (k == RHO || k >= SP0) {
-      const float eta = contact ? contact_eta32(q[-2 * st], q[-st], q[0], q[st], q[2 * st]) : 0.f;
-      ppm32<true>(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k], eta);
-    } else {
-      ppm32(q[-2 * st], q[-st], q[0], q[st], q[2 * st], qp[k], qm[k]);
-    }
+  for (int k = 1; k < F - 1; k += 2) {
+    const Samples2 v = samples2(Q, c, st, k, k + 1);
+    float2 p, m;
+    ppm32x2(v.s[0], v.s[1], v.s[2], v.s[3], v.s[4], p, m);
+    qp[k] = p.x;
+    qp[k + 1] = p.y;
+    qm[k] = m.x;
+    qm[k + 1] = m.y;
   }
 }
 
@@ -102,96 +187,114 @@ struct StepParamsF {
   float gamma, gm1, omega;
 };
 
-// ---- Kurganov-Tadmor flux at one quadrature point, FP32 --------------------
-// A side's state at the point: density, velocity, energy E = eps + rho|v|^2/2,
-// pressure p = (gamma-1) eps, sound speed, the rotating-frame advection
+// ---- Kurganov-Tadmor flux at quadrature points, FP32 ------------------------
+// Two points per call, in the two lanes (A, B) of every packed operation; a
+// single point runs with both lanes equal.
+//
+// A side's state at the points: density, velocity, energy E = eps +
+// rho|v|^2/2, pressure p = (gamma-1) eps, the rotating-frame advection
 // velocity normal to the face (u = v - omega z_hat x x_q) and |u_n| + c.
-struct Side32 {
-  float rho, vx, vy, vz, E, p, un, va, spd;
+struct Side32x2 {
+  float2 rho, vx, vy, vz, E, p, un, va, spd;
 };
-template <class Q>
-__device__ __forceinline__ Side32 side32(const Q& q, int a, float xq, float yq, const StepParamsF& P) {
-  Side32 s;
-  s.rho = q(RHO);
-  s.vx = q(SX);
-  s.vy = q(SY);
-  s.vz = q(SZ);
-  const float eps = q(EGAS);
-  const float v2 = __fmaf_rn(s.vz, s.vz, __fmaf_rn(s.vy, s.vy, __fmul_rn(s.vx, s.vx)));
-  s.E = __fmaf_rn(__fmul_rn(0.5f, s.rho), v2, eps);
-  s.p = __fmul_rn(P.gm1, eps);
-  const float c2 = __fdividef(__fmul_rn(P.gamma, s.p), s.rho);
-  const float c = __fmul_rn(c2, rsqrtf(c2));
-  const float ux = __fmaf_rn(P.omega, yq, s.vx), uy = __fmaf_rn(-P.omega, xq, s.vy);
+template <class QA, class QB>
+__device__ __forceinline__ Side32x2 side32x2(const QA& qa, const QB& qb, int a, float2 xq, float2 yq,
+                                             const StepParamsF& P) {
+  Side32x2 s;
+  s.rho = f2(qa(RHO), qb(RHO));
+  s.vx = f2(qa(SX), qb(SX));
+  s.vy = f2(qa(SY), qb(SY));
+  s.vz = f2(qa(SZ), qb(SZ));
+  const float2 eps = f2(qa(EGAS), qb(EGAS));
+  const float2 v2 = fma2(s.vz, s.vz, fma2(s.vy, s.vy, mul2(s.vx, s.vx)));
+  s.E = fma2(mul2(f2(0.5f), s.rho), v2, eps);
+  s.p = mul2(f2(P.gm1), eps);
+  const float2 gp = mul2(f2(P.gamma), s.p);
+  const float2 c2 = f2(__fdividef(gp.x, s.rho.x), __fdividef(gp.y, s.rho.y));
+  const float2 c = mul2(c2, f2(rsqrtf(c2.x), rsqrtf(c2.y)));
+  const float2 ux = fma2(f2(P.omega), yq, s.vx), uy = fma2(f2(-P.omega), xq, s.vy);
   s.un = (a == 0) ? ux : (a == 1) ? uy : s.vz;
   s.va = (a == 0) ? s.vx : (a == 1) ? s.vy : s.vz;
-  s.spd = __fadd_rn(fabsf(s.un), c);
+  s.spd = add2(abs2(s.un), c);
   return s;
 }
 
-// Conserved component k of a side and its physical flux along axis a.
-template <class Q>
-__device__ __forceinline__ void cons_flux32(const Q& q, const Side32& s, int a, int k, float& u, float& f) {
+// Conserved component k of a side and its physical flux along axis a (qk:
+// the reconstructed value of field k, used for the advected scalars).
+__device__ __forceinline__ void cons_flux32x2(float2 qk, const Side32x2& s, int a, int k, float2& u, float2& f) {
   if (k == RHO) {
     u = s.rho;
-    f = __fmul_rn(u, s.un);
+    f = mul2(u, s.un);
   } else if (k <= SZ) {
-    u = __fmul_rn(s.rho, k == SX ? s.vx : (k == SY ? s.vy : s.vz));
-    f = (k - SX == a) ? __fmaf_rn(u, s.un, s.p) : __fmul_rn(u, s.un);
+    u = mul2(s.rho, k == SX ? s.vx : (k == SY ? s.vy : s.vz));
+    f = (k - SX == a) ? fma2(u, s.un, s.p) : mul2(u, s.un);
   } else if (k == EGAS) {
     u = s.E;
-    f = __fmaf_rn(u, s.un, __fmul_rn(s.p, s.va));
+    f = fma2(u, s.un, mul2(s.p, s.va));
   } else {
-    u = q(k);
-    f = __fmul_rn(u, s.un);
+    u = qk;
+    f = mul2(u, s.un);
   }
 }
 
-// One quadrature point of a face of axis a: F_q = (F_L + F_R)/2 - a_q (U_R -
-// U_L)/2 with a_q = max(|u_n| + c) of the two sides, added to the face
-// group's sums G[k] += w F_q[k], and its momentum-flux torques about the
-// left and right cell centres, TL += (w h/2) dL x F_s and TR += (w h/2) dR x
-// F_s, with the levers (h/2) dL and (h/2) dR, dL = d, dR = d - 2 e_a.
-// ql(k), qr(k): the reconstructed primitives of the two sides (read when
-// needed).  wh = w h/2.
-template <class QL, class QR>
-__device__ __forceinline__ void point32(const QL& ql, const QR& qr, int a, float xq, float yq, float w, float wh,
-                                        const float dL[3], const float dR[3], const StepParamsF& P, float G[F],
-                                        float TL[3], float TR[3], float& amax) {
-  const Side32 L = side32(ql, a, xq, yq, P);
-  const Side32 R = side32(qr, a, xq, yq, P);
-  const float aq = fmaxf(L.spd, R.spd);
-  amax = fmaxf(amax, aq);
-  const float ha = __fmul_rn(0.5f, aq);
-  float fs[3];
+// Two quadrature points A, B of a face of axis a (kTwo = false: A only,
+// with both lanes equal), added to a face group's sums in the order A, B:
+// the point fluxes F_q = (F_L + F_R)/2 - a_q (U_R - U_L)/2 with a_q =
+// max(|u_n| + c) of the two sides, G[k] += w F_q[k], and the momentum-flux
+// torques about the left and right cell centres, TL += (w h/2) dL x F_s and
+// TR += (w h/2) dR x F_s (dL = d, dR = d - 2 e_a; the levers are (h/2) dL
+// and (h/2) dR), each a fused step; amax takes a_q.  qlA(k), qrA(k),
+// qlB(k), qrB(k): the reconstructed primitives of the two sides of A and B
+// (read when needed); xq, yq, dL, dR per lane; wA, wB the weights, whA =
+// wA h/2, whB = wB h/2.  dL and dR are in {-1, 0, 1}, so each cross-product
+// component is one rounding of an exact difference of exact products.
+template <bool kTwo, class QLA, class QRA, class QLB, class QRB>
+__device__ __forceinline__ void point_pair32(const QLA& qlA, const QRA& qrA, const QLB& qlB, const QRB& qrB, int a,
+                                             float2 xq, float2 yq, const float2 dL[3], const float2 dR[3],
+                                             const StepParamsF& P, float wA, float whA, float wB, float whB,
+                                             float G[F], float TL[3], float TR[3], float& amax) {
+  const Side32x2 L = side32x2(qlA, qlB, a, xq, yq, P);
+  const Side32x2 R = side32x2(qrA, qrB, a, xq, yq, P);
+  const float2 aq = f2(fmaxf(L.spd.x, R.spd.x), fmaxf(L.spd.y, R.spd.y));
+  amax = fmaxf(amax, kTwo ? fmaxf(aq.x, aq.y) : aq.x);
+  const float2 mha = mul2(f2(-0.5f), aq);
+  float2 fs[3];
 #pragma unroll
   for (int k = 0; k < F; ++k) {
-    float uL, fL, uR, fR;
-    cons_flux32(ql, L, a, k, uL, fL);
-    cons_flux32(qr, R, a, k, uR, fR);
-    const float fq = __fmaf_rn(-ha, __fsub_rn(uR, uL), __fmul_rn(0.5f, __fadd_rn(fL, fR)));
-    G[k] = __fmaf_rn(w, fq, G[k]);
+    float2 uL, fL, uR, fR;
+    cons_flux32x2(k >= TAU ? f2(qlA(k), qlB(k)) : f2(0.f), L, a, k, uL, fL);
+    cons_flux32x2(k >= TAU ? f2(qrA(k), qrB(k)) : f2(0.f), R, a, k, uR, fR);
+    const float2 fq = fma2(mha, sub2(uR, uL), mul2(f2(0.5f), add2(fL, fR)));
+    G[k] = __fmaf_rn(wA, fq.x, G[k]);
+    if (kTwo) G[k] = __fmaf_rn(wB, fq.y, G[k]);
     if (k >= SX && k <= SZ) fs[k - SX] = fq;
   }
-  const float cl[3] = {__fsub_rn(__fmul_rn(dL[1], fs[2]), __fmul_rn(dL[2], fs[1])),
-                       __fsub_rn(__fmul_rn(dL[2], fs[0]), __fmul_rn(dL[0], fs[2])),
-                       __fsub_rn(__fmul_rn(dL[0], fs[1]), __fmul_rn(dL[1], fs[0]))};
-  const float cr[3] = {__fsub_rn(__fmul_rn(dR[1], fs[2]), __fmul_rn(dR[2], fs[1])),
-                       __fsub_rn(__fmul_rn(dR[2], fs[0]), __fmul_rn(dR[0], fs[2])),
-                       __fsub_rn(__fmul_rn(dR[0], fs[1]), __fmul_rn(dR[1], fs[0]))};
+  const float2 mL[3] = {mul2(f2(-1.f), dL[0]), mul2(f2(-1.f), dL[1]), mul2(f2(-1.f), dL[2])};
+  const float2 mR[3] = {mul2(f2(-1.f), dR[0]), mul2(f2(-1.f), dR[1]), mul2(f2(-1.f), dR[2])};
+  const float2 cl[3] = {fma2(dL[1], fs[2], mul2(mL[2], fs[1])), fma2(dL[2], fs[0], mul2(mL[0], fs[2])),
+                        fma2(dL[0], fs[1], mul2(mL[1], fs[0]))};
+  const float2 cr[3] = {fma2(dR[1], fs[2], mul2(mR[2], fs[1])), fma2(dR[2], fs[0], mul2(mR[0], fs[2])),
+                        fma2(dR[0], fs[1], mul2(mR[1], fs[0]))};
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    TL[m] = __fmaf_rn(wh, cl[m], TL[m]);
-    TR[m] = __fmaf_rn(wh, cr[m], TR[m]);
+    TL[m] = __fmaf_rn(whA, cl[m].x, TL[m]);
+    TR[m] = __fmaf_rn(whA, cr[m].x, TR[m]);
+    if (kTwo) {
+      TL[m] = __fmaf_rn(whB, cl[m].y, TL[m]);
+      TR[m] = __fmaf_rn(whB, cr[m].y, TR[m]);
+    }
   }
 }
 
 // The 9 points of a face in their summation order: point n has offsets
 // (u1, u2) along the face's two transverse axes b < c,
 //   (1,1), (-1,-1), (1,0), (-1,0), (1,-1), (-1,1), (0,1), (0,-1), (0,0),
-// summed in three groups of three, (G0 + G1) + G2, each group a fused chain
-// from zero.  With one point per face (the old module) only the last, the
-// centre, with weight 1.  (u + 1 packed two bits per point.)
+// summed in three groups, points 0-3, 4-5 and 6-8, as (G0 + G1) + G2, each
+// group a fused chain from zero.  The points go in mirrored pairs (2p, 2p+1)
+// and the centre, and no group ends inside a pair.  With one point per face
+// (the old module) only the last, the centre, with weight 1.  (u + 1 packed
+// two bits per point.)
+__host__ __device__ constexpr bool face_group_ends(int n) { return n == 3 || n == 5 || n == 8; }
 __device__ __forceinline__ int face_u1(int n) { return ((86562 >> (2 * n)) & 3) - 1; }
 __device__ __forceinline__ int face_u2(int n) { return ((75858 >> (2 * n)) & 3) - 1; }
 // Newton-Cotes (Simpson) weight of a point, (1,4,1)x(1,4,1)/36, or 1 with

@@ -19,6 +19,7 @@
 // loads and writes FP32 primitives: a bulk TMA copy cannot convert, and an
 // FP64 staging buffer would not fit beside the FP32 primitives of two CTAs.
 #pragma once
+#include <type_traits>
 #include "hydro_mixed.cuh"
 
 namespace hyd {
@@ -194,59 +195,68 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
     // the 9 face points as 4 mirrored pairs and the centre (p = 4); with one
     // flux point per face (the old module) only the centre.  Pair p's two
     // points are points 2p and 2p + 1 of the face's summation order.
-#pragma unroll 1
-    for (int p = npt == 1 ? 4 : 0; p <= 4; ++p) {
+    // pair p (kTwo) or the centre p = 4: its lines through cell j, the face
+    // points they give with the previous cell's plus-states, and the new
+    // plus-states
+    auto pair_step = [&](int p, auto two) {
+      constexpr bool kTwo = decltype(two)::value;
       const int t1 = p / 3 - 1, t2 = p % 3 - 1;
       float qpA[F], qmA[F], qpB[F], qmB[F];
       if (kGate && smooth[cj]) {
         line10u(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
-        if (p != 4) line10u(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        if (kTwo) line10u(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
       } else if (kContact) {
         const float gk0 = __fmul_rn(PF.gamma, 0.1f);
         line10fc(Qf, cj, sa + t1 * sb + t2 * sc, gk0, PF.gm1, qpA, qmA);
-        if (p != 4) line10fc(Qf, cj, sa - t1 * sb - t2 * sc, gk0, PF.gm1, qpB, qmB);
+        if (kTwo) line10fc(Qf, cj, sa - t1 * sb - t2 * sc, gk0, PF.gm1, qpB, qmB);
       } else {
         line10f(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
-        if (p != 4) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+        if (kTwo) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
       }
       if (j >= 0) {
+        // the pair's two points (n = 2p, 2p + 1) in the two lanes; the centre
+        // in both
+        const int nA = 2 * p, nB = kTwo ? nA + 1 : nA;
+        const int u1A = face_u1(nA), u2A = face_u2(nA), u1B = face_u1(nB), u2B = face_u2(nB);
+        const int ptA = (u1A + 1) * 3 + (u2A + 1), ptB = (u1B + 1) * 3 + (u2B + 1);
+        float2 dL[3], dR[3];
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          if (p == 4 && side == 1) continue;
-          const int n = 2 * p + side;  // the point's place in the summation order
-          const int u1 = face_u1(n), u2 = face_u2(n);
-          const int pt = (u1 + 1) * 3 + (u2 + 1);
-          const float dL[3] = {(float)axis_comp(0, a, b, 1, u1, u2), (float)axis_comp(1, a, b, 1, u1, u2),
-                               (float)axis_comp(2, a, b, 1, u1, u2)};
-          const float dR[3] = {a == 0 ? -1.f : dL[0], a == 1 ? -1.f : dL[1], a == 2 ? -1.f : dL[2]};
-          const float xq = __fmaf_rn(half_h, dL[0], xc), yq = __fmaf_rn(half_h, dL[1], yc);
-          const float w = face_w(u1, u2, npt);
-          const float* qr = side ? qmB : qmA;
-          point32([&](int k) { return plus[pt][k]; }, [&](int k) { return qr[k]; }, a, xq, yq, w,
-                  __fmul_rn(w, half_h), dL, dR, PF, Gf, Gtl, Gtr, amax);
-          if (n % 3 == 2) {
-            // a group is complete: S = G0, then (S + G1), then (S + G2)
+        for (int m = 0; m < 3; ++m) {
+          dL[m] = f2((float)axis_comp(m, a, b, 1, u1A, u2A), (float)axis_comp(m, a, b, 1, u1B, u2B));
+          dR[m] = m == a ? f2(-1.f) : dL[m];
+        }
+        const float2 xq = fma2(f2(half_h), dL[0], f2(xc)), yq = fma2(f2(half_h), dL[1], f2(yc));
+        const float wA = face_w(u1A, u2A, npt), wB = face_w(u1B, u2B, npt);
+        point_pair32<kTwo>([&](int k) { return plus[ptA][k]; }, [&](int k) { return qmA[k]; },
+                           [&](int k) { return plus[ptB][k]; }, [&](int k) { return kTwo ? qmB[k] : qmA[k]; }, a,
+                           xq, yq, dL, dR, PF, wA, __fmul_rn(wA, half_h), wB, __fmul_rn(wB, half_h), Gf, Gtl, Gtr,
+                           amax);
+        // a group is complete after points 3, 5 and 8 (face_group_ends, never
+        // inside a pair): S = G0, then (S + G1), then (S + G2)
+        if (face_group_ends(nB)) {
 #pragma unroll
-            for (int k = 0; k < F; ++k) {
-              Sf[k] = first ? Gf[k] : __fadd_rn(Sf[k], Gf[k]);
-              Gf[k] = 0.f;
-            }
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-              Stl[m] = first ? Gtl[m] : __fadd_rn(Stl[m], Gtl[m]);
-              Str[m] = first ? Gtr[m] : __fadd_rn(Str[m], Gtr[m]);
-              Gtl[m] = Gtr[m] = 0.f;
-            }
-            first = false;
+          for (int k = 0; k < F; ++k) {
+            Sf[k] = first ? Gf[k] : __fadd_rn(Sf[k], Gf[k]);
+            Gf[k] = 0.f;
           }
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            Stl[m] = first ? Gtl[m] : __fadd_rn(Stl[m], Gtl[m]);
+            Str[m] = first ? Gtr[m] : __fadd_rn(Str[m], Gtr[m]);
+            Gtl[m] = Gtr[m] = 0.f;
+          }
+          first = false;
         }
       }
 #pragma unroll
       for (int k = 0; k < F; ++k) {
         plus[p][k] = qpA[k];
-        if (p != 4) plus[8 - p][k] = qpB[k];
+        if (kTwo) plus[8 - p][k] = qpB[k];
       }
-    }
+    };
+#pragma unroll 1
+    for (int p = npt == 1 ? 4 : 0; p < 4; ++p) pair_step(p, std::integral_constant<bool, true>{});
+    pair_step(4, std::integral_constant<bool, false>{});
     if (j >= 0) {
       // face j-1/2 is complete: its sums in FP64 (each converted once); the
       // a-difference of cell j-1 is exact in FP64

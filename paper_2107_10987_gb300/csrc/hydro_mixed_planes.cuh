@@ -15,8 +15,8 @@
 //      values towards +z into one of two z-buffers (Zp) that the next step
 //      reads;
 //   B  the fluxes of the x- and y-faces of plane k and of the z-faces between
-//      planes k-1 and k, three threads per face (three groups of three
-//      points, combined by warp shuffles in the fixed order), into face-sum
+//      planes k-1 and k, three threads per face (the face's three groups
+//      of points, combined by warp shuffles in the fixed order), into face-sum
 //      buffers (converted to FP64 once per face); meanwhile the primitives of
 //      plane k+3 are converted from the FP64 staging buffer that phase A
 //      filled from global memory, and two of the warps that have no face
@@ -28,12 +28,16 @@
 // 190 KB of shared memory instead of the whole padded sub-grid and runs 21
 // warps on its SM; the per-axis flux differences never leave the SM.
 //
-// The arithmetic is the row sweep's own: the same ppm32 on the same samples
+// The arithmetic is the row sweep's own: the same ppm32x2 on the same samples
 // (exactly symmetric under reversal of a line, so the orientation in which a
-// line is evaluated does not matter), the same point32, the same grouping of
+// line is evaluated does not matter; each lane rounds alike whichever field
+// or line shares its instruction), the same point_pair32 on the same pairs
+// in the same order, the same grouping of
 // each face sum, the same FP64 differences and finish_cell.  The two
 // decompositions therefore give the same bits.
 #pragma once
+#include <type_traits>
+
 #include "hydro_mixed_body.cuh"
 
 namespace hyd {
@@ -88,10 +92,10 @@ __device__ __forceinline__ float* r_bnd_slot(float* rbnd, int sd, int bi, int po
 }
 
 // Reconstruct one line of the cell at padded plane coordinates (ix, iy) of
-// padded plane zp along (dx, dy, dz), for the five fields f0 .. f0 + 4: both
-// interface values of each, to dp (towards +d) and dm (towards -d; nullptr:
-// not needed), field stride fst (dp, dm address field 0).  Samples from the
-// primitive ring.  kContact as line10fc.
+// padded plane zp along (dx, dy, dz), for the five fields f0 .. f0 + 4 (f0 =
+// 0 or 5): both interface values of each, to dp (towards +d) and dm (towards
+// -d; nullptr: not needed), field stride fst (dp, dm address field 0).
+// Samples from the primitive ring.  kContact as line10fc.
 template <bool kContact>
 __device__ __forceinline__ void plane_line(const float* __restrict__ ring, int ix, int iy, int zp, int dx, int dy,
                                            int dz, int f0, float* dp, float* dm, int fst, const StepParamsF& PF) {
@@ -104,20 +108,37 @@ __device__ __forceinline__ void plane_line(const float* __restrict__ ring, int i
     contact = contact_line32(ring[off[1] + RHO * kPl], ring[off[3] + RHO * kPl],
                              __fmul_rn(PF.gm1, ring[off[1] + EGAS * kPl]),
                              __fmul_rn(PF.gm1, ring[off[3] + EGAS * kPl]), __fmul_rn(PF.gamma, 0.1f));
+  // the five samples of fields fa and fb as pairs
+  auto samples = [&](int fa, int fb, float2 v[5]) {
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int f = f0 + i;
-    const float s0 = ring[off[0] + f * kPl], s1 = ring[off[1] + f * kPl], s2 = ring[off[2] + f * kPl],
-                s3 = ring[off[3] + f * kPl], s4 = ring[off[4] + f * kPl];
-    float qp, qm;
-    if (kContact && (f == RHO || f >= SP0)) {
-      const float eta = contact ? contact_eta32(s0, s1, s2, s3, s4) : 0.f;
-      ppm32<true>(s0, s1, s2, s3, s4, qp, qm, eta);
-    } else {
-      ppm32(s0, s1, s2, s3, s4, qp, qm);
-    }
+    for (int m = 0; m < 5; ++m) v[m] = f2(ring[off[m] + fa * kPl], ring[off[m] + fb * kPl]);
+  };
+  auto put = [&](int f, float qp, float qm) {
     dp[f * fst] = qp;
     if (dm) dm[f * fst] = qm;
+  };
+  // fields 0 .. 4: the density alone (the steepened field), then (1, 2) and
+  // (3, 4); fields 5 .. 9: (5, 6), (7, 8), then the species alone
+  static_assert(RHO == 0 && SP0 == F - 1 && F == 10, "field split of a half line");
+  const int fs = f0 == 0 ? RHO : SP0;
+  {
+    float2 v[5], qp, qm;
+    samples(fs, fs, v);
+    const float eta = (kContact && contact) ? contact_eta32(v[0].x, v[1].x, v[2].x, v[3].x, v[4].x) : 0.f;
+    if (kContact)
+      ppm32x2<true>(v[0], v[1], v[2], v[3], v[4], qp, qm, f2(eta));
+    else
+      ppm32x2(v[0], v[1], v[2], v[3], v[4], qp, qm);
+    put(fs, qp.x, qm.x);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int fa = (f0 == 0 ? 1 : 5) + 2 * i;
+    float2 v[5], qp, qm;
+    samples(fa, fa + 1, v);
+    ppm32x2(v[0], v[1], v[2], v[3], v[4], qp, qm);
+    put(fa, qp.x, qm.x);
+    put(fa + 1, qp.y, qm.y);
   }
 }
 
@@ -275,57 +296,89 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
         }
         // left-cell centre in FP32 (the row sweep's values)
         const float xc = coord[fx + 1], yc = coord[(N + 2) + fy + 1];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const int n = 3 * g + i;
-          if (npt == 1 && n != 8) continue;
-          const int u1 = face_u1(n), u2 = face_u2(n);
-          // d along (a, b, c) = (1, u1, u2), b < c the transverse axes
-          const int dxl = a == 0 ? 1 : u1, dyl = a == 1 ? 1 : (a == 0 ? u1 : u2), dzl = a == 2 ? 1 : u2;
-          const float dL[3] = {(float)dxl, (float)dyl, (float)dzl};
-          const float dR[3] = {a == 0 ? -1.f : dL[0], a == 1 ? -1.f : dL[1], a == 2 ? -1.f : dL[2]};
-          const int dxr = (int)dR[0], dyr = (int)dR[1], dzr = (int)dR[2];
-          // the left value R_left[dL] and the right value R_right[dR]
+        // point n of the face: its directions dL, dR (as small integers) and
+        // where its left value R_left[dL] and right value R_right[dR] live
+        struct Pt {
           const float* pl;
           const float* pr;
-          int sl = kRowR, sr = kRowR;
+          int sl, sr, dl[3], dr[3], u1, u2;
+        };
+        auto geom = [&](int n) {
+          Pt t;
+          t.u1 = face_u1(n);
+          t.u2 = face_u2(n);
+          const int u1 = t.u1, u2 = t.u2;
+          // d along (a, b, c) = (1, u1, u2), b < c the transverse axes
+          t.dl[0] = a == 0 ? 1 : u1;
+          t.dl[1] = a == 1 ? 1 : (a == 0 ? u1 : u2);
+          t.dl[2] = a == 2 ? 1 : u2;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) t.dr[m] = m == a ? -1 : t.dl[m];
+          const int cl = dcode(t.dl[0], t.dl[1], t.dl[2]), cr = dcode(t.dr[0], t.dr[1], t.dr[2]);
+          t.sl = t.sr = kRowR;
           if (a == 0) {
             const int bi = (u2 + 1) * 3 + (u1 + 1);
             if (fx < 0) {
-              pl = r_bnd_slot(rbnd, 0, bi, fy);
-              sl = kRowB;
+              t.pl = r_bnd_slot(rbnd, 0, bi, fy);
+              t.sl = kRowB;
             } else {
-              pl = r_int_slot(rint, zp, dcode(dxl, dyl, dzl), k, fy * N + fx);
+              t.pl = r_int_slot(rint, zp, cl, k, fy * N + fx);
             }
             if (fx + 1 >= N) {
-              pr = r_bnd_slot(rbnd, 1, bi, fy);
-              sr = kRowB;
+              t.pr = r_bnd_slot(rbnd, 1, bi, fy);
+              t.sr = kRowB;
             } else {
-              pr = r_int_slot(rint, zp, dcode(dxr, dyr, dzr), k, fy * N + fx + 1);
+              t.pr = r_int_slot(rint, zp, cr, k, fy * N + fx + 1);
             }
           } else if (a == 1) {
             const int bi = (u2 + 1) * 3 + (u1 + 1);
             if (fy < 0) {
-              pl = r_bnd_slot(rbnd, 2, bi, fx);
-              sl = kRowB;
+              t.pl = r_bnd_slot(rbnd, 2, bi, fx);
+              t.sl = kRowB;
             } else {
-              pl = r_int_slot(rint, zp, dcode(dxl, dyl, dzl), k, fy * N + fx);
+              t.pl = r_int_slot(rint, zp, cl, k, fy * N + fx);
             }
             if (fy + 1 >= N) {
-              pr = r_bnd_slot(rbnd, 3, bi, fx);
-              sr = kRowB;
+              t.pr = r_bnd_slot(rbnd, 3, bi, fx);
+              t.sr = kRowB;
             } else {
-              pr = r_int_slot(rint, zp, dcode(dxr, dyr, dzr), k, (fy + 1) * N + fx);
+              t.pr = r_int_slot(rint, zp, cr, k, (fy + 1) * N + fx);
             }
           } else {
-            pl = r_int_slot(rint, zp, dcode(dxl, dyl, dzl), k - 1, fy * N + fx);
-            pr = r_int_slot(rint, zp, dcode(dxr, dyr, dzr), k, fy * N + fx);
+            t.pl = r_int_slot(rint, zp, cl, k - 1, fy * N + fx);
+            t.pr = r_int_slot(rint, zp, cr, k, fy * N + fx);
           }
-          const float xq = __fmaf_rn(half_h, dL[0], xc), yq = __fmaf_rn(half_h, dL[1], yc);
-          const float w = face_w(u1, u2, npt);
-          point32([&](int q) { return pl[q * sl]; }, [&](int q) { return pr[q * sr]; }, a, xq, yq, w,
-                  __fmul_rn(w, half_h), dL, dR, PF, Gf, Gtl, Gtr, amax);
-        }
+          return t;
+        };
+        // the lane's group (face_group_ends): g = 0 the pairs (0, 1) and (2,
+        // 3), g = 1 the pair (4, 5), g = 2 the pair (6, 7) and the centre 8 in
+        // both lanes (with one flux point per face only the centre)
+        // points n and n + 1 in the two lanes (kTwo), or n alone
+        auto points = [&](auto two, int n) {
+          constexpr bool kTwo = decltype(two)::value;
+          const Pt tA = geom(n), tB = kTwo ? geom(n + 1) : tA;
+          float2 dL[3], dR[3];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            dL[m] = f2((float)tA.dl[m], (float)tB.dl[m]);
+            dR[m] = f2((float)tA.dr[m], (float)tB.dr[m]);
+          }
+          const float2 xq = fma2(f2(half_h), dL[0], f2(xc)), yq = fma2(f2(half_h), dL[1], f2(yc));
+          const float wA = face_w(tA.u1, tA.u2, npt), wB = face_w(tB.u1, tB.u2, npt);
+          point_pair32<kTwo>([&](int q) { return tA.pl[q * tA.sl]; }, [&](int q) { return tA.pr[q * tA.sr]; },
+                             [&](int q) { return tB.pl[q * tB.sl]; }, [&](int q) { return tB.pr[q * tB.sr]; }, a,
+                             xq, yq, dL, dR, PF, wA, __fmul_rn(wA, half_h), wB, __fmul_rn(wB, half_h), Gf, Gtl,
+                             Gtr, amax);
+        };
+        // the lane's group (face_group_ends): g = 0 the pairs (0, 1) and (2,
+        // 3), g = 1 the pair (4, 5), g = 2 the pair (6, 7) and the centre 8
+        // (with one flux point per face only the centre)
+        static_assert(face_group_ends(3) && face_group_ends(5) && face_group_ends(8), "lane groups");
+        using Two = std::integral_constant<bool, true>;
+        using One = std::integral_constant<bool, false>;
+        if (npt != 1) points(Two{}, g == 0 ? 0 : 2 * g + 2);  // 0, 4, 6
+        if (npt != 1 && g == 0) points(Two{}, 2);
+        if (g == 2) points(One{}, 8);
       }
       // the face's three groups, (G0 + G1) + G2, on the lane of group 0
       float out[16];

@@ -143,15 +143,15 @@ __device__ __forceinline__ double contact_eta64(double a0, double a1, double a2,
 
 // line10 with contact steepening of the density and species lines.  The line
 // is a contact, not a shock, where Colella & Woodward's gas-dynamics test
-// holds over its two neighbours (K0 = 0.1):
-//   gamma K0 |rho+ - rho-| / min(rho) >= |p+ - p-| / min(p),  p = (gamma-1) eps.
+// holds over its two neighbours (K0 = 0.1), multiplied through by the two
+// positive minima (no division):
+//   gamma K0 |rho+ - rho-| min(p) >= |p+ - p-| min(rho),  p = (gamma-1) eps.
 __device__ __forceinline__ void line10c(const double* __restrict__ Q, int c, int st, const StepParams& P,
                                         double qp[F], double qm[F]) {
   const double r0 = Q[RHO * S3 + c - st], r1 = Q[RHO * S3 + c + st];
   const double p0 = rmul(P.gm1, Q[EGAS * S3 + c - st]), p1 = rmul(P.gm1, Q[EGAS * S3 + c + st]);
-  const double drho = fabs(rsub(r1, r0)) / (r0 < r1 ? r0 : r1);
-  const double dp = fabs(rsub(p1, p0)) / (p0 < p1 ? p0 : p1);
-  const bool contact = !(rmul(rmul(P.gamma, 0.1), drho) < dp);
+  const double drho = fabs(rsub(r1, r0)), dp = fabs(rsub(p1, p0));
+  const bool contact = !(rmul(rmul(rmul(P.gamma, 0.1), drho), p0 < p1 ? p0 : p1) < rmul(dp, r0 < r1 ? r0 : r1));
 #pragma unroll
   for (int k = 0; k < F; ++k) {
     const double* q = Q + k * S3 + c;

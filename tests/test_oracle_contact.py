@@ -5,6 +5,9 @@ option Sec. III-B names, from Colella & Woodward 1984), pinned (CPU only):
   * each condition of the detection on its own: an inflection is required,
     a jump below 1 % of the values is left alone, a shock (large pressure
     jump) is left alone, and eta is clamped to [0, 1];
+  * the contact test, evaluated multiplied through by the two minima, gives
+    the decision of the quotient form of the criterion in exact rational
+    arithmetic, wherever the two sides differ by more than rounding;
   * mirror symmetry and scale invariance of the line; no change on lines of
     two values (every cell is then an extremum and is flattened);
   * on smooth data (16 cells per wavelength) nothing changes, bit for bit;
@@ -100,6 +103,35 @@ def test_detection_conditions(orc):
     for e, want in ((0.22, 0.0), (0.2, 20 * (0.2 / 3.6 - 0.05)), (0.15, 20 * (0.4 / 4.2 - 0.05)), (0.1, 1.0)):
         got = _eta(orc, [0.0, e, 0.5, 1 - e, 1.0])
         assert got == pytest.approx(want, abs=1e-14), (e, got, want)
+
+
+def test_contact_test_is_the_exact_criterion(orc):
+    """gamma K0 |drho| / min(rho) >= |dp| / min(p), decided in exact rational
+    arithmetic (gamma and K0 as the oracle's doubles), against the oracle's
+    decision on lines that steepen fully whenever the test passes.  Cases
+    whose two sides agree to 1e-12 are skipped: there rounding decides, in
+    either form."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(17)
+    a = [1.0, 1.0, 1.5, 2.0, 2.0]
+    n_pass = n_fail = 0
+    for i in range(4000):
+        gamma = (GAMMA, 1.4, 1.2)[i % 3]
+        rho = rng.uniform(0.1, 3.0, 2)
+        # pressure jumps spread around the test's boundary
+        p0 = rng.uniform(0.01, 5.0)
+        rel = float(gamma) * 0.1 * abs(rho[1] - rho[0]) / min(rho) * rng.uniform(0.5, 1.5)
+        p1 = p0 * (1.0 + rel) if rng.random() < 0.5 else p0 / (1.0 + rel)
+        lhs = Fr(gamma) * Fr(0.1) * abs(Fr(rho[1]) - Fr(rho[0])) / min(Fr(rho[0]), Fr(rho[1]))
+        rhs = abs(Fr(p1) - Fr(p0)) / min(Fr(p0), Fr(p1))
+        if abs(lhs - rhs) <= Fr(1, 10 ** 12) * max(lhs, rhs):
+            continue
+        want = lhs >= rhs
+        got = _eta(orc, a, tuple(rho), (p0, p1), gamma=gamma) > 0.0
+        assert got == want, (gamma, rho, p0, p1, float(lhs), float(rhs))
+        n_pass += want
+        n_fail += not want
+    assert n_pass > 1000 and n_fail > 1000
 
 
 def test_mirror_and_scale(orc):
