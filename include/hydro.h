@@ -98,8 +98,9 @@ typedef struct {
  * |dp|/min(p) over its two neighbours with K0 = 0.1 (evaluated as gamma K0
  * |drho| min(p) >= |dp| min(rho)), blends both interface
  * values with the neighbours' limited extrapolations by a weight in [0,1]
- * from its second differences, before the monotonicity fix-ups).  Not
- * available together with the learned indicator (EUNSUP).  Defaults: FP64,
+ * from its second differences, before the monotonicity fix-ups).  With the
+ * learned indicator on, cells it marks smooth take the unlimited formula
+ * and are not steepened; the others are.  Defaults: FP64,
  * cfl 0.4, eta1 1e-3, eta2 0.1, 9 points, contact 0. */
 typedef struct {
   int precision;   /* HYDRO_PREC_FP64 or HYDRO_PREC_MIXED */
@@ -149,7 +150,7 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
  * face-averaged fluxes and the 3 components of the momentum-flux torque
  * about the adjacent interior cell.
  * Errors: EINVAL (NULL ctx/batch/pointers, n_sub < 0, misaligned U, dt < 0),
- * EUNSUP (contact steepening with the learned indicator on), ENOMEM, ECUDA.
+ * ENOMEM, ECUDA.
  * n_sub == 0 is a no-op. */
 int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt, double* amax, double* face_flux,
                void* stream);
@@ -265,8 +266,7 @@ int hydro_conserved_sums(hydro_ctx_t* ctx, const hydro_batch_t* B, double* sums,
  * every GPU that loads the library until the process exits.
  *   - B->n_sub above HYDRO_STATIC_MAX_SUB returns HYDRO_ERANGE (split the
  *     batch); n_sub == 0 is a no-op; a mixed-precision context returns
- *     HYDRO_EUNSUP.  Other argument errors as hydro_step (EINVAL, and
- *     EUNSUP for contact steepening with the indicator on).
+ *     HYDRO_EUNSUP.  Other argument errors as hydro_step (EINVAL).
  *   - status: optional device word (caller-owned); it is set to zero, then
  *     receives this call's HYDRO_ST_* bits.  NULL: the bits go to an internal
  *     word nobody reads.
@@ -360,7 +360,7 @@ typedef struct hydro_graph hydro_graph_t;
  * b -> a.  Ten launches (two with fused: a clear of the context's sync words
  * and the step).  Errors: EINVAL (inconsistent descriptor, or state
  * buffers a.U and U_b that overlap), EUNSUP (fused with an adaptive mesh or
- * in FP64; contact steepening with the indicator), ENOMEM. */
+ * in FP64), ENOMEM. */
 int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
 
 /* Capture the two directions of hydro_rk3_step once into CUDA graphs

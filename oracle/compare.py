@@ -139,7 +139,7 @@ EPS32 = 2.0 ** -24  # unit roundoff of FP32
 
 
 def flux_ratio(faces: np.ndarray, scale: np.ndarray, h, U: np.ndarray | None = None,
-               amax: np.ndarray | None = None) -> np.ndarray:
+               amax: np.ndarray | None = None, gamma: float = 5.0 / 3.0) -> np.ndarray:
     """R[s, k]: the size of the terms rate k of sub-grid s is computed from,
     over its normalisation scale[s, k] ([n][F]).
 
@@ -151,7 +151,10 @@ def flux_ratio(faces: np.ndarray, scale: np.ndarray, h, U: np.ndarray | None = N
     where the two reconstructed states nearly agree and the signal speed a
     is large (hot, thin gas), the face flux is small but the dissipation
     terms a|U_k| / 2 are not, so with the padded states U [n][F][S][S][S]
-    and the signal speeds amax [n] the terms a |U_k| / h count too.  The
+    and the signal speeds amax [n] the terms a |U_k| / h count too, and so
+    does the pressure that the momentum flux s u_n + p e_a carries, p / h
+    with p = (gamma - 1)(E - |s|^2 / (2 rho)) (the face sums, when given,
+    include it; a step that exports none is measured by the states).  The
     spin rate is also made of point torques (x_q - x_c) x F_s with
     |x_q - x_c| ~ h/2, divided by h: terms of size max|F_s| / 2 and
     a |s| / 2, which cancel when the pressure or the momentum is nearly
@@ -171,6 +174,12 @@ def flux_ratio(faces: np.ndarray, scale: np.ndarray, h, U: np.ndarray | None = N
         smax = um[:, list(MOMENTUM)].max(axis=1)
         for k in SPIN:
             R[:, k] = np.maximum(R[:, k], 0.5 * np.asarray(amax) * smax)
+    if U is not None:
+        s2 = sum(U[:, k] ** 2 for k in MOMENTUM)
+        p = (gamma - 1.0) * (U[:, EGAS] - 0.5 * s2 / U[:, RHO])
+        pm = np.abs(p).reshape(n, -1).max(axis=1) / hs
+        for k in MOMENTUM:
+            R[:, k] = np.maximum(R[:, k], pm)
     return R / scale
 
 
@@ -184,7 +193,7 @@ FLOOR32 = 4e-7 # ~7 EPS32: one FP32 rounding of the sub-grid's own largest value
 
 
 def mixed_budget(ref: np.ndarray, pert: np.ndarray, faces: np.ndarray, h, U: np.ndarray | None = None,
-                 amax: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray]:
+                 amax: np.ndarray | None = None, gamma: float = 5.0 / 3.0) -> tuple[np.ndarray, np.ndarray]:
     """Per-sub-grid, per-field error budget [n][F] of the mixed-precision step
     against the oracle, in units of subgrid_scales(ref, h).
 
@@ -194,13 +203,14 @@ def mixed_budget(ref: np.ndarray, pert: np.ndarray, faces: np.ndarray, h, U: np.
     adds rounding of relative size ~EPS32 to every term of every point flux
     and point torque, which the FP64 divergence keeps: at most a few EPS32
     times the terms of the rate (R, flux_ratio; pass the padded states U
-    and the oracle's amax to include the dissipation terms).  That term
+    and the oracle's amax to include the dissipation and pressure terms;
+    gamma the adiabatic index of the states).  That term
     dominates where a rate is a small residual of large terms (near
     hydrostatic equilibrium, hot thin gas).
     Budget: C_SENS sens + C_ARITH EPS32 R + FLOOR32.  Returns (budget, sens)."""
     sc = subgrid_scales(ref, h)
     sens = _ratio(_per_sub(pert - ref), sc)
-    R = flux_ratio(faces, np.where(sc > 0, sc, 1.0), h, U, amax)
+    R = flux_ratio(faces, np.where(sc > 0, sc, 1.0), h, U, amax, gamma)
     R = np.where(sc > 0, R, 0.0)
     budget = np.where(sc > 0, C_SENS * sens + C_ARITH * EPS32 * R + FLOOR32, 0.0)
     return budget, sens
@@ -214,10 +224,10 @@ def mixed_error(got: np.ndarray, ref: np.ndarray, h) -> np.ndarray:
 
 
 def mixed_worst(got: np.ndarray, ref: np.ndarray, pert: np.ndarray, faces: np.ndarray, h,
-                U: np.ndarray | None = None, amax: np.ndarray | None = None) -> float:
+                U: np.ndarray | None = None, amax: np.ndarray | None = None, gamma: float = 5.0 / 3.0) -> float:
     """Largest error / budget over sub-grids and fields (<= 1 passes; a field
     exactly zero in the oracle must be exactly zero in the result)."""
-    budget, _ = mixed_budget(ref, pert, faces, h, U, amax)
+    budget, _ = mixed_budget(ref, pert, faces, h, U, amax, gamma)
     err = mixed_error(got, ref, h)
     exact = budget == 0.0
     r = np.where(exact, np.where(err > 0, np.inf, 0.0), err / np.where(exact, 1.0, budget))

@@ -136,7 +136,6 @@ int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
 
 int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st) {
   if (d->amr || c->mode.precision != HYDRO_PREC_MIXED || c->N != hyd::N) return HYDRO_EUNSUP;
-  if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;
   if (d->bc != HYDRO_BC_PERIODIC && d->bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
   if (!aligned16(d->a.U) || !aligned16(d->U_b) || !aligned16(d->dUdt)) return HYDRO_EINVAL;
   int rc = hydro_ctx_prepare_fused(c, d->a.n_sub);
@@ -234,7 +233,6 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   if (!B->U || !B->origin || !B->h || !dUdt || !amax) return HYDRO_EINVAL;
   if (!aligned16(B->U) || !aligned16(dUdt)) return HYDRO_EINVAL;
   const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
-  if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;
   int rc = ensure_status(c);
   if (rc) return rc;
   const int slots = step_slots(c, mixed);

@@ -323,8 +323,9 @@ cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long li
 
 size_t rk3_fused_sync_words(int n_sub) { return (size_t)kSyncHead + 2 * (size_t)n_sub; }
 
-// The fused kernel instances: [decomposition: 0 rows, 1 planes][variant:
-// 0 plain, 1 learned indicator (rows only), 2 contact steepening].
+// The fused kernel instances: the row sweep plain, with the learned
+// indicator, with contact steepening, with both; the plane sweep plain and
+// with contact steepening (the indicator runs in the row sweep only).
 template <class Body>
 static cudaError_t fused_attr(int* per_sm) {
   cudaError_t e = cudaFuncSetAttribute(hydro_rk3_fused_kernel<Body>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -342,16 +343,18 @@ cudaError_t prepare_rk3_fused(int num_sms, int planes, int* max_grid) {
   static unsigned long long done = 0;
   static int per_sm_dev[64][2];
   cudaError_t e = once_per_device(&done, [] {
-    int dev = 0, p[5] = {0, 0, 0, 0, 0};
+    int dev = 0, p[6] = {0, 0, 0, 0, 0, 0};
     cudaError_t r = cudaGetDevice(&dev);
     if (r == cudaSuccess) r = fused_attr<RowBody<false, false>>(&p[0]);
     if (r == cudaSuccess) r = fused_attr<RowBody<true, false>>(&p[1]);
     if (r == cudaSuccess) r = fused_attr<RowBody<false, true>>(&p[2]);
     if (r == cudaSuccess) r = fused_attr<PlaneBody<false>>(&p[3]);
     if (r == cudaSuccess) r = fused_attr<PlaneBody<true>>(&p[4]);
+    if (r == cudaSuccess) r = fused_attr<RowBody<true, true>>(&p[5]);
     if (r != cudaSuccess) return r;
     int rows = p[0] < p[1] ? p[0] : p[1];
     rows = rows < p[2] ? rows : p[2];
+    rows = rows < p[5] ? rows : p[5];
     if (rows > 2) rows = 2;
     int pl = p[3] < p[4] ? p[3] : p[4];
     if (pl > 1) pl = 1;
@@ -416,6 +419,7 @@ cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double*
   if (e != cudaSuccess) return e;
   if (planes && !S.gate)
     return S.P.contact ? launch_fused<PlaneBody<true>>(A, max_grid, st) : launch_fused<PlaneBody<false>>(A, max_grid, st);
+  if (S.gate && S.P.contact) return launch_fused<RowBody<true, true>>(A, max_grid, st);
   if (S.gate) return launch_fused<RowBody<true, false>>(A, max_grid, st);
   if (S.P.contact) return launch_fused<RowBody<false, true>>(A, max_grid, st);
   return launch_fused<RowBody<false, false>>(A, max_grid, st);

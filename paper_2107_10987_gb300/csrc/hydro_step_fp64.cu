@@ -242,7 +242,8 @@ constexpr long kWaitPolls = 1L << 24;
 // kGate: the learned smoothness indicator is on (A.gate): its decisions per
 // reconstructed cell follow the primitives in shared memory ([S3] bytes of
 // flags and [S3] of predictions after the state).  kContact: contact
-// steepening (A.P.contact; not combined with the indicator).  NN: the
+// steepening (A.P.contact; with the indicator, only the cells it does not
+// mark smooth are steepened).  NN: the
 // sub-grids' edge (8, or 16: each 8^3 octant tile is a work unit staged from
 // its 14^3 window of the 22^3 array, Tile<NN>).
 template <bool kGate, bool kContact = false, int NN = N>
@@ -511,6 +512,9 @@ static cudaError_t fp64_attrs() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(hydro_step_fp64_kernel<false, true, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)step_fp64_smem_bytes(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(hydro_step_fp64_kernel<true, true, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_fp64_smem_bytes(true));
   return e;
 }
 
@@ -524,7 +528,9 @@ cudaError_t prepare_step_fp64() {
 
 template <int NN>
 static void launch_fp64_nn(const StepArgs64& A, int grid, cudaStream_t st) {
-  if (A.gate)
+  if (A.gate && A.P.contact)
+    hydro_step_fp64_kernel<true, true, NN><<<grid, kThreads64, step_fp64_smem_bytes(true), st>>>(A);
+  else if (A.gate)
     hydro_step_fp64_kernel<true, false, NN><<<grid, kThreads64, step_fp64_smem_bytes(true), st>>>(A);
   else if (A.P.contact)
     hydro_step_fp64_kernel<false, true, NN><<<grid, kThreads64, step_fp64_smem_bytes(false), st>>>(A);

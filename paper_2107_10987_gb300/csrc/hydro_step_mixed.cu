@@ -86,6 +86,7 @@ static cudaError_t mixed_attrs() {
   cudaError_t e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, false, NN>, at, rows);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true, false, NN>, at, rows);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, true, NN>, at, rows);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true, true, NN>, at, rows);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<false, NN>, at, planes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<true, NN>, at, planes);
   return e;
@@ -109,7 +110,10 @@ static void launch_mixed_nn(const StepArgs64& A, int grid, int planes, cudaStrea
     else
       hydro_step_mixed_planes_kernel<false, NN><<<grid, kThreadsPl, kPlaneSmemBytes, st>>>(A);
   } else if (A.gate) {
-    hydro_step_mixed_kernel<true, false, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+    if (A.P.contact)
+      hydro_step_mixed_kernel<true, true, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
+    else
+      hydro_step_mixed_kernel<true, false, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   } else if (A.P.contact) {
     hydro_step_mixed_kernel<false, true, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
   } else {

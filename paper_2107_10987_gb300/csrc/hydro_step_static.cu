@@ -76,7 +76,6 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   if (!B->U || !B->origin || !B->h || !dUdt || !amax) return HYDRO_EINVAL;
   if ((((uintptr_t)B->U) & 15u) || (((uintptr_t)dUdt) & 15u)) return HYDRO_EINVAL;
   if (c->mode.precision != HYDRO_PREC_FP64 || c->N != hyd::N) return HYDRO_EUNSUP;
-  if (c->mode.contact && c->gate_on) return HYDRO_EUNSUP;  // as hydro_step
   DeviceAddrs a;
   int rc = addrs_for_current_device(&a);
   if (rc) return rc;

@@ -13,10 +13,15 @@ against the oracle's steepening (pinned in test_oracle_contact.py):
   * three RK3 steps of an advected contact: FP64 within 1e-12 of the oracle;
   * conservation on a periodic mesh, and the rates differ from the
     unsteepened ones;
-  * the mode's checks: contact outside {0, 1} and the indicator together
-    with steepening are rejected, in the separate and the fused step (the
-    fused step's steepening itself is held to the separate launches bit for
-    bit in test_gpu_planes.py).
+  * with the learned indicator on: the cells it marks smooth take the
+    unlimited formula and are not steepened, the others are; the step
+    against the oracle's masked steepened step (FP64 to 1e-12, mixed within
+    the budget), with a threshold placed in a gap of the network's outputs
+    so that the two sides' decisions cannot differ; and the fused step with
+    both options bit for bit against the separate launches;
+  * the mode's checks: contact outside {0, 1} is rejected (the fused step's
+    steepening itself is held to the separate launches bit for bit in
+    test_gpu_planes.py).
 The last test prints the step times with and without steepening.
 """
 import numpy as np
@@ -180,30 +185,131 @@ def test_contact_conserves_on_periodic_mesh(H, mixed):
 
 
 def test_contact_mode_checks(H):
-    import ctypes as C
-    from oracle import gate
-    from paper_2107_10987_gb300.uniform import UniformRun
     ctx = H.Context(GAMMA, 0.0)
     for bad in (2, -1):
         with pytest.raises(H.HydroError):
             H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=bad)
-    # steepening does not combine with the learned indicator, in the
-    # separate step or the fused one
-    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, contact=1)
-    U = contact_subgrids(8, 3)
-    o, h = W.uniform_mesh(2)
-    run = UniformRun(ctx, U, o, h, 2, H.HYDRO_BC_PERIODIC, fused=True)
-    theta = torch.tensor(np.random.default_rng(5).normal(0, 0.3, gate.NPARAM).astype(np.float32), device="cuda")
-    H.hydro_set_indicator(ctx, theta, 0.5)
-    with pytest.raises(H.HydroError):
-        gpu_step(H, ctx, U, np.asarray(o), np.full(8, h))
-    assert H._lib().hydro_rk3_step(H._cp(ctx), C.byref(run.desc), 0, None) == H.HYDRO_EUNSUP
-    H.hydro_set_indicator(ctx, None)
-    dU, _ = gpu_step(H, ctx, U, np.asarray(o), np.full(8, h))
-    assert np.all(np.isfinite(dU))
-    torch.cuda.synchronize()
+
+
+def planar_contacts(n, seed):
+    """Padded sub-grids [n][F][14][14][14], each with one planar density
+    contact (1 on one side, 1/4 on the other, 1/2 in the cells the plane
+    passes through) at a random normal and offset through the block, level
+    pressure 1, a uniform velocity
+    (|v_i| <= 0.3), small uniform spin and species half the density: most
+    cells sit in uniform neighbourhoods (the indicator's smooth cells), the
+    rest at a contact that steepening acts on.  Density and pressure are
+    exact in FP32."""
+    rng = np.random.default_rng(seed)
+    c = np.arange(14) - 6.5
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    out = np.empty((n, 10, 14, 14, 14))
+    for i in range(n):
+        nrm = rng.normal(size=3)
+        nrm /= np.linalg.norm(nrm)
+        dist = nrm[0] * X + nrm[1] * Y + nrm[2] * Z - rng.uniform(-3.0, 3.0)
+        # 1 behind the plane, 1/4 ahead, 1/2 in the cells it passes through
+        # (a contact spread over a cell, which steepening sharpens)
+        rho = np.where(dist < -0.5, 1.0, np.where(dist > 0.5, 0.25, 0.5))
+        sh = rho.shape
+        v = np.stack([np.full(sh, rng.uniform(-0.3, 0.3)) for _ in range(3)])
+        z = np.stack([np.full(sh, rng.uniform(-0.01, 0.01)) for _ in range(3)])
+        out[i] = W.conserved_from_primitive(rho, v, np.ones(sh), GAMMA, z=z, species=0.5 * rho)
+    return out
+
+
+def _indicator_mask(U, seed):
+    """Seeded indicator parameters, a threshold just above the network's
+    output for a uniform neighbourhood (all features zero) and in a gap of
+    at least 5e-5 to the next output, so that uniform cells are smooth and
+    the GPU's and the oracle's decisions cannot differ; and the oracle's
+    dilated smooth mask [n][14][14][14] on the reconstructed 10^3 block."""
+    from oracle import gate
+    n = U.shape[0]
+    theta = np.random.default_rng(seed).normal(0, 0.3, gate.NPARAM).astype(np.float32)
+    th = gate.bf16_round(theta)
+    out = gate.forward_infer(th, gate.features(U, GAMMA, lo=-2, hi=10))
+    c0 = float(gate.forward_infer(th, np.zeros((1, 54)))[0])
+    above = out[out > c0 + 1e-7]
+    gap = float(above.min()) - c0 if above.size else 1.0
+    assert gap > 5e-5, gap
+    thr = c0 + 0.5 * gap
+    pred = (out < thr).reshape(n, 12, 12, 12)
+    dil = np.ones((n, 10, 10, 10), bool)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                dil &= pred[:, dz:dz + 10, dy:dy + 10, dx:dx + 10]
+    mask = np.zeros((n, 14, 14, 14), np.uint8)
+    mask[:, 2:12, 2:12, 2:12] = dil
+    return theta, float(thr), mask
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_contact_with_indicator_matches_masked_oracle(H, orc, fp64):
+    """Steepening together with the learned indicator: cells marked smooth
+    take the unlimited formula and are not steepened, the others are
+    (reading of the indicator with steepening, pinned in
+    test_oracle_contact.py).  Planar contacts of density levels 1, 1/2 and
+    1/4 at a level pressure: the unlimited formula stays positive there, and
+    every steepening decision is exact in FP32 as in FP64."""
+    from oracle.compare import max_rel_error, mixed_worst, rate_floor
+    n = 12
+    U = planar_contacts(n, 81)
+    theta, thr, mask = _indicator_mask(U, 82)
+    assert 0.02 < mask.sum() / (n * 1000) < 0.98
+    rng = np.random.default_rng(83)
+    origin = rng.uniform(-1, 1, (n, 3))
+    h = rng.uniform(0.01, 0.1, n)
+    P = orc.OracleParams(gamma=GAMMA, contact=1)
+    ref, amo = orc.step_masked(P, U, origin, h, mask)
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64 if fp64 else H.HYDRO_PREC_MIXED, contact=1)
+    H.hydro_set_indicator(ctx, torch.tensor(theta, device="cuda"), thr)
+    dU, am = gpu_step(H, ctx, U, origin, h)
     assert H.hydro_status(ctx) == 0
-    run.close()
+    assert np.all(np.isfinite(dU))
+    # steepening acts on this data (the masked unsteepened step differs)
+    ref_plain, _ = orc.step_masked(orc.OracleParams(gamma=GAMMA), U, origin, h, mask)
+    assert max_rel_error(ref_plain, ref, h) > 1e-3
+    if fp64:
+        assert max_rel_error(dU, ref, h, rate_floor(U, amo, h)) <= 1e-12
+        assert np.allclose(am, amo, rtol=1e-14, atol=0)
+        return
+    pert, _ = orc.step_masked(P, U.astype(np.float32).astype(np.float64), origin, h, mask)
+    worst = mixed_worst(dU, ref, pert, None, h, U, amo)
+    print("mixed contact + indicator step: largest err/budget", worst)
+    assert worst <= 1.0
+
+
+def test_fused_contact_with_indicator_equals_separate_launches(H):
+    """The fused step with steepening and the indicator against the separate
+    launches: the interiors after every step and every dt, bit for bit."""
+    from paper_2107_10987_gb300.uniform import UniformRun
+    nb = (3, 2, 2)
+    n = nb[0] * nb[1] * nb[2]
+    U = planar_contacts(n, 91)
+    theta, thr, _ = _indicator_mask(U, 92)
+    h = 0.05
+    o = np.array([(8 * kx * h, 8 * ky * h, 8 * kz * h) for kz in range(nb[2]) for ky in range(nb[1])
+                  for kx in range(nb[0])])
+    runs = []
+    for fused in (False, True):
+        ctx = H.Context(GAMMA, 0.0)
+        H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, contact=1)
+        H.hydro_set_indicator(ctx, torch.tensor(theta, device="cuda"), thr)
+        runs.append((ctx, UniformRun(ctx, U, o, h, nb, H.HYDRO_BC_PERIODIC, fused=fused)))
+    (cs, sep), (cf, fus) = runs
+    for k in range(3):
+        sep.step()
+        fus.step()
+        torch.cuda.synchronize()
+        assert np.float64(fus.last_dt()).view(np.int64) == np.float64(sep.last_dt()).view(np.int64), k
+        a, b = fus.interior(), sep.interior()
+        assert bool((a.contiguous().view(torch.int64) == b.contiguous().view(torch.int64)).all()), k
+    assert H.hydro_status(cs) == 0 and H.hydro_status(cf) == 0
+    fus.close()
+    sep.close()
 
 
 def test_contact_step_cost(H):

@@ -41,12 +41,13 @@ def _bits(t):
     return t.contiguous().view(torch.int64)
 
 
-@pytest.mark.parametrize("variant", ["default", "old_module", "contact", "indicator"])
+@pytest.mark.parametrize("variant", ["default", "old_module", "contact", "indicator", "contact_indicator"])
 def test_static_step_matches_hydro_step_on_two_calls_in_a_row(H, variant):
     """Each sub-grid is computed by one CTA in a fixed order in both entry
     points, so the results are equal bit for bit, for every mode the FP64
     kernel has: the 9-point faces, the face-centre flux (old module),
-    contact steepening, the learned indicator.  A second call, after a
+    contact steepening, the learned indicator, and steepening with the
+    indicator.  A second call, after a
     warm-up, changes neither torch's nor the driver's count of free device
     memory."""
     dev = torch.device("cuda")
@@ -55,8 +56,10 @@ def test_static_step_matches_hydro_step_on_two_calls_in_a_row(H, variant):
         H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, flux_points=1)
     elif variant == "contact":
         H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=1)
-    elif variant == "indicator":
+    elif variant in ("indicator", "contact_indicator"):
         from oracle import gate
+        if variant == "contact_indicator":
+            H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, contact=1)
         rng = np.random.default_rng(21)
         theta = torch.tensor(rng.normal(0, 0.3, gate.NPARAM).astype(np.float32), device=dev)
         H.hydro_set_indicator(ctx, theta, 0.9)
@@ -65,7 +68,7 @@ def test_static_step_matches_hydro_step_on_two_calls_in_a_row(H, variant):
     # must not see anything the first left in the shared array
     for call, (n, seed) in enumerate(((H.HYDRO_STATIC_MAX_SUB, 31), (37, 32))):
         # smooth data under the indicator: the unlimited formula stays physical
-        U, o, h = _inputs(n, seed, dev, smooth=variant == "indicator")
+        U, o, h = _inputs(n, seed, dev, smooth=variant in ("indicator", "contact_indicator"))
         B = H.make_batch(U, o, h)
         dU_ref = torch.empty((n, 10, 8, 8, 8), dtype=torch.float64, device=dev)
         am_ref = torch.empty(n, dtype=torch.float64, device=dev)
