@@ -23,8 +23,8 @@ cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, i
 cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, int nn, cudaStream_t st);
 cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
                              int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
-                             int planes, cudaStream_t st);
-cudaError_t prepare_rk3_fused(int num_sms, int planes, int* max_grid);
+                             int planes, int nn, cudaStream_t st);
+cudaError_t prepare_rk3_fused(int num_sms, int planes, int nn, int* max_grid);
 size_t rk3_fused_sync_words(int n_sub);
 cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long limit_ns, cudaStream_t st);
 cudaError_t launch_sums(const double* U, const double* origin, const double* h, int n_sub, double* part,
@@ -122,20 +122,20 @@ static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, dou
 int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
   int rc = hydro_ctx_prepare(c, n_sub);
   if (rc) return rc;
-  rc = ensure_buf(&c->u2, &c->u2_bytes, (size_t)n_sub * hyd::F * hyd::N3 * sizeof(double),
+  rc = ensure_buf(&c->u2, &c->u2_bytes, (size_t)n_sub * hyd::F * c->N * c->N * c->N * sizeof(double),
                   "cudaMalloc(fused second-stage state)");
   if (rc) return rc;
   const size_t words = hyd::rk3_fused_sync_words(n_sub);
   rc = ensure_buf(&c->sync, &c->sync_bytes, (words * sizeof(unsigned) + 7) / 8 * 8, "cudaMalloc(fused sync words)");
   if (rc) return rc;
   int max_grid = 0;
-  cudaError_t e = hyd::prepare_rk3_fused(c->num_sms, 0, &max_grid);
+  cudaError_t e = hyd::prepare_rk3_fused(c->num_sms, 0, c->N, &max_grid);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_ctx_prepare_fused");
   return HYDRO_OK;
 }
 
 int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st) {
-  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED || c->N != hyd::N) return HYDRO_EUNSUP;
+  if (d->amr || c->mode.precision != HYDRO_PREC_MIXED) return HYDRO_EUNSUP;
   if (d->bc != HYDRO_BC_PERIODIC && d->bc != HYDRO_BC_OUTFLOW) return HYDRO_EINVAL;
   if (!aligned16(d->a.U) || !aligned16(d->U_b) || !aligned16(d->dUdt)) return HYDRO_EINVAL;
   int rc = hydro_ctx_prepare_fused(c, d->a.n_sub);
@@ -150,7 +150,7 @@ int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity,
   const double cfl = d->cfl > 0.0 ? d->cfl : c->mode.cfl;
   cudaError_t e = hyd::launch_rk3_fused(S, Y, c->u2, d->dt, reinterpret_cast<unsigned*>(c->sync), d->nbx, d->nby,
                                         d->nbz, d->bc, cfl, c->mode.de_eta2, c->gamma, c->num_sms,
-                                        eff_decomp(c) == HYDRO_DECOMP_PLANES, st);
+                                        eff_decomp(c) == HYDRO_DECOMP_PLANES, c->N, st);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_rk3_step (fused)");
   return HYDRO_OK;
 }

@@ -18,7 +18,12 @@ and flux correction) are templated on the sub-grid size.  Held to:
   * an adaptive mesh of 16^3 leaves: the two-pass ghost fill bitwise against
     the oracle's octree, a whole RK3 step within 1e-12 of it, and the GPU's
     16^3 and 8^3-cut runs bit for bit;
-  * the fused step and the allocation-free entry point reject 16^3 (EUNSUP).
+  * the fused RK3 step (each octant tile a work unit): bit for bit equal to
+    the separate 16^3 launches (row and plane sweeps, with and without
+    contact steepening; a ragged box with a blast, periodic and outflow; the
+    rotating polytrope with gravity), and without rotation to the fused step
+    on the same box cut into 8^3;
+  * the allocation-free entry point rejects 16^3 (EUNSUP).
 """
 import numpy as np
 import pytest
@@ -264,16 +269,74 @@ def test_sixteen_adaptive_mesh(H, oracle_mod):
     run8.close()
 
 
-def test_sixteen_rejections(H):
-    import ctypes as C
+def _blast_box(nx, ny, nz, seed=0, h=0.05):
+    """A box of seeded random density, pressure and velocity with a blast in
+    one corner (flow crosses periodic boundaries; no sub-grid is uniform)."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.2 * rng.random((nz, ny, nx))
+    p = 1e-3 * (1.0 + rng.random((nz, ny, nx)))
+    v = 0.1 * rng.normal(size=(3, nz, ny, nx))
+    p[:2, :2, :2] += (GAMMA - 1.0) * 1e-3 / (8 * h ** 3)
+    return W.conserved_from_primitive(rho, v, p, GAMMA), h
+
+
+def _run(H, N, Ui, o, h, nb, bc, fused, decomp, contact=0, omega=0.0, g=None, steps=3):
     from paper_2107_10987_gb300.uniform import UniformRun
-    ctx = H.Context(GAMMA, 0.0, N=16)
-    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
-    Ug, h, lo = W.sedov_box(32, GAMMA)
+    ctx = H.Context(GAMMA, omega, N=N)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, contact=contact)
+    H.hydro_set_launch(ctx, decomp)
+    run = UniformRun(ctx, Ui, o, h, nb, bc, g, fused=fused)
+    dts = []
+    for _ in range(steps):
+        run.step()
+        dts.append(run.last_dt())
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    out = run.interior()
+    run.close()
+    return out, np.array(dts)
+
+
+@pytest.mark.parametrize("decomp,contact", [("rows", 0), ("planes", 0), ("rows", 1), ("planes", 1)])
+@pytest.mark.parametrize("bc", ["periodic", "outflow"])
+def test_sixteen_fused_step(H, decomp, contact, bc):
+    """The fused step on a ragged box of 2 x 1 x 3 sub-grids of 16^3 with a
+    blast: the interiors and dt after each of three steps equal the separate
+    16^3 launches' bit for bit, and the fused step on the box cut into 8^3
+    (4 x 2 x 6 sub-grids) bit for bit."""
     from oracle import mesh
-    run = UniformRun(ctx, np.ascontiguousarray(mesh.unjoin(Ug, 16)), mesh.origins(2, 2, 2, 16, h, lo), h, 2,
-                     H.HYDRO_BC_OUTFLOW, fused=True)
-    assert H._lib().hydro_rk3_step(H._cp(ctx), C.byref(run.desc), 0, None) == H.HYDRO_EUNSUP
+    dec = {"rows": H.HYDRO_DECOMP_ROWS, "planes": H.HYDRO_DECOMP_PLANES}[decomp]
+    code = {"periodic": H.HYDRO_BC_PERIODIC, "outflow": H.HYDRO_BC_OUTFLOW}[bc]
+    Ug, h = _blast_box(32, 16, 48)
+    lo = (0.0, 0.0, 0.0)
+    res = {}
+    for N, nb in ((16, (2, 1, 3)), (8, (4, 2, 6))):
+        Ui = mesh.unjoin(Ug, N)
+        o = mesh.origins(*nb, N, h, lo)
+        for fused in ((True, False) if N == 16 else (True,)):
+            got, dts = _run(H, N, Ui, o, h, nb, code, fused, dec, contact)
+            res[N, fused] = (mesh.join(got.cpu().numpy(), *nb), dts)
+    (a, da), (b, db), (c, dc) = res[16, True], res[16, False], res[8, True]
+    assert np.array_equal(da.view(np.int64), db.view(np.int64)) and np.array_equal(da.view(np.int64),
+                                                                                    dc.view(np.int64))
+    assert np.array_equal(a.view(np.int64), b.view(np.int64)), int((a != b).sum())
+    assert np.array_equal(a.view(np.int64), c.view(np.int64)), int((a != c).sum())
+
+
+@pytest.mark.parametrize("decomp", ["rows", "planes"])
+def test_sixteen_fused_polytrope(H, decomp):
+    """The fused step on the rotating polytrope (omega = 0.2, gravity) cut
+    into 4^3 sub-grids of 16^3: bit for bit equal to the separate launches."""
+    dec = {"rows": H.HYDRO_DECOMP_ROWS, "planes": H.HYDRO_DECOMP_PLANES}[decomp]
+    Ui, g, o, h, _ = W.rotating_polytrope(4, GAMMA, N=16)
+    a, da = _run(H, 16, Ui, o, h, 4, H.HYDRO_BC_OUTFLOW, True, dec, omega=0.2, g=g, steps=2)
+    b, db = _run(H, 16, Ui, o, h, 4, H.HYDRO_BC_OUTFLOW, False, dec, omega=0.2, g=g, steps=2)
+    assert np.array_equal(da.view(np.int64), db.view(np.int64))
+    assert bool((bits(a) == bits(b)).all()), int((bits(a) != bits(b)).sum())
+
+
+def test_sixteen_rejections(H):
+    ctx = H.Context(GAMMA, 0.0, N=16)
     H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64)
     with pytest.raises(H.HydroError) as e:
         H.hydro_step_static(ctx, H.Batch(2, 16, 16, 16, None), 0.0, 16, 16)
@@ -281,4 +344,3 @@ def test_sixteen_rejections(H):
     with pytest.raises(H.HydroError) as e:
         H.Context(GAMMA, 0.0, N=12)
     assert e.value.code == H.HYDRO_EINVAL
-    run.close()
