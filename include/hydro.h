@@ -76,9 +76,9 @@ typedef struct hydro_ctx hydro_ctx_t;
  * be 3: the 5-cell PPM stencil plus the face-adjacent ghost row),
  * n_species >= 1.  With N = 16 the step kernels process each sub-grid as its
  * eight 8^3 octants, each read in place from its 14^3 window of the padded
- * array (no copy); the mesh kernels work on the 16^3 layout.  Not available
- * with N = 16: the fused RK3 step, hydro_step_static and hydro_gate_data
- * (EUNSUP). */
+ * array (no copy), and the fused RK3 step takes each octant as a work
+ * unit; the mesh kernels work on the 16^3 layout.  Not available with
+ * N = 16: hydro_step_static and hydro_gate_data (EUNSUP). */
 typedef struct {
   int N;
   int ghost;
