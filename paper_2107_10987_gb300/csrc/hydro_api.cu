@@ -21,9 +21,9 @@ cudaError_t launch_dt(const double* amax, const double* h, int n, double cfl, do
 cudaError_t launch_ghost_uniform(double* U, int nbx, int nby, int nbz, int bc, int num_sms, int nn,
                                  cudaStream_t st);
 cudaError_t launch_interior(double* U, double* I, int n_sub, bool scatter, int num_sms, int nn, cudaStream_t st);
-cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
-                             int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
-                             int planes, int nn, cudaStream_t st);
+cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, float* prims, double* dt_out,
+                             unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
+                             double gamma, int num_sms, int planes, int nn, cudaStream_t st);
 cudaError_t prepare_rk3_fused(int num_sms, int planes, int nn, int* max_grid);
 size_t rk3_fused_sync_words(int n_sub);
 cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long limit_ns, cudaStream_t st);
@@ -125,6 +125,9 @@ int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
   rc = ensure_buf(&c->u2, &c->u2_bytes, (size_t)n_sub * hyd::F * c->N * c->N * c->N * sizeof(double),
                   "cudaMalloc(fused second-stage state)");
   if (rc) return rc;
+  rc = ensure_buf(&c->prims, &c->prims_bytes, 2 * (size_t)n_sub * hyd::F * c->N * c->N * c->N * sizeof(float),
+                  "cudaMalloc(fused primitives)");
+  if (rc) return rc;
   const size_t words = hyd::rk3_fused_sync_words(n_sub);
   rc = ensure_buf(&c->sync, &c->sync_bytes, (words * sizeof(unsigned) + 7) / 8 * 8, "cudaMalloc(fused sync words)");
   if (rc) return rc;
@@ -148,7 +151,8 @@ int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity,
   }
   const hyd::StepArgs64 S = step_args(c, &X, d->dUdt, d->amax, nullptr);
   const double cfl = d->cfl > 0.0 ? d->cfl : c->mode.cfl;
-  cudaError_t e = hyd::launch_rk3_fused(S, Y, c->u2, d->dt, reinterpret_cast<unsigned*>(c->sync), d->nbx, d->nby,
+  cudaError_t e = hyd::launch_rk3_fused(S, Y, c->u2, reinterpret_cast<float*>(c->prims), d->dt,
+                                        reinterpret_cast<unsigned*>(c->sync), d->nbx, d->nby,
                                         d->nbz, d->bc, cfl, c->mode.de_eta2, c->gamma, c->num_sms,
                                         eff_decomp(c) == HYDRO_DECOMP_PLANES, c->N, st);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_rk3_step (fused)");
@@ -469,6 +473,7 @@ void hydro_destroy(hydro_ctx_t* c) {
   if (c->part) cudaFree(c->part);
   if (c->gate_w) cudaFree(c->gate_w);
   if (c->u2) cudaFree(c->u2);
+  if (c->prims) cudaFree(c->prims);
   if (c->sync) cudaFree(c->sync);
   delete c;
 }

@@ -25,6 +25,8 @@ struct hydro_ctx {
   float* gate_w;         // BF16-rounded indicator parameters (device)
   double* u2;            // fused RK3 step: second-stage state [n_sub][F][N^3]
   size_t u2_bytes;
+  double* prims;         // fused RK3 step: 2 x [n_sub][F][N^3] FP32 primitives (float words)
+  size_t prims_bytes;
   double* sync;          // fused RK3 step: barrier, work counter and per-sub-grid flags (unsigned words)
   size_t sync_bytes;
 };

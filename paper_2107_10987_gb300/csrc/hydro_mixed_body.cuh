@@ -127,6 +127,10 @@ __device__ __forceinline__ void finish_cell(const StepArgs64& A, const Io& io, c
 //   io.sidx(sub), io.offx(sub), io.offy(sub)  the sub-grid (for h, origin)
 //                             and the tile's x and y cell offsets in it
 //   io.load(sub, c, u)        conserved state u[F] of padded cell c
+//   Io::kPrims, io.load_prims(sub, c, q)  if kPrims: the FP32 primitives
+//                             q[F] of padded cell c instead (prims_mixed of
+//                             its state, non-physical cells reported by the
+//                             producer)
 //   io.own(sub, c, uc, u)     conserved state of interior cell c (padded index uc)
 //   io.store(sub, c, uc, du, u)  dU/dt of interior cell c; u is its state from own()
 //   io.grav(sub, c, gx, gy, gz)  gravity at interior cell c
@@ -151,12 +155,18 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
   sub_coords(coord, hd, o[0], o[1], offx, offy);
 
   // ---- 1-2. load the FP64 state, recover primitives, store FP32 ---------
+  // (an Io with kPrims supplies the primitives, recovered once per cell by
+  // whoever produced the state, and reports non-physical cells itself)
   bool bad = false;
   for (int c = tid; c < S3; c += kThreadsMx) {
-    double u[F];
-    io.load(sub, c, u);
     float q[F];
-    bad |= !prims_mixed(u, A.P.eta1, PF.gamma, q);
+    if constexpr (Io::kPrims) {
+      io.load_prims(sub, c, q);
+    } else {
+      double u[F];
+      io.load(sub, c, u);
+      bad |= !prims_mixed(u, A.P.eta1, PF.gamma, q);
+    }
 #pragma unroll
     for (int k = 0; k < F; ++k) Qf[k * S3 + c] = q[k];
   }

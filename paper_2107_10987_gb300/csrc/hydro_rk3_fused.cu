@@ -4,9 +4,9 @@
 
 namespace hyd {
 
-cudaError_t launch_rk3_fused16(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
-                               int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
-                               int planes, cudaStream_t st);
+cudaError_t launch_rk3_fused16(const StepArgs64& S, double* Y, double* U2, float* prims, double* dt_out,
+                               unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
+                               double gamma, int num_sms, int planes, cudaStream_t st);
 cudaError_t prepare_rk3_fused16(int num_sms, int planes, int* max_grid);
 
 // Self-test of the bounded wait: thread 0 waits on a flag that nothing sets
@@ -30,12 +30,14 @@ cudaError_t prepare_rk3_fused(int num_sms, int planes, int nn, int* max_grid) {
 }
 
 // nn: the sub-grids' edge (8 or 16).
-cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync, int nbx,
-                             int nby, int nbz, int bc, double cfl, double eta2, double gamma, int num_sms,
-                             int planes, int nn, cudaStream_t st) {
+cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, float* prims, double* dt_out,
+                             unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
+                             double gamma, int num_sms, int planes, int nn, cudaStream_t st) {
   if (nn == 16)
-    return launch_rk3_fused16(S, Y, U2, dt_out, sync, nbx, nby, nbz, bc, cfl, eta2, gamma, num_sms, planes, st);
-  return launch_fused_nn<8>(S, Y, U2, dt_out, sync, nbx, nby, nbz, bc, cfl, eta2, gamma, num_sms, planes, st);
+    return launch_rk3_fused16(S, Y, U2, prims, dt_out, sync, nbx, nby, nbz, bc, cfl, eta2, gamma, num_sms,
+                              planes, st);
+  return launch_fused_nn<8>(S, Y, U2, prims, dt_out, sync, nbx, nby, nbz, bc, cfl, eta2, gamma, num_sms, planes,
+                            st);
 }
 
 }  // namespace hyd

@@ -29,6 +29,14 @@
 // resident CTAs.  Each wait is still bounded in time and polls and reports
 // HYDRO_ST_TIMEOUT.
 //
+// The row sweep reads the FP32 primitives of its windows (prims_mixed of
+// the FP64 state) from a buffer that the producer of each state fills, once
+// per cell: a pass over X's interiors before stage 0 (with one more grid
+// barrier), the U1 writes and the stage-1 stores.  The separate launches
+// recover them in every padded cell of every window, from the same FP64
+// values, so the bits are the same; the conversions and the dual-energy
+// recovery in FP64 drop from 2,744 to 512 per sub-grid and stage.
+//
 // With 16^3 sub-grids a work unit is one of a sub-grid's eight 8^3 octant
 // tiles (Tile), and a sub-grid's U1 or U2 counts as published once all
 // eight tiles have added theirs to its flag.
@@ -53,14 +61,32 @@ struct FusedArgs {
   double cfl, eta2, inv_gamma;
   double alpha[3], beta[3];  // the stage coefficients of the update kernel
   long long wait_ns;    // bound of every wait
+  float* P[2];          // FP32 primitives of the stage inputs, [n][F][NN^3] each (row
+                        // sweep only; NULL otherwise): P[0] holds X's, then U2's;
+                        // P[1] holds U1's
 };
 constexpr int kSyncHead = 4;
 
 // Where the state of a tile (an 8^3 sub-grid, or an octant of a 16^3 one:
 // Tile) comes from, per stage (see above).
-template <int NN>
+// The FP32 primitives of one cell's state u (prims_mixed) into P at
+// compact cell ci of sub-grid s (NN^3 = n3 cells); a non-physical cell sets
+// the status bit.
+__device__ __forceinline__ void store_prims(const FusedArgs& A, float* P, int s, int ci, const double u[F], int n3) {
+  float q[F];
+  if (!prims_mixed(u, A.S.P.eta1, (float)A.S.P.gamma, q)) atomicOr(A.S.status, 1u);
+  float* p = P + (size_t)s * F * n3 + ci;
+#pragma unroll
+  for (int k = 0; k < F; ++k) p[(size_t)k * n3] = q[k];
+}
+
+// kPrims: the row sweep reads the FP32 primitives of its window from P
+// (recovered once per cell by the tile that produced the state) instead of
+// recovering them from the FP64 state of every padded cell.
+template <int NN, bool kPrimsIn = false>
 struct FusedIo {
   using T = Tile<NN>;
+  static constexpr bool kPrims = kPrimsIn;
   const FusedArgs& A;
   int stage;
   double dt;
@@ -112,6 +138,19 @@ struct FusedIo {
     state(os, (iz * NN + iy) * NN + ix, ((iz + G) * T::kS + (iy + G)) * T::kS + (ix + G), u, f0, nf);
   }
   __device__ __forceinline__ void load(const Sub& q, int c, double u[F]) const { load_fields(q, c, 0, F, u); }
+  // The primitives of padded cell c of the tile (kPrims): from the stage
+  // input's primitive buffer, at the source cell of the boundary map.
+  __device__ __forceinline__ void load_prims(const Sub& q, int c, float* u) const {
+    const int nx = A.nbx * NN, ny = A.nby * NN, nz = A.nbz * NN;
+    const int gx = bc_map(q.kx * NN + q.t.o[0] + c % S - G, nx, A.bc);
+    const int gy = bc_map(q.ky * NN + q.t.o[1] + (c / S) % S - G, ny, A.bc);
+    const int gz = bc_map(q.kz * NN + q.t.o[2] + c / (S * S) - G, nz, A.bc);
+    const int os = ((gz / NN) * A.nby + (gy / NN)) * A.nbx + (gx / NN);
+    const int ix = gx & (NN - 1), iy = gy & (NN - 1), iz = gz & (NN - 1);
+    const float* p = A.P[stage == 1 ? 1 : 0] + (size_t)os * F * T::kN3 + (iz * NN + iy) * NN + ix;
+#pragma unroll
+    for (int k = 0; k < F; ++k) u[k] = __ldcg(p + (size_t)k * T::kN3);
+  }
   __device__ __forceinline__ void own(const Sub& q, int c, int uc, double u[F]) const {
     state(q.t.s, q.t.cell(c), q.t.pad(uc), u);
   }
@@ -132,6 +171,7 @@ struct FusedIo {
       double* o = A.U2 + (size_t)s * F * T::kN3 + ci;
 #pragma unroll
       for (int k = 0; k < F; ++k) o[(size_t)k * T::kN3] = un[k];
+      if (kPrims) store_prims(A, A.P[0], s, ci, un, T::kN3);  // U2's, for stage 2
     } else {
       double* o = A.Y + (size_t)s * F * T::kS3 + pi;
 #pragma unroll
@@ -213,6 +253,7 @@ static __device__ bool wait_neighbours(const FusedArgs& A, const unsigned* flags
 template <bool kGate, bool kContact>
 struct RowBody {
   static constexpr int kThreads = kThreadsMx, kMinBlocks = 2;
+  static constexpr bool kPrims = true;  // reads its windows' primitives from FusedArgs::P
   static constexpr size_t kRed = (kMixedSmemBytes + 15) / 16 * 16;
   static constexpr size_t kSmem = kRed + sizeof(float) * (kThreadsMx / 32);
   RowMap R;
@@ -230,6 +271,7 @@ struct RowBody {
 template <bool kContact>
 struct PlaneBody {
   static constexpr int kThreads = kThreadsPl, kMinBlocks = 1;
+  static constexpr bool kPrims = false;
   static constexpr size_t kSmem = kPlaneSmemBytes;
   unsigned char* sm;
   __device__ PlaneBody(const StepArgs64&, unsigned char* p) : sm(p) {}
@@ -255,25 +297,48 @@ __global__ void __launch_bounds__(Body::kThreads, Body::kMinBlocks) hydro_rk3_fu
   unsigned* published = A.sync + kSyncHead;    // U2 tiles done, per sub-grid
   unsigned* published1 = published + n;        // U1 tiles done, per sub-grid
 
+  using Io = FusedIo<NN, Body::kPrims>;
+  // grid-wide barrier number k (1, 2, ...): every CTA arrives once per barrier
+  auto grid_sync = [&](unsigned k) {
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(arrive, 1u);
+      const bool ok = wait_geq(arrive, k * gridDim.x, abort, A.wait_ns);
+      if (!ok) {
+        atomicOr(A.S.status, 2u);
+        atomicExch(abort, 1u);
+      }
+      sh_ok = ok;
+    }
+    __syncthreads();
+    return sh_ok != 0;
+  };
+  unsigned barriers = 0;
+
+  // ---- the primitives of X's interiors (row sweep), once per cell --------
+  if (Body::kPrims) {
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      const T t(u);
+      const double* __restrict__ x = A.S.U + (size_t)t.s * F * T::kS3;
+      for (int c = tid; c < N3; c += Body::kThreads) {
+        const int uc = t.pad((((c >> 6) + G) * S + (((c >> 3) & (N - 1)) + G)) * S + ((c & (N - 1)) + G));
+        double xv[F];
+#pragma unroll
+        for (int k = 0; k < F; ++k) xv[k] = __ldg(x + (size_t)k * T::kS3 + uc);
+        store_prims(A, A.P[0], t.s, t.cell(c), xv, T::kN3);
+      }
+    }
+    if (!grid_sync(++barriers)) return;
+  }
+
   // ---- stage 0 --------------------------------------------------------
   {
-    const FusedIo<NN> io{A, 0, 0.0};
+    const Io io{A, 0, 0.0};
     for (int u = blockIdx.x; u < units; u += gridDim.x) body.run(A.S, io, u);
   }
 
   // ---- grid-wide barrier, then dt (the reduction of hydro_dt_kernel) ----
-  if (tid == 0) {
-    __threadfence();
-    atomicAdd(arrive, 1u);
-    const bool ok = wait_geq(arrive, gridDim.x, abort, A.wait_ns);
-    if (!ok) {
-      atomicOr(A.S.status, 2u);
-      atomicExch(abort, 1u);
-    }
-    sh_ok = ok;
-  }
-  __syncthreads();
-  if (!sh_ok) return;
+  if (!grid_sync(++barriers)) return;
   double m = INFINITY;
   for (int i = tid; i < n; i += Body::kThreads) m = fmin(m, A.S.h[i] / __ldcg(A.S.amax + i));
 #pragma unroll
@@ -304,6 +369,7 @@ __global__ void __launch_bounds__(Body::kThreads, Body::kMinBlocks) hydro_rk3_fu
       rk3_cell<true>(xv, xv, rv, dt, A.alpha[0], A.beta[0], A.eta2, A.inv_gamma, u1);
 #pragma unroll
       for (int k = 0; k < F; ++k) y[(size_t)k * T::kS3 + uc] = u1[k];
+      if (Body::kPrims) store_prims(A, A.P[1], t.s, ci, u1, T::kN3);
     }
     __syncthreads();
     if (tid == 0) {
@@ -326,7 +392,7 @@ __global__ void __launch_bounds__(Body::kThreads, Body::kMinBlocks) hydro_rk3_fu
     const int tu = stage == 1 ? u : u - units;
     const int s = tu / T::kTiles;
     if (!wait_neighbours(A, stage == 1 ? published1 : published, s, (unsigned)T::kTiles, abort, &sh_ok)) break;
-    body.run(A.S, FusedIo<NN>{A, stage, dt}, tu);  // ends with a barrier
+    body.run(A.S, Io{A, stage, dt}, tu);  // ends with a barrier
     if (stage == 1 && tid == 0) {
       __threadfence();
       atomicAdd(published + s, 1u);
@@ -401,12 +467,13 @@ static cudaError_t launch_fused(const FusedArgs& A, int max_grid, cudaStream_t s
 
 // One fused RK3 step of a mesh of NN^3 sub-grids; sync must hold
 // rk3_fused_sync_words(n_sub) words, and with 16^3 sub-grids amax is the
-// atomic maximum over each sub-grid's tiles: both are cleared here.  planes:
+// atomic maximum over each sub-grid's tiles: both are cleared here.  prims:
+// 2 n_sub F NN^3 floats of scratch for the row sweep's primitives.  planes:
 // the plane-sweep body (no learned indicator); otherwise the row sweep.
 template <int NN>
-static cudaError_t launch_fused_nn(const StepArgs64& S, double* Y, double* U2, double* dt_out, unsigned* sync,
-                                   int nbx, int nby, int nbz, int bc, double cfl, double eta2, double gamma,
-                                   int num_sms, int planes, cudaStream_t st) {
+static cudaError_t launch_fused_nn(const StepArgs64& S, double* Y, double* U2, float* prims, double* dt_out,
+                                   unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
+                                   double gamma, int num_sms, int planes, cudaStream_t st) {
   int max_grid = 0;
   cudaError_t e = prepare_fused_nn<NN>(num_sms, planes, &max_grid);
   if (e != cudaSuccess) return e;
@@ -414,6 +481,8 @@ static cudaError_t launch_fused_nn(const StepArgs64& S, double* Y, double* U2, d
   A.S = S;
   A.Y = Y;
   A.U2 = U2;
+  A.P[0] = prims;
+  A.P[1] = prims + (size_t)S.n_sub * F * Tile<NN>::kN3;
   A.dt_out = dt_out;
   A.sync = sync;
   A.nbx = nbx;

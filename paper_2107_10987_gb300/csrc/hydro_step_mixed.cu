@@ -14,6 +14,7 @@ namespace hyd {
 template <int NN>
 struct StepIo {
   using T = Tile<NN>;
+  static constexpr bool kPrims = false;
   const StepArgs64& A;
   using Sub = T;
   __device__ __forceinline__ Sub begin(int u) const { return T(u); }
