@@ -178,7 +178,7 @@ ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 26
 # kernel (the Sedov figures were taken on earlier builds of the kernels).
 TRAFFIC_PER_LAUNCH = {"fp64_sedov": None, "mixed_sedov": None, "fused_sedov": None,
                       "fp64_polytrope": None, "mixed_polytrope": None,
-                      "fused_polytrope": 8 * (3866324e3 + 3775503e3)}
+                      "fused_polytrope": 8 * (3454249e3 + 3838850e3)}
 
 
 def algorithmic_work():
