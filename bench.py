@@ -175,8 +175,9 @@ ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 26
 # fused RK3 step (three stages per launch).  Captures on the 256^3 polytrope
 # are taken on its 128^3 cut (4,096 sub-grids) and scaled by 8 (traffic
 # grows with the sub-grids processed).  None until captured for the current
-# kernel (the Sedov figures were taken on earlier builds of the kernels).
-TRAFFIC_PER_LAUNCH = {"fp64_sedov": None, "mixed_sedov": None, "fused_sedov": None,
+# kernel.
+TRAFFIC_PER_LAUNCH = {"fp64_sedov": 117935104.0 + 90517760.0, "mixed_sedov": 143687424.0 + 103432960.0,
+                      "fused_sedov": 807951689.0,
                       "fp64_polytrope": None, "mixed_polytrope": None,
                       "fused_polytrope": 8 * (3454249e3 + 3838850e3)}
 
