@@ -80,9 +80,9 @@ __device__ __forceinline__ int rel_pos(int p, int base, int n, int bc, int lo, i
 // restricted ghost cell in the 4^3 positions 2p-1 .. 2p+2 one level down: the
 // table entries of both sets are read once per leaf into shared memory.
 // Pass 1 reads interior cells only and writes ghost cells only, so each
-// thread takes two ghost cells at a time and issues all their loads (read-
+// thread takes four ghost cells at a time and issues all their loads (read-
 // only path) before their stores.
-constexpr int kAmrBatch = 2;
+constexpr int kAmrBatch = 4;
 
 template <int NN>
 __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
