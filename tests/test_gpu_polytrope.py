@@ -8,6 +8,11 @@ ambient density 1e-10) on the GPU, through the C ABI.
   budget (oracle.compare.mixed_budget: 8 sens + 8 eps32 R + 4e-7 per
   sub-grid, sens = the oracle's own change on FP32-rounded inputs, R the
   face-flux terms of each rate over its scale);
+* at full size (256^3, 32,768 sub-grids): sampled sub-grids of one launch
+  of each form against the oracle, and the fused step as the benchmark
+  runs it -- its first-stage rates on every sub-grid bit for bit equal to
+  the separate mixed step's, and after one RK3 step its interiors and dt
+  bit for bit equal to the separate launches';
 * accuracy at 64^3 over 100 RK3 steps, FP64 and mixed forms side by side:
   the L1 density error against the initial state (Sec. VI's measure with an
   absolute value), the drift of the total angular momentum about the
@@ -32,6 +37,13 @@ def H():
     from paper_2107_10987_gb300 import _build, hydro
     _build.build()
     return hydro
+
+
+@pytest.fixture(scope="module")
+def full_mesh():
+    """The 256^3 polytrope (32,768 sub-grids): interiors, gravity, origins, h."""
+    Ui, g, o, h, _ = W.rotating_polytrope(32, GAMMA)
+    return Ui, g, o, h
 
 
 class PolyRun:
@@ -158,14 +170,14 @@ def test_polytrope_fp64_and_mixed_over_100_steps(H):
         assert abs(r["dM"]) <= 1e-7, res
 
 
-def test_full_size_sampled_parity(H, oracle_mod):
+def test_full_size_sampled_parity(H, oracle_mod, full_mesh):
     """The full rotating-polytrope mesh (32,768 sub-grids, 256^3 cells, 7.2 GB
     of padded state) in one launch of each form, as the benchmark runs it;
     48 seeded sub-grids (and the first and last) against the oracle."""
     from oracle.compare import max_rel_error, mixed_worst, rate_floor
     core = oracle_mod.core
     nb = 32
-    Ui, g, o, h, _ = W.rotating_polytrope(nb, GAMMA)
+    Ui, g, o, h = full_mesh
     n = Ui.shape[0]
     dev = "cuda"
     U = torch.zeros((n, 10, 14, 14, 14), dtype=torch.float64, device=dev)
@@ -175,7 +187,6 @@ def test_full_size_sampled_parity(H, oracle_mod):
     B = H.make_batch(U, ot, ht, gt)
     ctx = H.Context(GAMMA, OMEGA)
     H.hydro_scatter_interior(ctx, B, torch.tensor(Ui, device=dev))
-    del Ui
     H.hydro_fill_ghosts_uniform(ctx, B, nb, nb, nb, H.HYDRO_BC_OUTFLOW)
     rng = np.random.default_rng(2024)
     idx = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 48, replace=False)]))
@@ -198,3 +209,37 @@ def test_full_size_sampled_parity(H, oracle_mod):
             print("polytrope 256^3 sampled, mixed: largest err/budget", worst)
             assert worst <= 1.0
     assert H.hydro_status(ctx) == 0
+
+
+def test_full_size_fused_step(H, full_mesh):
+    """The fused RK3 step on the full 256^3 mesh, in the launch configuration
+    the benchmark times: the first stage's rates it leaves in dU/dt equal the
+    separate mixed step's on every sub-grid bit for bit (that step is held
+    to the oracle above), and one fused RK3 step gives the separate
+    launches' interiors and dt bit for bit."""
+    from paper_2107_10987_gb300.uniform import UniformRun
+    Ui, g, o, h = full_mesh
+    nb = 32
+    runs = {}
+    for fused in (False, True):
+        ctx = H.Context(GAMMA, OMEGA)
+        H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, 0.4)
+        run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_OUTFLOW, g, fused=fused)
+        if not fused:
+            # the separate step kernel's rates on the initial state
+            H.hydro_fill_ghosts_uniform(ctx, run.batches[0], nb, nb, nb, H.HYDRO_BC_OUTFLOW)
+            dU0 = torch.empty_like(run.dU)
+            am0 = torch.empty_like(run.am)
+            H.hydro_step(ctx, run.batches[0], 0.0, dU0, am0)
+        run.step()
+        torch.cuda.synchronize()
+        assert H.hydro_status(ctx) == 0
+        runs[fused] = (run, ctx)
+    (sep, _), (fus, _) = runs[False], runs[True]
+    assert bool((fus.dU.view(torch.int64) == dU0.view(torch.int64)).all())
+    assert bool((fus.am.view(torch.int64) == am0.view(torch.int64)).all())
+    assert np.float64(fus.last_dt()).view(np.int64) == np.float64(sep.last_dt()).view(np.int64)
+    a, b = fus.interior(), sep.interior()
+    assert bool((a.view(torch.int64) == b.view(torch.int64)).all()), int((a != b).sum())
+    fus.close()
+    sep.close()
