@@ -10,7 +10,9 @@
 #include "hydro_ctx.h"
 
 namespace hyd {
-cudaError_t launch_step_fp64(const StepArgs64& A, int grid, int nn, cudaStream_t st);
+cudaError_t launch_step_fp64_lines(const StepArgs64& A, int grid, int nn, cudaStream_t st);
+cudaError_t prepare_step_fp64_lines();
+size_t step_fp64_lines_per_cta();
 cudaError_t launch_step_mixed(const StepArgs64& A, int grid, int planes, int nn, cudaStream_t st);
 cudaError_t prepare_step_fp64();
 cudaError_t prepare_step_mixed();
@@ -93,6 +95,15 @@ static int step_slots(const hydro_ctx* c, bool mixed) {
   return 2 * c->num_sms;
 }
 
+// The FP64 step's per-CTA line-end buffers for its persistent grid over
+// `units` tiles (2.08 MB per CTA).
+static int ensure_lines(hydro_ctx* c, int units) {
+  const int slots = step_slots(c, false);
+  const int grid = units < slots ? units : slots;
+  return ensure_buf(&c->lines, &c->lines_bytes, (size_t)grid * hyd::step_fp64_lines_per_cta() * sizeof(double),
+                    "cudaMalloc(FP64 line ends)");
+}
+
 static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, double* dUdt, double* amax,
                                  double* face_flux) {
   hyd::StepArgs64 A;
@@ -104,6 +115,7 @@ static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, dou
   A.amax = amax;
   A.face_flux = face_flux;
   A.scratch = c->scratch;
+  A.lines = c->lines;
   A.status = c->status;
   A.n_sub = B->n_sub;
   A.P.gamma = c->gamma;
@@ -178,7 +190,12 @@ int hydro_ctx_prepare(hydro_ctx* c, int n_sub) {
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
+  if (c->mode.precision == HYDRO_PREC_FP64) {
+    rc = ensure_lines(c, units);
+    if (rc) return rc;
+  }
   cudaError_t e = hyd::prepare_step_fp64();
+  if (e == cudaSuccess) e = hyd::prepare_step_fp64_lines();
   if (e == cudaSuccess) e = hyd::prepare_step_mixed();
   if (e != cudaSuccess) return cuda_fail(e, "hydro_ctx_prepare");
   return HYDRO_OK;
@@ -245,10 +262,14 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
+  if (!mixed) {
+    rc = ensure_lines(c, units);
+    if (rc) return rc;
+  }
   const hyd::StepArgs64 A = step_args(c, B, dUdt, amax, face_flux);
   cudaError_t e = mixed ? hyd::launch_step_mixed(A, grid, eff_decomp(c) == HYDRO_DECOMP_PLANES, c->N,
                                                   (cudaStream_t)stream)
-                        : hyd::launch_step_fp64(A, grid, c->N, (cudaStream_t)stream);
+                        : hyd::launch_step_fp64_lines(A, grid, c->N, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_step");
   return HYDRO_OK;
 }
@@ -470,6 +491,7 @@ void hydro_destroy(hydro_ctx_t* c) {
   if (!c) return;
   if (c->status) cudaFree(c->status);
   if (c->scratch) cudaFree(c->scratch);
+  if (c->lines) cudaFree(c->lines);
   if (c->part) cudaFree(c->part);
   if (c->gate_w) cudaFree(c->gate_w);
   if (c->u2) cudaFree(c->u2);

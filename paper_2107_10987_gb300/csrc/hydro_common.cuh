@@ -105,6 +105,7 @@ struct StepArgs64 {
   double* amax;
   double* face_flux;  // optional [n_sub][6][DQ][N][N] boundary-face sums (null: none)
   double* scratch;  // per-CTA scratch, kScratchPerSub doubles per CTA
+  double* lines;    // FP64 step with every line once: per-CTA line ends (null for the other kernels)
   unsigned* status;
   int n_sub;
   StepParams P;

@@ -17,6 +17,8 @@ struct hydro_ctx {
   unsigned* status;      // device word
   double* scratch;       // step scratch
   size_t scratch_bytes;
+  double* lines;         // FP64 step: per-CTA line ends
+  size_t lines_bytes;
   double* part;          // conservation partials
   size_t part_bytes;
   int gate_on;           // learned smoothness indicator active (mixed mode)

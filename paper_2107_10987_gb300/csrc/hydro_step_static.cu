@@ -92,6 +92,7 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.amax = amax;
   A.face_flux = nullptr;
   A.scratch = a.scratch;  // one slot per CTA, one CTA per sub-grid
+  A.lines = nullptr;      // the axis-sweep kernel keeps its lines on chip
   A.status = word;
   A.n_sub = B->n_sub;
   A.P.gamma = c->gamma;

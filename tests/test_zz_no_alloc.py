@@ -3,7 +3,11 @@
 Callers that cannot call cudaMalloc (a host code whose device memory all
 belongs to its own pool allocator, or a time loop that cannot afford an
 allocation's device-wide synchronisation) use this entry point; it runs the
-same FP64 step kernel with its scratch in a fixed array of the library.  This
+FP64 step with its scratch in a fixed array of the library: the axis-sweep
+kernel, which reconstructs each line inside its three sweeps, where
+hydro_step's kernel evaluates every line once per cell into a per-CTA buffer.
+The two organisations compute the same operations on the same operands, so
+the comparison below is also a bit-for-bit check of one against the other.  This
 file is collected last so that a run stopping at the first failure has run
 everything else before it.
 """
@@ -43,9 +47,10 @@ def _bits(t):
 
 @pytest.mark.parametrize("variant", ["default", "old_module", "contact", "indicator", "contact_indicator"])
 def test_static_step_matches_hydro_step_on_two_calls_in_a_row(H, variant):
-    """Each sub-grid is computed by one CTA in a fixed order in both entry
-    points, so the results are equal bit for bit, for every mode the FP64
-    kernel has: the 9-point faces, the face-centre flux (old module),
+    """Both entry points run the same arithmetic in a fixed order per
+    sub-grid (each line's values are ppm64's, the face sums keep their order),
+    so the results are equal bit for bit, for every mode the FP64
+    kernels have: the 9-point faces, the face-centre flux (old module),
     contact steepening, the learned indicator, and steepening with the
     indicator.  A second call, after a
     warm-up, changes neither torch's nor the driver's count of free device
