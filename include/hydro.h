@@ -379,6 +379,17 @@ int hydro_rk3_graph_launch(hydro_graph_t* g, void* stream);
  * synchronise.  Errors: EINVAL, ENOMEM. */
 int hydro_selftest_wait(hydro_ctx_t* ctx, double seconds, void* stream);
 
+/* Self-test of the exact FP64 helpers of the FP64 step kernels, which
+ * replace FP64 operations by integer operations on the bit patterns (PPM and
+ * the MC limiter of Sec. III-B; Colella & Woodward 1984).  For i < n (device
+ * arrays x, y of n doubles, out of 2n doubles):
+ *   out[2i]     = x_i / 2 as the kernels halve (0.5 x_i rounded to nearest),
+ *   out[2i + 1] = the MC-limited slope from the differences (x_i, y_i): 0 if
+ *                 x_i y_i <= 0, else sgn(y_i) min(2|x_i|, 2|y_i|, |x_i + y_i|/2).
+ * A caller compares them bit for bit with the FP64 operations they stand
+ * for.  Asynchronous.  Errors: EINVAL (n < 0, null pointers with n > 0). */
+int hydro_selftest_arith(const double* x, const double* y, int n, double* out, void* stream);
+
 /* Which buffer holds the current state: 0 = a, 1 = b. */
 int hydro_rk3_graph_state(const hydro_graph_t* g);
 

@@ -42,16 +42,36 @@ __device__ __forceinline__ double twice_nonneg(double x) {
 // the sign bit set (-0 and the negatives) is negative as a signed integer.
 __device__ __forceinline__ bool nonpositive(double x) { return __double_as_longlong(x) <= 0LL; }
 
+// x / 2 exactly as the FP64 product 0.5 x rounds it (to nearest, ties to
+// even), on the integer pipes: with the exponent field at least 2 the result
+// is normal and the field drops by one (infinities and NaNs pass unchanged);
+// below that the magnitude's bit pattern is the significand with its
+// implicit bit (field 1) or without (zero, subnormals), and half of it,
+// rounded to even, is the result's pattern (a carry into bit 52 is the
+// smallest normal, correctly encoded).
+__device__ __forceinline__ double half64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long sign = b & 0x8000000000000000ull, mag = b ^ sign;
+  unsigned long long r;
+  if (mag >= (2ull << 52))
+    r = mag < (0x7ffull << 52) ? mag - (1ull << 52) : mag;
+  else
+    r = (mag >> 1) + (mag & (mag >> 1) & 1ull);
+  return __longlong_as_double((long long)(r | sign));
+}
+
 // MC-limited slope of sample j from delta_{j-1} = a and delta_j = b:
 // 0 if a b <= 0, else sgn(b) min(2|a|, 2|b|, |a + b|/2).  The product test is
 // the FP64 product, compared on its bit pattern; min(2|a|, 2|b|) =
 // 2 min(|a|, |b|) exactly, the minima of non-negative values are taken and
-// the doubling done on the bit patterns, and with a b > 0 the sign of the
-// result is the sign bit of b: the same bits as the FP64 multiplications,
-// fmin and comparisons, with 3 instead of 9 FP64 instructions.
+// the doubling and halving done on the bit patterns, and with a b > 0 the
+// sign of the result is the sign bit of b: the same bits as the FP64
+// multiplications, fmin and comparisons, with 2 instead of 9 FP64
+// instructions.  (An integer form of the product test, exact but for a
+// fallback near the underflow threshold, measured slower.)
 __device__ __forceinline__ double slope64(double a, double b) {
   if (nonpositive(rmul(a, b))) return 0.0;
-  const double m = min_nonneg(twice_nonneg(min_nonneg(fabs(a), fabs(b))), rmul(0.5, fabs(radd(a, b))));
+  const double m = min_nonneg(twice_nonneg(min_nonneg(fabs(a), fabs(b))), half64(fabs(radd(a, b))));
   const long long sign = __double_as_longlong(b) & (long long)0x8000000000000000ull;
   return __longlong_as_double(__double_as_longlong(m) | sign);
 }
@@ -62,7 +82,7 @@ __device__ __forceinline__ double slope64(double a, double b) {
 // number, so a sweep along the line may compute it once for both.
 __device__ __forceinline__ double ppm_iface64(double sa, double sb, double Da, double Db) {
   const double sixth = 1.0 / 6.0;
-  return rsub(rmul(0.5, radd(sa, sb)), rmul(rsub(Db, Da), sixth));
+  return rsub(half64(radd(sa, sb)), rmul(rsub(Db, Da), sixth));
 }
 
 // Contact steepening of the interface values p (+d) and m (-d) of the
@@ -71,8 +91,8 @@ __device__ __forceinline__ double ppm_iface64(double sa, double sb, double Da, d
 __device__ __forceinline__ void ppm_steep64(double s1, double s3, double D0, double D2, double eta, double& p,
                                             double& m) {
   const double keep = rsub(1.0, eta);
-  p = radd(rmul(keep, p), rmul(eta, rsub(s3, rmul(0.5, D2))));
-  m = radd(rmul(keep, m), rmul(eta, radd(s1, rmul(0.5, D0))));
+  p = radd(rmul(keep, p), rmul(eta, rsub(s3, half64(D2))));
+  m = radd(rmul(keep, m), rmul(eta, radd(s1, half64(D0))));
 }
 
 // The monotonicity fix-ups of PPM on the interface values p (+d) and m (-d)
@@ -86,7 +106,7 @@ __device__ __forceinline__ void ppm_limit64(double s2, double& p, double& m) {
     m = s2;
   } else {
     const double dq = rsub(p, m);
-    const double lhs = rmul(dq, rsub(s2, rmul(0.5, radd(p, m))));
+    const double lhs = rmul(dq, rsub(s2, half64(radd(p, m))));
     const double rhs = rmul(rmul(dq, dq), sixth);  // >= +0
     const long long kl = order_key(lhs);
     if (kl > order_key(rhs)) {
@@ -191,59 +211,95 @@ __device__ __forceinline__ void line10u(const double* __restrict__ Q, int c, int
   }
 }
 
-// Physical side state at a quadrature point: conserved U, flux F along axis a,
-// signal speed |u_n| + c.  u = v - omega z_hat x x_q (rotating frame).
+// Physical side state at a quadrature point: conserved U, the normal
+// velocity u_n and the a-component v_a of v, the pressure p and the signal
+// speed |u_n| + c.  u = v - omega z_hat x x_q (rotating frame), so u_n is one
+// FMA of the selected components (exactly v_z along z).
 __device__ __forceinline__ void side64(const double q[F], int a, double xq, double yq, const StepParams& P,
-                                       double U[F], double Fl[F], double& spd) {
+                                       double U[F], double& un, double& va, double& p, double& spd) {
   const double rho = q[RHO], vx = q[1], vy = q[2], vz = q[3], eps = q[4];
-  const double ek = (0.5 * rho) * ((vx * vx + vy * vy) + vz * vz);
-  const double E = eps + ek;
-  const double p = P.gm1 * eps;
+  const double ek = half64(rho) * ((vx * vx + vy * vy) + vz * vz);
+  p = P.gm1 * eps;
   // c = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal
   // square root instead of a division and a square root (a few ulps from the
   // correctly rounded value); c = 0 where p <= 0 (a non-physical state)
   const double gp = P.gamma * p;
   const double c = (__double_as_longlong(gp) <= 0LL) ? 0.0 : gp * rsqrt(gp * rho);
-  const double ux = vx + P.omega * yq, uy = vy - P.omega * xq;
-  const double un = (a == 0) ? ux : (a == 1) ? uy : vz;
-  const double va = (a == 0) ? vx : (a == 1) ? vy : vz;
+  va = (a == 0) ? vx : (a == 1) ? vy : vz;
+  const double om = (a == 0) ? P.omega : (a == 1) ? -P.omega : 0.0;
+  const double r = (a == 0) ? yq : (a == 1) ? xq : 0.0;
+  un = fma(om, r, va);
   U[RHO] = rho;
   U[SX] = rho * vx;
   U[SY] = rho * vy;
   U[SZ] = rho * vz;
-  U[EGAS] = E;
+  U[EGAS] = eps + ek;
 #pragma unroll
   for (int k = TAU; k < F; ++k) U[k] = q[k];
-#pragma unroll
-  for (int k = 0; k < F; ++k) Fl[k] = U[k] * un;
-  Fl[SX + a] += p;
-  Fl[EGAS] += p * va;
   spd = fabs(un) + c;
 }
 
-// Kurganov-Tadmor flux at one point, accumulated with weight w into the face
-// sum and into the torques about the left (rl) and right (rr) cell centres.
+// d x g for an integer vector d with components in {-1, 0, 1}: each term is
+// +-g_i or zero, taken by sign selection, so one FP64 subtraction per
+// component.
+__device__ __forceinline__ double signed_pick(int d, double x) { return d == 0 ? 0.0 : (d > 0 ? x : -x); }
+
+// Kurganov-Tadmor flux at one point with half its Simpson weight hw = w/2:
+//   w F_q = hw (F_L + F_R) - hw a_q (U_R - U_L),  F = U u_n (+ p e_a, + p v_a),
+// accumulated per field into the face sum (F_L + F_R as two fused products,
+// the weight folded into the fused accumulation).  The point lies at
+// x_L + (h/2) d from the left cell's centre (integer d, d_a = 1); the torque
+// sum T accumulates d x (w F_q) of the momentum flux, so that the face's
+// torque about the left centre is (h/2) T and about the right centre (at
+// x_L + h e_a) (h/2) T - h e_a x (sum of w F_q).
 __device__ __forceinline__ void point64(const double qL[F], const double qR[F], int a, double xq, double yq,
-                                        double w, const double rl[3], const double rr[3], const StepParams& P,
-                                        double fsum[F], double tl[3], double tr[3], double& amax) {
-  double UL[F], FL[F], UR[F], FR[F], sL, sR;
-  side64(qL, a, xq, yq, P, UL, FL, sL);
-  side64(qR, a, xq, yq, P, UR, FR, sR);
+                                        double hw, int d0, int d1, int d2, const StepParams& P, double fsum[F],
+                                        double T[3], double& amax) {
+  double UL[F], UR[F], unL, unR, vaL, vaR, pL, pR, sL, sR;
+  side64(qL, a, xq, yq, P, UL, unL, vaL, pL, sL);
+  side64(qR, a, xq, yq, P, UR, unR, vaR, pR, sR);
   const double aq = max_nonneg(sL, sR);  // signal speeds are >= 0
   amax = max_nonneg(amax, aq);
-  double Fq[F];
+  const double hwa = hw * aq;
+  const double pp = pL + pR;
+  double g[3];
 #pragma unroll
   for (int k = 0; k < F; ++k) {
-    Fq[k] = 0.5 * (FL[k] + FR[k]) - (0.5 * aq) * (UR[k] - UL[k]);
-    fsum[k] += w * Fq[k];
+    // the pressure terms of F_L + F_R: p in the normal momentum, p v_a in the energy
+    double extra = 0.0;
+    if (k == SX || k == SY || k == SZ) extra = (a == k - SX) ? pp : 0.0;
+    if (k == EGAS) extra = fma(pL, vaL, pR * vaR);
+    const double sum = fma(UL[k], unL, fma(UR[k], unR, extra));
+    const double dif = UR[k] - UL[k];
+    if (k == SX || k == SY || k == SZ) {
+      const double gk = fma(hw, sum, -(hwa * dif));
+      g[k - SX] = gk;
+      fsum[k] += gk;
+    } else {
+      fsum[k] = fma(hw, sum, fma(-hwa, dif, fsum[k]));
+    }
   }
-  const double fx = Fq[SX], fy = Fq[SY], fz = Fq[SZ];
-  tl[0] += w * (rl[1] * fz - rl[2] * fy);
-  tl[1] += w * (rl[2] * fx - rl[0] * fz);
-  tl[2] += w * (rl[0] * fy - rl[1] * fx);
-  tr[0] += w * (rr[1] * fz - rr[2] * fy);
-  tr[1] += w * (rr[2] * fx - rr[0] * fz);
-  tr[2] += w * (rr[0] * fy - rr[1] * fx);
+  T[0] += signed_pick(d1, g[2]) - signed_pick(d2, g[1]);
+  T[1] += signed_pick(d2, g[0]) - signed_pick(d0, g[2]);
+  T[2] += signed_pick(d0, g[1]) - signed_pick(d1, g[0]);
+}
+
+// The face's torques about the left and right cell centres from point64's
+// torque sum T and face sum fsum: tl = (h/2) T, tr = (h/2) (T - 2 e_a x m)
+// with m the momentum part of fsum.
+__device__ __forceinline__ void face_torques64(const double T[3], const double fsum[F], int a, double half_h,
+                                               double tl[3], double tr[3]) {
+  const double mx = fsum[SX], my = fsum[SY], mz = fsum[SZ];
+  // e_a x m
+  const double ex = (a == 0) ? 0.0 : (a == 1) ? mz : -my;
+  const double ey = (a == 0) ? -mz : (a == 1) ? 0.0 : mx;
+  const double ez = (a == 0) ? my : (a == 1) ? -mx : 0.0;
+  tl[0] = half_h * T[0];
+  tl[1] = half_h * T[1];
+  tl[2] = half_h * T[2];
+  tr[0] = half_h * (T[0] - (ex + ex));
+  tr[1] = half_h * (T[1] - (ey + ey));
+  tr[2] = half_h * (T[2] - (ez + ez));
 }
 
 }  // namespace hyd

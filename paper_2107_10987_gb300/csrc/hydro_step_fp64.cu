@@ -143,11 +143,10 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
 #pragma unroll 1
     for (int j = -1; j <= N; ++j) {
       const int cj = c0 + j * sa;
-      double fsum[F], tl[3], tr[3];
+      double fsum[F], T[3];
 #pragma unroll
       for (int k = 0; k < F; ++k) fsum[k] = 0.0;
-      tl[0] = tl[1] = tl[2] = 0.0;
-      tr[0] = tr[1] = tr[2] = 0.0;
+      T[0] = T[1] = T[2] = 0.0;
       // left cell of face j-1/2 is (j-1) along a
       const int ci0 = axis_comp(0, a, b, j - 1, pb, pc) + ox, ci1 = axis_comp(1, a, b, j - 1, pb, pc) + oy;
       // the 9 face points as 4 mirrored pairs and the centre (p = 4); with one
@@ -178,12 +177,11 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
                       d2 = axis_comp(2, a, b, 1, u1, u2);
             const double xq = o[0] + h * ((ci0 + 0.5) + 0.5 * d0);
             const double yq = o[1] + h * ((ci1 + 0.5) + 0.5 * d1);
-            const double rl[3] = {half_h * d0, half_h * d1, half_h * d2};
-            // about the right cell the a-offset is d_a - 2 = -1
-            const double rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
-            const double w = A.P.face_points == 1 ? 1.0
-                             : (u1 == 0 && u2 == 0) ? (16.0 / 36.0) : (u1 == 0 || u2 == 0) ? (4.0 / 36.0) : (1.0 / 36.0);
-            point64(plus[pt], side ? qmB : qmA, a, xq, yq, w, rl, rr, A.P, fsum, tl, tr, amax);
+            // half the Simpson weight (1, 4, 1) x (1, 4, 1) / 36 of the point; 1/2
+            // for the single-point face flux
+            const double hw = A.P.face_points == 1 ? 0.5
+                             : (u1 == 0 && u2 == 0) ? (8.0 / 36.0) : (u1 == 0 || u2 == 0) ? (2.0 / 36.0) : (0.5 / 36.0);
+            point64(plus[pt], side ? qmB : qmA, a, xq, yq, hw, d0, d1, d2, A.P, fsum, T, amax);
           }
         }
 #pragma unroll
@@ -192,6 +190,8 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
           if (p != 4) plus[8 - p][k] = qpB[k];
         }
       }
+      double tl[3], tr[3];
+      face_torques64(T, fsum, a, half_h, tl, tr);
       if (j >= 1) {
         // interior cell i = j-1 along a: differences of its two a-faces
         const int i = j - 1;

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "hydro.h"
 #include "hydro_common.cuh"
 #include "hydro_fp64.cuh"
 #include "hydro_mixed.cuh"
@@ -373,11 +374,10 @@ __global__ void __launch_bounds__(kLThreads, 1) hydro_step_fp64_lines_kernel(Ste
 #pragma unroll 1
     for (int j = 0; j <= N; ++j) {
       // face j - 1/2 between the cells j - 1 (left) and j (right) along a
-      double fsum[F], tl[3], tr[3];
+      double fsum[F], T[3];
 #pragma unroll
       for (int k = 0; k < F; ++k) fsum[k] = 0.0;
-      tl[0] = tl[1] = tl[2] = 0.0;
-      tr[0] = tr[1] = tr[2] = 0.0;
+      T[0] = T[1] = T[2] = 0.0;
       const int ci0 = axis_comp(0, a, b, j - 1, pb, pc) + ox, ci1 = axis_comp(1, a, b, j - 1, pb, pc) + oy;
 #pragma unroll 1
       for (int qq = q0; qq <= 8; ++qq) {
@@ -397,13 +397,14 @@ __global__ void __launch_bounds__(kLThreads, 1) hydro_step_fp64_lines_kernel(Ste
                   d2 = axis_comp(2, a, b, 1, u1, u2);
         const double xq = o[0] + h * ((ci0 + 0.5) + 0.5 * d0);
         const double yq = o[1] + h * ((ci1 + 0.5) + 0.5 * d1);
-        const double rl[3] = {half_h * d0, half_h * d1, half_h * d2};
-        // about the right cell the a-offset is d_a - 2 = -1
-        const double rr[3] = {a == 0 ? -half_h : rl[0], a == 1 ? -half_h : rl[1], a == 2 ? -half_h : rl[2]};
-        const double w = A.P.face_points == 1 ? 1.0
-                         : (u1 == 0 && u2 == 0) ? (16.0 / 36.0) : (u1 == 0 || u2 == 0) ? (4.0 / 36.0) : (1.0 / 36.0);
-        point64(qL, qR, a, xq, yq, w, rl, rr, A.P, fsum, tl, tr, amax);
+        // half the Simpson weight (1, 4, 1) x (1, 4, 1) / 36 of the point; 1/2
+        // for the single-point face flux
+        const double hw = A.P.face_points == 1 ? 0.5
+                         : (u1 == 0 && u2 == 0) ? (8.0 / 36.0) : (u1 == 0 || u2 == 0) ? (2.0 / 36.0) : (0.5 / 36.0);
+        point64(qL, qR, a, xq, yq, hw, d0, d1, d2, A.P, fsum, T, amax);
       }
+      double tl[3], tr[3];
+      face_torques64(T, fsum, a, half_h, tl, tr);
       if (j >= 1) {
         // interior cell i = j-1 along a: differences of its two a-faces
         const int i = j - 1;
@@ -567,3 +568,24 @@ cudaError_t launch_step_fp64_lines(const StepArgs64& A, int grid, int nn, cudaSt
 }
 
 }  // namespace hyd
+
+namespace hyd {
+
+__global__ void selftest_arith_kernel(const double* __restrict__ x, const double* __restrict__ y, int n,
+                                      double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = x[i], b = y[i];
+    out[2 * i] = half64(a);
+    out[2 * i + 1] = slope64(a, b);
+  }
+}
+
+}  // namespace hyd
+
+extern "C" int hydro_selftest_arith(const double* x, const double* y, int n, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y || !out))) return HYDRO_EINVAL;
+  if (n == 0) return HYDRO_OK;
+  const int grid = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  hyd::selftest_arith_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(x, y, n, out);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}

@@ -27,7 +27,7 @@ EXPORTS = ("hydro_create", "hydro_set_mode", "hydro_step", "hydro_update", "hydr
            "hydro_rk3_graph_state", "hydro_rk3_graph_destroy", "hydro_gate_data", "hydro_mlp_forward",
            "hydro_mlp_work_bytes", "hydro_mlp_loss_grad", "hydro_mlp_adam", "hydro_set_indicator",
            "hydro_fill_ghosts_amr", "hydro_flux_correct_amr", "hydro_autotune_step", "hydro_selftest_wait",
-           "hydro_set_launch", "hydro_get_launch")
+           "hydro_set_launch", "hydro_get_launch", "hydro_selftest_arith")
 HYDRO_ST_MESH = 0x4
 HYDRO_GATE_NPARAM, HYDRO_GATE_NIN = 2849, 54
 
@@ -101,6 +101,7 @@ def _lib(load: bool = True):
         L.hydro_rk3_graph_state.argtypes = [vp]
         L.hydro_rk3_graph_destroy.argtypes = [vp]
         L.hydro_selftest_wait.argtypes = [vp, dp, vp]
+        L.hydro_selftest_arith.argtypes = [vp, vp, ip, vp, vp]
         L.hydro_gate_data.argtypes = [vp, C.POINTER(Batch), vp, vp, vp]
         L.hydro_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
         L.hydro_mlp_work_bytes.argtypes = [ip]
@@ -278,6 +279,15 @@ def make_rk3_desc(Ua, Ub, origin, h, nb, bc, dUdt, amax, dt, cfl=0.4, g=None, me
 
 def hydro_selftest_wait(ctx, seconds: float = 0.01, stream=None):
     _check(_lib().hydro_selftest_wait(_cp(ctx), float(seconds), _stream(stream)), "hydro_selftest_wait")
+
+
+def hydro_selftest_arith(x, y, out, stream=None):
+    """The FP64 kernels' integer-pipe halving and MC slope on device float64
+    tensors x, y (n values) into out (2n values)."""
+    n = x.numel()
+    if y.numel() != n or out.numel() != 2 * n:
+        raise ValueError("x, y: n values; out: 2n values")
+    _check(_lib().hydro_selftest_arith(_ptr(x), _ptr(y), n, _ptr(out), _stream(stream)), "hydro_selftest_arith")
 
 
 def hydro_rk3_step(ctx, desc: RK3Desc, parity: int, stream=None):

@@ -56,6 +56,9 @@ def test_host_side_argument_checks(lib):
     assert lib.hydro_create(C.byref(H.Layout(8, 3, 1)), float("nan"), 0.0, C.byref(out)) == H.HYDRO_EINVAL
     assert lib.hydro_step(None, None, 0.0, None, None, None, None) == H.HYDRO_EINVAL
     assert lib.hydro_update(None, None, None, None, 0.0, None, 0, None, None) == H.HYDRO_EINVAL
+    assert lib.hydro_selftest_arith(None, None, -1, None, None) == H.HYDRO_EINVAL
+    assert lib.hydro_selftest_arith(None, None, 4, None, None) == H.HYDRO_EINVAL
+    assert lib.hydro_selftest_arith(None, None, 0, None, None) == H.HYDRO_OK
     assert lib.hydro_strerror(H.HYDRO_EINVAL).startswith(b"invalid")
     lib.hydro_destroy(None)  # no-op
 
