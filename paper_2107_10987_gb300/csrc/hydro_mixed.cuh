@@ -219,71 +219,77 @@ __device__ __forceinline__ Side32x2 side32x2(const QA& qa, const QB& qb, int a, 
   return s;
 }
 
-// Conserved component k of a side and its physical flux along axis a (qk:
-// the reconstructed value of field k, used for the advected scalars).
-__device__ __forceinline__ void cons_flux32x2(float2 qk, const Side32x2& s, int a, int k, float2& u, float2& f) {
-  if (k == RHO) {
-    u = s.rho;
-    f = mul2(u, s.un);
-  } else if (k <= SZ) {
-    u = mul2(s.rho, k == SX ? s.vx : (k == SY ? s.vy : s.vz));
-    f = (k - SX == a) ? fma2(u, s.un, s.p) : mul2(u, s.un);
-  } else if (k == EGAS) {
-    u = s.E;
-    f = fma2(u, s.un, mul2(s.p, s.va));
-  } else {
-    u = qk;
-    f = mul2(u, s.un);
-  }
+// Conserved component k of a side (qk: the reconstructed value of field k,
+// used for the advected scalars).
+__device__ __forceinline__ float2 cons32x2(float2 qk, const Side32x2& s, int k) {
+  if (k == RHO) return s.rho;
+  if (k <= SZ) return mul2(s.rho, k == SX ? s.vx : (k == SY ? s.vy : s.vz));
+  if (k == EGAS) return s.E;
+  return qk;
 }
 
 // Two quadrature points A, B of a face of axis a (kTwo = false: A only,
 // with both lanes equal), added to a face group's sums in the order A, B:
-// the point fluxes F_q = (F_L + F_R)/2 - a_q (U_R - U_L)/2 with a_q =
-// max(|u_n| + c) of the two sides, G[k] += w F_q[k], and the momentum-flux
-// torques about the left and right cell centres, TL += (w h/2) dL x F_s and
-// TR += (w h/2) dR x F_s (dL = d, dR = d - 2 e_a; the levers are (h/2) dL
-// and (h/2) dR), each a fused step; amax takes a_q.  qlA(k), qrA(k),
+// the point fluxes 2 F_q = (F_L + F_R) - a_q (U_R - U_L) with a_q =
+// max(|u_n| + c) of the two sides and F_L + F_R = U_L u_nL + U_R u_nR (+ the
+// pressure terms: p_L + p_R in the normal momentum, p_L v_aL + p_R v_aR in
+// the energy) as two fused steps, G[k] += (w/2) (2 F_q[k]), and the momentum-
+// flux torque about the left cell centre, TL += (w h/4) d x (2 F_s) (the
+// lever is (h/2) d), each a fused step; amax takes a_q.  qlA(k), qrA(k),
 // qlB(k), qrB(k): the reconstructed primitives of the two sides of A and B
-// (read when needed); xq, yq, dL, dR per lane; wA, wB the weights, whA =
-// wA h/2, whB = wB h/2.  dL and dR are in {-1, 0, 1}, so each cross-product
-// component is one rounding of an exact difference of exact products.
+// (read when needed); xq, yq, d per lane; hwA = wA/2, hwB = wB/2 and hqA =
+// wA h/4, hqB = wB h/4 (exact halvings of the weights w and w h/2, so each
+// sum gets the same value as with the weights applied to F_q).  d is in
+// {-1, 0, 1}, so each cross-product component is one rounding of an exact
+// difference of exact products.  The torque about the right centre follows
+// per face (right_torque32).
 template <bool kTwo, class QLA, class QRA, class QLB, class QRB>
 __device__ __forceinline__ void point_pair32(const QLA& qlA, const QRA& qrA, const QLB& qlB, const QRB& qrB, int a,
-                                             float2 xq, float2 yq, const float2 dL[3], const float2 dR[3],
-                                             const StepParamsF& P, float wA, float whA, float wB, float whB,
-                                             float G[F], float TL[3], float TR[3], float& amax) {
+                                             float2 xq, float2 yq, const float2 dL[3], const StepParamsF& P,
+                                             float hwA, float hqA, float hwB, float hqB, float G[F], float TL[3],
+                                             float& amax) {
   const Side32x2 L = side32x2(qlA, qlB, a, xq, yq, P);
   const Side32x2 R = side32x2(qrA, qrB, a, xq, yq, P);
   const float2 aq = f2(fmaxf(L.spd.x, R.spd.x), fmaxf(L.spd.y, R.spd.y));
   amax = fmaxf(amax, kTwo ? fmaxf(aq.x, aq.y) : aq.x);
-  const float2 mha = mul2(f2(-0.5f), aq);
+  const float2 naq = mul2(f2(-1.f), aq);
+  const float2 pp = add2(L.p, R.p);
+  const float2 pw = fma2(L.p, L.va, mul2(R.p, R.va));
   float2 fs[3];
 #pragma unroll
   for (int k = 0; k < F; ++k) {
-    float2 uL, fL, uR, fR;
-    cons_flux32x2(k >= TAU ? f2(qlA(k), qlB(k)) : f2(0.f), L, a, k, uL, fL);
-    cons_flux32x2(k >= TAU ? f2(qrA(k), qrB(k)) : f2(0.f), R, a, k, uR, fR);
-    const float2 fq = fma2(mha, sub2(uR, uL), mul2(f2(0.5f), add2(fL, fR)));
-    G[k] = __fmaf_rn(wA, fq.x, G[k]);
-    if (kTwo) G[k] = __fmaf_rn(wB, fq.y, G[k]);
-    if (k >= SX && k <= SZ) fs[k - SX] = fq;
+    const float2 uL = cons32x2(k >= TAU ? f2(qlA(k), qlB(k)) : f2(0.f), L, k);
+    const float2 uR = cons32x2(k >= TAU ? f2(qrA(k), qrB(k)) : f2(0.f), R, k);
+    float2 sum;
+    if (k == EGAS)
+      sum = fma2(uL, L.un, fma2(uR, R.un, pw));
+    else if (k >= SX && k <= SZ)
+      sum = fma2(uL, L.un, fma2(uR, R.un, k - SX == a ? pp : f2(0.f)));
+    else
+      sum = fma2(uL, L.un, mul2(uR, R.un));
+    const float2 fq2 = fma2(naq, sub2(uR, uL), sum);
+    G[k] = __fmaf_rn(hwA, fq2.x, G[k]);
+    if (kTwo) G[k] = __fmaf_rn(hwB, fq2.y, G[k]);
+    if (k >= SX && k <= SZ) fs[k - SX] = fq2;
   }
   const float2 mL[3] = {mul2(f2(-1.f), dL[0]), mul2(f2(-1.f), dL[1]), mul2(f2(-1.f), dL[2])};
-  const float2 mR[3] = {mul2(f2(-1.f), dR[0]), mul2(f2(-1.f), dR[1]), mul2(f2(-1.f), dR[2])};
   const float2 cl[3] = {fma2(dL[1], fs[2], mul2(mL[2], fs[1])), fma2(dL[2], fs[0], mul2(mL[0], fs[2])),
                         fma2(dL[0], fs[1], mul2(mL[1], fs[0]))};
-  const float2 cr[3] = {fma2(dR[1], fs[2], mul2(mR[2], fs[1])), fma2(dR[2], fs[0], mul2(mR[0], fs[2])),
-                        fma2(dR[0], fs[1], mul2(mR[1], fs[0]))};
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    TL[m] = __fmaf_rn(whA, cl[m].x, TL[m]);
-    TR[m] = __fmaf_rn(whA, cr[m].x, TR[m]);
-    if (kTwo) {
-      TL[m] = __fmaf_rn(whB, cl[m].y, TL[m]);
-      TR[m] = __fmaf_rn(whB, cr[m].y, TR[m]);
-    }
+    TL[m] = __fmaf_rn(hqA, cl[m].x, TL[m]);
+    if (kTwo) TL[m] = __fmaf_rn(hqB, cl[m].y, TL[m]);
   }
+}
+
+// A face's momentum-flux torque about the right cell centre (x_L + h e_a)
+// from the one about the left centre, tl, and the face's momentum sums
+// S[SX..SZ]: tr = tl - h e_a x S, one fused step per nonzero component.
+__device__ __forceinline__ void right_torque32(int a, float h, const float S[F], const float tl[3], float tr[3]) {
+  // (e_a x S) components: a = 0: (0, -Sz, Sy); a = 1: (Sz, 0, -Sx); a = 2: (-Sy, Sx, 0)
+  tr[0] = a == 0 ? tl[0] : __fmaf_rn(a == 1 ? -h : h, a == 1 ? S[SZ] : S[SY], tl[0]);
+  tr[1] = a == 1 ? tl[1] : __fmaf_rn(a == 0 ? h : -h, a == 0 ? S[SZ] : S[SX], tl[1]);
+  tr[2] = a == 2 ? tl[2] : __fmaf_rn(a == 0 ? -h : h, a == 0 ? S[SY] : S[SX], tl[2]);
 }
 
 // The 9 points of a face in their summation order: point n has offsets

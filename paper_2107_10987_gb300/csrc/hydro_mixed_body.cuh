@@ -190,14 +190,14 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
 #pragma unroll 1
   for (int j = -1; j <= N; ++j) {
     const int cj = c0 + j * sa;
-    // face j-1/2: completed groups S (fluxes, left and right torques) and the
+    // face j-1/2: completed groups S (fluxes, left-cell torques) and the
     // group being summed, G
-    float Sf[F], Stl[3], Str[3], Gf[F], Gtl[3], Gtr[3];
+    float Sf[F], Stl[3], Gf[F], Gtl[3];
     bool first = true;
 #pragma unroll
     for (int k = 0; k < F; ++k) Gf[k] = 0.f;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) Gtl[m] = Gtr[m] = 0.f;
+    for (int m = 0; m < 3; ++m) Gtl[m] = 0.f;
     // cell-centre coordinates of the left cell j - 1 (FP64 -> FP32 once; an
     // explicit FMA, so that every kernel instance rounds them alike)
     const float xc = coord[axis_comp(0, a, b, j - 1, pb, pc) + 1],
@@ -229,18 +229,16 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
         const int nA = 2 * p, nB = kTwo ? nA + 1 : nA;
         const int u1A = face_u1(nA), u2A = face_u2(nA), u1B = face_u1(nB), u2B = face_u2(nB);
         const int ptA = (u1A + 1) * 3 + (u2A + 1), ptB = (u1B + 1) * 3 + (u2B + 1);
-        float2 dL[3], dR[3];
+        float2 dL[3];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
+        for (int m = 0; m < 3; ++m)
           dL[m] = f2((float)axis_comp(m, a, b, 1, u1A, u2A), (float)axis_comp(m, a, b, 1, u1B, u2B));
-          dR[m] = m == a ? f2(-1.f) : dL[m];
-        }
         const float2 xq = fma2(f2(half_h), dL[0], f2(xc)), yq = fma2(f2(half_h), dL[1], f2(yc));
         const float wA = face_w(u1A, u2A, npt), wB = face_w(u1B, u2B, npt);
         point_pair32<kTwo>([&](int k) { return plus[ptA][k]; }, [&](int k) { return qmA[k]; },
                            [&](int k) { return plus[ptB][k]; }, [&](int k) { return kTwo ? qmB[k] : qmA[k]; }, a,
-                           xq, yq, dL, dR, PF, wA, __fmul_rn(wA, half_h), wB, __fmul_rn(wB, half_h), Gf, Gtl, Gtr,
-                           amax);
+                           xq, yq, dL, PF, 0.5f * wA, 0.5f * __fmul_rn(wA, half_h), 0.5f * wB,
+                           0.5f * __fmul_rn(wB, half_h), Gf, Gtl, amax);
         // a group is complete after points 3, 5 and 8 (face_group_ends, never
         // inside a pair): S = G0, then (S + G1), then (S + G2)
         if (face_group_ends(nB)) {
@@ -252,8 +250,7 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
             Stl[m] = first ? Gtl[m] : __fadd_rn(Stl[m], Gtl[m]);
-            Str[m] = first ? Gtr[m] : __fadd_rn(Str[m], Gtr[m]);
-            Gtl[m] = Gtr[m] = 0.f;
+            Gtl[m] = 0.f;
           }
           first = false;
         }
@@ -271,6 +268,8 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
       // face j-1/2 is complete: its sums in FP64 (each converted once); the
       // a-difference of cell j-1 is exact in FP64
       double fd[F], tld[3];
+      float Str[3];
+      right_torque32(a, h, Sf, Stl, Str);
 #pragma unroll
       for (int k = 0; k < F; ++k) fd[k] = (double)Sf[k];
 #pragma unroll

@@ -272,11 +272,11 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
       // x- and y-faces of plane k (k < N), z-faces between k-1 and k
       const bool zface = slot >= kNFaceXY;
       const bool active = lane < 30 && slot < kNFaceXY + N * N && (k < N || zface);
-      float Gf[F], Gtl[3], Gtr[3];
+      float Gf[F], Gtl[3];
 #pragma unroll
       for (int q = 0; q < F; ++q) Gf[q] = 0.f;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) Gtl[m] = Gtr[m] = 0.f;
+      for (int m = 0; m < 3; ++m) Gtl[m] = 0.f;
       int a = 0, fx = 0, fy = 0;  // face axis; the left cell's (x, y) in plane k (or k-1 for z-faces)
       if (active) {
         if (slot < N * (N + 1)) {
@@ -357,18 +357,15 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
         auto points = [&](auto two, int n) {
           constexpr bool kTwo = decltype(two)::value;
           const Pt tA = geom(n), tB = kTwo ? geom(n + 1) : tA;
-          float2 dL[3], dR[3];
+          float2 dL[3];
 #pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            dL[m] = f2((float)tA.dl[m], (float)tB.dl[m]);
-            dR[m] = f2((float)tA.dr[m], (float)tB.dr[m]);
-          }
+          for (int m = 0; m < 3; ++m) dL[m] = f2((float)tA.dl[m], (float)tB.dl[m]);
           const float2 xq = fma2(f2(half_h), dL[0], f2(xc)), yq = fma2(f2(half_h), dL[1], f2(yc));
           const float wA = face_w(tA.u1, tA.u2, npt), wB = face_w(tB.u1, tB.u2, npt);
           point_pair32<kTwo>([&](int q) { return tA.pl[q * tA.sl]; }, [&](int q) { return tA.pr[q * tA.sr]; },
                              [&](int q) { return tB.pl[q * tB.sl]; }, [&](int q) { return tB.pr[q * tB.sr]; }, a,
-                             xq, yq, dL, dR, PF, wA, __fmul_rn(wA, half_h), wB, __fmul_rn(wB, half_h), Gf, Gtl,
-                             Gtr, amax);
+                             xq, yq, dL, PF, 0.5f * wA, 0.5f * __fmul_rn(wA, half_h), 0.5f * wB,
+                             0.5f * __fmul_rn(wB, half_h), Gf, Gtl, amax);
         };
         // the lane's group (face_group_ends): g = 0 the pairs (0, 1) and (2,
         // 3), g = 1 the pair (4, 5), g = 2 the pair (6, 7) and the centre 8
@@ -383,11 +380,13 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
       // the face's three groups, (G0 + G1) + G2, on the lane of group 0
       float out[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float v = q < F ? Gf[q] : (q < F + 3 ? Gtl[q - F] : Gtr[q - F - 3]);
+      for (int q = 0; q < F + 3; ++q) {
+        const float v = q < F ? Gf[q] : Gtl[q - F];
         const float v1 = __shfl_down_sync(0xffffffffu, v, 1), v2 = __shfl_down_sync(0xffffffffu, v, 2);
         out[q] = npt == 1 ? v2 : __fadd_rn(__fadd_rn(v, v1), v2);
       }
+      // the torque about the right cell centre from the face's sums
+      right_torque32(a, h, out, out + F, out + F + 3);
       if (active && g == 0) {
         double* dst = zface ? zsum + (size_t)(k % 3) * 16 * N * N + (slot - kNFaceXY) : fsum + slot;
         const int dstride = zface ? N * N : kNFaceXY;
