@@ -176,10 +176,13 @@ ALGO = {"fp64_flops_per_subgrid_stage": 6565962.0, "bytes_per_subgrid_stage": 26
 # are taken on its 128^3 cut (4,096 sub-grids) and scaled by 8 (traffic
 # grows with the sub-grids processed).  None until captured for the current
 # kernel.
-TRAFFIC_PER_LAUNCH = {"fp64_sedov": 117935104.0 + 90517760.0, "mixed_sedov": 143687424.0 + 103432960.0,
-                      "fused_sedov": 807951689.0,
+# Sedov: the mean over the 42 (fused: 14) launches of one ncu launch list of
+# `--workload sedov --precision both --steps 3 --warmup 3`; polytrope: one
+# full capture at 128^3.
+TRAFFIC_PER_LAUNCH = {"fp64_sedov": 1503850831.0 + 1085510120.0, "mixed_sedov": 142870894.0 + 93039927.0,
+                      "fused_sedov": 342275310.0 + 444961573.0,
                       "fp64_polytrope": None, "mixed_polytrope": None,
-                      "fused_polytrope": 8 * (3454249e3 + 3838850e3)}
+                      "fused_polytrope": 8 * (3430653e3 + 3719836e3)}
 
 
 def algorithmic_work():
