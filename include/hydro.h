@@ -149,6 +149,9 @@ int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
  * (upper) of axis a; per face cell [c][b] (b < c the transverse axes) the F
  * face-averaged fluxes and the 3 components of the momentum-flux torque
  * about the adjacent interior cell.
+ * Scratch (context-owned, allocated on first need and kept): per persistent
+ * CTA 159,744 bytes of flux differences, and in FP64 mode 2,496,000 bytes of
+ * line-end buffer (380 MB for one CTA per SM on a 152-SM GPU).
  * Errors: EINVAL (NULL ctx/batch/pointers, n_sub < 0, misaligned U, dt < 0),
  * ENOMEM, ECUDA.
  * n_sub == 0 is a no-op. */
@@ -161,9 +164,12 @@ int hydro_step(hydro_ctx_t* ctx, const hydro_batch_t* B, double dt, double* dUdt
  *                        threads per sub-grid, two CTAs per SM in mixed
  *                        precision); the edge lines of a cell are
  *                        reconstructed in two axis sweeps and the vertex lines
- *                        in three (27 line evaluations per cell).  The FP64
- *                        kernels and the learned indicator use it; the
- *                        default.
+ *                        in three (27 line evaluations per cell).  The
+ *                        learned indicator uses it; the default.  The FP64
+ *                        form (ROWS or AUTO; PLANES is mixed only) walks
+ *                        each of the 13 lines once per cell along its own
+ *                        direction into a per-CTA buffer, then sweeps the
+ *                        faces by rows.
  *   HYDRO_DECOMP_PLANES  mixed precision: the sub-grid swept plane by plane
  *                        along z by 768 threads (one CTA per SM), each of the
  *                        13 lines through a cell reconstructed once, the
@@ -260,8 +266,8 @@ int hydro_conserved_sums(hydro_ctx_t* ctx, const hydro_batch_t* B, double* sums,
  * code that gives all device memory to its own pool allocator, or a time
  * loop that cannot afford the device-wide synchronisation an allocation may
  * cause.  It computes exactly what hydro_step computes (FP64 mode only, with
- * the context's flux points, contact steepening and learned indicator), with
- * the same kernel, but takes its scratch from a fixed array compiled into
+ * the context's flux points, contact steepening and learned indicator), bit
+ * for bit, but takes its scratch from a fixed array compiled into
  * the library: HYDRO_STATIC_MAX_SUB slots of 159,744 bytes (30.7 MB), held by
  * every GPU that loads the library until the process exits.
  *   - B->n_sub above HYDRO_STATIC_MAX_SUB returns HYDRO_ERANGE (split the
