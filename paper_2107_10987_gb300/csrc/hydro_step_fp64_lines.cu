@@ -13,7 +13,7 @@
 //      next tile's copies are issued as soon as phase 3 no longer reads it,
 //      so they overlap phases 4 and 5); primitives replace it in place;
 //   2. (learned smoothness indicator, optional) its per-cell decisions;
-//   3. lines: one work item per (field, run), a run being a maximal segment
+//   3. lines: one work item per (field group, run), a run being a maximal segment
 //      of consecutive cells along one of the 13 directions d among the cells
 //      that need that line (the interior, and the face-adjacent ghost cells
 //      of the faces whose normal component of d is nonzero).  The item walks
@@ -23,14 +23,14 @@
 //      number for the cell x and its neighbour x + d), then applies the
 //      per-cell steepening and monotonicity fix-ups and stores both
 //      interface values of the cell in a per-CTA buffer in global memory
-//      (L2-resident: 26 values per field and cell);
+//      (26 values per field and cell, read back from L2 or DRAM in phase 4);
 //   4. faces: 192 threads, one per (axis, transverse row), sweep their row's
 //      9 faces in the order of hydro_step_fp64.cu and sum the 9 Kurganov-
 //      Tadmor point fluxes with the Simpson weights from the stored values;
 //      per-axis flux differences go to the step scratch;
 //   5. divergence, sources and dU/dt as in hydro_step_fp64.cu.
 // Runs are listed once per device, longest first, so that the lanes of a
-// warp walk runs of equal length.  The walk's arithmetic is ppm64's,
+// warp mostly walk runs of equal length.  The walk's arithmetic is ppm64's,
 // operation for operation, on the same operands (the reversed line gives
 // the mirrored values bit for bit), so the stored values are those the axis
 // sweeps compute.
