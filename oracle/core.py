@@ -29,7 +29,8 @@ def build(force: bool = False) -> str:
 
 class _P(C.Structure):
     _fields_ = [("gamma", C.c_double), ("omega", C.c_double), ("eta1", C.c_double), ("eta2", C.c_double),
-                ("N", C.c_int), ("G", C.c_int), ("nf", C.c_int), ("face_points", C.c_int), ("contact", C.c_int)]
+                ("N", C.c_int), ("G", C.c_int), ("nf", C.c_int), ("face_points", C.c_int), ("contact", C.c_int),
+                ("spin", C.c_int)]
 
 
 @dataclass
@@ -45,10 +46,11 @@ class OracleParams:
     nf: int = 10
     face_points: int = 9  # 1: flux at the face centres only (the old hydro module, Sec. III-B)
     contact: int = 0  # 1: PPM contact steepening of density and species (optional in Sec. III-B)
+    spin: int = 0  # 1: a cell's spin feeds back into the velocity at its quadrature points (parity unpinned)
 
     def c(self) -> _P:
         return _P(self.gamma, self.omega, self.eta1, self.eta2, self.N, self.G, self.nf, self.face_points,
-                  self.contact)
+                  self.contact, self.spin)
 
 
 _lib = None
@@ -72,6 +74,8 @@ def lib():
         l.orc_ppm_line_eta.restype = None
         l.orc_contact_eta.argtypes = [C.POINTER(_P), dp, dp, dp]
         l.orc_contact_eta.restype = C.c_double
+        l.orc_spin_velocity.argtypes = [C.POINTER(_P), C.c_double, dp, C.c_double, dp, dp]
+        l.orc_spin_velocity.restype = None
         l.orc_point_flux.argtypes = [C.POINTER(_P), dp, dp, C.c_int, dp, dp, dp]
         l.orc_count_ops.argtypes = [C.POINTER(_P), dp, dp, C.c_double, C.POINTER(C.c_long)]
         ip = C.POINTER(C.c_int)
@@ -181,6 +185,16 @@ def contact_eta(P: OracleParams, a5, rho2, p2) -> float:
     r = np.ascontiguousarray(rho2, dtype=np.float64)
     p = np.ascontiguousarray(p2, dtype=np.float64)
     return lib().orc_contact_eta(C.byref(P.c()), _dp(a), _dp(r), _dp(p))
+
+
+def spin_velocity(P: OracleParams, rho: float, z, h: float, r) -> np.ndarray:
+    """The spin feedback's velocity increment at offset r from the centre of a
+    cell of density rho, spin density z and width h."""
+    zz = np.ascontiguousarray(z, dtype=np.float64)
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    dv = np.zeros(3)
+    lib().orc_spin_velocity(C.byref(P.c()), float(rho), _dp(zz), float(h), _dp(rr), _dp(dv))
+    return dv
 
 
 def point_flux(P: OracleParams, qL, qR, axis: int, xq) -> tuple[np.ndarray, float]:

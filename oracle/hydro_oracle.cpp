@@ -17,6 +17,8 @@
 //   * rotating-frame, gravity and spin-torque sources;
 //   * the maximum signal speed over all quadrature points (CFL);
 //   * the SSP-RK3 stage update with the dual-energy tracer resync.
+//   * optionally, the spin's feedback into the velocity at the quadrature
+//     points (spin_feedback: parity unpinned beyond its checks).
 // Where the paper defers a detail to the Octo-Tiger method paper, the reading
 // taken is stated at the line that uses it.  Every function is templated on
 // the scalar type so that an operation-counting type yields the exact number
@@ -100,6 +102,8 @@ struct Params {
                     // 1: flux at the face centre only (the old module, Sec. III-B)
   int contact;      // 1: PPM contact-discontinuity detection and steepening of the
                     // density and species lines (optional in Sec. III-B); 0: off
+  int spin;         // 1: the spin of a cell feeds back into the velocity
+                    // reconstructed at its quadrature points (spin_feedback); 0: off
 };
 
 // Primitive recovery of one cell (Sec. III-B; dual energy after Bryan 1995).
@@ -259,6 +263,31 @@ void point_flux(const Params& P, const T* qL, const T* qR, int a, const T xq[3],
   aq = max_(sL, sR);
   for (int k = 0; k < P.nf; ++k)
     Fq[k] = T(0.5) * (FL[k] + FR[k]) - (T(0.5) * aq) * (UR[k] - UL[k]);
+}
+
+// Spin feedback into the reconstructed velocity.  PARITY UNPINNED beyond the
+// checks in tests/test_oracle_spin.py (the reduction to the plain method at
+// z = 0, conservation, the rigid-rotation moment of inertia, dissipation of a
+// uniform spin): the paper names the rotating-frame and spin treatment of the
+// hydro module but defers its definition to the Octo-Tiger method paper.
+// Reading, in the manner of Despres & Labourasse (2015): the spin angular
+// momentum density z of a cell (its angular momentum about its own centre,
+// per unit volume) is carried as a rigid rotation of the cell's material,
+// omega = z / I with I = rho h^2 / 6 the moment of inertia per unit volume of
+// a uniform cube of side h about an axis through its centre, and the
+// velocity reconstructed at a point x_q of the cell's surface gains that
+// rotation's velocity omega x (x_q - x_c).  rho and z are the cell's
+// averages (U at stored cell index c).
+template <class T>
+void spin_feedback(const Params& P, const T* U, long c, double h, const T xq[3], const T xc[3], T* q) {
+  const int S = P.N + 2 * P.G;
+  const long S3 = (long)S * S * S;
+  const T I = (U[RHO * S3 + c] * T(h * h)) / T(6.0);
+  const T om[3] = {U[ZX * S3 + c] / I, U[ZY * S3 + c] / I, U[ZZ * S3 + c] / I};
+  const T r[3] = {xq[0] - xc[0], xq[1] - xc[1], xq[2] - xc[2]};
+  q[1] = q[1] + (om[1] * r[2] - om[2] * r[1]);
+  q[2] = q[2] + (om[2] * r[0] - om[0] * r[2]);
+  q[3] = q[3] + (om[0] * r[1] - om[1] * r[0]);
 }
 
 // Newton-Cotes (Simpson) weights on the 3x3 face points: (1,4,1)x(1,4,1)/36.
@@ -427,6 +456,15 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
               T qL[kMaxF], qR[kMaxF], Fq[kMaxF], aq;
               recon(ci[0], ci[1], ci[2], d, qL);
               recon(cr[0], cr[1], cr[2], dr, qR);
+              if (P.spin) {
+                T xl[3], xr[3];
+                for (int m = 0; m < 3; ++m) {
+                  xl[m] = T(origin[m]) + T(h) * T(ci[m] + 0.5);
+                  xr[m] = T(origin[m]) + T(h) * T(cr[m] + 0.5);
+                }
+                spin_feedback(P, U, at(ci[0], ci[1], ci[2]), h, xq, xl, qL);
+                spin_feedback(P, U, at(cr[0], cr[1], cr[2]), h, xq, xr, qR);
+              }
               point_flux(P, qL, qR, a, xq, Fq, aq);
               if (first) { am = aq; first = false; }
               else am = max_(am, aq);
@@ -588,7 +626,7 @@ extern "C" {
 
 struct orc_params {
   double gamma, omega, eta1, eta2;
-  int N, G, nf, face_points, contact;
+  int N, G, nf, face_points, contact, spin;
 };
 
 static orc::Params to_p(const orc_params* p) {
@@ -597,6 +635,7 @@ static orc::Params to_p(const orc_params* p) {
   P.N = p->N; P.G = p->G; P.nf = p->nf;
   P.face_points = p->face_points == 1 ? 1 : 9;
   P.contact = p->contact ? 1 : 0;
+  P.spin = p->spin ? 1 : 0;
   return P;
 }
 
@@ -679,6 +718,25 @@ void orc_ppm_line_eta(const double* s5, double eta, double* qp, double* qm) {
 double orc_contact_eta(const orc_params* p, const double* a5, const double* rho2, const double* p2) {
   const orc::Params P = to_p(p);
   return orc::contact_eta<double>(P, a5, rho2, p2);
+}
+
+// The spin feedback's velocity increment at offset r from the centre of a
+// cell of density rho, spin density z[3] and width h (spin_feedback on a
+// one-cell array).
+void orc_spin_velocity(const orc_params* p, double rho, const double* z, double h, const double* r, double* dv) {
+  orc::Params P = to_p(p);
+  P.N = 1;
+  P.G = 0;
+  double U[orc::kMaxF] = {}, q[orc::kMaxF] = {};
+  U[orc::RHO] = rho;
+  U[orc::ZX] = z[0];
+  U[orc::ZY] = z[1];
+  U[orc::ZZ] = z[2];
+  const double xc[3] = {0.0, 0.0, 0.0};
+  orc::spin_feedback<double>(P, U, 0, h, r, xc, q);
+  dv[0] = q[1];
+  dv[1] = q[2];
+  dv[2] = q[3];
 }
 
 // Central flux at one quadrature point from primitive states qL, qR.
