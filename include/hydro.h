@@ -100,8 +100,15 @@ typedef struct {
  * values with the neighbours' limited extrapolations by a weight in [0,1]
  * from its second differences, before the monotonicity fix-ups).  With the
  * learned indicator on, cells it marks smooth take the unlimited formula
- * and are not steepened; the others are.  Defaults: FP64,
- * cfl 0.4, eta1 1e-3, eta2 0.1, 9 points, contact 0. */
+ * and are not steepened; the others are.
+ * spin: 1 feeds each cell's spin angular momentum back into the velocity
+ * reconstructed at its quadrature points, read as a rigid rotation of the
+ * cell's material: omega = z / I, I = rho h^2 / 6 (a uniform cube about its
+ * centre), and v(x_q) += omega x (x_q - x_c), i.e. +-(3 / (rho h)) z x d at
+ * the point x_c +- (h/2) d (cell averages rho and z; the paper defers the
+ * spin treatment to the Octo-Tiger method paper, so this is a reading, in
+ * the manner of Despres & Labourasse 2015).  Defaults: FP64,
+ * cfl 0.4, eta1 1e-3, eta2 0.1, 9 points, contact 0, spin 0. */
 typedef struct {
   int precision;   /* HYDRO_PREC_FP64 or HYDRO_PREC_MIXED */
   double cfl;
@@ -109,6 +116,7 @@ typedef struct {
   double de_eta2;
   int flux_points; /* 9 (0 means 9) or 1 */
   int contact;     /* 0 or 1 */
+  int spin;        /* 0 or 1 */
 } hydro_mode_t;
 
 /* A batch of leaf sub-grids (device pointers).  g may be NULL. */
@@ -128,8 +136,8 @@ typedef struct {
 int hydro_create(const hydro_layout_t* layout, double gamma, double omega, hydro_ctx_t** out);
 
 /* Replace the run-time options.  Errors: EINVAL (unknown precision, cfl or
- * thresholds outside (0,1], flux_points not in {0, 1, 9}, contact not in
- * {0, 1}). */
+ * thresholds outside (0,1], flux_points not in {0, 1, 9}, contact or spin
+ * not in {0, 1}). */
 int hydro_set_mode(hydro_ctx_t* ctx, const hydro_mode_t* mode);
 
 /* One stage of the semi-discrete operator on every sub-grid of the batch

@@ -124,6 +124,7 @@ static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, dou
   A.P.eta1 = c->mode.de_eta1;
   A.P.face_points = c->mode.flux_points == 1 ? 1 : 9;
   A.P.contact = c->mode.contact ? 1 : 0;
+  A.P.spin = c->mode.spin ? 1 : 0;
   A.gate = c->gate_on ? 1 : 0;
   A.gate_w = c->gate_w;
   A.gate_logit_thr = (float)c->gate_logit_thr;
@@ -223,6 +224,7 @@ int hydro_create(const hydro_layout_t* L, double gamma, double omega, hydro_ctx_
   c->mode.de_eta2 = 0.1;
   c->mode.flux_points = 9;
   c->mode.contact = 0;
+  c->mode.spin = 0;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
@@ -241,6 +243,7 @@ int hydro_set_mode(hydro_ctx_t* c, const hydro_mode_t* m) {
     return HYDRO_EINVAL;
   if (m->flux_points != 0 && m->flux_points != 1 && m->flux_points != 9) return HYDRO_EINVAL;
   if (m->contact != 0 && m->contact != 1) return HYDRO_EINVAL;
+  if (m->spin != 0 && m->spin != 1) return HYDRO_EINVAL;
   c->mode = *m;
   if (c->mode.flux_points == 0) c->mode.flux_points = 9;
   return HYDRO_OK;

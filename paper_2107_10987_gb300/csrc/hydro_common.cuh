@@ -93,6 +93,7 @@ struct StepParams {
   double gamma, gm1, omega, eta1;
   int face_points;  // 9: Simpson sum of the 9 face points; 1: the face centre only
   int contact;      // 1: PPM contact steepening of the density and species lines
+  int spin;         // 1: a cell's spin feeds back into the velocity at its points (spin_dv64)
 };
 
 // Arguments of the step kernels (device pointers; layouts as in hydro.h).

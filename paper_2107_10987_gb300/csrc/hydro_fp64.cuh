@@ -244,6 +244,20 @@ __device__ __forceinline__ void side64(const double q[F], int a, double xq, doub
 // component.
 __device__ __forceinline__ double signed_pick(int d, double x) { return d == 0 ? 0.0 : (d > 0 ? x : -x); }
 
+// Spin feedback at a cell's point x_c + (h/2) d: the velocity there of the
+// cell's rigid rotation omega = z / I, I = rho h^2 / 6 (a uniform cube about
+// its centre), omega x (h/2) d = (3 / (rho h)) z x d, for the cell's averages
+// rho and z and k3h = 3 / h.  z x d by sign selection (d in {-1, 0, 1}^3), so
+// the increment at x_c - (h/2) d is exactly the negative.  Explicitly rounded
+// (no contraction), so that every kernel that adds it gets the same bits.
+__device__ __forceinline__ void spin_dv64(double rho, double zx, double zy, double zz, double k3h, int dx, int dy,
+                                          int dz, double dv[3]) {
+  const double k = k3h / rho;
+  dv[0] = rmul(k, rsub(signed_pick(dz, zy), signed_pick(dy, zz)));
+  dv[1] = rmul(k, rsub(signed_pick(dx, zz), signed_pick(dz, zx)));
+  dv[2] = rmul(k, rsub(signed_pick(dy, zx), signed_pick(dx, zy)));
+}
+
 // Kurganov-Tadmor flux at one point with half its Simpson weight hw = w/2:
 //   w F_q = hw (F_L + F_R) - hw a_q (U_R - U_L),  F = U u_n (+ p e_a, + p v_a),
 // accumulated per field into the face sum (F_L + F_R as two fused products,

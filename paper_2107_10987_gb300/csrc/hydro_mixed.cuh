@@ -185,7 +185,24 @@ __device__ __forceinline__ void line10fc(const float* __restrict__ Q, int c, int
 
 struct StepParamsF {
   float gamma, gm1, omega;
+  int spin;   // the spin feedback (spin_dv32) on (the kernels take it as a template parameter)
+  float k3h;  // its 3 / h, (float)(3 / h) of the sub-grid's FP64 h
 };
+
+// Spin feedback at a cell's point x_c + (h/2) d, FP32: the velocity there of
+// the cell's rigid rotation omega = z / I, I = rho h^2 / 6 (a uniform cube
+// about its centre), (3 / (rho h)) z x d, from the cell's FP32 primitives rho
+// and z; z x d by sign selection (d in {-1, 0, 1}^3), so the increment at
+// x_c - (h/2) d is exactly the negative and a line walked either way gets
+// the same values.  Every operation explicitly rounded.
+__device__ __forceinline__ float spin_pick32(int d, float x) { return d == 0 ? 0.f : (d > 0 ? x : -x); }
+__device__ __forceinline__ void spin_dv32(float rho, float zx, float zy, float zz, float k3h, int dx, int dy, int dz,
+                                          float dv[3]) {
+  const float k = __fdiv_rn(k3h, rho);
+  dv[0] = __fmul_rn(k, __fsub_rn(spin_pick32(dz, zy), spin_pick32(dy, zz)));
+  dv[1] = __fmul_rn(k, __fsub_rn(spin_pick32(dx, zz), spin_pick32(dz, zx)));
+  dv[2] = __fmul_rn(k, __fsub_rn(spin_pick32(dy, zx), spin_pick32(dx, zy)));
+}
 
 // ---- Kurganov-Tadmor flux at quadrature points, FP32 ------------------------
 // Two points per call, in the two lanes (A, B) of every packed operation; a

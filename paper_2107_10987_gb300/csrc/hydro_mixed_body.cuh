@@ -140,17 +140,17 @@ __device__ __forceinline__ void finish_cell(const StepArgs64& A, const Io& io, c
 // shared memory; D: the CTA's scratch (kScratchPerSub doubles).  Ends with
 // a barrier, so the next sub-grid may reuse all of them.
 // kContact: contact steepening of the density and species lines (line10fc).
-template <bool kGate, bool kContact = false, class Io>
+template <bool kGate, bool kContact = false, bool kSpin = false, class Io>
 __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io, int s, const RowMap& R, float* Qf,
                                               float* red, double* __restrict__ D) {
   uint8_t* smooth = reinterpret_cast<uint8_t*>(Qf + F * S3);
   float* coord = reinterpret_cast<float*>(smooth + 2 * S3);
   const int tid = threadIdx.x;
-  const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega};
   const int a = R.a, b = R.b, pb = R.pb, pc = R.pc, sa = R.sa, sb = R.sb, sc = R.sc;
   const typename Io::Sub sub = io.begin(s);
   const int si = io.sidx(sub), offx = io.offx(sub), offy = io.offy(sub);
   const double hd = A.h[si];
+  const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega, A.P.spin, (float)(3.0 / hd)};
   const double o[3] = {A.origin[3 * si + 0], A.origin[3 * si + 1], A.origin[3 * si + 2]};
   sub_coords(coord, hd, o[0], o[1], offx, offy);
 
@@ -222,6 +222,28 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
       } else {
         line10f(Qf, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
         if (kTwo) line10f(Qf, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
+      }
+      if constexpr (kSpin) {
+        // the cell's spin fed back into the velocity at both ends of both
+        // lines (spin_dv32; the plane sweep's values, bit for bit)
+        const float rc = Qf[RHO * S3 + cj], zx = Qf[ZX * S3 + cj], zy = Qf[ZY * S3 + cj], zz = Qf[ZZ * S3 + cj];
+        float dv[3];
+        spin_dv32(rc, zx, zy, zz, PF.k3h, axis_comp(0, a, b, 1, t1, t2), axis_comp(1, a, b, 1, t1, t2),
+                  axis_comp(2, a, b, 1, t1, t2), dv);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          qpA[1 + m] = __fadd_rn(qpA[1 + m], dv[m]);
+          qmA[1 + m] = __fsub_rn(qmA[1 + m], dv[m]);
+        }
+        if (kTwo) {
+          spin_dv32(rc, zx, zy, zz, PF.k3h, axis_comp(0, a, b, 1, -t1, -t2), axis_comp(1, a, b, 1, -t1, -t2),
+                    axis_comp(2, a, b, 1, -t1, -t2), dv);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            qpB[1 + m] = __fadd_rn(qpB[1 + m], dv[m]);
+            qmB[1 + m] = __fsub_rn(qmB[1 + m], dv[m]);
+          }
+        }
       }
       if (j >= 0) {
         // the pair's two points (n = 2p, 2p + 1) in the two lanes; the centre

@@ -96,7 +96,7 @@ __device__ __forceinline__ float* r_bnd_slot(float* rbnd, int sd, int bi, int po
 // 0 or 5): both interface values of each, to dp (towards +d) and dm (towards
 // -d; nullptr: not needed), field stride fst (dp, dm address field 0).
 // Samples from the primitive ring.  kContact as line10fc.
-template <bool kContact>
+template <bool kContact, bool kSpin>
 __device__ __forceinline__ void plane_line(const float* __restrict__ ring, int ix, int iy, int zp, int dx, int dy,
                                            int dz, int f0, float* dp, float* dm, int fst, const StepParamsF& PF) {
   int off[5];
@@ -131,12 +131,28 @@ __device__ __forceinline__ void plane_line(const float* __restrict__ ring, int i
       ppm32x2(v[0], v[1], v[2], v[3], v[4], qp, qm);
     put(fs, qp.x, qm.x);
   }
+  // the cell's spin fed back into the velocity at both ends (spin_dv32; the
+  // row sweep's values, bit for bit)
+  float dv[3] = {0.f, 0.f, 0.f};
+  const bool spin = kSpin && f0 == 0;
+  if (spin)
+    spin_dv32(ring[off[2] + RHO * kPl], ring[off[2] + ZX * kPl], ring[off[2] + ZY * kPl], ring[off[2] + ZZ * kPl],
+              PF.k3h, dx, dy, dz, dv);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int fa = (f0 == 0 ? 1 : 5) + 2 * i;
     float2 v[5], qp, qm;
     samples(fa, fa + 1, v);
     ppm32x2(v[0], v[1], v[2], v[3], v[4], qp, qm);
+    if (spin) {
+      // fields 1, 2 (i = 0) and 3 (i = 1) are the velocity
+      qp.x = __fadd_rn(qp.x, dv[2 * i]);
+      qm.x = __fsub_rn(qm.x, dv[2 * i]);
+      if (i == 0) {
+        qp.y = __fadd_rn(qp.y, dv[1]);
+        qm.y = __fsub_rn(qm.y, dv[1]);
+      }
+    }
     put(fa, qp.x, qm.x);
     put(fa + 1, qp.y, qm.y);
   }
@@ -146,7 +162,7 @@ __device__ __forceinline__ void plane_line(const float* __restrict__ ring, int i
 //   io.load_fields(sub, c, f0, nf, u)   fields f0 .. f0+nf-1 of padded cell c
 // (nf <= 5).  sm: the CTA's dynamic shared memory (kPlaneSmemBytes).  Ends
 // with a barrier.  Must be called by all kThreadsPl threads.
-template <bool kContact, class Io>
+template <bool kContact, bool kSpin, class Io>
 __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const Io& io, int s, unsigned char* sm) {
   double* stage = reinterpret_cast<double*>(sm + PlaneSmem::stage);
   double* s01 = reinterpret_cast<double*>(sm + PlaneSmem::s01);
@@ -159,10 +175,10 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
   float* coord = reinterpret_cast<float*>(sm + PlaneSmem::coord);
   float* red = reinterpret_cast<float*>(sm + PlaneSmem::red);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega};
   const typename Io::Sub sub = io.begin(s);
   const int si = io.sidx(sub), offx = io.offx(sub), offy = io.offy(sub);
   const double hd = A.h[si];
+  const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega, A.P.spin, (float)(3.0 / hd)};
   const float h = (float)hd, half_h = 0.5f * h;
   const double o[3] = {A.origin[3 * si + 0], A.origin[3 * si + 1], A.origin[3 * si + 2]};
   const double inv_h = 1.0 / hd;
@@ -228,7 +244,7 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
           const int code = 14 + L, dx = code % 3 - 1, dy = (code / 3) % 3 - 1, dz = code / 9 - 1;
           float* dp = r_int_slot(rint, zp, code, k, cell);
           float* dm = r_int_slot(rint, zp, 26 - code, k, cell);
-          plane_line<kContact>(ring, x + G, y + G, zpk, dx, dy, dz, f0, dp, dm, kRowR, PF);
+          plane_line<kContact, kSpin>(ring, x + G, y + G, zpk, dx, dy, dz, f0, dp, dm, kRowR, PF);
         } else {
           // face-adjacent ghost cell: the 9 lines into the sub-grid
           const int j = li - 13 * N * N, sd = j / (9 * N), bi = (j % (9 * N)) / N, pos = j % N;
@@ -245,7 +261,7 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
             dx = u1;
             dy = sd == 2 ? 1 : -1;
           }
-          plane_line<kContact>(ring, x + G, y + G, zpk, dx, dy, u2, f0, r_bnd_slot(rbnd, sd, bi, pos), nullptr,
+          plane_line<kContact, kSpin>(ring, x + G, y + G, zpk, dx, dy, u2, f0, r_bnd_slot(rbnd, sd, bi, pos), nullptr,
                                kRowB, PF);
         }
       }
@@ -257,7 +273,7 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
         const int zi = li / (N * N), cell = li % (N * N), x = cell % N, y = cell / N;
         const int dx = zi % 3 - 1, dy = zi / 3 - 1, dz = k < 0 ? 1 : -1;
         float* dp = r_int_slot(rint, zp, dcode(dx, dy, dz), k, cell);
-        plane_line<kContact>(ring, x + G, y + G, zpk, dx, dy, dz, f0, dp, nullptr, kRowR, PF);
+        plane_line<kContact, kSpin>(ring, x + G, y + G, zpk, dx, dy, dz, f0, dp, nullptr, kRowR, PF);
       }
     }
     if (pf_do) {

@@ -8,6 +8,10 @@ cudaError_t launch_rk3_fused16(const StepArgs64& S, double* Y, double* U2, float
                                unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
                                double gamma, int num_sms, int planes, cudaStream_t st);
 cudaError_t prepare_rk3_fused16(int num_sms, int planes, int* max_grid);
+cudaError_t launch_rk3_fused_spin(const StepArgs64& S, double* Y, double* U2, float* prims, double* dt_out,
+                                  unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
+                                  double gamma, int num_sms, int planes, int nn, cudaStream_t st);
+cudaError_t prepare_rk3_fused_spin(int num_sms, int planes, int nn, int* max_grid);
 
 // Self-test of the bounded wait: thread 0 waits on a flag that nothing sets
 // (flag[0], abort flag[1], both zero) and reports the expiry in the status
@@ -25,7 +29,12 @@ cudaError_t launch_wait_selftest(unsigned* words, unsigned* status, long long li
 
 size_t rk3_fused_sync_words(int n_sub) { return (size_t)kSyncHead + 2 * (size_t)n_sub; }
 
+// Both the plain instances and those with the spin feedback (once per
+// device), so that a capture finds either ready; *max_grid for the plain ones.
 cudaError_t prepare_rk3_fused(int num_sms, int planes, int nn, int* max_grid) {
+  int spin_grid = 0;
+  cudaError_t e = prepare_rk3_fused_spin(num_sms, planes, nn, &spin_grid);
+  if (e != cudaSuccess) return e;
   return nn == 16 ? prepare_rk3_fused16(num_sms, planes, max_grid) : prepare_fused_nn<8>(num_sms, planes, max_grid);
 }
 
@@ -33,6 +42,9 @@ cudaError_t prepare_rk3_fused(int num_sms, int planes, int nn, int* max_grid) {
 cudaError_t launch_rk3_fused(const StepArgs64& S, double* Y, double* U2, float* prims, double* dt_out,
                              unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
                              double gamma, int num_sms, int planes, int nn, cudaStream_t st) {
+  if (S.P.spin)
+    return launch_rk3_fused_spin(S, Y, U2, prims, dt_out, sync, nbx, nby, nbz, bc, cfl, eta2, gamma, num_sms,
+                                 planes, nn, st);
   if (nn == 16)
     return launch_rk3_fused16(S, Y, U2, prims, dt_out, sync, nbx, nby, nbz, bc, cfl, eta2, gamma, num_sms,
                               planes, st);

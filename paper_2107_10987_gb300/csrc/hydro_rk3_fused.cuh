@@ -250,7 +250,7 @@ static __device__ bool wait_neighbours(const FusedArgs& A, const unsigned* flags
 // row sweep (two CTAs of kThreadsMx threads per SM, per-CTA scratch of flux
 // differences; with or without the learned indicator and contact
 // steepening) and the plane sweep (one CTA of kThreadsPl threads per SM).
-template <bool kGate, bool kContact>
+template <bool kGate, bool kContact, bool kSpin = false>
 struct RowBody {
   static constexpr int kThreads = kThreadsMx, kMinBlocks = 2;
   static constexpr bool kPrims = true;  // reads its windows' primitives from FusedArgs::P
@@ -265,10 +265,10 @@ struct RowBody {
         D(S.scratch + (size_t)blockIdx.x * kScratchPerSub) {}
   template <class Io>
   __device__ __forceinline__ void run(const StepArgs64& S, const Io& io, int s) const {
-    mixed_subgrid<kGate, kContact>(S, io, s, R, Qf, red, D);
+    mixed_subgrid<kGate, kContact, kSpin>(S, io, s, R, Qf, red, D);
   }
 };
-template <bool kContact>
+template <bool kContact, bool kSpin = false>
 struct PlaneBody {
   static constexpr int kThreads = kThreadsPl, kMinBlocks = 1;
   static constexpr bool kPrims = false;
@@ -277,7 +277,7 @@ struct PlaneBody {
   __device__ PlaneBody(const StepArgs64&, unsigned char* p) : sm(p) {}
   template <class Io>
   __device__ __forceinline__ void run(const StepArgs64& S, const Io& io, int s) const {
-    mixed_subgrid_planes<kContact>(S, io, s, sm);
+    mixed_subgrid_planes<kContact, kSpin>(S, io, s, sm);
   }
 };
 
@@ -416,19 +416,19 @@ static cudaError_t fused_attr(int* per_sm) {
 // Opt in to the dynamic shared memory (once per device); the most CTAs of
 // the decomposition's kernels that can be resident at once (the cooperative
 // launch's limit).
-template <int NN>
+template <int NN, bool kSpin = false>
 static cudaError_t prepare_fused_nn(int num_sms, int planes, int* max_grid) {
   static unsigned long long done = 0;
   static int per_sm_dev[64][2];
   cudaError_t e = once_per_device(&done, [] {
     int dev = 0, p[6] = {0, 0, 0, 0, 0, 0};
     cudaError_t r = cudaGetDevice(&dev);
-    if (r == cudaSuccess) r = fused_attr<RowBody<false, false>, NN>(&p[0]);
-    if (r == cudaSuccess) r = fused_attr<RowBody<true, false>, NN>(&p[1]);
-    if (r == cudaSuccess) r = fused_attr<RowBody<false, true>, NN>(&p[2]);
-    if (r == cudaSuccess) r = fused_attr<PlaneBody<false>, NN>(&p[3]);
-    if (r == cudaSuccess) r = fused_attr<PlaneBody<true>, NN>(&p[4]);
-    if (r == cudaSuccess) r = fused_attr<RowBody<true, true>, NN>(&p[5]);
+    if (r == cudaSuccess) r = fused_attr<RowBody<false, false, kSpin>, NN>(&p[0]);
+    if (r == cudaSuccess) r = fused_attr<RowBody<true, false, kSpin>, NN>(&p[1]);
+    if (r == cudaSuccess) r = fused_attr<RowBody<false, true, kSpin>, NN>(&p[2]);
+    if (r == cudaSuccess) r = fused_attr<PlaneBody<false, kSpin>, NN>(&p[3]);
+    if (r == cudaSuccess) r = fused_attr<PlaneBody<true, kSpin>, NN>(&p[4]);
+    if (r == cudaSuccess) r = fused_attr<RowBody<true, true, kSpin>, NN>(&p[5]);
     if (r != cudaSuccess) return r;
     int rows = p[0] < p[1] ? p[0] : p[1];
     rows = rows < p[2] ? rows : p[2];
@@ -470,12 +470,14 @@ static cudaError_t launch_fused(const FusedArgs& A, int max_grid, cudaStream_t s
 // atomic maximum over each sub-grid's tiles: both are cleared here.  prims:
 // 2 n_sub F NN^3 floats of scratch for the row sweep's primitives.  planes:
 // the plane-sweep body (no learned indicator); otherwise the row sweep.
-template <int NN>
+// kSpin: the instances with the spin feedback (hydro_mode_t.spin), which the
+// others carry none of.
+template <int NN, bool kSpin = false>
 static cudaError_t launch_fused_nn(const StepArgs64& S, double* Y, double* U2, float* prims, double* dt_out,
                                    unsigned* sync, int nbx, int nby, int nbz, int bc, double cfl, double eta2,
                                    double gamma, int num_sms, int planes, cudaStream_t st) {
   int max_grid = 0;
-  cudaError_t e = prepare_fused_nn<NN>(num_sms, planes, &max_grid);
+  cudaError_t e = prepare_fused_nn<NN, kSpin>(num_sms, planes, &max_grid);
   if (e != cudaSuccess) return e;
   FusedArgs A;
   A.S = S;
@@ -506,12 +508,12 @@ static cudaError_t launch_fused_nn(const StepArgs64& S, double* Y, double* U2, f
     if (e != cudaSuccess) return e;
   }
   if (planes && !S.gate)
-    return S.P.contact ? launch_fused<PlaneBody<true>, NN>(A, max_grid, st)
-                       : launch_fused<PlaneBody<false>, NN>(A, max_grid, st);
-  if (S.gate && S.P.contact) return launch_fused<RowBody<true, true>, NN>(A, max_grid, st);
-  if (S.gate) return launch_fused<RowBody<true, false>, NN>(A, max_grid, st);
-  if (S.P.contact) return launch_fused<RowBody<false, true>, NN>(A, max_grid, st);
-  return launch_fused<RowBody<false, false>, NN>(A, max_grid, st);
+    return S.P.contact ? launch_fused<PlaneBody<true, kSpin>, NN>(A, max_grid, st)
+                       : launch_fused<PlaneBody<false, kSpin>, NN>(A, max_grid, st);
+  if (S.gate && S.P.contact) return launch_fused<RowBody<true, true, kSpin>, NN>(A, max_grid, st);
+  if (S.gate) return launch_fused<RowBody<true, false, kSpin>, NN>(A, max_grid, st);
+  if (S.P.contact) return launch_fused<RowBody<false, true, kSpin>, NN>(A, max_grid, st);
+  return launch_fused<RowBody<false, false, kSpin>, NN>(A, max_grid, st);
 }
 
 }  // namespace hyd

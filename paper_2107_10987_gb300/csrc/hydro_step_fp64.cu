@@ -165,6 +165,29 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
           line10(Q, cj, sa + t1 * sb + t2 * sc, qpA, qmA);
           if (p != 4) line10(Q, cj, sa - t1 * sb - t2 * sc, qpB, qmB);
         }
+        if (A.P.spin) {
+          // the cell's spin fed back into the velocity at both ends of both
+          // lines (spin_dv64; the lines kernel's values, bit for bit)
+          const double k3h = 3.0 / h;
+          double dv[3];
+          spin_dv64(Q[RHO * S3 + cj], Q[ZX * S3 + cj], Q[ZY * S3 + cj], Q[ZZ * S3 + cj], k3h,
+                    axis_comp(0, a, b, 1, t1, t2), axis_comp(1, a, b, 1, t1, t2), axis_comp(2, a, b, 1, t1, t2), dv);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            qpA[1 + m] = radd(qpA[1 + m], dv[m]);
+            qmA[1 + m] = rsub(qmA[1 + m], dv[m]);
+          }
+          if (p != 4) {
+            spin_dv64(Q[RHO * S3 + cj], Q[ZX * S3 + cj], Q[ZY * S3 + cj], Q[ZZ * S3 + cj], k3h,
+                      axis_comp(0, a, b, 1, -t1, -t2), axis_comp(1, a, b, 1, -t1, -t2),
+                      axis_comp(2, a, b, 1, -t1, -t2), dv);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+              qpB[1 + m] = radd(qpB[1 + m], dv[m]);
+              qmB[1 + m] = rsub(qmB[1 + m], dv[m]);
+            }
+          }
+        }
         if (j >= 0) {
 #pragma unroll 1
           for (int side = 0; side < 2; ++side) {

@@ -139,7 +139,8 @@ static int g_runs_total = 0, g_runs_axis = 0;
 // of the cell.
 template <bool kGate, bool kContact, int NG>
 __device__ __forceinline__ void line_run(const double* __restrict__ Q, const uint8_t* __restrict__ smooth,
-                                         const StepParams& P, double* __restrict__ R, uint32_t e, int k0) {
+                                         const StepParams& P, double* __restrict__ R, uint32_t e, int k0,
+                                         double k3h) {
   const int c0 = (int)(e & 0xfffu), b0 = (int)((e >> 12) & 0x3ffu), n = (int)((e >> 22) & 0xfu);
   const int dx = (int)((e >> 26) & 3u) - 1, dy = (int)((e >> 28) & 3u) - 1, dz = (int)(e >> 30) - 1;
   const int sv = dx + S * dy + S * S * dz;                             // shared-memory stride along d
@@ -198,6 +199,16 @@ __device__ __forceinline__ void line_run(const double* __restrict__ Q, const uin
       Dm[f] = Dc[f];
       Dc[f] = Dp;
       qm[f] = qp;
+    }
+    if (NG == 4 && k0 == 0 && P.spin) {
+      // the cell's spin fed back into the velocity at both ends (spin_dv64)
+      double dv[3];
+      spin_dv64(Q[RHO * S3 + ci], Q[ZX * S3 + ci], Q[ZY * S3 + ci], Q[ZZ * S3 + ci], k3h, dx, dy, dz, dv);
+#pragma unroll
+      for (int m3 = 0; m3 < 3; ++m3) {
+        p[(1 + m3) % NG] = radd(p[(1 + m3) % NG], dv[m3]);
+        m[(1 + m3) % NG] = rsub(m[(1 + m3) % NG], dv[m3]);
+      }
     }
     double2* wp = reinterpret_cast<double2*>(Rp + i * bv);
     double2* wm = reinterpret_cast<double2*>(Rm + i * bv);
@@ -309,15 +320,16 @@ __global__ void __launch_bounds__(kLThreads, 1) hydro_step_fp64_lines_kernel(Ste
 
     // ---- 3. every line once: (field group, run) items, group-major ----------
     {
+      const double k3h = 3.0 / A.h[s];  // the spin feedback's 3 / h
       const int n_items = 3 * n_runs;
 #pragma unroll 1
       for (int it = tid; it < n_items; it += kLThreads) {
         const int g = it / n_runs;
         const uint32_t e = g_line_runs[it - g * n_runs];
         if (g < 2)
-          line_run<kGate, kContact, 4>(Q, smooth, A.P, R, e, 4 * g);
+          line_run<kGate, kContact, 4>(Q, smooth, A.P, R, e, 4 * g, k3h);
         else
-          line_run<kGate, kContact, 2>(Q, smooth, A.P, R, e, 8);
+          line_run<kGate, kContact, 2>(Q, smooth, A.P, R, e, 8, k3h);
       }
     }
     // the last reads of Q for this tile are done: order them before the bulk

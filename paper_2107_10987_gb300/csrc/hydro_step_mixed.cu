@@ -1,125 +1,24 @@
-// hydro_step_mixed.cu -- the per-sub-grid hydro step in mixed precision:
-// one persistent launch over a batch of ghost-filled sub-grids, each read
-// from the padded state and its dU/dt written out.  Two decompositions of a
-// sub-grid with the same arithmetic: the row sweep (hydro_mixed_body.cuh,
-// which also carries the learned indicator) and the plane sweep
-// (hydro_mixed_planes.cuh).
-#include "hydro_mixed_planes.cuh"
+// hydro_step_mixed.cu -- the mixed-precision step kernels without the spin
+// feedback, their shared-memory opt-in and the dispatch (with the spin
+// feedback: hydro_step_mixed_spin.cu).
+#include "hydro_step_mixed.cuh"
 
 namespace hyd {
 
-// Padded state in, dU/dt and amax out, for the 8^3 tiles of NN^3 sub-grids
-// (Tile).  Holds a reference to the kernel's parameters, so its pointers
-// stay in the parameter bank (no registers).
-template <int NN>
-struct StepIo {
-  using T = Tile<NN>;
-  static constexpr bool kPrims = false;
-  const StepArgs64& A;
-  using Sub = T;
-  __device__ __forceinline__ Sub begin(int u) const { return T(u); }
-  __device__ __forceinline__ int sidx(const Sub& q) const { return q.s; }
-  __device__ __forceinline__ int offx(const Sub& q) const { return q.o[0]; }
-  __device__ __forceinline__ int offy(const Sub& q) const { return q.o[1]; }
-  __device__ __forceinline__ void load(const Sub& q, int c, double u[F]) const { load_fields(q, c, 0, F, u); }
-  __device__ __forceinline__ void load_fields(const Sub& q, int c, int f0, int nf, double* u) const {
-    const double* __restrict__ Us = A.U + (size_t)q.s * F * T::kS3 + (size_t)f0 * T::kS3 + q.pad(c);
-#pragma unroll
-    for (int k = 0; k < nf; ++k) u[k] = __ldg(Us + (size_t)k * T::kS3);
-  }
-  // only the fields the sources read (rho, s, z_x, z_y)
-  __device__ __forceinline__ void own(const Sub& q, int, int uc, double u[F]) const {
-    const double* __restrict__ Us = A.U + (size_t)q.s * F * T::kS3 + q.pad(uc);
-#pragma unroll
-    for (int k = 0; k < F; ++k) u[k] = (k <= SZ || k == ZX || k == ZY) ? __ldg(Us + (size_t)k * T::kS3) : 0.0;
-  }
-  __device__ __forceinline__ void store(const Sub& q, int c, int, const double du[F], const double*) const {
-    double* dU = A.dUdt + (size_t)q.s * F * T::kN3 + q.cell(c);
-#pragma unroll
-    for (int k = 0; k < F; ++k) dU[(size_t)k * T::kN3] = du[k];
-  }
-  __device__ __forceinline__ void grav(const Sub& q, int c, double& gx, double& gy, double& gz) const {
-    const double* gs = A.g + (size_t)q.s * 3 * T::kN3 + q.cell(c);
-    gx = gs[0];
-    gy = gs[T::kN3];
-    gz = gs[2 * T::kN3];
-  }
-  __device__ __forceinline__ void face(const Sub& q, int f, int k, int pc, int pb, double v) const {
-    if (q.outer(f)) A.face_flux[q.face(f, k, pc, pb)] = v;
-  }
-  __device__ __forceinline__ void amax(const Sub& q, double m) const {
-    if (T::kTiles == 1)
-      A.amax[q.s] = m;
-    else
-      atomic_max_nonneg(A.amax + q.s, m);  // cleared before the launch
-  }
-};
-
-// kGate: the learned smoothness indicator is on (A.gate); the kernel without
-// it carries none of the indicator's registers.  kContact: contact
-// steepening (A.P.contact; not combined with the indicator).
-template <bool kGate, bool kContact = false, int NN = N>
-__global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_kernel(StepArgs64 A) {
-  extern __shared__ __align__(128) float Qf[];  // [F][S3] FP32 primitives, then [2][S3] smooth flags
-  __shared__ float red[kThreadsMx / 32];
-  double* __restrict__ D = A.scratch + (size_t)blockIdx.x * kScratchPerSub;
-  const RowMap R = row_map(threadIdx.x);
-  const StepIo<NN> io{A};
-  const int units = A.n_sub * Tile<NN>::kTiles;
-  for (int u = blockIdx.x; u < units; u += gridDim.x) mixed_subgrid<kGate, kContact>(A, io, u, R, Qf, red, D);
-}
-
-// The plane sweep: one CTA of kThreadsPl threads per SM (no indicator).
-template <bool kContact, int NN = N>
-__global__ void __launch_bounds__(kThreadsPl, 1) hydro_step_mixed_planes_kernel(StepArgs64 A) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  const StepIo<NN> io{A};
-  const int units = A.n_sub * Tile<NN>::kTiles;
-  for (int u = blockIdx.x; u < units; u += gridDim.x) mixed_subgrid_planes<kContact>(A, io, u, sm);
-}
+void launch_step_mixed_spin(const StepArgs64& A, int grid, int planes, int nn, cudaStream_t st);
+cudaError_t prepare_step_mixed_spin();
 
 size_t step_mixed_smem_bytes() { return kMixedSmemBytes; }
 
-template <int NN>
-static cudaError_t mixed_attrs() {
-  const int rows = (int)step_mixed_smem_bytes(), planes = (int)kPlaneSmemBytes;
-  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, false, NN>, at, rows);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true, false, NN>, at, rows);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<false, true, NN>, at, rows);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_kernel<true, true, NN>, at, rows);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<false, NN>, at, planes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(hydro_step_mixed_planes_kernel<true, NN>, at, planes);
-  return e;
-}
-
-// Opt in to the kernels' dynamic shared memory once per device (no
-// allocation; call before any stream capture).
+// Opt in to the kernels' dynamic shared memory once per device, with and
+// without the spin feedback (no allocation; call before any stream capture).
 cudaError_t prepare_step_mixed() {
   static unsigned long long done = 0;
-  return once_per_device(&done, [] {
-    cudaError_t e = mixed_attrs<8>();
-    return e == cudaSuccess ? mixed_attrs<16>() : e;
+  cudaError_t e = once_per_device(&done, [] {
+    cudaError_t r = mixed_attrs<8, false>();
+    return r == cudaSuccess ? mixed_attrs<16, false>() : r;
   });
-}
-
-template <int NN>
-static void launch_mixed_nn(const StepArgs64& A, int grid, int planes, cudaStream_t st) {
-  if (planes && !A.gate) {
-    if (A.P.contact)
-      hydro_step_mixed_planes_kernel<true, NN><<<grid, kThreadsPl, kPlaneSmemBytes, st>>>(A);
-    else
-      hydro_step_mixed_planes_kernel<false, NN><<<grid, kThreadsPl, kPlaneSmemBytes, st>>>(A);
-  } else if (A.gate) {
-    if (A.P.contact)
-      hydro_step_mixed_kernel<true, true, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
-    else
-      hydro_step_mixed_kernel<true, false, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
-  } else if (A.P.contact) {
-    hydro_step_mixed_kernel<false, true, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
-  } else {
-    hydro_step_mixed_kernel<false, false, NN><<<grid, kThreadsMx, step_mixed_smem_bytes(), st>>>(A);
-  }
+  return e == cudaSuccess ? prepare_step_mixed_spin() : e;
 }
 
 // planes: the plane-sweep decomposition (grid: CTAs, at most one per SM);
@@ -133,10 +32,13 @@ cudaError_t launch_step_mixed(const StepArgs64& A, int grid, int planes, int nn,
   if (nn == 16) {
     e = cudaMemsetAsync(A.amax, 0, (size_t)A.n_sub * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    launch_mixed_nn<16>(A, grid, planes, st);
-  } else {
-    launch_mixed_nn<8>(A, grid, planes, st);
   }
+  if (A.P.spin)
+    launch_step_mixed_spin(A, grid, planes, nn, st);
+  else if (nn == 16)
+    launch_mixed_nn<16, false>(A, grid, planes, st);
+  else
+    launch_mixed_nn<8, false>(A, grid, planes, st);
   return cudaGetLastError();
 }
 

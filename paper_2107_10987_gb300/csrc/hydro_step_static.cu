@@ -100,6 +100,7 @@ extern "C" int hydro_step_static(hydro_ctx_t* c, const hydro_batch_t* B, double 
   A.P.omega = c->omega;
   A.P.eta1 = c->mode.de_eta1;
   A.P.face_points = c->mode.flux_points == 1 ? 1 : 9;
+  A.P.spin = c->mode.spin ? 1 : 0;
   A.P.contact = c->mode.contact ? 1 : 0;
   // the learned indicator as the context has it (its parameters are the
   // context's own device copy, made by hydro_set_indicator)

@@ -48,7 +48,7 @@ class Layout(C.Structure):
 
 class Mode(C.Structure):
     _fields_ = [("precision", C.c_int), ("cfl", C.c_double), ("de_eta1", C.c_double), ("de_eta2", C.c_double),
-                ("flux_points", C.c_int), ("contact", C.c_int)]
+                ("flux_points", C.c_int), ("contact", C.c_int), ("spin", C.c_int)]
 
 
 class Batch(C.Structure):
@@ -177,8 +177,10 @@ def hydro_create(layout: Layout, gamma: float, omega: float) -> int:
     return out.value
 
 
-def hydro_set_mode(ctx, precision=HYDRO_PREC_FP64, cfl=0.4, de_eta1=1e-3, de_eta2=0.1, flux_points=9, contact=0):
-    _check(_lib().hydro_set_mode(_cp(ctx), C.byref(Mode(precision, cfl, de_eta1, de_eta2, flux_points, contact))),
+def hydro_set_mode(ctx, precision=HYDRO_PREC_FP64, cfl=0.4, de_eta1=1e-3, de_eta2=0.1, flux_points=9, contact=0,
+                   spin=0):
+    _check(_lib().hydro_set_mode(_cp(ctx), C.byref(Mode(precision, cfl, de_eta1, de_eta2, flux_points, contact,
+                                                        spin))),
            "hydro_set_mode")
 
 

@@ -1,0 +1,192 @@
+"""The spin feedback (hydro_mode_t.spin = 1) in the step kernels, through the
+C ABI, against the oracle's spin feedback (a reading, pinned as far as it can
+be in test_oracle_spin.py):
+  * FP64 step: <= 1e-12 per field against the oracle with and without
+    rotation and gravity, on random sub-grids whose spin moves the points by
+    up to about the flow speed; the feedback changes the rates far above that;
+  * the allocation-free entry point gives hydro_step's bits in spin mode;
+  * mixed step: within the mixed-precision budget;
+  * the row and plane decompositions agree bit for bit, and the fused step
+    equals the separate launches bit for bit, in spin mode;
+  * conservation of mass, momentum, energy, tracer and species on a periodic
+    mesh in both precisions (the total angular momentum is pinned on the
+    oracle, which the FP64 step matches);
+  * spin outside {0, 1} is rejected.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2107_10987_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GAMMA = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2107_10987_gb300 import _build, hydro
+    _build.build()
+    return hydro
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_mod):
+    return oracle_mod.core
+
+
+def _bits(t):
+    return t.contiguous().view(torch.int64)
+
+
+def _inputs(n, seed):
+    """Random sub-grids, h in [0.05, 0.1], spin scaled so that 3|z|/(rho h)
+    stays below about 1.2 (the flow speeds are up to 1)."""
+    U = W.random_subgrids(n, seed, GAMMA)
+    U[:, 6:9] *= 0.2
+    rng = np.random.default_rng(seed + 1)
+    origin = rng.uniform(-1, 1, (n, 3))
+    h = rng.uniform(0.05, 0.1, n)
+    return U, origin, h
+
+
+def gpu_step(H, ctx, U, origin, h, g=None, static=False):
+    dev = torch.device("cuda")
+    n = U.shape[0]
+    Ut = torch.tensor(U, device=dev)
+    ot = torch.tensor(origin, device=dev)
+    ht = torch.tensor(h, device=dev)
+    gt = torch.tensor(g, device=dev) if g is not None else None
+    dU = torch.full((n, 10, 8, 8, 8), float("nan"), dtype=torch.float64, device=dev)
+    am = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    B = H.make_batch(Ut, ot, ht, gt)
+    if static:
+        H.hydro_step_static(ctx, B, 0.0, dU, am)
+    else:
+        H.hydro_step(ctx, B, 0.0, dU, am)
+    torch.cuda.synchronize()
+    return dU, am
+
+
+@pytest.mark.parametrize("omega,gravity", [(0.0, False), (0.25, True)])
+def test_fp64_spin_step_matches_oracle(H, orc, omega, gravity):
+    from oracle.compare import max_rel_error, rate_floor
+    n = 96
+    U, origin, h = _inputs(n, 41)
+    g = np.random.default_rng(43).uniform(-1, 1, (n, 3, 8, 8, 8)) if gravity else None
+    ctx = H.Context(GAMMA, omega)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, spin=1)
+    dU, am = gpu_step(H, ctx, U, origin, h, g)
+    assert H.hydro_status(ctx) == 0
+    dU, am = dU.cpu().numpy(), am.cpu().numpy()
+    P = orc.OracleParams(gamma=GAMMA, omega=omega, spin=1)
+    ref, amo, _ = orc.step(P, U, origin, h, g)
+    assert np.all(np.isfinite(dU))
+    assert max_rel_error(dU, ref, h, rate_floor(U, amo, h, omega, g)) <= 1e-12
+    assert np.allclose(am, amo, rtol=1e-13, atol=0)
+    # the feedback acts on this data
+    ref0, _, _ = orc.step(orc.OracleParams(gamma=GAMMA, omega=omega), U, origin, h, g)
+    assert max_rel_error(ref0, ref, h) > 1e-3
+
+
+def test_static_entry_point_gives_the_same_bits(H):
+    U, origin, h = _inputs(64, 45)
+    ctx = H.Context(GAMMA, 0.1)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, spin=1)
+    a, am = gpu_step(H, ctx, U, origin, h)
+    b, bm = gpu_step(H, ctx, U, origin, h, static=True)
+    assert bool((_bits(a) == _bits(b)).all()) and bool((_bits(am) == _bits(bm)).all())
+
+
+def test_mixed_spin_step_within_budget(H, orc):
+    from oracle.compare import mixed_budget, mixed_error, mixed_worst
+    n = 96
+    U, origin, h = _inputs(n, 47)
+    ctx = H.Context(GAMMA, 0.2)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, spin=1)
+    dU, am = gpu_step(H, ctx, U, origin, h)
+    assert H.hydro_status(ctx) == 0
+    dU, am = dU.cpu().numpy(), am.cpu().numpy()
+    P = orc.OracleParams(gamma=GAMMA, omega=0.2, spin=1)
+    ref, amo, _, faces = orc.step(P, U, origin, h, faces=True)
+    pert, _, _ = orc.step(P, U.astype(np.float32).astype(np.float64), origin, h)
+    assert np.all(np.isfinite(dU))
+    worst = mixed_worst(dU, ref, pert, faces, h, U, amo)
+    print("mixed spin step: largest err/budget", worst)
+    assert worst <= 1.0
+    assert np.allclose(am, amo, rtol=1e-5, atol=0)
+    budget, _ = mixed_budget(ref, pert, faces, h, U, amo)
+    ref0, _, _ = orc.step(orc.OracleParams(gamma=GAMMA, omega=0.2), U, origin, h)
+    d0 = mixed_error(ref0, ref, h)
+    assert d0[:, 1:4].max() > 100 * budget[:, 1:4].max(), (d0.max(), budget.max())
+
+
+def test_decompositions_and_fused_step_bitwise(H):
+    from test_gpu_fused import blast_mesh
+    from test_gpu_planes import _fused_vs_separate
+    R, Pl = H.HYDRO_DECOMP_ROWS, H.HYDRO_DECOMP_PLANES
+    # separate step: rows against planes, rates and amax
+    U, origin, h = _inputs(48, 49)
+    out = []
+    for dec in (R, Pl):
+        c = H.Context(GAMMA, 0.2)
+        H.hydro_set_mode(c, H.HYDRO_PREC_MIXED, spin=1)
+        H.hydro_set_launch(c, dec)
+        out.append(gpu_step(H, c, U, origin, h))
+        assert H.hydro_status(c) == 0
+    assert bool((_bits(out[0][0]) == _bits(out[1][0])).all())
+    assert bool((_bits(out[0][1]) == _bits(out[1][1])).all())
+    # fused step against the separate launches, each decomposition against the other
+    nb = (3, 2, 2)
+    Um, om, hm = blast_mesh(*nb)
+    rng = np.random.default_rng(51)
+    Um[:, 6:9] = rng.uniform(-1e-3, 1e-3, Um[:, 6:9].shape)
+    for df, ds in ((Pl, R), (R, Pl)):
+        cs = []
+        for dec in (df, ds):
+            c = H.Context(GAMMA, 0.0)
+            H.hydro_set_mode(c, H.HYDRO_PREC_MIXED, spin=1)
+            H.hydro_set_launch(c, dec)
+            cs.append(c)
+        _fused_vs_separate(H, cs[0], cs[1], Um, om, hm, nb, H.HYDRO_BC_PERIODIC, steps=2)
+        assert H.hydro_status(cs[0]) == 0 and H.hydro_status(cs[1]) == 0
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_spin_conserves_on_periodic_mesh(H, mixed):
+    from oracle import mesh
+    rng = np.random.default_rng(53)
+    n, h = 16, 1.0 / 16
+    sh = (n, n, n)
+    rho = rng.uniform(0.5, 2.0, sh)
+    v = rng.uniform(-0.3, 0.3, (3,) + sh)
+    p = rng.uniform(0.2, 1.0, sh)
+    z = rng.uniform(-1.0, 1.0, (3,) + sh) * rho * h * 0.1
+    Ug = W.conserved_from_primitive(rho, v, p, GAMMA, z=z, species=0.5 * rho)
+    U = torch.tensor(mesh.split(mesh.pad_box(Ug, 3, "periodic"), 8, 3), device="cuda")
+    lo = (-0.5, -0.5, -0.5)
+    o = torch.tensor(mesh.origins(2, 2, 2, 8, h, lo), device="cuda")
+    hh = torch.full((8,), h, dtype=torch.float64, device="cuda")
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED if mixed else H.HYDRO_PREC_FP64, spin=1)
+    dU = torch.empty((8, 10, 8, 8, 8), dtype=torch.float64, device="cuda")
+    am = torch.empty(8, dtype=torch.float64, device="cuda")
+    H.hydro_step(ctx, H.make_batch(U, o, hh), 0.0, dU, am)
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    d = dU.cpu().numpy()
+    tot = d.sum(axis=(0, 2, 3, 4))
+    scale = np.abs(d).sum(axis=(0, 2, 3, 4))
+    tol = 1e-6 if mixed else 1e-13
+    for k in (0, 1, 2, 3, 4, 5, 9):
+        assert abs(tot[k]) <= tol * scale[k], (k, tot[k], scale[k])
+
+
+def test_spin_mode_checks(H):
+    ctx = H.Context(GAMMA, 0.0)
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, spin=2)
+    assert e.value.code == H.HYDRO_EINVAL
