@@ -246,7 +246,7 @@ def train_indicator(dev):
     return params, thr, ev
 
 
-def run_form(args, H, dev, precision, flush, indicator=None, fused=False, contact=False, workload="polytrope",
+def run_form(args, H, dev, precision, flush, indicator=None, fused=False, contact=False, workload="polytrope", spin=False,
              steps=None, state=None):
     """Warm-up, then `steps` timed RK3 steps of one precision form on a
     workload; returns timings and the final density.  Separate launches: the
@@ -256,6 +256,7 @@ def run_form(args, H, dev, precision, flush, indicator=None, fused=False, contac
     so that the step kernel can be timed alone.  fused: hydro_rk3_step with
     the descriptor's fused flag (one persistent launch per time step, mixed
     precision).  contact: PPM contact steepening on (hydro_mode_t.contact).
+    spin: the spin feedback on (hydro_mode_t.spin).
     state: a make_state() result to start from (it is advanced in place)."""
     import torch
     steps = args.steps if steps is None else steps
@@ -263,7 +264,7 @@ def run_form(args, H, dev, precision, flush, indicator=None, fused=False, contac
     st = state if state is not None else make_state(dev, H, workload)
     nb, n, cells = st["nb"], st["n"], st["cells"]
     ctx = H.Context(GAMMA, st["omega"])
-    H.hydro_set_mode(ctx, precision, 0.4, contact=1 if contact else 0)
+    H.hydro_set_mode(ctx, precision, 0.4, contact=1 if contact else 0, spin=1 if spin else 0)
     if indicator is not None:
         H.hydro_set_indicator(ctx, indicator[0], indicator[1])
     Ua, origin, hv, g = st["U"], st["origin"], st["h"], st["g"]
@@ -443,8 +444,8 @@ def amr_measure(args, H, dev, flush, precision, steps, indicator=None):
 
 def contact_measure(args, H, dev, flush, res):
     """PPM contact steepening (hydro_mode_t.contact = 1) on the Sedov mesh of
-    512 sub-grids: the mixed and the FP64 RK3 step as separate launches (the
-    fused step does not steepen), each beside the same form without
+    512 sub-grids: the mixed and the FP64 RK3 step as separate launches (so
+    that the step kernel is timed alone), each beside the same form without
     steepening (res: sedov_mixed_separate, sedov_fp64) when that was
     measured.  Values are this GPU's (the block runs on rank 0)."""
     out = {"workload": WORKLOADS["sedov"]["desc"],
@@ -463,6 +464,31 @@ def contact_measure(args, H, dev, flush, res):
             if p["steps"] == r["steps"]:
                 ent["max_rel_density_diff_vs_unsteepened"] = ((r["rho"] - p["rho"]).abs().max().item() /
                                                               p["rho"].abs().max().item())
+        out[name] = ent
+    return out
+
+
+def spin_measure(args, H, dev, flush, res):
+    """The spin feedback (hydro_mode_t.spin = 1) on the Sedov mesh of 512
+    sub-grids: the fused mixed step, the mixed step as separate launches and
+    the FP64 step, each beside the same form without it (res) when that was
+    measured.  The spin starts at zero and grows from the torques of the face
+    fluxes as the blast expands."""
+    out = {"workload": WORKLOADS["sedov"]["desc"],
+           "note": "each cell's spin fed back into the velocity at its quadrature points (rigid-rotation "
+                   "reading); the spin starts at zero and builds up from the face torques"}
+    for name, prec, fused in (("mixed", H.HYDRO_PREC_MIXED, True), ("mixed_separate", H.HYDRO_PREC_MIXED, False),
+                              ("fp64", H.HYDRO_PREC_FP64, False)):
+        r = run_form(args, H, dev, prec, flush, fused=fused, spin=True, workload="sedov")
+        cells = r["cells"]
+        ent = {"value": cells * r["steps"] / r["t_dev"], "ms_per_step": 1e3 * r["t_dev"] / r["steps"],
+               "kernel_ms": 1e3 * r["kern_s"], "device_status": r["status"]}
+        if name in res:
+            p = res[name]
+            ent["step_cost_vs_without"] = (r["t_dev"] / r["steps"]) / (p["t_dev"] / p["steps"])
+            if p["steps"] == r["steps"]:
+                ent["max_rel_density_diff_vs_without"] = ((r["rho"] - p["rho"]).abs().max().item() /
+                                                          p["rho"].abs().max().item())
         out[name] = ent
     return out
 
@@ -790,6 +816,11 @@ def gpu_arm(args):
                 line["contact_steepening"] = contact_measure(args, H, dev, flush, sres)
             except Exception as e:  # an optional block: it never costs the headline line
                 line["contact_steepening"] = {"error": f"{type(e).__name__}: {e}"}
+        if args.spin and args.sedov:  # beside the Sedov forms it is compared with
+            try:
+                line["spin_feedback"] = spin_measure(args, H, dev, flush, sres)
+            except Exception as e:  # an optional block: it never costs the headline line
+                line["spin_feedback"] = {"error": f"{type(e).__name__}: {e}"}
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, wl)
         print(json.dumps(line), flush=True)
@@ -902,6 +933,8 @@ def main():
                     help="skip the rotating-polytrope measurement")
     ap.add_argument("--no-contact", dest="contact", action="store_false",
                     help="skip the contact-steepening measurement")
+    ap.add_argument("--no-spin", dest="spin", action="store_false",
+                    help="skip the spin-feedback measurement")
     ap.add_argument("--no-sedov", dest="sedov", action="store_false",
                     help="skip the 512-sub-grid Sedov measurement")
     ap.add_argument("--no-subgrid16", dest="subgrid16", action="store_false",
