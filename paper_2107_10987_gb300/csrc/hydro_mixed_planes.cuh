@@ -178,7 +178,8 @@ __device__ __forceinline__ void mixed_subgrid_planes(const StepArgs64& A, const 
   const typename Io::Sub sub = io.begin(s);
   const int si = io.sidx(sub), offx = io.offx(sub), offy = io.offy(sub);
   const double hd = A.h[si];
-  const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega, A.P.spin, (float)(3.0 / hd)};
+  const StepParamsF PF{(float)A.P.gamma, (float)A.P.gm1, (float)A.P.omega, kSpin ? 1 : 0,
+                       kSpin ? (float)(3.0 / hd) : 0.f};
   const float h = (float)hd, half_h = 0.5f * h;
   const double o[3] = {A.origin[3 * si + 0], A.origin[3 * si + 1], A.origin[3 * si + 2]};
   const double inv_h = 1.0 / hd;
