@@ -198,10 +198,11 @@ def test_sedov_blast_with_spin_feedback(H):
     """The Sedov blast (512 sub-grids, 64^3, outflow) to t = 0.05 with the
     spin feedback in both precisions: mass conserved to round-off, no
     non-physical state, and the shell within 1.5 cells of the similarity
-    radius.  (The reading feeds back the whole spin, so it also acts on
-    rotation that the reconstruction already resolves: the spin-coupled
-    flow amplifies rounding-level asymmetries to the percent level by then
-    and takes 2-3 times more steps, so mirror symmetry is not asserted.)"""
+    radius.  (The reading has no limiter: the spin of the evacuated centre
+    over its small rho h^2 / 6 gives rotation much faster than the flow,
+    which takes 2-3 times more steps and amplifies rounding-level
+    asymmetries to the percent level by then, so mirror symmetry is not
+    asserted.)"""
     from oracle import analytic
     from test_gpu_parity import run_rk3_gpu
     Ug, h, lo = W.sedov_box(64, GAMMA)
