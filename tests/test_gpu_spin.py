@@ -13,6 +13,8 @@ be in test_oracle_spin.py):
     oracle, which the FP64 step matches);
   * the Sedov blast with the feedback: conservative, physical, the shell at
     the similarity radius;
+  * 16^3 sub-grids: bit for bit equal to the box cut into 8^3, the fused
+    16^3 step to the separate launches;
   * spin outside {0, 1} is rejected.
 """
 import numpy as np
@@ -223,3 +225,40 @@ def test_sedov_blast_with_spin_feedback(H):
         assert abs(r_peak - R) < 1.5 * h, (r_peak, R)
         assert rho.sum() == pytest.approx(64.0 ** 3, rel=1e-12)
         ctx.close()
+
+
+@pytest.mark.parametrize("prec,decomp", [("fp64", "rows"), ("mixed", "rows"), ("mixed", "planes")])
+def test_sixteen_cubed_sub_grids_with_spin(H, prec, decomp):
+    """16^3 sub-grids with the feedback (a ragged box of 2 x 1 x 3 of them,
+    a blast and a random spin, periodic): after each of three RK3 steps the
+    interiors and dt equal the same box cut into 8^3 sub-grids bit for bit,
+    and in mixed precision the fused step equals the separate launches."""
+    from oracle import mesh
+    from paper_2107_10987_gb300.uniform import UniformRun
+    from test_gpu_subgrid16 import _blast_box
+    Ug, h = _blast_box(32, 16, 48)
+    Ug[6:9] = np.random.default_rng(55).uniform(-1e-3, 1e-3, Ug[6:9].shape)
+    p = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED}[prec]
+    dec = {"rows": H.HYDRO_DECOMP_ROWS, "planes": H.HYDRO_DECOMP_PLANES}[decomp]
+    res = {}
+    for N, nb in ((16, (2, 1, 3)), (8, (4, 2, 6))):
+        Ui = mesh.unjoin(Ug, N)
+        o = mesh.origins(*nb, N, h, (0.0, 0.0, 0.0))
+        for fused in ((False, True) if prec == "mixed" and N == 16 else (False,)):
+            ctx = H.Context(GAMMA, 0.0, N=N)
+            H.hydro_set_mode(ctx, p, spin=1)
+            H.hydro_set_launch(ctx, dec)
+            run = UniformRun(ctx, Ui, o, h, nb, H.HYDRO_BC_PERIODIC, fused=fused)
+            dts = []
+            for _ in range(3):
+                run.step()
+                dts.append(run.last_dt())
+            torch.cuda.synchronize()
+            assert H.hydro_status(ctx) == 0
+            res[N, fused] = (mesh.join(run.interior().cpu().numpy(), *nb), np.array(dts))
+            run.close()
+    a, da = res[16, False]
+    for key in res:
+        b, db = res[key]
+        assert np.array_equal(db.view(np.int64), da.view(np.int64)), key
+        assert np.array_equal(b.view(np.int64), a.view(np.int64)), (key, int((a != b).sum()))
