@@ -15,6 +15,7 @@ be in test_oracle_spin.py):
     the similarity radius;
   * 16^3 sub-grids: bit for bit equal to the box cut into 8^3, the fused
     16^3 step to the separate launches;
+  * graph replay of the RK3 step equals the direct launches bit for bit;
   * spin outside {0, 1} is rejected.
 """
 import numpy as np
@@ -262,3 +263,29 @@ def test_sixteen_cubed_sub_grids_with_spin(H, prec, decomp):
         b, db = res[key]
         assert np.array_equal(db.view(np.int64), da.view(np.int64)), key
         assert np.array_equal(b.view(np.int64), a.view(np.int64)), (key, int((a != b).sum()))
+
+
+@pytest.mark.parametrize("prec,fused", [("fp64", False), ("mixed", False), ("mixed", True)])
+def test_graph_replay_with_spin(H, prec, fused):
+    """The RK3 step captured into a CUDA graph in spin mode (the instances
+    with the feedback prepared before the capture) replays the direct
+    launches bit for bit."""
+    from test_gpu_fused import blast_mesh
+    from paper_2107_10987_gb300.uniform import UniformRun
+    nb = (2, 2, 2)
+    U, o, h = blast_mesh(*nb)
+    U[:, 6:9] = np.random.default_rng(57).uniform(-1e-3, 1e-3, U[:, 6:9].shape)
+    p = {"fp64": H.HYDRO_PREC_FP64, "mixed": H.HYDRO_PREC_MIXED}[prec]
+    out = []
+    for graph in (False, True):
+        ctx = H.Context(GAMMA, 0.0)
+        H.hydro_set_mode(ctx, p, spin=1)
+        run = UniformRun(ctx, U, o, h, nb, H.HYDRO_BC_PERIODIC, fused=fused)
+        for _ in range(3):
+            run.step(use_graph=graph)
+        torch.cuda.synchronize()
+        assert H.hydro_status(ctx) == 0
+        out.append((run.interior().clone(), run.last_dt()))
+        run.close()
+    assert bool((_bits(out[0][0]) == _bits(out[1][0])).all())
+    assert np.float64(out[0][1]).view(np.int64) == np.float64(out[1][1]).view(np.int64)
