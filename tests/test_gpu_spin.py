@@ -16,6 +16,8 @@ be in test_oracle_spin.py):
   * 16^3 sub-grids: bit for bit equal to the box cut into 8^3, the fused
     16^3 step to the separate launches;
   * graph replay of the RK3 step equals the direct launches bit for bit;
+  * with contact steepening and the learned indicator too, against the
+    oracle's masked step;
   * spin outside {0, 1} is rejected.
 """
 import numpy as np
@@ -289,3 +291,41 @@ def test_graph_replay_with_spin(H, prec, fused):
         run.close()
     assert bool((_bits(out[0][0]) == _bits(out[1][0])).all())
     assert np.float64(out[0][1]).view(np.int64) == np.float64(out[1][1]).view(np.int64)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_spin_with_contact_and_indicator_matches_masked_oracle(H, orc, fp64):
+    """All three options together: the learned indicator (its smooth cells
+    take the unlimited formula), contact steepening of the others, and the
+    spin feedback on every cell's points, against the oracle's masked step
+    with both options (FP64 <= 1e-12, mixed within the budget), and the
+    allocation-free entry point's bits in FP64."""
+    from oracle.compare import max_rel_error, mixed_worst, rate_floor
+    from test_gpu_contact import _indicator_mask, planar_contacts
+    n = 12
+    U = planar_contacts(n, 85)
+    theta, thr, mask = _indicator_mask(U, 86)
+    rng = np.random.default_rng(87)
+    origin = rng.uniform(-1, 1, (n, 3))
+    h = rng.uniform(0.05, 0.1, n)
+    P = orc.OracleParams(gamma=GAMMA, contact=1, spin=1)
+    ref, amo = orc.step_masked(P, U, origin, h, mask)
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64 if fp64 else H.HYDRO_PREC_MIXED, contact=1, spin=1)
+    H.hydro_set_indicator(ctx, torch.tensor(theta, device="cuda"), thr)
+    dUt, amt = gpu_step(H, ctx, U, origin, h)
+    assert H.hydro_status(ctx) == 0
+    dU, am = dUt.cpu().numpy(), amt.cpu().numpy()
+    assert np.all(np.isfinite(dU))
+    ref0, _ = orc.step_masked(orc.OracleParams(gamma=GAMMA, contact=1), U, origin, h, mask)
+    assert max_rel_error(ref0, ref, h) > 1e-3  # the feedback acts
+    if fp64:
+        assert max_rel_error(dU, ref, h, rate_floor(U, amo, h)) <= 1e-12
+        assert np.allclose(am, amo, rtol=1e-13, atol=0)
+        s, sm = gpu_step(H, ctx, U, origin, h, static=True)
+        assert bool((_bits(s) == _bits(dUt)).all()) and bool((_bits(sm) == _bits(amt)).all())
+        return
+    pert, _ = orc.step_masked(P, U.astype(np.float32).astype(np.float64), origin, h, mask)
+    worst = mixed_worst(dU, ref, pert, None, h, U, amo)
+    print("mixed spin + contact + indicator: largest err/budget", worst)
+    assert worst <= 1.0
