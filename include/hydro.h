@@ -105,9 +105,12 @@ typedef struct {
  * reconstructed at its quadrature points, read as a rigid rotation of the
  * cell's material: omega = z / I, I = rho h^2 / 6 (a uniform cube about its
  * centre), and v(x_q) += omega x (x_q - x_c), i.e. +-(3 / (rho h)) z x d at
- * the point x_c +- (h/2) d (cell averages rho and z; the paper defers the
- * spin treatment to the Octo-Tiger method paper, so this is a reading, in
- * the manner of Despres & Labourasse 2015).  Defaults: FP64,
+ * the point x_c +- (h/2) d (cell averages rho and z), with omega scaled down
+ * where the rotation's corner, at |omega| h sqrt(3)/2, would outrun the
+ * cell's sound speed sqrt(gamma (gamma-1) eps / rho), so that it moves at
+ * that speed (no feedback for eps <= 0).  The paper defers the spin
+ * treatment to the Octo-Tiger method paper, so this is a reading, in the
+ * manner of Despres & Labourasse 2015.  Defaults: FP64,
  * cfl 0.4, eta1 1e-3, eta2 0.1, 9 points, contact 0, spin 0. */
 typedef struct {
   int precision;   /* HYDRO_PREC_FP64 or HYDRO_PREC_MIXED */

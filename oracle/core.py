@@ -74,7 +74,7 @@ def lib():
         l.orc_ppm_line_eta.restype = None
         l.orc_contact_eta.argtypes = [C.POINTER(_P), dp, dp, dp]
         l.orc_contact_eta.restype = C.c_double
-        l.orc_spin_velocity.argtypes = [C.POINTER(_P), C.c_double, dp, C.c_double, dp, dp]
+        l.orc_spin_velocity.argtypes = [C.POINTER(_P), C.c_double, C.c_double, dp, C.c_double, dp, dp]
         l.orc_spin_velocity.restype = None
         l.orc_point_flux.argtypes = [C.POINTER(_P), dp, dp, C.c_int, dp, dp, dp]
         l.orc_count_ops.argtypes = [C.POINTER(_P), dp, dp, C.c_double, C.POINTER(C.c_long)]
@@ -187,13 +187,14 @@ def contact_eta(P: OracleParams, a5, rho2, p2) -> float:
     return lib().orc_contact_eta(C.byref(P.c()), _dp(a), _dp(r), _dp(p))
 
 
-def spin_velocity(P: OracleParams, rho: float, z, h: float, r) -> np.ndarray:
+def spin_velocity(P: OracleParams, rho: float, eps: float, z, h: float, r) -> np.ndarray:
     """The spin feedback's velocity increment at offset r from the centre of a
-    cell of density rho, spin density z and width h."""
+    cell of density rho, internal energy density eps, spin density z and
+    width h."""
     zz = np.ascontiguousarray(z, dtype=np.float64)
     rr = np.ascontiguousarray(r, dtype=np.float64)
     dv = np.zeros(3)
-    lib().orc_spin_velocity(C.byref(P.c()), float(rho), _dp(zz), float(h), _dp(rr), _dp(dv))
+    lib().orc_spin_velocity(C.byref(P.c()), float(rho), float(eps), _dp(zz), float(h), _dp(rr), _dp(dv))
     return dv
 
 

@@ -268,22 +268,35 @@ void point_flux(const Params& P, const T* qL, const T* qR, int a, const T xq[3],
 // Spin feedback into the reconstructed velocity.  PARITY UNPINNED beyond the
 // checks in tests/test_oracle_spin.py (the reduction to the plain method at
 // z = 0, conservation, the rigid-rotation moment of inertia, dissipation of a
-// uniform spin): the paper names the rotating-frame and spin treatment of the
-// hydro module but defers its definition to the Octo-Tiger method paper.
+// uniform spin, the sound-speed bound): the paper names the rotating-frame
+// and spin treatment of the hydro module but defers its definition to the
+// Octo-Tiger method paper.
 // Reading, in the manner of Despres & Labourasse (2015): the spin angular
 // momentum density z of a cell (its angular momentum about its own centre,
 // per unit volume) is carried as a rigid rotation of the cell's material,
 // omega = z / I with I = rho h^2 / 6 the moment of inertia per unit volume of
 // a uniform cube of side h about an axis through its centre, and the
 // velocity reconstructed at a point x_q of the cell's surface gains that
-// rotation's velocity omega x (x_q - x_c).  rho and z are the cell's
-// averages (U at stored cell index c).
+// rotation's velocity omega x (x_q - x_c).  The rotation is taken as
+// subsonic: where its fastest point, a corner at |omega| h sqrt(3) / 2,
+// would outrun the cell's sound speed c = sqrt(gamma (gamma-1) eps / rho),
+// omega is scaled down to reach c there (c = 0 for eps <= 0).  rho, eps and
+// z are the cell's primitives (Q at stored cell index c).
 template <class T>
-void spin_feedback(const Params& P, const T* U, long c, double h, const T xq[3], const T xc[3], T* q) {
+void spin_feedback(const Params& P, const std::vector<T>& Q, long c, double h, const T xq[3], const T xc[3], T* q) {
   const int S = P.N + 2 * P.G;
   const long S3 = (long)S * S * S;
-  const T I = (U[RHO * S3 + c] * T(h * h)) / T(6.0);
-  const T om[3] = {U[ZX * S3 + c] / I, U[ZY * S3 + c] / I, U[ZZ * S3 + c] / I};
+  const T rho = Q[RHO * S3 + c], eps = Q[EGAS * S3 + c];
+  const T I = (rho * T(h * h)) / T(6.0);
+  T om[3] = {Q[ZX * S3 + c] / I, Q[ZY * S3 + c] / I, Q[ZZ * S3 + c] / I};
+  const T wabs = sqrt_((om[0] * om[0] + om[1] * om[1]) + om[2] * om[2]);
+  const T vcorner = wabs * T(0.5 * h * std::sqrt(3.0));
+  const T cs2 = (T(P.gamma * (P.gamma - 1.0)) * eps) / rho;
+  const T cs = T(0.0) < cs2 ? sqrt_(cs2) : T(0.0);
+  if (cs < vcorner) {
+    const T theta = cs / vcorner;
+    for (int m = 0; m < 3; ++m) om[m] = theta * om[m];
+  }
   const T r[3] = {xq[0] - xc[0], xq[1] - xc[1], xq[2] - xc[2]};
   q[1] = q[1] + (om[1] * r[2] - om[2] * r[1]);
   q[2] = q[2] + (om[2] * r[0] - om[0] * r[2]);
@@ -462,8 +475,8 @@ void step_subgrid(const Params& P, const T* U, const double origin[3], double h,
                   xl[m] = T(origin[m]) + T(h) * T(ci[m] + 0.5);
                   xr[m] = T(origin[m]) + T(h) * T(cr[m] + 0.5);
                 }
-                spin_feedback(P, U, at(ci[0], ci[1], ci[2]), h, xq, xl, qL);
-                spin_feedback(P, U, at(cr[0], cr[1], cr[2]), h, xq, xr, qR);
+                spin_feedback(P, Q, at(ci[0], ci[1], ci[2]), h, xq, xl, qL);
+                spin_feedback(P, Q, at(cr[0], cr[1], cr[2]), h, xq, xr, qR);
               }
               point_flux(P, qL, qR, a, xq, Fq, aq);
               if (first) { am = aq; first = false; }
@@ -721,19 +734,22 @@ double orc_contact_eta(const orc_params* p, const double* a5, const double* rho2
 }
 
 // The spin feedback's velocity increment at offset r from the centre of a
-// cell of density rho, spin density z[3] and width h (spin_feedback on a
-// one-cell array).
-void orc_spin_velocity(const orc_params* p, double rho, const double* z, double h, const double* r, double* dv) {
+// cell of density rho, internal energy density eps, spin density z[3] and
+// width h (spin_feedback on a one-cell array).
+void orc_spin_velocity(const orc_params* p, double rho, double eps, const double* z, double h, const double* r,
+                       double* dv) {
   orc::Params P = to_p(p);
   P.N = 1;
   P.G = 0;
-  double U[orc::kMaxF] = {}, q[orc::kMaxF] = {};
-  U[orc::RHO] = rho;
-  U[orc::ZX] = z[0];
-  U[orc::ZY] = z[1];
-  U[orc::ZZ] = z[2];
+  std::vector<double> Q(orc::kMaxF, 0.0);
+  double q[orc::kMaxF] = {};
+  Q[orc::RHO] = rho;
+  Q[orc::EGAS] = eps;
+  Q[orc::ZX] = z[0];
+  Q[orc::ZY] = z[1];
+  Q[orc::ZZ] = z[2];
   const double xc[3] = {0.0, 0.0, 0.0};
-  orc::spin_feedback<double>(P, U, 0, h, r, xc, q);
+  orc::spin_feedback<double>(P, Q, 0, h, r, xc, q);
   dv[0] = q[1];
   dv[1] = q[2];
   dv[2] = q[3];

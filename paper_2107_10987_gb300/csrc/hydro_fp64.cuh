@@ -246,13 +246,22 @@ __device__ __forceinline__ double signed_pick(int d, double x) { return d == 0 ?
 
 // Spin feedback at a cell's point x_c + (h/2) d: the velocity there of the
 // cell's rigid rotation omega = z / I, I = rho h^2 / 6 (a uniform cube about
-// its centre), omega x (h/2) d = (3 / (rho h)) z x d, for the cell's averages
-// rho and z and k3h = 3 / h.  z x d by sign selection (d in {-1, 0, 1}^3), so
-// the increment at x_c - (h/2) d is exactly the negative.  Explicitly rounded
-// (no contraction), so that every kernel that adds it gets the same bits.
-__device__ __forceinline__ void spin_dv64(double rho, double zx, double zy, double zz, double k3h, int dx, int dy,
-                                          int dz, double dv[3]) {
-  const double k = k3h / rho;
+// its centre), omega x (h/2) d = (3 / (rho h)) z x d, for the cell's
+// primitives rho, eps and z and k3h = 3 / h, gg1 = gamma (gamma - 1).  The
+// rotation is subsonic: where its corner speed sqrt(3) (3 / (rho h)) |z|
+// exceeds the sound speed c = sqrt(gg1 eps / rho), the factor 3 / (rho h) is
+// replaced by the one that reaches c there, c / (sqrt(3) |z|) (none for
+// eps <= 0).  The test compares rho c^2 with rho times the corner speed
+// squared, so that only a capped cell divides again.  z x d by sign
+// selection (d in {-1, 0, 1}^3), so the increment at x_c - (h/2) d is
+// exactly the negative.  Explicitly rounded (no contraction), so that every
+// kernel that adds it gets the same bits.
+__device__ __forceinline__ void spin_dv64(double rho, double eps, double zx, double zy, double zz, double k3h,
+                                          double gg1, int dx, int dy, int dz, double dv[3]) {
+  double k = k3h / rho;
+  const double z2 = radd(radd(rmul(zx, zx), rmul(zy, zy)), rmul(zz, zz));
+  const double rc2 = rmul(gg1, eps);
+  if (rc2 < rmul(rmul(3.0, rmul(k3h, k)), z2)) k = rc2 > 0.0 ? sqrt(rc2 / rmul(rmul(3.0, rho), z2)) : 0.0;
   dv[0] = rmul(k, rsub(signed_pick(dz, zy), signed_pick(dy, zz)));
   dv[1] = rmul(k, rsub(signed_pick(dx, zz), signed_pick(dz, zx)));
   dv[2] = rmul(k, rsub(signed_pick(dy, zx), signed_pick(dx, zy)));

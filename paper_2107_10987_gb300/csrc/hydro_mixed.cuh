@@ -191,14 +191,20 @@ struct StepParamsF {
 
 // Spin feedback at a cell's point x_c + (h/2) d, FP32: the velocity there of
 // the cell's rigid rotation omega = z / I, I = rho h^2 / 6 (a uniform cube
-// about its centre), (3 / (rho h)) z x d, from the cell's FP32 primitives rho
-// and z; z x d by sign selection (d in {-1, 0, 1}^3), so the increment at
-// x_c - (h/2) d is exactly the negative and a line walked either way gets
-// the same values.  Every operation explicitly rounded.
+// about its centre), (3 / (rho h)) z x d, from the cell's FP32 primitives
+// rho, eps and z (gg1 = gamma (gamma - 1)); subsonic as spin_dv64 (the
+// factor scaled where the corner speed would exceed the sound speed); z x d
+// by sign selection (d in {-1, 0, 1}^3), so the increment at x_c - (h/2) d
+// is exactly the negative and a line walked either way gets the same values.
+// Every operation explicitly rounded.
 __device__ __forceinline__ float spin_pick32(int d, float x) { return d == 0 ? 0.f : (d > 0 ? x : -x); }
-__device__ __forceinline__ void spin_dv32(float rho, float zx, float zy, float zz, float k3h, int dx, int dy, int dz,
-                                          float dv[3]) {
-  const float k = __fdiv_rn(k3h, rho);
+__device__ __forceinline__ void spin_dv32(float rho, float eps, float zx, float zy, float zz, float k3h, float gg1,
+                                          int dx, int dy, int dz, float dv[3]) {
+  float k = __fdiv_rn(k3h, rho);
+  const float z2 = __fadd_rn(__fadd_rn(__fmul_rn(zx, zx), __fmul_rn(zy, zy)), __fmul_rn(zz, zz));
+  const float rc2 = __fmul_rn(gg1, eps);
+  if (rc2 < __fmul_rn(__fmul_rn(3.f, __fmul_rn(k3h, k)), z2))
+    k = rc2 > 0.f ? __fsqrt_rn(__fdiv_rn(rc2, __fmul_rn(__fmul_rn(3.f, rho), z2))) : 0.f;
   dv[0] = __fmul_rn(k, __fsub_rn(spin_pick32(dz, zy), spin_pick32(dy, zz)));
   dv[1] = __fmul_rn(k, __fsub_rn(spin_pick32(dx, zz), spin_pick32(dz, zx)));
   dv[2] = __fmul_rn(k, __fsub_rn(spin_pick32(dy, zx), spin_pick32(dx, zy)));

@@ -227,9 +227,10 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
       if constexpr (kSpin) {
         // the cell's spin fed back into the velocity at both ends of both
         // lines (spin_dv32; the plane sweep's values, bit for bit)
-        const float rc = Qf[RHO * S3 + cj], zx = Qf[ZX * S3 + cj], zy = Qf[ZY * S3 + cj], zz = Qf[ZZ * S3 + cj];
+        const float rc = Qf[RHO * S3 + cj], ec = Qf[EGAS * S3 + cj], zx = Qf[ZX * S3 + cj],
+                    zy = Qf[ZY * S3 + cj], zz = Qf[ZZ * S3 + cj], gg1 = __fmul_rn(PF.gamma, PF.gm1);
         float dv[3];
-        spin_dv32(rc, zx, zy, zz, PF.k3h, axis_comp(0, a, b, 1, t1, t2), axis_comp(1, a, b, 1, t1, t2),
+        spin_dv32(rc, ec, zx, zy, zz, PF.k3h, gg1, axis_comp(0, a, b, 1, t1, t2), axis_comp(1, a, b, 1, t1, t2),
                   axis_comp(2, a, b, 1, t1, t2), dv);
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
@@ -237,8 +238,8 @@ __device__ __forceinline__ void mixed_subgrid(const StepArgs64& A, const Io& io,
           qmA[1 + m] = __fsub_rn(qmA[1 + m], dv[m]);
         }
         if (kTwo) {
-          spin_dv32(rc, zx, zy, zz, PF.k3h, axis_comp(0, a, b, 1, -t1, -t2), axis_comp(1, a, b, 1, -t1, -t2),
-                    axis_comp(2, a, b, 1, -t1, -t2), dv);
+          spin_dv32(rc, ec, zx, zy, zz, PF.k3h, gg1, axis_comp(0, a, b, 1, -t1, -t2),
+                    axis_comp(1, a, b, 1, -t1, -t2), axis_comp(2, a, b, 1, -t1, -t2), dv);
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
             qpB[1 + m] = __fadd_rn(qpB[1 + m], dv[m]);

@@ -136,8 +136,8 @@ __device__ __forceinline__ void plane_line(const float* __restrict__ ring, int i
   float dv[3] = {0.f, 0.f, 0.f};
   const bool spin = kSpin && f0 == 0;
   if (spin)
-    spin_dv32(ring[off[2] + RHO * kPl], ring[off[2] + ZX * kPl], ring[off[2] + ZY * kPl], ring[off[2] + ZZ * kPl],
-              PF.k3h, dx, dy, dz, dv);
+    spin_dv32(ring[off[2] + RHO * kPl], ring[off[2] + EGAS * kPl], ring[off[2] + ZX * kPl], ring[off[2] + ZY * kPl],
+              ring[off[2] + ZZ * kPl], PF.k3h, __fmul_rn(PF.gamma, PF.gm1), dx, dy, dz, dv);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int fa = (f0 == 0 ? 1 : 5) + 2 * i;

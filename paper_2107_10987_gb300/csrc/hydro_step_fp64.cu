@@ -170,16 +170,18 @@ __global__ void __launch_bounds__(kThreads64, 1) hydro_step_fp64_kernel(StepArgs
           // lines (spin_dv64; the lines kernel's values, bit for bit)
           const double k3h = 3.0 / h;
           double dv[3];
-          spin_dv64(Q[RHO * S3 + cj], Q[ZX * S3 + cj], Q[ZY * S3 + cj], Q[ZZ * S3 + cj], k3h,
-                    axis_comp(0, a, b, 1, t1, t2), axis_comp(1, a, b, 1, t1, t2), axis_comp(2, a, b, 1, t1, t2), dv);
+          const double gg1 = rmul(A.P.gamma, A.P.gm1);
+          spin_dv64(Q[RHO * S3 + cj], Q[EGAS * S3 + cj], Q[ZX * S3 + cj], Q[ZY * S3 + cj], Q[ZZ * S3 + cj], k3h,
+                    gg1, axis_comp(0, a, b, 1, t1, t2), axis_comp(1, a, b, 1, t1, t2), axis_comp(2, a, b, 1, t1, t2),
+                    dv);
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
             qpA[1 + m] = radd(qpA[1 + m], dv[m]);
             qmA[1 + m] = rsub(qmA[1 + m], dv[m]);
           }
           if (p != 4) {
-            spin_dv64(Q[RHO * S3 + cj], Q[ZX * S3 + cj], Q[ZY * S3 + cj], Q[ZZ * S3 + cj], k3h,
-                      axis_comp(0, a, b, 1, -t1, -t2), axis_comp(1, a, b, 1, -t1, -t2),
+            spin_dv64(Q[RHO * S3 + cj], Q[EGAS * S3 + cj], Q[ZX * S3 + cj], Q[ZY * S3 + cj], Q[ZZ * S3 + cj], k3h,
+                      gg1, axis_comp(0, a, b, 1, -t1, -t2), axis_comp(1, a, b, 1, -t1, -t2),
                       axis_comp(2, a, b, 1, -t1, -t2), dv);
 #pragma unroll
             for (int m = 0; m < 3; ++m) {

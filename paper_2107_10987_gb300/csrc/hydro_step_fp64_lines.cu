@@ -203,7 +203,8 @@ __device__ __forceinline__ void line_run(const double* __restrict__ Q, const uin
     if (NG == 4 && k0 == 0 && P.spin) {
       // the cell's spin fed back into the velocity at both ends (spin_dv64)
       double dv[3];
-      spin_dv64(Q[RHO * S3 + ci], Q[ZX * S3 + ci], Q[ZY * S3 + ci], Q[ZZ * S3 + ci], k3h, dx, dy, dz, dv);
+      spin_dv64(Q[RHO * S3 + ci], Q[EGAS * S3 + ci], Q[ZX * S3 + ci], Q[ZY * S3 + ci], Q[ZZ * S3 + ci], k3h,
+                rmul(P.gamma, P.gm1), dx, dy, dz, dv);
 #pragma unroll
       for (int m3 = 0; m3 < 3; ++m3) {
         p[(1 + m3) % NG] = radd(p[(1 + m3) % NG], dv[m3]);

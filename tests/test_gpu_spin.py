@@ -3,7 +3,9 @@ C ABI, against the oracle's spin feedback (a reading, pinned as far as it can
 be in test_oracle_spin.py):
   * FP64 step: <= 1e-12 per field against the oracle with and without
     rotation and gravity, on random sub-grids whose spin moves the points by
-    up to about the flow speed; the feedback changes the rates far above that;
+    up to about the flow speed, so that the subsonic bound caps about a fifth
+    of the cells and leaves the rest; the feedback changes the rates far
+    above that;
   * the allocation-free entry point gives hydro_step's bits in spin mode;
   * mixed step: within the mixed-precision budget;
   * the row and plane decompositions agree bit for bit, and the fused step
@@ -60,6 +62,17 @@ def _inputs(n, seed):
     return U, origin, h
 
 
+def _capped_fraction(U, h):
+    """Share of cells whose rotation's corner, at sqrt(3) 3|z|/(rho h), would
+    outrun the sound speed sqrt(gamma (gamma-1) eps / rho) (these inputs are
+    far from the dual-energy switch: eps = E - |s|^2/(2 rho))."""
+    rho, s, E, z = U[:, 0], U[:, 1:4], U[:, 4], U[:, 6:9]
+    eps = E - 0.5 * (s ** 2).sum(1) / rho
+    c = np.sqrt(GAMMA * (GAMMA - 1.0) * np.maximum(eps, 0.0) / rho)
+    corner = np.sqrt(3.0) * 3.0 * np.sqrt((z ** 2).sum(1)) / (rho * h[:, None, None, None])
+    return float((corner > c).mean())
+
+
 def gpu_step(H, ctx, U, origin, h, g=None, static=False):
     dev = torch.device("cuda")
     n = U.shape[0]
@@ -83,6 +96,7 @@ def test_fp64_spin_step_matches_oracle(H, orc, omega, gravity):
     from oracle.compare import max_rel_error, rate_floor
     n = 96
     U, origin, h = _inputs(n, 41)
+    assert 0.1 < _capped_fraction(U, h) < 0.5  # both sides of the subsonic bound
     g = np.random.default_rng(43).uniform(-1, 1, (n, 3, 8, 8, 8)) if gravity else None
     ctx = H.Context(GAMMA, omega)
     H.hydro_set_mode(ctx, H.HYDRO_PREC_FP64, spin=1)
@@ -112,6 +126,7 @@ def test_mixed_spin_step_within_budget(H, orc):
     from oracle.compare import mixed_budget, mixed_error, mixed_worst
     n = 96
     U, origin, h = _inputs(n, 47)
+    assert 0.1 < _capped_fraction(U, h) < 0.5
     ctx = H.Context(GAMMA, 0.2)
     H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED, spin=1)
     dU, am = gpu_step(H, ctx, U, origin, h)

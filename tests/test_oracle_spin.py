@@ -3,7 +3,8 @@
 The spin treatment of the hydro module is deferred by the paper to the
 Octo-Tiger method paper, so the feedback of a cell's spin into the velocity
 reconstructed at its quadrature points is a reading (a rigid rotation of the
-cell's material, omega = z / I, I = rho h^2 / 6, added as omega x (x_q - x_c)):
+cell's material, omega = z / I, I = rho h^2 / 6, added as omega x (x_q - x_c),
+subsonic at the cell's corners):
 parity unpinned beyond these checks, each chosen so that a plausible mistake
 fails one of them:
   * rigid rotation by quadrature -> the moment of inertia (the factor 6, h^2),
@@ -15,6 +16,8 @@ fails one of them:
                                     spinning medium at rest must lose spin to
                                     the dissipation between counter-moving cell
                                     surfaces, and change nothing else)
+  * sound-speed bound            -> the corner of a fast rotation moves at the
+                                    sound speed, in the rotation's direction
 """
 import numpy as np
 import pytest
@@ -50,9 +53,30 @@ def test_rigid_rotation_moment_of_inertia_by_quadrature(orc):
         P = orc.OracleParams(spin=1)
         for _ in range(5):
             r = rng.uniform(-0.5, 0.5, 3) * h
-            dv = orc.spin_velocity(P, rho, z, h, r)
+            dv = orc.spin_velocity(P, rho, 1e12, z, h, r)  # hot: the rotation is subsonic
             want = np.cross(om0, r)
             assert np.allclose(dv, want, rtol=1e-12, atol=1e-14 * np.abs(om0).max() * h), (dv, want)
+
+
+def test_fast_rotation_is_bounded_by_the_sound_speed(orc):
+    """A rotation whose corners would move faster than the cell's sound
+    speed c = sqrt(gamma (gamma-1) eps / rho) is scaled down to reach c
+    there: with omega perpendicular to a corner's offset the corner moves at
+    exactly c, in the direction of omega x r; a slow rotation is unchanged;
+    eps <= 0 (no sound speed) leaves no feedback."""
+    P = orc.OracleParams(spin=1)
+    rho, eps, h = 1.7, 0.3, 0.05
+    c = np.sqrt(GAMMA * (GAMMA - 1.0) * eps / rho)
+    r = 0.5 * h * np.array([1.0, 1.0, 1.0])
+    axis = np.array([1.0, -1.0, 0.0]) / np.sqrt(2.0)  # perpendicular to r
+    I = rho * h * h / 6.0
+    for speed in (0.5 * c, 3.0 * c, 1e6 * c):
+        om = axis * speed / np.linalg.norm(r)  # corner speed |om||r| = speed
+        dv = orc.spin_velocity(P, rho, eps, I * om, h, r)
+        want = np.cross(om, r) * min(1.0, c / speed)
+        assert np.allclose(dv, want, rtol=1e-13, atol=0), (speed, dv, want)
+        assert np.linalg.norm(dv) <= c * (1 + 1e-13)
+    assert np.array_equal(orc.spin_velocity(P, rho, 0.0, I * axis, h, r), np.zeros(3))
 
 
 def test_zero_spin_reduces_to_the_plain_method(orc):
