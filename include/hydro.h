@@ -355,7 +355,14 @@ typedef struct {
   /* Adaptive mesh (NULL: the uniform nbx x nby x nbz mesh above).  With a mesh
    * each stage runs hydro_fill_ghosts_amr, hydro_step with face_flux and
    * hydro_flux_correct_amr instead of the uniform ghost fill (nbx, nby, nbz
-   * and bc are then ignored). */
+   * and bc are then ignored).  In HYDRO_PREC_MIXED with 8^3 leaves and the
+   * row sweep (no contact steepening or spin feedback) the fill only
+   * prolongs the ghost cells inside coarser leaves and the step reads the
+   * others where they live: a same-level leaf's interior, or the mean of
+   * the eight children in a finer leaf, from a restriction image of every
+   * leaf in the context (n_sub x F x 64 doubles).  The new state and *dt
+   * equal the full sequence's bit for bit; the ghost cells of the state
+   * buffers held by same-level or finer leaves are then not written. */
   const hydro_amr_t* amr;
   double* face_flux;  /* [n_sub][6][F+3][N][N], used with amr */
   /* Nonzero: the whole time step as one persistent launch (uniform mesh and

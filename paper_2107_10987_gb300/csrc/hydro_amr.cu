@@ -2,10 +2,6 @@
 // octree of NN^3 sub-grids, NN = 8 or 16 (2:1 balanced across faces, edges
 // and vertices).
 //
-// Leaves are found through dense per-level tables (hydro_amr_t): at level l
-// entry ((k 2^l) + j) 2^l + i is the leaf index at that sub-grid position,
-// -1 where the position is refined, -2 where it lies inside a coarser leaf.
-//
 // Ghost fill, two launches: (1) a ghost cell held by a same-level leaf is
 // copied, one over a refined position is the mean of its 8 finer cells
 // (taken in (dz, dy, dx) order and summed pairwise, ((a0+a1)+(a2+a3)) +
@@ -23,45 +19,15 @@
 // x F_s.  Both operations use explicitly rounded arithmetic so that the FP64
 // oracle's values are reproduced.
 #include "hydro.h"
-#include "hydro_common.cuh"
+#include "hydro_amr.cuh"
 #include "hydro_ctx.h"
 
 namespace hyd {
-
-struct AMRArgs {
-  double* U;
-  const int* table;
-  const int* leaf_level;
-  const int* leaf_ijk;
-  int lmin, lmax, bc, n_sub;
-  unsigned* status;
-};
-
-__device__ __forceinline__ long level_offset(int l, int lmin) {
-  // sum_{m = lmin}^{l-1} 8^m
-  long off = 0;
-  for (int m = lmin; m < l; ++m) off += 1L << (3 * m);
-  return off;
-}
-
-// The leaf (or -1 / -2) holding global cell (gx, gy, gz) of level l, for
-// leaves of NN^3 cells.
-template <int NN>
-__device__ __forceinline__ int lookup(const AMRArgs& A, int l, int gx, int gy, int gz) {
-  if (l < A.lmin || l > A.lmax) return -3;
-  const int n = 1 << l;
-  return A.table[level_offset(l, A.lmin) + ((long)(gz / NN) * n + (gy / NN)) * n + (gx / NN)];
-}
 
 // Boundary-face value [s][f][q][pc][pb] of leaves of NN^3 cells.
 template <int NN>
 __device__ __forceinline__ size_t face_index_nn(int s, int f, int q, int pc, int pb) {
   return ((((size_t)s * 6 + f) * DQ + q) * NN + pc) * NN + pb;
-}
-
-__device__ __forceinline__ int bc_amr(int g, int n, int bc) {
-  if (bc == 0) return g < 0 ? g + n : (g >= n ? g - n : g);
-  return g < 0 ? 0 : (g >= n ? n - 1 : g);
 }
 
 // Position of a ghost cell's sub-grid relative to a base position, after the
@@ -200,19 +166,56 @@ __device__ __forceinline__ double quarter64(double x) {
   return rmul(x, 0.25);
 }
 
-// Prolongation of one fine ghost cell from coarse cell C (padded pointer to
-// field 0): U_C + s_x o_x + s_y o_y + s_z o_z, all ten fields.
-template <int NN>
-__device__ __forceinline__ void prolong_cell(const double* C, const double off[3], double* dst) {
-  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
+// The six face neighbours of coarse cell C (global cell Cw of level lc, Cp
+// its padded pointer in its leaf), minus and plus along x, y, z: pointer to
+// field 0 and field stride.  Without kDirect every neighbour is read from
+// the coarse leaf's padded array, whose ghost cells the first pass filled;
+// with kDirect a neighbour outside the coarse leaf's interior is read where
+// it lives (amr_source: a same-level leaf's interior or a finer leaf's
+// restriction image), which are the values the first pass would copy there.
+template <int NN, bool kDirect>
+__device__ __forceinline__ void coarse_stencil(const AMRArgs& A, LevelRef Lc, LevelRef Lcf, const int Cw[3],
+                                               const double* Cp, const double* nbp[6], int nbs[6]) {
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LM = NN - 1;
   const int st[3] = {1, LS, LS * LS};
 #pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const int j = 2 * d + sg, step = sg ? 1 : -1;
+      nbp[j] = Cp + step * st[d];
+      nbs[j] = LS3;
+      if (kDirect) {
+        const int loc = (Cw[d] & LM) + step;
+        if (loc < 0 || loc > LM) {
+          int g[3] = {Cw[0], Cw[1], Cw[2]};
+          g[d] = bc_amr(Cw[d] + step, NN * Lc.n, A.bc);
+          size_t sd;
+          const double* p = amr_source<NN>(A, Lc, Lcf, g[0], g[1], g[2], sd);
+          if (p) {
+            nbp[j] = p;
+            nbs[j] = (int)sd;
+          }
+        }
+      }
+    }
+}
+
+// Prolongation of one fine ghost cell from coarse cell C (padded pointer to
+// field 0, face neighbours from coarse_stencil): U_C + s_x o_x + s_y o_y +
+// s_z o_z, all ten fields.
+template <int NN>
+__device__ __forceinline__ void prolong_cell(const double* C, const double* const nbp[6], const int nbs[6],
+                                             const double off[3], double* dst) {
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS;
+#pragma unroll
   for (int k = 0; k < F; ++k) {
-    const double* q = C + (size_t)k * LS3;
-    double v = q[0];
+    const double c = C[(size_t)k * LS3];
+    double v = c;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double dp = rsub(q[st[d]], q[0]), dm = rsub(q[0], q[-st[d]]);
+      const double dp = rsub(nbp[2 * d + 1][(size_t)k * nbs[2 * d + 1]], c);
+      const double dm = rsub(c, nbp[2 * d][(size_t)k * nbs[2 * d]]);
       v = radd(v, rmul(minmod64(dp, dm), off[d]));
     }
     dst[(size_t)k * LS3] = v;
@@ -224,8 +227,9 @@ __device__ __forceinline__ void prolong_cell(const double* C, const double off[3
 // fields' minmod slopes once and writes every child that is one of the
 // leaf's ghost cells (the same values as prolonging child by child).  Ghost
 // cells outside the domain (outflow: clamped positions) are prolonged one by
-// one afterwards.
-template <int NN>
+// one afterwards.  kDirect: the coarse cells' neighbours are read where they
+// live (coarse_stencil), so that the first pass need not run.
+template <int NN, bool kDirect>
 __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A) {
   constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
   __shared__ int coarser;  // some neighbour position of the leaf lies inside a coarser leaf
@@ -251,6 +255,7 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
     if (!coarser) continue;
     const int b[3] = {A.leaf_ijk[3 * s] * NN, A.leaf_ijk[3 * s + 1] * NN, A.leaf_ijk[3 * s + 2] * NN};
     const int ncell = NN << l, nc = ncell >> 1;
+    const LevelRef Lc = level_ref(A, l - 1), Lcf = level_ref(A, l);  // the coarse level and this one
     double* dstb = A.U + (size_t)s * F * LS3;
     // the coarse block covering the leaf's padded region: NN/2 + 4 cells an axis
     constexpr int LB = NN / 2 + 4;
@@ -278,26 +283,28 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
         if (in && !interior) mask |= 1 << dch;
       }
       if (!mask) continue;
-      const int tc = lookup<NN>(A, l - 1, Cw[0], Cw[1], Cw[2]);
+      const int tc = lookup_at<NN>(A, Lc, Cw[0], Cw[1], Cw[2]);
       if (tc == -2) atomicOr(A.status, 4u);  // two levels coarser: not 2:1 balanced
       if (tc < 0) continue;                  // refined at level l-1: pass 1 filled these
       const double* Cp =
           A.U + (size_t)tc * F * LS3 + (((Cw[2] & LM) + G) * LS + ((Cw[1] & LM) + G)) * LS + ((Cw[0] & LM) + G);
+      const double* nbp[6];
+      int nbs[6];
+      coarse_stencil<NN, kDirect>(A, Lc, Lcf, Cw, Cp, nbp, nbs);
       // per field: the quarter slopes t_d = s_d / 4 once (the child offsets are
       // +-1/4, and -(s/4) = s * (-1/4) exactly), then the children's values
       // ((c +- t_x) +- t_y) +- t_z as a tree of partial sums -- the same
       // additions, in the same order, as prolonging child by child
-      const int st[3] = {1, LS, LS * LS};
       const int need_x = ((mask & 0x55) ? 1 : 0) | ((mask & 0xaa) ? 2 : 0);  // children with x offset -, +
       double* dst0 = dstb + ((2 * C[2] - b[2] + G) * LS + (2 * C[1] - b[1] + G)) * LS + (2 * C[0] - b[0] + G);
 #pragma unroll 1
       for (int k = 0; k < F; ++k) {
-        const double* q = Cp + (size_t)k * LS3;
-        const double c = q[0];
+        const double c = Cp[(size_t)k * LS3];
         double t[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const double dp = rsub(q[st[d]], c), dm = rsub(c, q[-st[d]]);
+          const double dp = rsub(nbp[2 * d + 1][(size_t)k * nbs[2 * d + 1]], c);
+          const double dm = rsub(c, nbp[2 * d][(size_t)k * nbs[2 * d]]);
           t[d] = quarter64(minmod64(dp, dm));
         }
         double vx[2];
@@ -328,30 +335,97 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
       const int gx = b[0] + lx, gy = b[1] + ly, gz = b[2] + lz;
       if (gx >= 0 && gx < ncell && gy >= 0 && gy < ncell && gz >= 0 && gz < ncell) continue;
       const int cx = bc_amr(gx, ncell, 1), cy = bc_amr(gy, ncell, 1), cz = bc_amr(gz, ncell, 1);
-      if (lookup<NN>(A, l, cx, cy, cz) != -2) continue;
+      if (lookup_at<NN>(A, Lcf, cx, cy, cz) != -2) continue;
       const int px = cx >> 1, py = cy >> 1, pz = cz >> 1;
-      const int tc = lookup<NN>(A, l - 1, px, py, pz);
+      const int tc = lookup_at<NN>(A, Lc, px, py, pz);
       if (tc < 0) {
         atomicOr(A.status, 4u);
         continue;
       }
       const double* Cp = A.U + (size_t)tc * F * LS3 + (((pz & LM) + G) * LS + ((py & LM) + G)) * LS + ((px & LM) + G);
+      const int Cw[3] = {px, py, pz};
+      const double* nbp[6];
+      int nbs[6];
+      coarse_stencil<NN, kDirect>(A, Lc, Lcf, Cw, Cp, nbp, nbs);
       const double off[3] = {(cx & 1) ? 0.25 : -0.25, (cy & 1) ? 0.25 : -0.25, (cz & 1) ? 0.25 : -0.25};
-      prolong_cell<NN>(Cp, off, dstb + c);
+      prolong_cell<NN>(Cp, nbp, nbs, off, dstb + c);
+    }
+  }
+}
+
+// Each leaf's restriction image: image cell (i, j, k) of field f is the mean
+// of the leaf's cells (2i + dx, 2j + dy, 2k + dz), in the first pass's order
+// and rounding (children at d = dx + 2 dy + 4 dz, summed pairwise, times
+// 1/8), so it equals the value that pass writes into a coarser leaf's ghost
+// cell over this leaf.
+template <int NN>
+__global__ void __launch_bounds__(256) hydro_amr_restrict_kernel(const double* __restrict__ U,
+                                                                 double* __restrict__ img, int n_sub) {
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, H2 = NN / 2, I3 = img_cells<NN>();
+  for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
+    for (int e = threadIdx.x; e < F * I3; e += blockDim.x) {
+      const int k = e / I3, i = e % I3;
+      const int x = i % H2, y = (i / H2) % H2, z = i / (H2 * H2);
+      const double* p = U + ((size_t)s * F + k) * LS3 + ((2 * z + G) * LS + (2 * y + G)) * LS + (2 * x + G);
+      const double a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + LS), a3 = __ldg(p + LS + 1);
+      const double a4 = __ldg(p + LS * LS), a5 = __ldg(p + LS * LS + 1), a6 = __ldg(p + LS * LS + LS),
+                   a7 = __ldg(p + LS * LS + LS + 1);
+      img[((size_t)s * F + k) * I3 + i] =
+          rmul(radd(radd(radd(a0, a1), radd(a2, a3)), radd(radd(a4, a5), radd(a6, a7))), 0.125);
     }
   }
 }
 
 // One thread per interior cell of a leaf; the cell's faces on the leaf
 // boundary that border finer leaves are corrected in the order x-, x+, y-, ...
+// The leaf's six face neighbours are looked up once (bit 2a + side of
+// `finer`: refined at the leaf's level), and a leaf with none, most of a
+// mesh, is left at once; for the others the four finer leaves across each
+// such face (fine[2a + side][2 qc + qb], qb and qc the halves of the face
+// along its transverse axes b < c) are looked up once too.
 template <int NN>
 __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, const double* h, const double* faces,
                                                                  double* dUdt) {
-  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
+  constexpr int LN3 = NN * NN * NN, LM = NN - 1, H2 = NN / 2;
+  __shared__ int finer;
+  __shared__ int fine[6][4];
   for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
     const int l = A.leaf_level[s];
     const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
     const int n = 1 << l;
+    __syncthreads();  // the previous leaf's flags are no longer read
+    if (threadIdx.x == 0) finer = 0;
+    __syncthreads();
+    if (threadIdx.x < 6 && l < A.lmax) {
+      const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
+      int nb[3] = {ijk[0], ijk[1], ijk[2]};
+      nb[a] += side ? 1 : -1;
+      bool in = true;
+      if (nb[a] < 0 || nb[a] >= n) {
+        if (A.bc != 0) in = false;
+        else nb[a] = (nb[a] + n) % n;
+      }
+      if (in && lookup<NN>(A, l, nb[0] * NN, nb[1] * NN, nb[2] * NN) == -1) atomicOr(&finer, 1 << threadIdx.x);
+    }
+    __syncthreads();
+    const int fl = finer;
+    if (!fl) continue;
+    if (threadIdx.x < 24) {
+      const int j = threadIdx.x >> 2, a = j >> 1, side = j & 1, qb = threadIdx.x & 1, qc = (threadIdx.x >> 1) & 1;
+      const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+      int o = -3;
+      if (fl & (1 << j)) {
+        const int nf = 2 * n;
+        int pf[3];
+        pf[a] = side ? 2 * (ijk[a] + 1) : 2 * ijk[a] - 1;
+        if (pf[a] < 0 || pf[a] >= nf) pf[a] = (pf[a] + nf) % nf;  // periodic wrap
+        pf[b] = 2 * ijk[b] + qb;
+        pf[c] = 2 * ijk[c] + qc;
+        o = lookup<NN>(A, l + 1, pf[0] * NN, pf[1] * NN, pf[2] * NN);
+      }
+      fine[j][threadIdx.x & 3] = o;
+    }
+    __syncthreads();
     const double hc = h[s];
     for (int cell = threadIdx.x; cell < LN3; cell += blockDim.x) {
       const int cl[3] = {cell % NN, (cell / NN) % NN, cell / (NN * NN)};
@@ -361,13 +435,7 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
         const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
         for (int side = 0; side < 2; ++side) {
           if (cl[a] != (side ? NN - 1 : 0)) continue;
-          int nb[3] = {ijk[0], ijk[1], ijk[2]};
-          nb[a] += side ? 1 : -1;
-          if (nb[a] < 0 || nb[a] >= n) {
-            if (A.bc != 0) continue;
-            nb[a] = (nb[a] + n) % n;
-          }
-          if (lookup<NN>(A, l, nb[0] * NN, nb[1] * NN, nb[2] * NN) != -1) continue;
+          if (!(fl & (1 << (2 * a + side)))) continue;
           if (!touched) {
 #pragma unroll
             for (int k = 0; k < F; ++k) du[k] = dUdt[((size_t)s * F + k) * LN3 + cell];
@@ -379,15 +447,15 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
 #pragma unroll
           for (int k = 0; k < F; ++k) fsum[k] = 0.0;
           bool ok = true;
+          // the fine leaf across this half of the face: the same for the
+          // four sub-faces of the cell
+          const int o = fine[2 * a + side][2 * (pc / H2) + pb / H2];
           for (int dc = 0; dc < 2; ++dc)
             for (int db = 0; db < 2; ++db) {
               int gf[3];
               gf[a] = side ? (ijk[a] + 1) * 2 * NN : ijk[a] * 2 * NN - 1;
               gf[b] = 2 * (ijk[b] * NN + pb) + db;
               gf[c] = 2 * (ijk[c] * NN + pc) + dc;
-              const int nf = NN << (l + 1);
-              if (gf[a] < 0 || gf[a] >= nf) gf[a] = (gf[a] + nf) % nf;  // periodic wrap
-              const int o = lookup<NN>(A, l + 1, gf[0], gf[1], gf[2]);
               if (o < 0) {
                 ok = false;
                 continue;
@@ -434,7 +502,7 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
 
 }  // namespace hyd
 
-static hyd::AMRArgs amr_args(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M) {
+hyd::AMRArgs hydro_amr_args(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M) {
   hyd::AMRArgs A;
   A.U = B->U;
   A.table = M->table;
@@ -445,6 +513,7 @@ static hyd::AMRArgs amr_args(hydro_ctx_t* c, const hydro_batch_t* B, const hydro
   A.bc = M->bc;
   A.n_sub = B->n_sub;
   A.status = c->status;
+  A.image = c->amr_img;
   return A;
 }
 
@@ -463,16 +532,16 @@ int hydro_fill_ghosts_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_am
   if (!B->U) return HYDRO_EINVAL;
   int rc = hydro_ctx_prepare(c, 0);
   if (rc) return rc;
-  hyd::AMRArgs A = amr_args(c, B, M);
+  hyd::AMRArgs A = hydro_amr_args(c, B, M);
   const int cap = c->num_sms * 8;
   const int grid = B->n_sub < cap ? B->n_sub : cap;
   cudaStream_t st = (cudaStream_t)stream;
   if (c->N == 16) {
     hyd::hydro_ghost_amr_kernel<16><<<grid, 256, 0, st>>>(A);
-    hyd::hydro_ghost_amr_prolong_kernel<16><<<grid, 256, 0, st>>>(A);
+    hyd::hydro_ghost_amr_prolong_kernel<16, false><<<grid, 256, 0, st>>>(A);
   } else {
     hyd::hydro_ghost_amr_kernel<8><<<grid, 256, 0, st>>>(A);
-    hyd::hydro_ghost_amr_prolong_kernel<8><<<grid, 256, 0, st>>>(A);
+    hyd::hydro_ghost_amr_prolong_kernel<8, false><<<grid, 256, 0, st>>>(A);
   }
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
@@ -484,7 +553,7 @@ int hydro_flux_correct_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_a
   if (!B->h || !face_flux || !dUdt) return HYDRO_EINVAL;
   int rc = hydro_ctx_prepare(c, 0);
   if (rc) return rc;
-  hyd::AMRArgs A = amr_args(c, B, M);
+  hyd::AMRArgs A = hydro_amr_args(c, B, M);
   const int cap = c->num_sms * 8;
   const int grid = B->n_sub < cap ? B->n_sub : cap;
   if (c->N == 16)
@@ -495,3 +564,22 @@ int hydro_flux_correct_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_a
 }
 
 }  // extern "C"
+
+// The lean fill of the adaptive RK3 sequence (8^3 leaves; the step's loader
+// reads same-level and finer neighbours itself): every leaf's restriction
+// image, then the ghost cells inside coarser leaves, prolonged from coarse
+// cells whose neighbours are read where they live.  Ghost cells held by
+// same-level or finer leaves are left as they were.  The image buffer
+// (hydro_ctx_prepare_amr) must hold n_sub leaves.
+int hydro_fill_ghosts_amr_lean(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M, cudaStream_t st) {
+  if (!c || !B || B->n_sub < 0 || !amr_ok(M) || c->N != 8) return HYDRO_EINVAL;
+  if (B->n_sub == 0) return HYDRO_OK;
+  if (!B->U || !c->amr_img || c->amr_img_bytes < (size_t)B->n_sub * hyd::F * hyd::img_cells<8>() * sizeof(double))
+    return HYDRO_EINVAL;
+  hyd::AMRArgs A = hydro_amr_args(c, B, M);
+  const int cap = c->num_sms * 8;
+  const int grid = B->n_sub < cap ? B->n_sub : cap;
+  hyd::hydro_amr_restrict_kernel<8><<<grid, 256, 0, st>>>(B->U, c->amr_img, B->n_sub);
+  hyd::hydro_ghost_amr_prolong_kernel<8, true><<<grid, 256, 0, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}

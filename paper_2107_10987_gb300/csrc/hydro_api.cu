@@ -6,10 +6,12 @@
 #include <new>
 
 #include "hydro.h"
+#include "hydro_amr.cuh"
 #include "hydro_common.cuh"
 #include "hydro_ctx.h"
 
 namespace hyd {
+cudaError_t launch_step_mixed_amr(const StepArgs64& A, const AMRArgs& M, int grid, cudaStream_t st);
 cudaError_t launch_step_fp64_lines(const StepArgs64& A, int grid, int nn, cudaStream_t st);
 cudaError_t prepare_step_fp64_lines();
 size_t step_fp64_lines_per_cta();
@@ -199,6 +201,45 @@ int hydro_ctx_prepare(hydro_ctx* c, int n_sub) {
   if (e == cudaSuccess) e = hyd::prepare_step_fp64_lines();
   if (e == cudaSuccess) e = hyd::prepare_step_mixed();
   if (e != cudaSuccess) return cuda_fail(e, "hydro_ctx_prepare");
+  return HYDRO_OK;
+}
+
+bool hydro_amr_direct_ok(const hydro_ctx* c) {
+  return c->N == hyd::N && c->mode.precision == HYDRO_PREC_MIXED && !c->mode.contact && !c->mode.spin &&
+         eff_decomp(c) == HYDRO_DECOMP_ROWS;
+}
+
+int hydro_ctx_prepare_amr(hydro_ctx* c, int n_sub) {
+  int rc = hydro_ctx_prepare(c, n_sub);
+  if (rc) return rc;
+  return ensure_buf(&c->amr_img, &c->amr_img_bytes,
+                    (size_t)n_sub * hyd::F * (hyd::N / 2) * (hyd::N / 2) * (hyd::N / 2) * sizeof(double),
+                    "cudaMalloc(restriction images)");
+}
+
+hyd::AMRArgs hydro_amr_args(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M);
+
+// The mixed row sweep over the leaves of an adaptive mesh, its loader
+// reading same-level neighbours' interiors and finer neighbours' restriction
+// images itself (hydro_fill_ghosts_amr_lean before it): the same dU/dt,
+// amax and boundary faces, bit for bit, as hydro_step after the full fill.
+int hydro_step_amr_direct(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_t* M, double* dUdt, double* amax,
+                          double* face_flux, cudaStream_t st) {
+  if (!c || !B || !M || B->n_sub < 0 || !hydro_amr_direct_ok(c)) return HYDRO_EINVAL;
+  if (B->n_sub == 0) return HYDRO_OK;
+  if (!B->U || !B->origin || !B->h || !dUdt || !amax || !face_flux) return HYDRO_EINVAL;
+  if (!aligned16(B->U) || !aligned16(dUdt)) return HYDRO_EINVAL;
+  int rc = hydro_ctx_prepare_amr(c, B->n_sub);
+  if (rc) return rc;
+  const int slots = step_slots(c, true);
+  const int grid = B->n_sub < slots ? B->n_sub : slots;
+  rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
+                  "cudaMalloc(step scratch)");
+  if (rc) return rc;
+  const hyd::StepArgs64 A = step_args(c, B, dUdt, amax, face_flux);
+  const hyd::AMRArgs Am = hydro_amr_args(c, B, M);
+  const cudaError_t e = hyd::launch_step_mixed_amr(A, Am, grid, st);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_step_amr_direct");
   return HYDRO_OK;
 }
 
@@ -500,6 +541,7 @@ void hydro_destroy(hydro_ctx_t* c) {
   if (c->u2) cudaFree(c->u2);
   if (c->prims) cudaFree(c->prims);
   if (c->sync) cudaFree(c->sync);
+  if (c->amr_img) cudaFree(c->amr_img);
   delete c;
 }
 

@@ -31,6 +31,8 @@ struct hydro_ctx {
   size_t prims_bytes;
   double* sync;          // fused RK3 step: barrier, work counter and per-sub-grid flags (unsigned words)
   size_t sync_bytes;
+  double* amr_img;       // adaptive RK3 step: each leaf's restriction image [n_sub][F][(N/2)^3]
+  size_t amr_img_bytes;
 };
 
 // Allocate the context's status word and the step scratch for a batch of
@@ -42,4 +44,13 @@ int hydro_ctx_prepare(hydro_ctx* c, int n_sub);
 // allocating its buffers on first use (hydro_ctx_prepare_fused before a
 // capture).
 int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub);
+// The adaptive RK3 sequence with direct neighbour reads: whether this
+// context's step takes it (mixed precision, 8^3 leaves, row sweep, no
+// contact steepening or spin feedback), its image buffer for n_sub leaves
+// (allocated before a stream capture), its lean ghost fill and its step.
+bool hydro_amr_direct_ok(const hydro_ctx* c);
+int hydro_ctx_prepare_amr(hydro_ctx* c, int n_sub);
+int hydro_fill_ghosts_amr_lean(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_t* M, cudaStream_t st);
+int hydro_step_amr_direct(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_t* M, double* dUdt, double* amax,
+                          double* face_flux, cudaStream_t st);
 int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st);

@@ -12,6 +12,10 @@
 // The first update writes the second buffer, so the step's initial state X
 // is kept without a copy; the next step runs Y -> X.  Two graphs (X->Y and
 // Y->X) are instantiated and replayed alternately.
+// On an adaptive mesh in mixed precision (8^3 leaves, row sweep, no contact
+// steepening or spin feedback) the ghost fill is the lean one and the step
+// reads same-level and finer neighbours itself (hydro_step_mixed_amr.cu):
+// the same values, bit for bit, without copying them into ghost cells.
 #include <cmath>
 #include <new>
 
@@ -36,7 +40,12 @@ static int rk3_enqueue(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, 
   int rc;
   for (int k = 0; k < 3; ++k) {
     const hydro_batch_t* B = (k == 0) ? &X : &Y;
-    if (d->amr) {
+    if (d->amr && hydro_amr_direct_ok(ctx)) {
+      if ((rc = hydro_ctx_prepare_amr(ctx, B->n_sub))) return rc;
+      if ((rc = hydro_fill_ghosts_amr_lean(ctx, B, d->amr, st))) return rc;
+      if ((rc = hydro_step_amr_direct(ctx, B, d->amr, d->dUdt, d->amax, d->face_flux, st))) return rc;
+      if ((rc = hydro_flux_correct_amr(ctx, B, d->amr, d->face_flux, d->dUdt, st))) return rc;
+    } else if (d->amr) {
       if ((rc = hydro_fill_ghosts_amr(ctx, B, d->amr, st))) return rc;
       if ((rc = hydro_step(ctx, B, 0.0, d->dUdt, d->amax, d->face_flux, st))) return rc;
       if ((rc = hydro_flux_correct_amr(ctx, B, d->amr, d->face_flux, d->dUdt, st))) return rc;
@@ -82,7 +91,9 @@ int hydro_rk3_graph_create(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, hydro_gr
     return HYDRO_ECUDA;
   }
   // everything the launches need is allocated before the capture
-  int rc = d->fused ? hydro_ctx_prepare_fused(ctx, d->a.n_sub) : hydro_ctx_prepare(ctx, d->a.n_sub);
+  int rc = d->fused ? hydro_ctx_prepare_fused(ctx, d->a.n_sub)
+           : (d->amr && hydro_amr_direct_ok(ctx)) ? hydro_ctx_prepare_amr(ctx, d->a.n_sub)
+                                                   : hydro_ctx_prepare(ctx, d->a.n_sub);
   for (int p = 0; p < 2 && rc == HYDRO_OK; ++p) {
     if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       rc = HYDRO_ECUDA;

@@ -7,18 +7,21 @@ namespace hyd {
 
 void launch_step_mixed_spin(const StepArgs64& A, int grid, int planes, int nn, cudaStream_t st);
 cudaError_t prepare_step_mixed_spin();
+cudaError_t prepare_step_mixed_amr();
 
 size_t step_mixed_smem_bytes() { return kMixedSmemBytes; }
 
 // Opt in to the kernels' dynamic shared memory once per device, with and
-// without the spin feedback (no allocation; call before any stream capture).
+// without the spin feedback and for the adaptive mesh's direct loader (no
+// allocation; call before any stream capture).
 cudaError_t prepare_step_mixed() {
   static unsigned long long done = 0;
   cudaError_t e = once_per_device(&done, [] {
     cudaError_t r = mixed_attrs<8, false>();
     return r == cudaSuccess ? mixed_attrs<16, false>() : r;
   });
-  return e == cudaSuccess ? prepare_step_mixed_spin() : e;
+  if (e == cudaSuccess) e = prepare_step_mixed_spin();
+  return e == cudaSuccess ? prepare_step_mixed_amr() : e;
 }
 
 // planes: the plane-sweep decomposition (grid: CTAs, at most one per SM);

@@ -204,3 +204,82 @@ def test_batched_4096_leaf_mesh(H, mixed, oracle_mod):
         worst = mixed_worst(got, ref, pert, faces, h_s, Us, amo)
         print("AMR shell mixed: largest err/budget", worst)
         assert worst <= 1.0
+
+
+def _manual_rk3(H, ctx, mesh, U, origin, h, steps, cfl=0.4):
+    """RK3 steps through the public calls with the full two-pass ghost fill:
+    ghost fill, step with boundary faces, coarse-fine flux correction, dt
+    after the first stage, update.  Returns the final state and dt."""
+    n = U.shape[0]
+    X, Y = U.clone(), torch.zeros_like(U)
+    dU = torch.empty((n, 10, 8, 8, 8), dtype=torch.float64, device="cuda")
+    am = torch.empty(n, dtype=torch.float64, device="cuda")
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    faces = torch.empty((n, 6, 13, 8, 8), dtype=torch.float64, device="cuda")
+    for _ in range(steps):
+        for k in range(3):
+            B = H.make_batch(X if k == 0 else Y, origin, h)
+            H.hydro_fill_ghosts_amr(ctx, B, mesh)
+            H.hydro_step(ctx, B, 0.0, dU, am, faces)
+            H.hydro_flux_correct_amr(ctx, B, mesh, faces, dU)
+            if k == 0:
+                H.hydro_dt(ctx, am, h, n, cfl, dt)
+            H.hydro_update(ctx, B, X, dU, 0.0, dt, k, Y if k == 0 else None)
+        X, Y = Y, X
+    return X, dt
+
+
+@pytest.mark.parametrize("case", ["small-outflow", "small-periodic", "shell", "shell-indicator"])
+def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
+    """In mixed precision the adaptive RK3 step skips the fill's copies and
+    restrictions: its step kernel reads same-level neighbours' interiors and
+    finer neighbours' restriction images, and only ghost cells inside coarser
+    leaves are prolonged into the leaf's own array.  The state after two RK3
+    steps and dt equal, bit for bit, the same sequence through the public
+    calls with the full ghost fill, and so do the device status bits; the new
+    state buffer's ghost cells held by same-level leaves are left unwritten
+    (the direct path ran)."""
+    from paper_2107_10987_gb300.amr import AMRRun
+    if case.startswith("small"):
+        lev, ijk, U, o, h = small()
+        bc = H.HYDRO_BC_PERIODIC if case.endswith("periodic") else H.HYDRO_BC_OUTFLOW
+    else:
+        lev, ijk, _ = W.amr_shell_mesh()
+        U = W.amr_shell_state(lev, ijk, GAMMA)
+        bc = H.HYDRO_BC_OUTFLOW
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
+    if case.endswith("indicator"):
+        from oracle import gate
+        theta = np.random.default_rng(31).normal(0, 0.3, gate.NPARAM).astype(np.float32)
+        c0 = float(gate.forward_infer(gate.bf16_round(theta), np.zeros((1, 54)))[0])
+        H.hydro_set_indicator(ctx, torch.tensor(theta, device="cuda"), c0 + 1e-6)  # uniform blocks smooth
+    run = AMRRun(ctx, U, lev, ijk, bc)
+    run.step()
+    torch.cuda.synchronize()
+    # the first step's state buffer started at zero: same-level ghosts stay so
+    Ug = run.U
+    lo = Ug[:, 0, 0:3, 3:-3, 3:-3]  # the -z ghost layers over the leaf's face
+    assert (lo == 0).any()
+    run.step()
+    torch.cuda.synchronize()
+    st_direct = H.hydro_status(ctx)
+    want, dt = _manual_rk3(H, ctx, run.mesh, torch.as_tensor(U, device="cuda"), run.origin, run.h, 2)
+    torch.cuda.synchronize()
+    # seeded indicator parameters may mark cells at the shell smooth, where
+    # the unlimited formula can leave a non-physical state: both paths flag it
+    assert H.hydro_status(ctx) == st_direct
+    if not case.endswith("indicator"):
+        assert st_direct == 0
+    a = run.U[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64)
+    b = want[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64)
+    assert torch.equal(a, b)
+    assert torch.equal(run.dt.view(torch.int64), dt.view(torch.int64))
+    # graph replay of the direct path gives the same state
+    grun = AMRRun(ctx, U, lev, ijk, bc)
+    grun.step(use_graph=True)
+    grun.step(use_graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(grun.U[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64), a)
+    grun.close()
+    run.close()
