@@ -311,6 +311,12 @@ typedef struct {
   const int* leaf_level;
   const int* leaf_ijk;
   int bc;               /* HYDRO_BC_OUTFLOW or HYDRO_BC_PERIODIC */
+  /* Optional (NULL: index order): a permutation of 0 .. n_sub-1, the order
+   * in which the adaptive-mesh kernels take the leaves.  Results do not
+   * depend on it; an order that keeps neighbours close (a space-filling
+   * curve) keeps their reads of each other in L2.  An entry outside
+   * 0 .. n_sub-1 is skipped and sets HYDRO_ST_MESH. */
+  const int* order;
 } hydro_amr_t;
 
 /* Ghost fill of the leaves of an adaptive mesh (the ghost exchange of Sec.

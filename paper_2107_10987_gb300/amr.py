@@ -18,7 +18,7 @@ from . import hydro as H
 
 class AMRDesc(C.Structure):
     _fields_ = [("lmin", C.c_int), ("lmax", C.c_int), ("table", C.c_void_p), ("leaf_level", C.c_void_p),
-                ("leaf_ijk", C.c_void_p), ("bc", C.c_int)]
+                ("leaf_ijk", C.c_void_p), ("bc", C.c_int), ("order", C.c_void_p)]
 
 
 def build_tables(level: np.ndarray, ijk: np.ndarray):
@@ -39,10 +39,27 @@ def build_tables(level: np.ndarray, ijk: np.ndarray):
     return lmin, lmax, flat
 
 
-class AMRMesh:
-    """Device copy of the tables and leaf coordinates of a mesh."""
+def morton_order(level: np.ndarray, ijk: np.ndarray) -> np.ndarray:
+    """The leaves along the Z-order (Morton) curve of their first cells at the
+    finest level: a permutation of 0 .. n-1 that keeps spatial neighbours
+    close, for the kernels' processing order (int32)."""
+    level = np.asarray(level, dtype=np.int64)
+    ijk = np.asarray(ijk, dtype=np.int64)
+    lmax = int(level.max())
+    p = ijk << (lmax - level)[:, None]
+    key = np.zeros(len(level), dtype=np.int64)
+    for b in range(lmax + 1):
+        for d in range(3):
+            key |= ((p[:, d] >> b) & 1) << (3 * b + d)
+    return np.argsort(key, kind="stable").astype(np.int32)
 
-    def __init__(self, level, ijk, bc: int = H.HYDRO_BC_OUTFLOW, device="cuda"):
+
+class AMRMesh:
+    """Device copy of the tables and leaf coordinates of a mesh, and the order
+    in which the kernels take the leaves (order="morton": along the Z-order
+    curve, None: index order; results are the same either way)."""
+
+    def __init__(self, level, ijk, bc: int = H.HYDRO_BC_OUTFLOW, device="cuda", order="morton"):
         self.level = np.asarray(level, dtype=np.int32)
         self.ijk = np.ascontiguousarray(ijk, dtype=np.int32)
         self.lmin, self.lmax, flat = build_tables(self.level, self.ijk)
@@ -50,18 +67,22 @@ class AMRMesh:
         self.leaf_level = torch.tensor(self.level, device=device)
         self.leaf_ijk = torch.tensor(self.ijk.reshape(-1), device=device)
         self.bc = bc
+        self.order = (torch.tensor(morton_order(self.level, self.ijk), device=device) if order == "morton"
+                      else None)
         self.desc = AMRDesc(self.lmin, self.lmax, self.table.data_ptr(), self.leaf_level.data_ptr(),
-                            self.leaf_ijk.data_ptr(), bc)
+                            self.leaf_ijk.data_ptr(), bc,
+                            self.order.data_ptr() if self.order is not None else None)
 
 
 class AMRRun:
     """RK3 time stepping of a batch of AMR leaves through the C ABI: two state
     buffers (ping-pong), the work buffers, and optionally a captured graph."""
 
-    def __init__(self, ctx, U, level, ijk, bc: int = H.HYDRO_BC_OUTFLOW, cfl: float = 0.4, device="cuda"):
+    def __init__(self, ctx, U, level, ijk, bc: int = H.HYDRO_BC_OUTFLOW, cfl: float = 0.4, device="cuda",
+                 order="morton"):
         from . import workloads as W
         self.ctx = ctx
-        self.mesh = AMRMesh(level, ijk, bc, device)
+        self.mesh = AMRMesh(level, ijk, bc, device, order)
         N = getattr(ctx, "N", 8)  # the leaves' edge (8 or 16)
         o, h = W.amr_geometry(level, ijk, N)
         n = len(level)

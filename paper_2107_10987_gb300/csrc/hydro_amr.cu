@@ -56,7 +56,9 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_kernel(AMRArgs A) {
   __shared__ int nb[27];   // level l:   relative position (-1..1)^3
   __shared__ int nbf[64];  // level l+1: relative position (-1..2)^3 from 2p
   const int tid = threadIdx.x;
-  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
+  for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
+    const int s = leaf_at(A, u);
+    if (s < 0) continue;
     const int l = A.leaf_level[s];
     const int pi[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
     const int n = 1 << l, ncell = NN << l;
@@ -233,7 +235,9 @@ template <int NN, bool kDirect>
 __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A) {
   constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
   __shared__ int coarser;  // some neighbour position of the leaf lies inside a coarser leaf
-  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
+  for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
+    const int s = leaf_at(A, u);
+    if (s < 0) continue;
     const int l = A.leaf_level[s];
     if (l <= A.lmin) continue;  // no coarser leaves
     // Every ghost cell of the leaf lies, after the boundary map, in one of
@@ -300,13 +304,30 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
 #pragma unroll 1
       for (int k = 0; k < F; ++k) {
         const double c = Cp[(size_t)k * LS3];
-        double t[3];
+        double qp[3], qm[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const double dp = rsub(nbp[2 * d + 1][(size_t)k * nbs[2 * d + 1]], c);
-          const double dm = rsub(c, nbp[2 * d][(size_t)k * nbs[2 * d]]);
-          t[d] = quarter64(minmod64(dp, dm));
+          qp[d] = nbp[2 * d + 1][(size_t)k * nbs[2 * d + 1]];
+          qm[d] = nbp[2 * d][(size_t)k * nbs[2 * d]];
         }
+        // A coarse cell whose six neighbours have its bits (finite, not -0:
+        // a uniform region) has the slopes c - c = +0, and every child is
+        // ((c -+ 0) -+ 0) -+ 0 = c exactly: stored without the FP64 work.
+        const long long cb = __double_as_longlong(c);
+        bool flat = ((cb >> 52) & 0x7ff) != 0x7ff && cb != (long long)0x8000000000000000ULL;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          flat = flat && __double_as_longlong(qp[d]) == cb && __double_as_longlong(qm[d]) == cb;
+        if (flat) {
+#pragma unroll
+          for (int dch = 0; dch < 8; ++dch)
+            if (mask & (1 << dch))
+              dst0[(size_t)k * LS3 + ((dch >> 2) * LS + ((dch >> 1) & 1)) * LS + (dch & 1)] = c;
+          continue;
+        }
+        double t[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) t[d] = quarter64(minmod64(rsub(qp[d], c), rsub(c, qm[d])));
         double vx[2];
         if (need_x & 1) vx[0] = radd(c, -t[0]);
         if (need_x & 2) vx[1] = radd(c, t[0]);
@@ -389,7 +410,9 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
   constexpr int LN3 = NN * NN * NN, LM = NN - 1, H2 = NN / 2;
   __shared__ int finer;
   __shared__ int fine[6][4];
-  for (int s = blockIdx.x; s < A.n_sub; s += gridDim.x) {
+  for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
+    const int s = leaf_at(A, u);
+    if (s < 0) continue;
     const int l = A.leaf_level[s];
     const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
     const int n = 1 << l;
@@ -514,6 +537,7 @@ hyd::AMRArgs hydro_amr_args(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_
   A.n_sub = B->n_sub;
   A.status = c->status;
   A.image = c->amr_img;
+  A.order = M->order;
   return A;
 }
 

@@ -21,7 +21,18 @@ struct AMRArgs {
   // [n_sub][F][(NN/2)^3]: each leaf's restriction image (the means of its
   // 2^3 cell blocks, written by hydro_amr_restrict_kernel), or null
   double* image;
+  const int* order;  // the order in which kernels take the leaves, or null
 };
+
+// The leaf that work unit u (0 <= u < n_sub) takes, or -1 (with status bit
+// 4) for an order entry outside the leaves.
+__device__ __forceinline__ int leaf_at(const AMRArgs& A, int u) {
+  if (!A.order) return u;
+  const int s = __ldg(A.order + u);
+  if ((unsigned)s < (unsigned)A.n_sub) return s;
+  if (threadIdx.x == 0) atomicOr(A.status, 4u);
+  return -1;
+}
 
 __device__ __forceinline__ long level_offset(int l, int lmin) {
   // sum_{m = lmin}^{l-1} 8^m

@@ -27,8 +27,9 @@ struct AmrStepIo {
     LevelRef L, Lf;   // the tables of the leaf's level and the next finer one
     int bx, by, bz;   // the global cell (at that level) of its first interior cell
   };
-  __device__ __forceinline__ Sub begin(int u) const {
-    const T t(u);
+  // s: the leaf (one tile per 8^3 leaf)
+  __device__ __forceinline__ Sub begin(int s) const {
+    const T t(s);
     const int l = M.leaf_level[t.s];
     return Sub{t, level_ref(M, l), level_ref(M, l + 1), M.leaf_ijk[3 * t.s] * N, M.leaf_ijk[3 * t.s + 1] * N,
                M.leaf_ijk[3 * t.s + 2] * N};
@@ -85,7 +86,10 @@ __global__ void __launch_bounds__(kThreadsMx, 2) hydro_step_mixed_amr_kernel(Ste
   double* __restrict__ D = A.scratch + (size_t)blockIdx.x * kScratchPerSub;
   const RowMap R = row_map(threadIdx.x);
   const AmrStepIo io{A, M};
-  for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) mixed_subgrid<kGate>(A, io, u, R, Qf, red, D);
+  for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
+    const int s = leaf_at(M, u);  // the same for the whole CTA
+    if (s >= 0) mixed_subgrid<kGate>(A, io, s, R, Qf, red, D);
+  }
 }
 
 cudaError_t prepare_step_mixed_amr() {

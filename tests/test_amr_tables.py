@@ -58,3 +58,24 @@ def test_tables_of_the_shell_mesh():
     counts = _check(lev, ijk)
     assert counts["leaf"] == len(lev)
     assert counts["refined"] > 0 and counts["coarse"] > 0
+
+
+def test_morton_order_is_the_z_curve():
+    """The processing order is a permutation; on a uniform level it is the
+    bit interleave x0 y0 z0 x1 y1 z1 ... of the positions, and with mixed
+    levels a coarse leaf sits where its first finest-level cell does."""
+    from paper_2107_10987_gb300.amr import morton_order
+    lev = np.full(64, 2, dtype=np.int32)
+    ijk = np.array([(i, j, k) for k in range(4) for j in range(4) for i in range(4)], dtype=np.int32)
+    rng = np.random.default_rng(5)
+    perm = rng.permutation(64)
+    o = morton_order(lev[perm], ijk[perm])
+    assert sorted(o.tolist()) == list(range(64))
+    def z(p):
+        return sum(((int(p[d]) >> b) & 1) << (3 * b + d) for b in range(2) for d in range(3))
+    keys = [z(ijk[perm][s]) for s in o]
+    assert keys == list(range(64))
+    # one level-1 leaf among level-2 leaves: between the leaves before and after its corner
+    lev2 = np.array([1, 2, 2], dtype=np.int32)
+    ijk2 = np.array([(1, 0, 0), (0, 0, 0), (3, 0, 0)], dtype=np.int32)
+    assert morton_order(lev2, ijk2).tolist() == [1, 0, 2]

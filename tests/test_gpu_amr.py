@@ -30,12 +30,23 @@ def small():
     return lev, ijk, U, o, h
 
 
-def test_amr_ghost_fill_bitwise(H, oracle_mod):
+@pytest.mark.parametrize("data", ["perturbed", "uniform-background"])
+def test_amr_ghost_fill_bitwise(H, oracle_mod, data):
+    """Both passes against the oracle's octree fill, bit for bit: on
+    perturbed data, and on the blob at rest outside its compact support,
+    where coarse cells with bitwise-equal neighbours are prolonged without
+    arithmetic (their slopes are exactly zero) except where the value is -0
+    (set in one momentum field: -0 + +0 = +0 decides some children)."""
     from oracle import amr
     from paper_2107_10987_gb300.amr import AMRMesh
     lev, ijk, U, o, h = small()
-    rng = np.random.default_rng(2)
-    U[:, :, 3:-3, 3:-3, 3:-3] *= rng.uniform(0.9, 1.1, U[:, :, 3:-3, 3:-3, 3:-3].shape)  # non-smooth data
+    if data == "perturbed":
+        rng = np.random.default_rng(2)
+        U[:, :, 3:-3, 3:-3, 3:-3] *= rng.uniform(0.9, 1.1, U[:, :, 3:-3, 3:-3, 3:-3].shape)  # non-smooth data
+    else:
+        sx = U[:, 1]
+        sx[sx == 0.0] = -0.0
+        assert np.signbit(sx).any()
     want = amr.fill_ghosts(amr.Octree(lev, ijk), U)
     ctx = H.Context(GAMMA, 0.0)
     mesh = AMRMesh(lev, ijk)
@@ -282,4 +293,45 @@ def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
     torch.cuda.synchronize()
     assert torch.equal(grun.U[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64), a)
     grun.close()
+    run.close()
+
+
+def test_leaf_order_changes_nothing(H, oracle_mod):
+    """The order in which the kernels take the leaves (hydro_amr_t.order)
+    changes no bit: the full ghost fill, flux correction and RK3 steps in
+    both precisions along the Morton curve equal those in index order; an
+    order entry outside the leaves is skipped and flagged (HYDRO_ST_MESH)."""
+    from paper_2107_10987_gb300.amr import AMRMesh, AMRRun
+    lev, ijk, _ = W.amr_shell_mesh()
+    U = W.amr_shell_state(lev, ijk, GAMMA)
+    for prec in (H.HYDRO_PREC_MIXED, H.HYDRO_PREC_FP64):
+        ctx = H.Context(GAMMA, 0.0)
+        H.hydro_set_mode(ctx, prec)
+        runs = [AMRRun(ctx, U, lev, ijk, order=o) for o in ("morton", None)]
+        assert runs[0].mesh.order is not None and runs[1].mesh.order is None
+        for r in runs:
+            for _ in range(2 if prec == H.HYDRO_PREC_MIXED else 1):
+                r.step()
+        torch.cuda.synchronize()
+        assert H.hydro_status(ctx) == 0
+        a, b = (r.U[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64) for r in runs)
+        assert torch.equal(a, b)
+        # the public two-pass fill in either order
+        fills = []
+        for r in runs:
+            Ut = torch.as_tensor(U, device="cuda").clone()
+            H.hydro_fill_ghosts_amr(ctx, H.make_batch(Ut, r.origin, r.h), r.mesh)
+            fills.append(Ut)
+        torch.cuda.synchronize()
+        assert torch.equal(fills[0].view(torch.int64), fills[1].view(torch.int64))
+        for r in runs:
+            r.close()
+    # an entry outside 0 .. n_sub-1: that unit is skipped, the status says so
+    mesh = AMRMesh(lev, ijk)
+    mesh.order[7] = len(lev)
+    Ut = torch.as_tensor(U, device="cuda").clone()
+    run = AMRRun(ctx, U, lev, ijk)
+    H.hydro_fill_ghosts_amr(ctx, H.make_batch(Ut, run.origin, run.h), mesh)
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) & 4
     run.close()
