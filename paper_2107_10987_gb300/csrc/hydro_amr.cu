@@ -233,8 +233,14 @@ __device__ __forceinline__ void prolong_cell(const double* C, const double* cons
 // live (coarse_stencil), so that the first pass need not run.
 template <int NN, bool kDirect>
 __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A) {
-  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, LM = NN - 1, LSH = NN == 8 ? 3 : 4;
+  constexpr int LS = NN + 2 * G, LS3 = LS * LS * LS, LM = NN - 1;
+  // the coarse block covering the leaf's padded region: NN/2 + 4 cells an axis
+  constexpr int LB = NN / 2 + 4;
   __shared__ int coarser;  // some neighbour position of the leaf lies inside a coarser leaf
+  // the coarse cells of the block that have children to prolong (block index,
+  // coarse leaf), gathered first so that each warp's lanes all have work
+  __shared__ int nwork;
+  __shared__ int2 work[LB * LB * LB];
   for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
     const int s = leaf_at(A, u);
     if (s < 0) continue;
@@ -243,8 +249,11 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
     // Every ghost cell of the leaf lies, after the boundary map, in one of
     // the 27 positions around it at its level; a leaf none of whose positions
     // is inside a coarser leaf (most of them) has nothing to prolong.
-    __syncthreads();  // the previous leaf's flag is no longer read
-    if (threadIdx.x == 0) coarser = 0;
+    __syncthreads();  // the previous leaf's flag and work list are no longer read
+    if (threadIdx.x == 0) {
+      coarser = 0;
+      nwork = 0;
+    }
     __syncthreads();
     if (threadIdx.x < 27) {
       const int n = 1 << l, t = threadIdx.x;
@@ -261,10 +270,10 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
     const int ncell = NN << l, nc = ncell >> 1;
     const LevelRef Lc = level_ref(A, l - 1), Lcf = level_ref(A, l);  // the coarse level and this one
     double* dstb = A.U + (size_t)s * F * LS3;
-    // the coarse block covering the leaf's padded region: NN/2 + 4 cells an axis
-    constexpr int LB = NN / 2 + 4;
-    for (int i = threadIdx.x; i < LB * LB * LB; i += blockDim.x) {
-      int C[3], Cw[3];
+    // coarse cell i of the block: its global cell C (Cw after the boundary
+    // map) and the mask of its children that are ghost cells of this leaf
+    // (padded range, not interior); 0 outside the domain (outflow)
+    auto coarse_cell = [&](int i, int C[3], int Cw[3]) {
       const int ii[3] = {i % LB, (i / LB) % LB, i / (LB * LB)};
       bool out = false;
 #pragma unroll
@@ -276,8 +285,6 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
           else out = true;
         }
       }
-      if (out) continue;
-      // children of C that are ghost cells of this leaf (padded range, not interior)
       int mask = 0;
 #pragma unroll
       for (int dch = 0; dch < 8; ++dch) {
@@ -286,10 +293,23 @@ __global__ void __launch_bounds__(256) hydro_ghost_amr_prolong_kernel(AMRArgs A)
         const bool interior = (unsigned)f[0] < (unsigned)NN && (unsigned)f[1] < (unsigned)NN && (unsigned)f[2] < (unsigned)NN;
         if (in && !interior) mask |= 1 << dch;
       }
-      if (!mask) continue;
+      return out ? 0 : mask;
+    };
+    for (int i = threadIdx.x; i < LB * LB * LB; i += blockDim.x) {
+      int C[3], Cw[3];
+      if (!coarse_cell(i, C, Cw)) continue;
       const int tc = lookup_at<NN>(A, Lc, Cw[0], Cw[1], Cw[2]);
       if (tc == -2) atomicOr(A.status, 4u);  // two levels coarser: not 2:1 balanced
-      if (tc < 0) continue;                  // refined at level l-1: pass 1 filled these
+      if (tc < 0) continue;                  // refined at level l-1: held at this level or finer
+      work[atomicAdd(&nwork, 1)] = make_int2(i, tc);
+    }
+    __syncthreads();
+    const int nw = nwork;
+    for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+      const int2 wk = work[j];
+      const int tc = wk.y;
+      int C[3], Cw[3];
+      const int mask = coarse_cell(wk.x, C, Cw);
       const double* Cp =
           A.U + (size_t)tc * F * LS3 + (((Cw[2] & LM) + G) * LS + ((Cw[1] & LM) + G)) * LS + ((Cw[0] & LM) + G);
       const double* nbp[6];
@@ -397,128 +417,276 @@ __global__ void __launch_bounds__(256) hydro_amr_restrict_kernel(const double* _
   }
 }
 
-// One thread per interior cell of a leaf; the cell's faces on the leaf
-// boundary that border finer leaves are corrected in the order x-, x+, y-, ...
-// The leaf's six face neighbours are looked up once (bit 2a + side of
-// `finer`: refined at the leaf's level), and a leaf with none, most of a
-// mesh, is left at once; for the others the four finer leaves across each
-// such face (fine[2a + side][2 qc + qb], qb and qc the halves of the face
-// along its transverse axes b < c) are looked up once too.
+// Coarse-fine flux correction of a leaf, in parts shared by the separate
+// kernel and the update of the adaptive RK3 sequence.
+//
+// leaf_finer: the leaf's six face neighbours looked up once (bit 2a + side
+// of the result: refined at the leaf's level) and, for such faces, the four
+// finer leaves across each (fine[2a + side][2 qc + qb], qb and qc the halves
+// of the face along its transverse axes b < c).  Every thread of the block
+// calls it (it synchronises) and gets the same result.
+template <int NN>
+__device__ __forceinline__ int leaf_finer(const AMRArgs& A, int l, const int ijk[3], int* finer, int (*fine)[4]) {
+  const int n = 1 << l;
+  __syncthreads();  // the previous leaf's tables are no longer read
+  if (threadIdx.x == 0) *finer = 0;
+  __syncthreads();
+  if (threadIdx.x < 6 && l < A.lmax) {
+    const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
+    int nb[3] = {ijk[0], ijk[1], ijk[2]};
+    nb[a] += side ? 1 : -1;
+    bool in = true;
+    if (nb[a] < 0 || nb[a] >= n) {
+      if (A.bc != 0) in = false;
+      else nb[a] = (nb[a] + n) % n;
+    }
+    if (in && lookup<NN>(A, l, nb[0] * NN, nb[1] * NN, nb[2] * NN) == -1) atomicOr(finer, 1 << threadIdx.x);
+  }
+  __syncthreads();
+  const int fl = *finer;
+  if (!fl) return 0;
+  if (threadIdx.x < 24) {
+    const int j = threadIdx.x >> 2, a = j >> 1, side = j & 1, qb = threadIdx.x & 1, qc = (threadIdx.x >> 1) & 1;
+    const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+    int o = -3;
+    if (fl & (1 << j)) {
+      const int nf = 2 * n;
+      int pf[3];
+      pf[a] = side ? 2 * (ijk[a] + 1) : 2 * ijk[a] - 1;
+      if (pf[a] < 0 || pf[a] >= nf) pf[a] = (pf[a] + nf) % nf;  // periodic wrap
+      pf[b] = 2 * ijk[b] + qb;
+      pf[c] = 2 * ijk[c] + qc;
+      o = lookup<NN>(A, l + 1, pf[0] * NN, pf[1] * NN, pf[2] * NN);
+    }
+    fine[j][threadIdx.x & 3] = o;
+  }
+  __syncthreads();
+  return fl;
+}
+
+// Whether interior cell `cell` lies on a leaf face flagged in fl.
+template <int NN>
+__device__ __forceinline__ bool on_finer_face(int cell, int fl) {
+  const int cl[3] = {cell % NN, (cell / NN) % NN, cell / (NN * NN)};
+  bool on = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    on |= (((fl >> (2 * a)) & 1) && cl[a] == 0) || (((fl >> (2 * a + 1)) & 1) && cl[a] == NN - 1);
+  return on;
+}
+
+// The corrections of interior cell `cell` of leaf s (cell width hc), added
+// to its rates du in the order x-, x+, y-, y+, z-, z+: a face bordering finer
+// leaves takes the mean of the 4 fine sub-face fluxes instead of its own,
+// and the mean of the fine torques moved to the cell centre,
+// T(x_C) = T(x_f) + (x_f - x_C) x F_s.
+template <int NN>
+__device__ __forceinline__ void correct_cell(const AMRArgs& A, const double* faces, int s, const int ijk[3],
+                                             double hc, int fl, const int (*fine)[4], int cell, double du[F]) {
+  constexpr int LM = NN - 1, H2 = NN / 2;
+  const int cl[3] = {cell % NN, (cell / NN) % NN, cell / (NN * NN)};
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+    for (int side = 0; side < 2; ++side) {
+      if (cl[a] != (side ? NN - 1 : 0)) continue;
+      if (!(fl & (1 << (2 * a + side)))) continue;
+      const double sgn = side ? 1.0 : -1.0;
+      const int pb = cl[b], pc = cl[c];
+      double fsum[F], tsum[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < F; ++k) fsum[k] = 0.0;
+      // the fine leaf across this half of the face: the same for the four
+      // sub-faces of the cell
+      const int o = fine[2 * a + side][2 * (pc / H2) + pb / H2];
+      if (o < 0) {
+        atomicOr(A.status, 4u);
+        continue;
+      }
+      for (int dc = 0; dc < 2; ++dc)
+        for (int db = 0; db < 2; ++db) {
+          int gf[3];
+          gf[a] = side ? (ijk[a] + 1) * 2 * NN : ijk[a] * 2 * NN - 1;
+          gf[b] = 2 * (ijk[b] * NN + pb) + db;
+          gf[c] = 2 * (ijk[c] * NN + pc) + dc;
+          const int loc[3] = {gf[0] & LM, gf[1] & LM, gf[2] & LM};
+          const double* ff = faces + face_index_nn<NN>(o, 2 * a + (side ? 0 : 1), 0, loc[c], loc[b]);
+          const size_t qs = (size_t)NN * NN;  // stride between quantities
+          double r[3];
+          r[a] = rmul(0.75 * sgn, hc);
+          r[b] = rmul(db ? 0.25 : -0.25, hc);
+          r[c] = rmul(dc ? 0.25 : -0.25, hc);
+          const double Fx = ff[SX * qs], Fy = ff[SY * qs], Fz = ff[SZ * qs];
+          const double tor[3] = {rsub(rmul(r[1], Fz), rmul(r[2], Fy)), rsub(rmul(r[2], Fx), rmul(r[0], Fz)),
+                                 rsub(rmul(r[0], Fy), rmul(r[1], Fx))};
+#pragma unroll
+          for (int k = 0; k < F; ++k) fsum[k] = radd(fsum[k], ff[k * qs]);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) tsum[m] = radd(tsum[m], radd(ff[(F + m) * qs], tor[m]));
+        }
+      const double* own = faces + face_index_nn<NN>(s, 2 * a + side, 0, pc, pb);
+      const size_t qs = (size_t)NN * NN;
+      const double coef = -(sgn / hc);
+      double corr[F];
+#pragma unroll
+      for (int k = 0; k < F; ++k) corr[k] = rmul(coef, rsub(rmul(fsum[k], 0.25), own[k * qs]));
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+        corr[ZX + m] = radd(corr[ZX + m], rmul(coef, rsub(rmul(tsum[m], 0.25), own[(F + m) * qs])));
+#pragma unroll
+      for (int k = 0; k < F; ++k) du[k] = radd(du[k], corr[k]);
+    }
+  }
+}
+
+// Each leaf's finer-neighbour table, as leaf_finer leaves it in shared
+// memory: entry 0 the flags, entry 1 + 4 (2a + side) + 2 qc + qb the finer
+// leaf across that half of a flagged face (-3 for faces not flagged).  Eight
+// lanes per leaf, one per face (lanes 6 and 7 idle); the flags are the
+// group's ballot.
+template <int NN>
+__global__ void __launch_bounds__(256) hydro_amr_finer_kernel(AMRArgs A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = t >> 3, j = t & 7;
+  bool refined = false;
+  int o[4] = {-3, -3, -3, -3};
+  if (s < A.n_sub && j < 6) {
+    const int l = A.leaf_level[s], n = 1 << l;
+    const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
+    const int a = j >> 1, side = j & 1, b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+    int nb[3] = {ijk[0], ijk[1], ijk[2]};
+    nb[a] += side ? 1 : -1;
+    bool in = l < A.lmax;
+    if (nb[a] < 0 || nb[a] >= n) {
+      if (A.bc != 0) in = false;
+      else nb[a] = (nb[a] + n) % n;
+    }
+    refined = in && lookup<NN>(A, l, nb[0] * NN, nb[1] * NN, nb[2] * NN) == -1;
+    if (refined) {
+      const int nf = 2 * n;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int pf[3];
+        pf[a] = side ? 2 * (ijk[a] + 1) : 2 * ijk[a] - 1;
+        if (pf[a] < 0 || pf[a] >= nf) pf[a] = (pf[a] + nf) % nf;  // periodic wrap
+        pf[b] = 2 * ijk[b] + (q & 1);
+        pf[c] = 2 * ijk[c] + (q >> 1);
+        o[q] = lookup<NN>(A, l + 1, pf[0] * NN, pf[1] * NN, pf[2] * NN);
+      }
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, refined);
+  if (s < A.n_sub) {
+    int* e = A.finer_tab + (size_t)s * kFinerTab;
+    if (j == 0) e[0] = (int)((m >> (threadIdx.x & 24)) & 0x3fu);
+    if (j < 6)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) e[1 + 4 * j + q] = o[q];
+  }
+}
+
+// correct_cell as a call of its own, for kernels whose common path should
+// not carry its registers (the few boundary cells of leaves with finer
+// neighbours pass their rates through this local array).
+template <int NN>
+__device__ __noinline__ void correct_cell_call(const AMRArgs& A, const double* faces, int s, const int* ijk,
+                                               double hc, int fl, const int (*fine)[4], int cell, double* du) {
+  const int p[3] = {ijk[0], ijk[1], ijk[2]};
+  correct_cell<NN>(A, faces, s, p, hc, fl, fine, cell, du);
+}
+
+// One thread per interior cell of a leaf; a leaf with no finer face
+// neighbour, most of a mesh, is left at once.
 template <int NN>
 __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, const double* h, const double* faces,
                                                                  double* dUdt) {
-  constexpr int LN3 = NN * NN * NN, LM = NN - 1, H2 = NN / 2;
+  constexpr int LN3 = NN * NN * NN;
   __shared__ int finer;
   __shared__ int fine[6][4];
   for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
     const int s = leaf_at(A, u);
     if (s < 0) continue;
-    const int l = A.leaf_level[s];
     const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
-    const int n = 1 << l;
-    __syncthreads();  // the previous leaf's flags are no longer read
-    if (threadIdx.x == 0) finer = 0;
-    __syncthreads();
-    if (threadIdx.x < 6 && l < A.lmax) {
-      const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
-      int nb[3] = {ijk[0], ijk[1], ijk[2]};
-      nb[a] += side ? 1 : -1;
-      bool in = true;
-      if (nb[a] < 0 || nb[a] >= n) {
-        if (A.bc != 0) in = false;
-        else nb[a] = (nb[a] + n) % n;
-      }
-      if (in && lookup<NN>(A, l, nb[0] * NN, nb[1] * NN, nb[2] * NN) == -1) atomicOr(&finer, 1 << threadIdx.x);
-    }
-    __syncthreads();
-    const int fl = finer;
+    const int fl = leaf_finer<NN>(A, A.leaf_level[s], ijk, &finer, fine);
     if (!fl) continue;
-    if (threadIdx.x < 24) {
-      const int j = threadIdx.x >> 2, a = j >> 1, side = j & 1, qb = threadIdx.x & 1, qc = (threadIdx.x >> 1) & 1;
-      const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
-      int o = -3;
-      if (fl & (1 << j)) {
-        const int nf = 2 * n;
-        int pf[3];
-        pf[a] = side ? 2 * (ijk[a] + 1) : 2 * ijk[a] - 1;
-        if (pf[a] < 0 || pf[a] >= nf) pf[a] = (pf[a] + nf) % nf;  // periodic wrap
-        pf[b] = 2 * ijk[b] + qb;
-        pf[c] = 2 * ijk[c] + qc;
-        o = lookup<NN>(A, l + 1, pf[0] * NN, pf[1] * NN, pf[2] * NN);
-      }
-      fine[j][threadIdx.x & 3] = o;
-    }
-    __syncthreads();
     const double hc = h[s];
     for (int cell = threadIdx.x; cell < LN3; cell += blockDim.x) {
-      const int cl[3] = {cell % NN, (cell / NN) % NN, cell / (NN * NN)};
+      if (!on_finer_face<NN>(cell, fl)) continue;
       double du[F];
-      bool touched = false;
-      for (int a = 0; a < 3; ++a) {
-        const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
-        for (int side = 0; side < 2; ++side) {
-          if (cl[a] != (side ? NN - 1 : 0)) continue;
-          if (!(fl & (1 << (2 * a + side)))) continue;
-          if (!touched) {
 #pragma unroll
-            for (int k = 0; k < F; ++k) du[k] = dUdt[((size_t)s * F + k) * LN3 + cell];
-            touched = true;
-          }
-          const double sgn = side ? 1.0 : -1.0;
-          const int pb = cl[b], pc = cl[c];
-          double fsum[F], tsum[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < F; ++k) du[k] = dUdt[((size_t)s * F + k) * LN3 + cell];
+      correct_cell<NN>(A, faces, s, ijk, hc, fl, fine, cell, du);
 #pragma unroll
-          for (int k = 0; k < F; ++k) fsum[k] = 0.0;
-          bool ok = true;
-          // the fine leaf across this half of the face: the same for the
-          // four sub-faces of the cell
-          const int o = fine[2 * a + side][2 * (pc / H2) + pb / H2];
-          for (int dc = 0; dc < 2; ++dc)
-            for (int db = 0; db < 2; ++db) {
-              int gf[3];
-              gf[a] = side ? (ijk[a] + 1) * 2 * NN : ijk[a] * 2 * NN - 1;
-              gf[b] = 2 * (ijk[b] * NN + pb) + db;
-              gf[c] = 2 * (ijk[c] * NN + pc) + dc;
-              if (o < 0) {
-                ok = false;
-                continue;
-              }
-              const int loc[3] = {gf[0] & LM, gf[1] & LM, gf[2] & LM};
-              const double* ff = faces + face_index_nn<NN>(o, 2 * a + (side ? 0 : 1), 0, loc[c], loc[b]);
-              const size_t qs = (size_t)NN * NN;  // stride between quantities
-              double r[3];
-              r[a] = rmul(0.75 * sgn, hc);
-              r[b] = rmul(db ? 0.25 : -0.25, hc);
-              r[c] = rmul(dc ? 0.25 : -0.25, hc);
-              const double Fx = ff[SX * qs], Fy = ff[SY * qs], Fz = ff[SZ * qs];
-              const double tor[3] = {rsub(rmul(r[1], Fz), rmul(r[2], Fy)), rsub(rmul(r[2], Fx), rmul(r[0], Fz)),
-                                     rsub(rmul(r[0], Fy), rmul(r[1], Fx))};
+      for (int k = 0; k < F; ++k) dUdt[((size_t)s * F + k) * LN3 + cell] = du[k];
+    }
+  }
+}
+
+// The update of the adaptive RK3 sequence with direct neighbour reads (8^3
+// leaves): per leaf, in the mesh's order, the coarse-fine flux correction of
+// its boundary cells (written back to dUdt, as the separate kernel leaves
+// it), the SSP-RK3 stage update of every interior cell (rk3_cell, as
+// hydro_update) from A.U and U0 into Uout, and with kImage the new state's
+// restriction image (as hydro_amr_restrict_kernel) for the next stage's
+// fill: the same bits as the separate launches, without reading the new
+// state back.
+template <bool kMixed, bool kImage>
+__global__ void __launch_bounds__(256, 3) hydro_update_amr_kernel(AMRArgs A, const double* h, const double* faces,
+                                                               double* dUdt, const double* U0, double* Uout,
+                                                               const double* dt_dev, double alpha, double beta,
+                                                               double eta2, double inv_gamma) {
+  constexpr int NN = 8, LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, H2 = NN / 2,
+                I3 = img_cells<NN>();
+  __shared__ double img_s[kImage ? F * LN3 : 1];  // the leaf's new state, for its image
+  const double dt = *dt_dev;
+  for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
+    const int s = leaf_at(A, u);
+    if (s < 0) continue;
+    const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
+    const int* ft = A.finer_tab + (size_t)s * kFinerTab;
+    const int fl = __ldg(ft);
+    const int(*fine)[4] = reinterpret_cast<const int(*)[4]>(ft + 1);
+    const double hc = h[s];
+    const size_t ub = (size_t)s * F * LS3, db = (size_t)s * F * LN3;
+    for (int cell = threadIdx.x; cell < LN3; cell += blockDim.x) {
+      const int x = cell % NN, y = (cell / NN) % NN, z = cell / (NN * NN);
+      const size_t uc = ub + ((z + G) * LS + (y + G)) * LS + (x + G), dc = db + cell;
+      if (fl && on_finer_face<NN>(cell, fl)) {
+        // the corrected rates go back to dUdt (as the separate kernel leaves
+        // them) and are read below like every cell's
+        double Rc[F];
 #pragma unroll
-              for (int k = 0; k < F; ++k) fsum[k] = radd(fsum[k], ff[k * qs]);
+        for (int k = 0; k < F; ++k) Rc[k] = dUdt[dc + (size_t)k * LN3];
+        correct_cell_call<NN>(A, faces, s, ijk, hc, fl, fine, cell, Rc);
 #pragma unroll
-              for (int m = 0; m < 3; ++m) tsum[m] = radd(tsum[m], radd(ff[(F + m) * qs], tor[m]));
-            }
-          if (!ok) {
-            atomicOr(A.status, 4u);
-            continue;
-          }
-          const double* own = faces + face_index_nn<NN>(s, 2 * a + side, 0, pc, pb);
-          const size_t qs = (size_t)NN * NN;
-          const double coef = -(sgn / hc);
-          double corr[F];
-#pragma unroll
-          for (int k = 0; k < F; ++k) corr[k] = rmul(coef, rsub(rmul(fsum[k], 0.25), own[k * qs]));
-#pragma unroll
-          for (int m = 0; m < 3; ++m)
-            corr[ZX + m] = radd(corr[ZX + m], rmul(coef, rsub(rmul(tsum[m], 0.25), own[(F + m) * qs])));
-#pragma unroll
-          for (int k = 0; k < F; ++k) du[k] = radd(du[k], corr[k]);
-        }
+        for (int k = 0; k < F; ++k) dUdt[dc + (size_t)k * LN3] = Rc[k];
       }
-      if (touched) {
+      double Uc[F], U0c[F], R[F], un[F];
 #pragma unroll
-        for (int k = 0; k < F; ++k) dUdt[((size_t)s * F + k) * LN3 + cell] = du[k];
+      for (int k = 0; k < F; ++k) {
+        Uc[k] = A.U[uc + (size_t)k * LS3];
+        U0c[k] = U0[uc + (size_t)k * LS3];
+        R[k] = dUdt[dc + (size_t)k * LN3];
       }
+      rk3_cell<kMixed>(Uc, U0c, R, dt, alpha, beta, eta2, inv_gamma, un);
+#pragma unroll
+      for (int k = 0; k < F; ++k) Uout[uc + (size_t)k * LS3] = un[k];
+      if (kImage) {
+#pragma unroll
+        for (int k = 0; k < F; ++k) img_s[k * LN3 + cell] = un[k];
+      }
+    }
+    if (kImage) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < F * I3; e += blockDim.x) {
+        const int k = e / I3, i = e % I3;
+        const int x = i % H2, y = (i / H2) % H2, z = i / (H2 * H2);
+        const double* p = img_s + k * LN3 + ((2 * z) * NN + 2 * y) * NN + 2 * x;
+        const double a0 = p[0], a1 = p[1], a2 = p[NN], a3 = p[NN + 1];
+        const double a4 = p[NN * NN], a5 = p[NN * NN + 1], a6 = p[NN * NN + NN], a7 = p[NN * NN + NN + 1];
+        A.image[((size_t)s * F + k) * I3 + i] =
+            rmul(radd(radd(radd(a0, a1), radd(a2, a3)), radd(radd(a4, a5), radd(a6, a7))), 0.125);
+      }
+      __syncthreads();  // img_s is free for the next leaf
     }
   }
 }
@@ -538,6 +706,7 @@ hyd::AMRArgs hydro_amr_args(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_
   A.status = c->status;
   A.image = c->amr_img;
   A.order = M->order;
+  A.finer_tab = reinterpret_cast<int*>(c->amr_finer);
   return A;
 }
 
@@ -591,19 +760,63 @@ int hydro_flux_correct_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_a
 
 // The lean fill of the adaptive RK3 sequence (8^3 leaves; the step's loader
 // reads same-level and finer neighbours itself): every leaf's restriction
-// image, then the ghost cells inside coarser leaves, prolonged from coarse
-// cells whose neighbours are read where they live.  Ghost cells held by
-// same-level or finer leaves are left as they were.  The image buffer
-// (hydro_ctx_prepare_amr) must hold n_sub leaves.
-int hydro_fill_ghosts_amr_lean(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M, cudaStream_t st) {
+// image and finer-neighbour table (with restrict_first; otherwise the
+// previous stage's update wrote the images for this state), then the ghost cells inside coarser leaves, prolonged
+// from coarse cells whose neighbours are read where they live.  Ghost cells
+// held by same-level or finer leaves are left as they were.  The image
+// buffer (hydro_ctx_prepare_amr) must hold n_sub leaves.
+int hydro_fill_ghosts_amr_lean(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M, bool restrict_first,
+                               cudaStream_t st) {
   if (!c || !B || B->n_sub < 0 || !amr_ok(M) || c->N != 8) return HYDRO_EINVAL;
   if (B->n_sub == 0) return HYDRO_OK;
   if (!B->U || !c->amr_img || c->amr_img_bytes < (size_t)B->n_sub * hyd::F * hyd::img_cells<8>() * sizeof(double))
     return HYDRO_EINVAL;
+  if (!c->amr_finer || c->amr_finer_bytes < (size_t)B->n_sub * hyd::kFinerTab * sizeof(int)) return HYDRO_EINVAL;
   hyd::AMRArgs A = hydro_amr_args(c, B, M);
   const int cap = c->num_sms * 8;
   const int grid = B->n_sub < cap ? B->n_sub : cap;
-  hyd::hydro_amr_restrict_kernel<8><<<grid, 256, 0, st>>>(B->U, c->amr_img, B->n_sub);
+  if (restrict_first) {
+    hyd::hydro_amr_restrict_kernel<8><<<grid, 256, 0, st>>>(B->U, c->amr_img, B->n_sub);
+    hyd::hydro_amr_finer_kernel<8><<<(8 * B->n_sub + 255) / 256, 256, 0, st>>>(A);
+  }
   hyd::hydro_ghost_amr_prolong_kernel<8, true><<<grid, 256, 0, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
+
+// The coarse-fine flux correction and the SSP-RK3 stage update of the
+// adaptive RK3 sequence in one launch (hydro_update_amr_kernel): B->U the
+// stage's state, U0 the step's initial state, Uout the new state (B->U in
+// place after the first stage), dt on the device; with image the new
+// state's restriction images for the next stage's lean fill.
+int hydro_update_amr_lean(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M, const double* U0,
+                          double* dUdt, const double* face_flux, const double* dt_dev, int stage, double* Uout,
+                          bool image, cudaStream_t st) {
+  if (!c || !B || B->n_sub < 0 || !amr_ok(M) || c->N != 8 || stage < 0 || stage > 2) return HYDRO_EINVAL;
+  if (B->n_sub == 0) return HYDRO_OK;
+  if (!B->U || !B->h || !U0 || !dUdt || !face_flux || !dt_dev || !Uout) return HYDRO_EINVAL;
+  if (!c->amr_finer || c->amr_finer_bytes < (size_t)B->n_sub * hyd::kFinerTab * sizeof(int)) return HYDRO_EINVAL;
+  if (image && (!c->amr_img ||
+                c->amr_img_bytes < (size_t)B->n_sub * hyd::F * hyd::img_cells<8>() * sizeof(double)))
+    return HYDRO_EINVAL;
+  static const double alpha[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double beta[3] = {1.0, 0.25, 2.0 / 3.0};
+  hyd::AMRArgs A = hydro_amr_args(c, B, M);
+  const int cap = c->num_sms * 8;
+  const int grid = B->n_sub < cap ? B->n_sub : cap;
+  const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
+  const double eta2 = c->mode.de_eta2, ig = 1.0 / c->gamma;
+  const double al = alpha[stage], be = beta[stage];
+  if (mixed && image)
+    hyd::hydro_update_amr_kernel<true, true><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev, al,
+                                                                    be, eta2, ig);
+  else if (mixed)
+    hyd::hydro_update_amr_kernel<true, false><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev, al,
+                                                                     be, eta2, ig);
+  else if (image)
+    hyd::hydro_update_amr_kernel<false, true><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev, al,
+                                                                     be, eta2, ig);
+  else
+    hyd::hydro_update_amr_kernel<false, false><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev,
+                                                                      al, be, eta2, ig);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }

@@ -22,7 +22,13 @@ struct AMRArgs {
   // 2^3 cell blocks, written by hydro_amr_restrict_kernel), or null
   double* image;
   const int* order;  // the order in which kernels take the leaves, or null
+  // [n_sub][kFinerTab]: per leaf, the faces that border finer leaves (bits
+  // 2a + side) and the four finer leaves across each (hydro_amr_finer_kernel),
+  // or null
+  int* finer_tab;
 };
+
+constexpr int kFinerTab = 25;
 
 // The leaf that work unit u (0 <= u < n_sub) takes, or -1 (with status bit
 // 4) for an order entry outside the leaves.

@@ -212,9 +212,12 @@ bool hydro_amr_direct_ok(const hydro_ctx* c) {
 int hydro_ctx_prepare_amr(hydro_ctx* c, int n_sub) {
   int rc = hydro_ctx_prepare(c, n_sub);
   if (rc) return rc;
-  return ensure_buf(&c->amr_img, &c->amr_img_bytes,
-                    (size_t)n_sub * hyd::F * (hyd::N / 2) * (hyd::N / 2) * (hyd::N / 2) * sizeof(double),
-                    "cudaMalloc(restriction images)");
+  rc = ensure_buf(&c->amr_img, &c->amr_img_bytes,
+                  (size_t)n_sub * hyd::F * (hyd::N / 2) * (hyd::N / 2) * (hyd::N / 2) * sizeof(double),
+                  "cudaMalloc(restriction images)");
+  if (rc) return rc;
+  return ensure_buf(&c->amr_finer, &c->amr_finer_bytes, ((size_t)n_sub * hyd::kFinerTab * sizeof(int) + 7) & ~7ul,
+                    "cudaMalloc(finer-neighbour tables)");
 }
 
 hyd::AMRArgs hydro_amr_args(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M);
@@ -542,6 +545,7 @@ void hydro_destroy(hydro_ctx_t* c) {
   if (c->prims) cudaFree(c->prims);
   if (c->sync) cudaFree(c->sync);
   if (c->amr_img) cudaFree(c->amr_img);
+  if (c->amr_finer) cudaFree(c->amr_finer);
   delete c;
 }
 

@@ -33,6 +33,8 @@ struct hydro_ctx {
   size_t sync_bytes;
   double* amr_img;       // adaptive RK3 step: each leaf's restriction image [n_sub][F][(N/2)^3]
   size_t amr_img_bytes;
+  double* amr_finer;     // adaptive RK3 step: each leaf's finer-neighbour table (int words)
+  size_t amr_finer_bytes;
 };
 
 // Allocate the context's status word and the step scratch for a batch of
@@ -47,10 +49,15 @@ int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub);
 // The adaptive RK3 sequence with direct neighbour reads: whether this
 // context's step takes it (mixed precision, 8^3 leaves, row sweep, no
 // contact steepening or spin feedback), its image buffer for n_sub leaves
-// (allocated before a stream capture), its lean ghost fill and its step.
+// (allocated before a stream capture), its lean ghost fill, its step, and
+// its flux correction with the stage update.
 bool hydro_amr_direct_ok(const hydro_ctx* c);
 int hydro_ctx_prepare_amr(hydro_ctx* c, int n_sub);
-int hydro_fill_ghosts_amr_lean(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_t* M, cudaStream_t st);
+int hydro_fill_ghosts_amr_lean(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_t* M, bool restrict_first,
+                               cudaStream_t st);
+int hydro_update_amr_lean(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_t* M, const double* U0,
+                          double* dUdt, const double* face_flux, const double* dt_dev, int stage, double* Uout,
+                          bool image, cudaStream_t st);
 int hydro_step_amr_direct(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_t* M, double* dUdt, double* amax,
                           double* face_flux, cudaStream_t st);
 int hydro_rk3_fused_enqueue(hydro_ctx* c, const hydro_rk3_desc_t* d, int parity, cudaStream_t st);

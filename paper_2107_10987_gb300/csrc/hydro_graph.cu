@@ -41,10 +41,16 @@ static int rk3_enqueue(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, 
   for (int k = 0; k < 3; ++k) {
     const hydro_batch_t* B = (k == 0) ? &X : &Y;
     if (d->amr && hydro_amr_direct_ok(ctx)) {
+      // the first stage restricts its state; the updates of the first two
+      // write the next state's restriction images
       if ((rc = hydro_ctx_prepare_amr(ctx, B->n_sub))) return rc;
-      if ((rc = hydro_fill_ghosts_amr_lean(ctx, B, d->amr, st))) return rc;
+      if ((rc = hydro_fill_ghosts_amr_lean(ctx, B, d->amr, k == 0, st))) return rc;
       if ((rc = hydro_step_amr_direct(ctx, B, d->amr, d->dUdt, d->amax, d->face_flux, st))) return rc;
-      if ((rc = hydro_flux_correct_amr(ctx, B, d->amr, d->face_flux, d->dUdt, st))) return rc;
+      if (k == 0 && (rc = hydro_dt(ctx, d->amax, d->a.h, d->a.n_sub, d->cfl, d->dt, st))) return rc;
+      if ((rc = hydro_update_amr_lean(ctx, B, d->amr, X.U, d->dUdt, d->face_flux, d->dt, k,
+                                      k == 0 ? Y.U : B->U, k < 2, st)))
+        return rc;
+      continue;
     } else if (d->amr) {
       if ((rc = hydro_fill_ghosts_amr(ctx, B, d->amr, st))) return rc;
       if ((rc = hydro_step(ctx, B, 0.0, d->dUdt, d->amax, d->face_flux, st))) return rc;
