@@ -803,7 +803,7 @@ def gpu_arm(args):
             sres = {}
         if args.amr:
             line["amr_batched"] = {"workload": "adaptive octree, ~4,096 leaves of 8^3 at levels 3-6 refined around a "
-                                               "blast shell of radius 0.3, leaf order shuffled (seed 1234), outflow",
+                                               "blast shell of radius 0.3, leaf order shuffled (seed 1234; the kernels take the leaves along their Morton curve), outflow",
                                    "mixed": amr_measure(args, H, dev, flush, H.HYDRO_PREC_MIXED, args.steps),
                                    "fp64": amr_measure(args, H, dev, flush, H.HYDRO_PREC_FP64, max(2, args.steps // 5))}
             if indicator is not None:

@@ -502,7 +502,9 @@ __device__ __forceinline__ void correct_cell(const AMRArgs& A, const double* fac
         atomicOr(A.status, 4u);
         continue;
       }
+#pragma unroll
       for (int dc = 0; dc < 2; ++dc)
+#pragma unroll
         for (int db = 0; db < 2; ++db) {
           int gf[3];
           gf[a] = side ? (ijk[a] + 1) * 2 * NN : ijk[a] * 2 * NN - 1;
@@ -584,29 +586,30 @@ __global__ void __launch_bounds__(256) hydro_amr_finer_kernel(AMRArgs A) {
   }
 }
 
-// correct_cell as a call of its own, for kernels whose common path should
-// not carry its registers (the few boundary cells of leaves with finer
-// neighbours pass their rates through this local array).
-template <int NN>
-__device__ __noinline__ void correct_cell_call(const AMRArgs& A, const double* faces, int s, const int* ijk,
-                                               double hc, int fl, const int (*fine)[4], int cell, double* du) {
-  const int p[3] = {ijk[0], ijk[1], ijk[2]};
-  correct_cell<NN>(A, faces, s, p, hc, fl, fine, cell, du);
-}
-
 // One thread per interior cell of a leaf; a leaf with no finer face
-// neighbour, most of a mesh, is left at once.
-template <int NN>
+// neighbour, most of a mesh, is left at once.  kTable: the leaf's flags and
+// finer leaves come from A.finer_tab (hydro_amr_finer_kernel) instead of
+// being looked up here.
+template <int NN, bool kTable>
 __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, const double* h, const double* faces,
                                                                  double* dUdt) {
   constexpr int LN3 = NN * NN * NN;
   __shared__ int finer;
-  __shared__ int fine[6][4];
+  __shared__ int fine_s[6][4];
   for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
     const int s = leaf_at(A, u);
     if (s < 0) continue;
     const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
-    const int fl = leaf_finer<NN>(A, A.leaf_level[s], ijk, &finer, fine);
+    int fl;
+    const int(*fine)[4];
+    if (kTable) {
+      const int* ft = A.finer_tab + (size_t)s * kFinerTab;
+      fl = __ldg(ft);
+      fine = reinterpret_cast<const int(*)[4]>(ft + 1);
+    } else {
+      fl = leaf_finer<NN>(A, A.leaf_level[s], ijk, &finer, fine_s);
+      fine = fine_s;
+    }
     if (!fl) continue;
     const double hc = h[s];
     for (int cell = threadIdx.x; cell < LN3; cell += blockDim.x) {
@@ -622,18 +625,15 @@ __global__ void __launch_bounds__(256) hydro_flux_correct_kernel(AMRArgs A, cons
 }
 
 // The update of the adaptive RK3 sequence with direct neighbour reads (8^3
-// leaves): per leaf, in the mesh's order, the coarse-fine flux correction of
-// its boundary cells (written back to dUdt, as the separate kernel leaves
-// it), the SSP-RK3 stage update of every interior cell (rk3_cell, as
-// hydro_update) from A.U and U0 into Uout, and with kImage the new state's
-// restriction image (as hydro_amr_restrict_kernel) for the next stage's
-// fill: the same bits as the separate launches, without reading the new
-// state back.
+// leaves): per leaf, in the mesh's order, the SSP-RK3 stage update of every
+// interior cell (rk3_cell, as hydro_update) from A.U and U0 into Uout, and
+// with kImage the new state's restriction image (as
+// hydro_amr_restrict_kernel) for the next stage's fill: the same bits as
+// the separate launches, without reading the new state back.
 template <bool kMixed, bool kImage>
-__global__ void __launch_bounds__(256, 3) hydro_update_amr_kernel(AMRArgs A, const double* h, const double* faces,
-                                                               double* dUdt, const double* U0, double* Uout,
-                                                               const double* dt_dev, double alpha, double beta,
-                                                               double eta2, double inv_gamma) {
+__global__ void __launch_bounds__(256) hydro_update_amr_kernel(AMRArgs A, const double* dUdt, const double* U0,
+                                                               double* Uout, const double* dt_dev, double alpha,
+                                                               double beta, double eta2, double inv_gamma) {
   constexpr int NN = 8, LS = NN + 2 * G, LS3 = LS * LS * LS, LN3 = NN * NN * NN, H2 = NN / 2,
                 I3 = img_cells<NN>();
   __shared__ double img_s[kImage ? F * LN3 : 1];  // the leaf's new state, for its image
@@ -641,25 +641,10 @@ __global__ void __launch_bounds__(256, 3) hydro_update_amr_kernel(AMRArgs A, con
   for (int u = blockIdx.x; u < A.n_sub; u += gridDim.x) {
     const int s = leaf_at(A, u);
     if (s < 0) continue;
-    const int ijk[3] = {A.leaf_ijk[3 * s], A.leaf_ijk[3 * s + 1], A.leaf_ijk[3 * s + 2]};
-    const int* ft = A.finer_tab + (size_t)s * kFinerTab;
-    const int fl = __ldg(ft);
-    const int(*fine)[4] = reinterpret_cast<const int(*)[4]>(ft + 1);
-    const double hc = h[s];
     const size_t ub = (size_t)s * F * LS3, db = (size_t)s * F * LN3;
     for (int cell = threadIdx.x; cell < LN3; cell += blockDim.x) {
       const int x = cell % NN, y = (cell / NN) % NN, z = cell / (NN * NN);
       const size_t uc = ub + ((z + G) * LS + (y + G)) * LS + (x + G), dc = db + cell;
-      if (fl && on_finer_face<NN>(cell, fl)) {
-        // the corrected rates go back to dUdt (as the separate kernel leaves
-        // them) and are read below like every cell's
-        double Rc[F];
-#pragma unroll
-        for (int k = 0; k < F; ++k) Rc[k] = dUdt[dc + (size_t)k * LN3];
-        correct_cell_call<NN>(A, faces, s, ijk, hc, fl, fine, cell, Rc);
-#pragma unroll
-        for (int k = 0; k < F; ++k) dUdt[dc + (size_t)k * LN3] = Rc[k];
-      }
       double Uc[F], U0c[F], R[F], un[F];
 #pragma unroll
       for (int k = 0; k < F; ++k) {
@@ -750,9 +735,9 @@ int hydro_flux_correct_amr(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_a
   const int cap = c->num_sms * 8;
   const int grid = B->n_sub < cap ? B->n_sub : cap;
   if (c->N == 16)
-    hyd::hydro_flux_correct_kernel<16><<<grid, 256, 0, (cudaStream_t)stream>>>(A, B->h, face_flux, dUdt);
+    hyd::hydro_flux_correct_kernel<16, false><<<grid, 256, 0, (cudaStream_t)stream>>>(A, B->h, face_flux, dUdt);
   else
-    hyd::hydro_flux_correct_kernel<8><<<grid, 256, 0, (cudaStream_t)stream>>>(A, B->h, face_flux, dUdt);
+    hyd::hydro_flux_correct_kernel<8, false><<<grid, 256, 0, (cudaStream_t)stream>>>(A, B->h, face_flux, dUdt);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 
@@ -783,11 +768,12 @@ int hydro_fill_ghosts_amr_lean(hydro_ctx_t* c, const hydro_batch_t* B, const hyd
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 
-// The coarse-fine flux correction and the SSP-RK3 stage update of the
-// adaptive RK3 sequence in one launch (hydro_update_amr_kernel): B->U the
-// stage's state, U0 the step's initial state, Uout the new state (B->U in
-// place after the first stage), dt on the device; with image the new
-// state's restriction images for the next stage's lean fill.
+// The coarse-fine flux correction (from the finer-neighbour tables of the
+// lean fill) and the SSP-RK3 stage update of the adaptive RK3 sequence
+// (hydro_update_amr_kernel): B->U the stage's state, U0 the step's initial
+// state, Uout the new state (B->U in place after the first stage), dt on
+// the device; with image the new state's restriction images for the next
+// stage's lean fill.
 int hydro_update_amr_lean(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_amr_t* M, const double* U0,
                           double* dUdt, const double* face_flux, const double* dt_dev, int stage, double* Uout,
                           bool image, cudaStream_t st) {
@@ -806,17 +792,14 @@ int hydro_update_amr_lean(hydro_ctx_t* c, const hydro_batch_t* B, const hydro_am
   const bool mixed = c->mode.precision == HYDRO_PREC_MIXED;
   const double eta2 = c->mode.de_eta2, ig = 1.0 / c->gamma;
   const double al = alpha[stage], be = beta[stage];
+  hyd::hydro_flux_correct_kernel<8, true><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt);
   if (mixed && image)
-    hyd::hydro_update_amr_kernel<true, true><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev, al,
-                                                                    be, eta2, ig);
+    hyd::hydro_update_amr_kernel<true, true><<<grid, 256, 0, st>>>(A, dUdt, U0, Uout, dt_dev, al, be, eta2, ig);
   else if (mixed)
-    hyd::hydro_update_amr_kernel<true, false><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev, al,
-                                                                     be, eta2, ig);
+    hyd::hydro_update_amr_kernel<true, false><<<grid, 256, 0, st>>>(A, dUdt, U0, Uout, dt_dev, al, be, eta2, ig);
   else if (image)
-    hyd::hydro_update_amr_kernel<false, true><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev, al,
-                                                                     be, eta2, ig);
+    hyd::hydro_update_amr_kernel<false, true><<<grid, 256, 0, st>>>(A, dUdt, U0, Uout, dt_dev, al, be, eta2, ig);
   else
-    hyd::hydro_update_amr_kernel<false, false><<<grid, 256, 0, st>>>(A, B->h, face_flux, dUdt, U0, Uout, dt_dev,
-                                                                      al, be, eta2, ig);
+    hyd::hydro_update_amr_kernel<false, false><<<grid, 256, 0, st>>>(A, dUdt, U0, Uout, dt_dev, al, be, eta2, ig);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
