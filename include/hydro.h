@@ -387,8 +387,11 @@ typedef struct {
 typedef struct hydro_graph hydro_graph_t;
 
 /* Enqueue one time step on a stream: parity 0 advances a -> b, 1 advances
- * b -> a.  Ten launches (two with fused: a clear of the context's sync words
- * and the step).  Errors: EINVAL (inconsistent descriptor, or state
+ * b -> a.  Ten launches on a uniform mesh (two with fused: a clear of the
+ * context's sync words and the step); on an adaptive mesh 16 (five per
+ * stage and dt), or 15 in the direct-read form (four per stage, two more at
+ * the first stage for its restriction images and finer-neighbour tables,
+ * and dt).  Errors: EINVAL (inconsistent descriptor, or state
  * buffers a.U and U_b that overlap), EUNSUP (fused with an adaptive mesh or
  * in FP64), ENOMEM. */
 int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void* stream);
