@@ -240,7 +240,7 @@ def _manual_rk3(H, ctx, mesh, U, origin, h, steps, cfl=0.4):
     return X, dt
 
 
-@pytest.mark.parametrize("case", ["small-outflow", "small-periodic", "shell", "shell-indicator"])
+@pytest.mark.parametrize("case", ["small-outflow", "small-periodic", "small-rotating", "shell", "shell-indicator"])
 def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
     """In mixed precision the adaptive RK3 step skips the fill's copies and
     restrictions: its step kernel reads same-level neighbours' interiors and
@@ -249,7 +249,8 @@ def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
     steps and dt equal, bit for bit, the same sequence through the public
     calls with the full ghost fill, and so do the device status bits; the new
     state buffer's ghost cells held by same-level leaves are left unwritten
-    (the direct path ran)."""
+    (the direct path ran).  small-rotating: in a frame rotating at 0.2, so
+    that the frame's and the spin sources act."""
     from paper_2107_10987_gb300.amr import AMRRun
     if case.startswith("small"):
         lev, ijk, U, o, h = small()
@@ -258,7 +259,7 @@ def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
         lev, ijk, _ = W.amr_shell_mesh()
         U = W.amr_shell_state(lev, ijk, GAMMA)
         bc = H.HYDRO_BC_OUTFLOW
-    ctx = H.Context(GAMMA, 0.0)
+    ctx = H.Context(GAMMA, 0.2 if case.endswith("rotating") else 0.0)
     H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
     if case.endswith("indicator"):
         from oracle import gate
