@@ -399,7 +399,11 @@ int hydro_rk3_step(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, int parity, void
 /* Capture the two directions of hydro_rk3_step once into CUDA graphs
  * (allocating the context's scratch beforehand, so replays allocate nothing).
  * The state starts in buffer a.  The descriptor's buffers must stay valid
- * and unchanged in address while the graph exists. */
+ * and unchanged in address while the graph exists.  A later call on the
+ * context that needs larger work buffers (a bigger batch) allocates new
+ * ones and keeps the old ones, which the graph uses, until hydro_destroy;
+ * the graph and such calls must not run concurrently (one context per
+ * stream).  Destroy the graphs before the context. */
 int hydro_rk3_graph_create(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, hydro_graph_t** out);
 
 /* Replay one time step on a stream (alternating a -> b and b -> a). */

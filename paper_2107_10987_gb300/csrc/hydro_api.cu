@@ -66,9 +66,21 @@ static int ensure_status(hydro_ctx* c) {
   return HYDRO_OK;
 }
 
-static int ensure_buf(double** buf, size_t* have, size_t need, const char* what) {
+// Grow one of the context's work buffers to `need` bytes (no-op if it is
+// large enough).  The old allocation is freed, or, once a graph has been
+// captured on the context, kept until hydro_destroy: a graph replays with
+// the addresses it was captured with.
+static int ensure_buf(hydro_ctx* c, double** buf, size_t* have, size_t need, const char* what) {
   if (*have >= need) return HYDRO_OK;
-  if (*buf) cudaFree(*buf);
+  if (*buf && c->had_graph) {
+    try {
+      c->retired.push_back(*buf);
+    } catch (...) {
+      return HYDRO_ENOMEM;
+    }
+  } else if (*buf) {
+    cudaFree(*buf);
+  }
   *buf = nullptr;
   *have = 0;
   cudaError_t e = cudaMalloc(buf, need);
@@ -102,7 +114,7 @@ static int step_slots(const hydro_ctx* c, bool mixed) {
 static int ensure_lines(hydro_ctx* c, int units) {
   const int slots = step_slots(c, false);
   const int grid = units < slots ? units : slots;
-  return ensure_buf(&c->lines, &c->lines_bytes, (size_t)grid * hyd::step_fp64_lines_per_cta() * sizeof(double),
+  return ensure_buf(c, &c->lines, &c->lines_bytes, (size_t)grid * hyd::step_fp64_lines_per_cta() * sizeof(double),
                     "cudaMalloc(FP64 line ends)");
 }
 
@@ -137,14 +149,14 @@ static hyd::StepArgs64 step_args(const hydro_ctx* c, const hydro_batch_t* B, dou
 int hydro_ctx_prepare_fused(hydro_ctx* c, int n_sub) {
   int rc = hydro_ctx_prepare(c, n_sub);
   if (rc) return rc;
-  rc = ensure_buf(&c->u2, &c->u2_bytes, (size_t)n_sub * hyd::F * c->N * c->N * c->N * sizeof(double),
+  rc = ensure_buf(c, &c->u2, &c->u2_bytes, (size_t)n_sub * hyd::F * c->N * c->N * c->N * sizeof(double),
                   "cudaMalloc(fused second-stage state)");
   if (rc) return rc;
-  rc = ensure_buf(&c->prims, &c->prims_bytes, 2 * (size_t)n_sub * hyd::F * c->N * c->N * c->N * sizeof(float),
+  rc = ensure_buf(c, &c->prims, &c->prims_bytes, 2 * (size_t)n_sub * hyd::F * c->N * c->N * c->N * sizeof(float),
                   "cudaMalloc(fused primitives)");
   if (rc) return rc;
   const size_t words = hyd::rk3_fused_sync_words(n_sub);
-  rc = ensure_buf(&c->sync, &c->sync_bytes, (words * sizeof(unsigned) + 7) / 8 * 8, "cudaMalloc(fused sync words)");
+  rc = ensure_buf(c, &c->sync, &c->sync_bytes, (words * sizeof(unsigned) + 7) / 8 * 8, "cudaMalloc(fused sync words)");
   if (rc) return rc;
   int max_grid = 0;
   cudaError_t e = hyd::prepare_rk3_fused(c->num_sms, 0, c->N, &max_grid);
@@ -190,7 +202,7 @@ int hydro_ctx_prepare(hydro_ctx* c, int n_sub) {
   const int slots = 2 * c->num_sms;  // the most any launch uses
   const int units = step_units(c, n_sub);
   const int grid = units < slots ? units : slots;
-  rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
+  rc = ensure_buf(c, &c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
   if (c->mode.precision == HYDRO_PREC_FP64) {
@@ -212,11 +224,11 @@ bool hydro_amr_direct_ok(const hydro_ctx* c) {
 int hydro_ctx_prepare_amr(hydro_ctx* c, int n_sub) {
   int rc = hydro_ctx_prepare(c, n_sub);
   if (rc) return rc;
-  rc = ensure_buf(&c->amr_img, &c->amr_img_bytes,
+  rc = ensure_buf(c, &c->amr_img, &c->amr_img_bytes,
                   (size_t)n_sub * hyd::F * (hyd::N / 2) * (hyd::N / 2) * (hyd::N / 2) * sizeof(double),
                   "cudaMalloc(restriction images)");
   if (rc) return rc;
-  return ensure_buf(&c->amr_finer, &c->amr_finer_bytes, ((size_t)n_sub * hyd::kFinerTab * sizeof(int) + 7) & ~7ul,
+  return ensure_buf(c, &c->amr_finer, &c->amr_finer_bytes, ((size_t)n_sub * hyd::kFinerTab * sizeof(int) + 7) & ~7ul,
                     "cudaMalloc(finer-neighbour tables)");
 }
 
@@ -236,7 +248,7 @@ int hydro_step_amr_direct(hydro_ctx* c, const hydro_batch_t* B, const hydro_amr_
   if (rc) return rc;
   const int slots = step_slots(c, true);
   const int grid = B->n_sub < slots ? B->n_sub : slots;
-  rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
+  rc = ensure_buf(c, &c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
   const hyd::StepArgs64 A = step_args(c, B, dUdt, amax, face_flux);
@@ -306,7 +318,7 @@ int hydro_step(hydro_ctx_t* c, const hydro_batch_t* B, double dt, double* dUdt, 
   const int slots = step_slots(c, mixed);
   const int units = step_units(c, B->n_sub);
   const int grid = units < slots ? units : slots;
-  rc = ensure_buf(&c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
+  rc = ensure_buf(c, &c->scratch, &c->scratch_bytes, (size_t)grid * hyd::kScratchPerSub * sizeof(double),
                   "cudaMalloc(step scratch)");
   if (rc) return rc;
   if (!mixed) {
@@ -499,7 +511,7 @@ int hydro_gather_interior(hydro_ctx_t* c, const hydro_batch_t* B, double* interi
 
 int hydro_conserved_sums(hydro_ctx_t* c, const hydro_batch_t* B, double* sums, void* stream) {
   if (!c || !B || !sums || B->n_sub <= 0 || !B->U || !B->origin || !B->h) return HYDRO_EINVAL;
-  int rc = ensure_buf(&c->part, &c->part_bytes, (size_t)B->n_sub * (hyd::F + 1) * sizeof(double),
+  int rc = ensure_buf(c, &c->part, &c->part_bytes, (size_t)B->n_sub * (hyd::F + 1) * sizeof(double),
                       "cudaMalloc(sum partials)");
   if (rc) return rc;
   cudaError_t e = hyd::launch_sums(B->U, B->origin, B->h, B->n_sub, c->part, sums, c->N, (cudaStream_t)stream);
@@ -546,6 +558,7 @@ void hydro_destroy(hydro_ctx_t* c) {
   if (c->sync) cudaFree(c->sync);
   if (c->amr_img) cudaFree(c->amr_img);
   if (c->amr_finer) cudaFree(c->amr_finer);
+  for (void* p : c->retired) cudaFree(p);
   delete c;
 }
 

@@ -1,6 +1,7 @@
 // hydro_ctx.h -- the context behind the opaque hydro_ctx_t of include/hydro.h.
 #pragma once
 #include <cstddef>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -35,6 +36,11 @@ struct hydro_ctx {
   size_t amr_img_bytes;
   double* amr_finer;     // adaptive RK3 step: each leaf's finer-neighbour table (int words)
   size_t amr_finer_bytes;
+  // Once a CUDA graph has been captured on the context, a work buffer that
+  // has to grow keeps its old allocation here (graphs hold its address)
+  // until hydro_destroy.
+  bool had_graph;
+  std::vector<void*> retired;
 };
 
 // Allocate the context's status word and the step scratch for a batch of

@@ -121,6 +121,7 @@ int hydro_rk3_graph_create(hydro_ctx_t* ctx, const hydro_rk3_desc_t* d, hydro_gr
     return rc;
   }
   g->parity = 0;
+  ctx->had_graph = true;  // from now on the context keeps grown-out buffers
   *out = g;
   return HYDRO_OK;
 }

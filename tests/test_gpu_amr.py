@@ -336,3 +336,31 @@ def test_leaf_order_changes_nothing(H, oracle_mod):
     torch.cuda.synchronize()
     assert H.hydro_status(ctx) & 4
     run.close()
+
+
+def test_graph_keeps_its_buffers_when_the_context_grows(H, oracle_mod):
+    """A captured graph replays with the work buffers it was captured with:
+    after a larger mesh has grown the context's step scratch, restriction
+    images and finer-neighbour tables, the small mesh's graph still gives
+    the bits of direct launches (the grown-out buffers are kept until the
+    context is destroyed)."""
+    from paper_2107_10987_gb300.amr import AMRRun
+    lev, ijk, U, o, h = small()
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
+    grun = AMRRun(ctx, U, lev, ijk)
+    grun.step(use_graph=True)  # captured with buffers for the small mesh
+    lev2, ijk2, _ = W.amr_shell_mesh()
+    big = AMRRun(ctx, W.amr_shell_state(lev2, ijk2, GAMMA), lev2, ijk2)
+    big.step()  # grows the context's buffers
+    grun.step(use_graph=True)
+    ref = AMRRun(ctx, U, lev, ijk)
+    ref.step()
+    ref.step()
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    a = grun.U[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64)
+    b = ref.U[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64)
+    assert torch.equal(a, b)
+    for r in (grun, big, ref):
+        r.close()
