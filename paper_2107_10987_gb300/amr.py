@@ -79,7 +79,7 @@ class AMRRun:
     buffers (ping-pong), the work buffers, and optionally a captured graph."""
 
     def __init__(self, ctx, U, level, ijk, bc: int = H.HYDRO_BC_OUTFLOW, cfl: float = 0.4, device="cuda",
-                 order="morton"):
+                 order="morton", g=None):
         from . import workloads as W
         self.ctx = ctx
         self.mesh = AMRMesh(level, ijk, bc, device, order)
@@ -95,8 +95,10 @@ class AMRRun:
         self.am = torch.empty(n, dtype=torch.float64, device=device)
         self.dt = torch.empty(1, dtype=torch.float64, device=device)
         self.faces = torch.empty((n, 6, 13, N, N), dtype=torch.float64, device=device)
+        # g: optional gravitational acceleration [n][3][N][N][N] at the cell centres
+        self.g = torch.as_tensor(g, device=device) if g is not None else None
         self.desc = H.make_rk3_desc(self.bufs[0], self.bufs[1], self.origin, self.h, None, bc, self.dU, self.am,
-                                    self.dt, cfl, mesh=self.mesh, face_flux=self.faces)
+                                    self.dt, cfl, g=self.g, mesh=self.mesh, face_flux=self.faces)
         self.parity = 0
         self.graph = None
         self.t = 0.0

@@ -217,7 +217,7 @@ def test_batched_4096_leaf_mesh(H, mixed, oracle_mod):
         assert worst <= 1.0
 
 
-def _manual_rk3(H, ctx, mesh, U, origin, h, steps, cfl=0.4):
+def _manual_rk3(H, ctx, mesh, U, origin, h, steps, cfl=0.4, g=None):
     """RK3 steps through the public calls with the full two-pass ghost fill:
     ghost fill, step with boundary faces, coarse-fine flux correction, dt
     after the first stage, update.  Returns the final state and dt."""
@@ -229,7 +229,7 @@ def _manual_rk3(H, ctx, mesh, U, origin, h, steps, cfl=0.4):
     faces = torch.empty((n, 6, 13, 8, 8), dtype=torch.float64, device="cuda")
     for _ in range(steps):
         for k in range(3):
-            B = H.make_batch(X if k == 0 else Y, origin, h)
+            B = H.make_batch(X if k == 0 else Y, origin, h, g)
             H.hydro_fill_ghosts_amr(ctx, B, mesh)
             H.hydro_step(ctx, B, 0.0, dU, am, faces)
             H.hydro_flux_correct_amr(ctx, B, mesh, faces, dU)
@@ -240,7 +240,8 @@ def _manual_rk3(H, ctx, mesh, U, origin, h, steps, cfl=0.4):
     return X, dt
 
 
-@pytest.mark.parametrize("case", ["small-outflow", "small-periodic", "small-rotating", "shell", "shell-indicator"])
+@pytest.mark.parametrize("case", ["small-outflow", "small-periodic", "small-rotating", "small-gravity", "shell",
+                                  "shell-indicator"])
 def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
     """In mixed precision the adaptive RK3 step skips the fill's copies and
     restrictions: its step kernel reads same-level neighbours' interiors and
@@ -250,7 +251,8 @@ def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
     calls with the full ghost fill, and so do the device status bits; the new
     state buffer's ghost cells held by same-level leaves are left unwritten
     (the direct path ran).  small-rotating: in a frame rotating at 0.2, so
-    that the frame's and the spin sources act."""
+    that the frame's and the spin sources act; small-gravity: with a seeded
+    gravitational acceleration field."""
     from paper_2107_10987_gb300.amr import AMRRun
     if case.startswith("small"):
         lev, ijk, U, o, h = small()
@@ -266,7 +268,10 @@ def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
         theta = np.random.default_rng(31).normal(0, 0.3, gate.NPARAM).astype(np.float32)
         c0 = float(gate.forward_infer(gate.bf16_round(theta), np.zeros((1, 54)))[0])
         H.hydro_set_indicator(ctx, torch.tensor(theta, device="cuda"), c0 + 1e-6)  # uniform blocks smooth
-    run = AMRRun(ctx, U, lev, ijk, bc)
+    g = None
+    if case.endswith("gravity"):
+        g = torch.tensor(np.random.default_rng(37).uniform(-1, 1, (len(lev), 3, 8, 8, 8)), device="cuda")
+    run = AMRRun(ctx, U, lev, ijk, bc, g=g)
     run.step()
     torch.cuda.synchronize()
     # the first step's state buffer started at zero: same-level ghosts stay so
@@ -276,7 +281,7 @@ def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
     run.step()
     torch.cuda.synchronize()
     st_direct = H.hydro_status(ctx)
-    want, dt = _manual_rk3(H, ctx, run.mesh, torch.as_tensor(U, device="cuda"), run.origin, run.h, 2)
+    want, dt = _manual_rk3(H, ctx, run.mesh, torch.as_tensor(U, device="cuda"), run.origin, run.h, 2, g=g)
     torch.cuda.synchronize()
     # seeded indicator parameters may mark cells at the shell smooth, where
     # the unlimited formula can leave a non-physical state: both paths flag it
@@ -288,7 +293,7 @@ def test_mixed_rk3_reads_neighbours_directly(H, case, oracle_mod):
     assert torch.equal(a, b)
     assert torch.equal(run.dt.view(torch.int64), dt.view(torch.int64))
     # graph replay of the direct path gives the same state
-    grun = AMRRun(ctx, U, lev, ijk, bc)
+    grun = AMRRun(ctx, U, lev, ijk, bc, g=g)
     grun.step(use_graph=True)
     grun.step(use_graph=True)
     torch.cuda.synchronize()
