@@ -369,3 +369,44 @@ def test_graph_keeps_its_buffers_when_the_context_grows(H, oracle_mod):
     assert torch.equal(a, b)
     for r in (grun, big, ref):
         r.close()
+
+
+@pytest.mark.parametrize("bc", ["periodic", "outflow"])
+def test_single_level_direct_rk3_equals_uniform_rk3(H, bc, oracle_mod):
+    """On one level nothing is prolonged or corrected, so the mixed
+    direct-read RK3 step of a single-level octree (leaves shuffled, taken
+    along the Morton curve) must give the uniform mesh's RK3 step (ghost
+    fill, row sweep, update) bit for bit, periodic wrap-around and outflow
+    clamping included."""
+    from paper_2107_10987_gb300.amr import AMRRun
+    from paper_2107_10987_gb300.uniform import UniformRun
+    nb = 4
+    n = nb ** 3
+    code = {"periodic": H.HYDRO_BC_PERIODIC, "outflow": H.HYDRO_BC_OUTFLOW}[bc]
+    U = W.random_subgrids(n, 53, GAMMA)
+    U[:, :, :3] = 0.0
+    U[:, :, -3:] = 0.0
+    U[:, :, :, :3] = 0.0
+    U[:, :, :, -3:] = 0.0
+    U[:, :, :, :, :3] = 0.0
+    U[:, :, :, :, -3:] = 0.0
+    kk = np.arange(n)
+    ijk = np.stack([kk % nb, (kk // nb) % nb, kk // (nb * nb)], 1)  # s = (kz nb + ky) nb + kx
+    lev = np.full(n, 2)
+    o, h = W.amr_geometry(lev, ijk)
+    ctx = H.Context(GAMMA, 0.0)
+    H.hydro_set_mode(ctx, H.HYDRO_PREC_MIXED)
+    uni = UniformRun(ctx, U, o, h, nb, code)
+    perm = np.random.default_rng(59).permutation(n)
+    amr = AMRRun(ctx, U[perm], lev[perm], ijk[perm], code)
+    for _ in range(2):
+        uni.step()
+        amr.step()
+    torch.cuda.synchronize()
+    assert H.hydro_status(ctx) == 0
+    a = amr.U[:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64)
+    b = uni.U[torch.tensor(perm, device="cuda")][:, :, 3:-3, 3:-3, 3:-3].contiguous().view(torch.int64)
+    assert torch.equal(a, b)
+    assert torch.equal(amr.dt.view(torch.int64), uni.dt.view(torch.int64))
+    uni.close()
+    amr.close()
